@@ -1,0 +1,271 @@
+#!/usr/bin/env python
+"""Benchmark of the Lippmann-Schwinger Nystrom hot path on one B300.
+
+A step is one full left-preconditioned FP64 GMRES solve (tol 1e-8) of the
+two-material disk (off-centre inclusion; n_opt = 1.5 + 0.2 exp(-|x|^2/0.1)
+outside, 2.2 inside), k = 20, 2,680 curved triangles x 15 nodes = 40,200 nodes,
+Cartesian preconditioner on 256^2 over [-1.2, 1.2]^2, one plane wave at pi/4,
+plus its far-field pattern at 64 angles.  Setup (correction and preconditioner
+factors) is excluded, as the paper excludes it from its solve times.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line.  Under torchrun every rank solves its own incident
+direction (independent replicas, no collective); value = all solves / max time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "two-material disk, k=20, 40,200 nodes (2,680 curved P4 triangles), 256^2 Cartesian preconditioner, tol 1e-8"
+METRIC = "LS GMRES solves/s (FP64, preconditioned)"
+# Preconditioned GMRES iterations of this workload as measured by the GPU arm;
+# the reference arm scales its sampled matvec cost by it.
+REFERENCE_ITERS = 20
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clocks, throttle reasons)."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def cpu_baseline(wl, u_gpu, Lu_gpu, iters, n_rows=1536, n_corr=48):
+    """The oracle as it stands, timed on a bounded sample of the same workload:
+    n_rows rows of the naive pair sum and n_corr rows of the correction for the
+    GPU's solution vector (also giving the sampled matvec error vs the oracle)."""
+    from threadpoolctl import threadpool_limits
+    from oracle.nystrom import naive_rows
+    from oracle.vdim import correction_matrix
+
+    n = wl.mesh.n_nodes
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(n, n_rows, replace=False))
+    crow = rows[:: max(1, n_rows // n_corr)][:n_corr]
+    f = wl.m * u_gpu
+    with threadpool_limits(1):
+        t0 = time.perf_counter()
+        nv = naive_rows(wl.mesh.nodes, wl.mesh.weights, wl.k, f, rows)
+        t1 = time.perf_counter()
+        dV = correction_matrix(wl.mesh, wl.k, 3.0, rows=crow)
+        t2 = time.perf_counter()
+    ref = u_gpu[crow] + wl.k**2 * (nv[np.searchsorted(rows, crow)] + dV @ f)
+    err = float(np.linalg.norm(Lu_gpu[crow] - ref) / np.linalg.norm(ref))
+    t_apply = (t1 - t0) / n_rows * n + (t2 - t1) / n_corr * n       # one L apply, extrapolated
+    t_solve = iters * t_apply
+    return {
+        "value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+        "sample": f"{n_rows} pair-sum rows x {n} sources + {n_corr} correction rows, extrapolated to "
+                  f"{iters} L applies per solve (preconditioner and Krylov work not counted)",
+        "seconds": round(t2 - t0, 2), "pairs_per_s": n_rows * (n - 1) / (t1 - t0),
+    }, err
+
+
+def reference_arm(args):
+    """--impl reference: the oracle as it stands, each step a bounded sample."""
+    from lsinput.workloads import two_material
+    from threadpoolctl import threadpool_limits
+    from oracle.nystrom import naive_rows
+    from oracle.vdim import correction_matrix
+
+    wl = two_material("small")
+    n = wl.mesh.n_nodes
+    x = np.exp(1j * wl.k * (wl.mesh.nodes @ np.array([np.cos(np.pi / 4), np.sin(np.pi / 4)])))
+    f = wl.m * x
+    rows = np.arange(0, n, n // 256)[:256]
+    times = []
+    with threadpool_limits(1):
+        for s in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            naive_rows(wl.mesh.nodes, wl.mesh.weights, wl.k, f, rows)
+            t1 = time.perf_counter()
+            correction_matrix(wl.mesh, wl.k, 3.0, rows=rows[:8])
+            t2 = time.perf_counter()
+            if s >= args.warmup:
+                times.append(((t1 - t0) / rows.size + (t2 - t1) / 8) * n * REFERENCE_ITERS)
+    t_solve = statistics.mean(times)
+    value = 1.0 / t_solve
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"per step: 256 pair-sum rows + 8 correction rows of one L apply, "
+                                       f"extrapolated to {n} rows x {REFERENCE_ITERS} iterations"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = _env_rank()
+    if args.impl == "reference":
+        if rank == 0:
+            reference_arm(args)
+        return
+
+    import torch
+    import paper_2608_17615_b300 as L
+    from lsinput.workloads import two_material
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = two_material("small")
+    n = wl.mesh.n_nodes
+    t0 = time.perf_counter()
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, tol=1e-8)
+    setup_s = time.perf_counter() - t0
+    fp64_peak = L.probe_fp64()
+    # each rank solves its own direction (replicas)
+    angle = np.pi / 4 + 2 * np.pi * rank / max(world, 1) if world > 1 else np.pi / 4
+    d = np.array([np.cos(angle), np.sin(angle)])
+    b = torch.from_numpy(np.exp(1j * wl.k * (wl.mesh.nodes @ d))).cuda()
+    u = torch.empty_like(b)
+    n_ff = wl.ff_angles.size
+    uinf = torch.empty(n_ff, dtype=torch.complex128, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 512 MB > 126 MB L2
+    for _ in range(args.warmup):
+        op.solve_dev(b.view(1, -1), u.view(1, -1), wl.ff_angles, uinf.view(1, -1))
+    torch.cuda.synchronize()
+    op.set_timing(True)
+    stream = torch.cuda.current_stream()
+    iters_list, step_ms = [], []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            it, st = op.solve_dev(b.view(1, -1), u.view(1, -1), wl.ff_angles, uinf.view(1, -1))
+            e1.record(stream)
+            iters_list.append(int(it[0]))
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    ps_ms, ps_launches, launches = op.stats()
+    op.set_timing(False)
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    iters = statistics.mean(iters_list)
+    value = world * args.steps / (total_ms * 1e-3)
+    pairs_per_solve = iters * n * (n - 1)
+    # roofline of the pair-sum kernel (FP64 ALU bound)
+    avg_launch_s = ps_ms / max(ps_launches, 1) * 1e-3
+    flops_per_pair = FLOPS_PER_PAIR
+    achieved = flops_per_pair * n * (n - 1) / avg_launch_s / 1e12
+    peak = fp64_peak / 1e3
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_pairsum", "flops_per_pair": flops_per_pair,
+                "peak_source": "measured FP64 FMA probe (ls_probe_fp64), same run",
+                "kernel_ms_per_launch": avg_launch_s * 1e3, "kernel_share_of_step": ps_ms / total_ms}
+    # end to end through the host-buffer entry point
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        uh, uinfh, hist, it_h, st_h = op.solve([angle], wl.ff_angles)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e = {"value": world * args.steps / (sum(e2e_ms) * 1e-3), "unit": "solves/s",
+           "h2d_bytes_per_step": 8 * (1 + n_ff), "d2h_bytes_per_step": 16 * n + 16 * n_ff + 8 * (int(it_h[0]) + 1)}
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nodes": n, "k": wl.k, "grid": [wl.nx, wl.ny],
+                       "l2": "flushed (512 MB write) before every timed step", "parallelism": "replicas"},
+            "iterations": iters, "pairs_per_s": world * pairs_per_solve * args.steps / (total_ms * 1e-3),
+            "matvecs_per_s": world * iters * args.steps / (total_ms * 1e-3), "setup_s": setup_s,
+            "wall_s_timed": wall, "roofline": roofline, "gpu_launches": launches, "clocks": clocks.summary(),
+            "e2e": e2e}
+    if rank == 0 and not args.no_cpu_baseline:
+        Lu = torch.empty_like(u)
+        op.apply_dev(u, Lu)
+        cb, err = cpu_baseline(wl, u.cpu().numpy(), Lu.cpu().numpy(), int(round(iters)))
+        line["cpu_baseline"] = cb
+        line["matvec_rel_err_vs_oracle"] = err
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# FP64 floating-point operations per pair in k_pairsum (asymptotic branch, z > 6),
+# FMA counted as 2: distance 5, rsqrt 9, scaling 5, two degree-14 Horner
+# polynomials 56, sincos 40, amplitude rsqrt and phase 14, complex accumulate 8.
+FLOPS_PER_PAIR = 137
+
+if __name__ == "__main__":
+    main()

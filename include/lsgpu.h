@@ -1,0 +1,186 @@
+/*
+ * lsgpu.h -- C ABI of the B300 (sm_103a) Lippmann-Schwinger Nystrom hot path.
+ *
+ * Method: arXiv 2608.17615, "Fast high-order solvers for the Lippmann-Schwinger
+ * equation in piecewise-smooth heterogeneous media".  The library solves the
+ * Nystrom system L u = b of Eq. nystrom_linear_system,
+ *
+ *     L = I + k^2 V M                         (Eq. linear_system_matrix)
+ *     (V f)_j = sum_{n != j} G(y_j, y_n) w_n f_n + sum_q dV_jq f_q
+ *     G(x, y) = (i/4) H0^(1)(k |x - y|),     M = diag(m(y_j)),  m = 1 - n
+ *
+ * on the quadrature nodes y_j of a curved triangle mesh: a dense pair sum plus
+ * the sparse VDIM near/self correction dV (Eq. DIM_decomp, local-patch form),
+ * by unrestarted GMRES (Section 6) with optional left preconditioning by
+ * P = I + T_C^Q (S - I) T_Q^C (Eq. preconditioner_factored, Approach II
+ * transfers Eq. T_H^C_def, sparsifying preconditioner S = C^{-1} A, Eq. LC_def).
+ *
+ * Conventions
+ *  - Complex numbers are interleaved pairs of doubles (re, im) (complex128).
+ *  - Host arrays passed in are copied; the caller keeps ownership.  Device
+ *    arrays (suffix _dev) are borrowed for the duration of the call, must hold
+ *    the stated number of elements, and are read/written on the operator's
+ *    stream; the call returns after the work is enqueued and synchronised.
+ *  - Every function returns an ls_status; on failure ls_last_error() returns
+ *    a thread-local message.  No function aborts the process.
+ *  - Handles are not thread-safe: one thread uses one ls_op at a time.
+ */
+#ifndef LSGPU_H
+#define LSGPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LS_OK = 0,
+    LS_EINVAL = 1,      /* bad argument (null pointer, size, mesh inconsistency, NaN input) */
+    LS_ENOMEM = 2,      /* device or host allocation failed */
+    LS_ECUDA = 3,       /* a CUDA runtime / library call failed */
+    LS_ESINGULAR = 4,   /* a block of the Cartesian matrix C could not be factored */
+    LS_ENOCONV = 5      /* GMRES hit max_iter; outputs hold the last iterate */
+} ls_status;
+
+typedef struct ls_mesh ls_mesh;
+typedef struct ls_op ls_op;
+
+/* Build parameters of an operator. */
+typedef struct {
+    double  tol;          /* GMRES stop: ||P(b - L u_k)|| / ||P b|| <= tol          */
+    int32_t max_iter;     /* GMRES iteration cap (the paper stops at 600)            */
+    int32_t use_precond;  /* 1: left-precondition with P; 0: plain GMRES             */
+    double  kappa;        /* VDIM patch radius in units of the target element size   */
+    double  box[4];       /* Cartesian grid box xmin, xmax, ymin, ymax (Section 4)    */
+    int32_t nx, ny;       /* grid nodes per direction, endpoints included; the step
+                             (xmax - xmin)/(nx - 1) must equal (ymax - ymin)/(ny - 1) */
+} ls_params;
+
+/* Defaults: tol 1e-8, max_iter 600, use_precond 1, kappa 3, box [-1.2,1.2]^2, 256 x 256. */
+void ls_params_default(ls_params* p);
+
+/*
+ * Mesh of N_T curved triangles with 15 quadrature nodes each (Section 3:
+ * conforming curved mesh of every subdomain Omega_l; the meshes of different
+ * subdomains need not match across an interface).
+ *   vert_xy     [n_vert][2]     vertex coordinates
+ *   elem_vert   [n_elem][3]     vertex ids, counter-clockwise; edge e runs from
+ *                               elem_vert[t][e] to elem_vert[t][(e+1)%3]
+ *   elem_domain [n_elem]        subdomain id l >= 0 (contrast smooth on each)
+ *   edge_curve  [n_elem][3]     -1: straight edge; c >= 0: arc of curve c
+ *   edge_theta  [n_elem][3][2]  arc parameter range (theta_start, theta_end)
+ *   curves      [n_curve][6]    polar curves (cx, cy, R, a, m, phi):
+ *                               gamma(t) = c + R (1 + a cos(m t + phi)) (cos t, sin t)
+ *   nodes_xy    [15 n_elem][2]  quadrature nodes, element-major (node j lies in
+ *                               element j / 15); all interior to their element
+ *   weights     [15 n_elem]     quadrature weights (Jacobian included)
+ * Elements of one subdomain must share edges exactly (same vertex ids).
+ * Errors: LS_EINVAL for null pointers, n_elem < 1, ids out of range, or a
+ * clockwise/degenerate element.
+ */
+ls_status ls_mesh_create(int32_t n_vert, const double* vert_xy,
+                         int32_t n_elem, const int32_t* elem_vert, const int32_t* elem_domain,
+                         const int32_t* edge_curve, const double* edge_theta,
+                         int32_t n_curve, const double* curves,
+                         const double* nodes_xy, const double* weights,
+                         ls_mesh** out);
+void ls_mesh_destroy(ls_mesh* mesh);
+int32_t ls_mesh_num_nodes(const ls_mesh* mesh);
+
+/*
+ * Operator L = I + k^2 V M on a mesh (Eq. linear_system_matrix) and, when
+ * params->use_precond, the preconditioner P (Eq. preconditioner_factored).
+ *   k        wavenumber > 0
+ *   m        [N_Q] complex contrast m(y_j) = 1 - n(y_j) at the nodes
+ *   m_grid   [nx * ny] complex contrast at the grid nodes (x fastest), zero
+ *            outside the scatterer; required when use_precond, else may be NULL
+ *   stream   cudaStream_t (NULL = default stream) for all device work
+ * Setup builds the VDIM correction dV in extended precision on the host
+ * (OpenMP) and the preconditioner factors on the device; it is not part of
+ * the timed solve.  The mesh may be destroyed afterwards.
+ * Errors: LS_EINVAL (k <= 0, NaN contrast, bad grid), LS_ENOMEM, LS_ECUDA,
+ * LS_ESINGULAR (a Schur block of C is singular).
+ */
+ls_status ls_operator_create(const ls_mesh* mesh, double k, const double* m, const double* m_grid,
+                             const ls_params* params, void* stream, ls_op** out);
+void ls_op_destroy(ls_op* op);
+int32_t ls_op_num_nodes(const ls_op* op);
+
+/* y = L x on device buffers x_dev, y_dev of N_Q complex (they may not alias). */
+ls_status ls_apply_dev(ls_op* op, const void* x_dev, void* y_dev);
+/* Same with host buffers; includes the host<->device copies. */
+ls_status ls_apply(ls_op* op, const double* x, double* y);
+/* y = P x (Eq. preconditioner_factored) on device buffers; LS_EINVAL without a preconditioner. */
+ls_status ls_apply_precond_dev(ls_op* op, const void* x_dev, void* y_dev);
+
+/*
+ * Plain pair sum y_j = sum_{n != j} G(y_j, y_n) w_n f_n (the naive Nystrom
+ * quadrature of V_Omega[f], Eq. vol_pot) on device buffers of N_Q complex.
+ */
+ls_status ls_pairsum_dev(ls_op* op, const void* f_dev, void* y_dev);
+
+/*
+ * Full solve for R plane waves u_inc = exp(i k d . y), d = (cos a, sin a)
+ * (b_j = u_inc(y_j), Eq. nystrom_linear_system), with host outputs:
+ *   dir_angles [R];  ff_angles [n_ff]
+ *   u_out    [R][N_Q] complex total field at the nodes (may be NULL)
+ *   uinf_out [R][n_ff] complex far-field pattern
+ *            u_inf(t) = -k^2 e^{i pi/4} / sqrt(8 pi k) sum_j w_j m_j u_j e^{-i k (cos t, sin t) . y_j}
+ *            (may be NULL)
+ *   hist_out [R][max_iter + 1] relative residual estimates (may be NULL)
+ *   iters_out [R] iterations taken (may be NULL)
+ * Returns LS_ENOCONV when any right-hand side hit max_iter (outputs are still
+ * written).
+ */
+ls_status ls_solve(ls_op* op, int32_t R, const double* dir_angles,
+                   int32_t n_ff, const double* ff_angles,
+                   double* u_out, double* uinf_out, double* hist_out, int32_t* iters_out);
+
+/*
+ * Device-buffer solve for R right-hand sides b_dev [R][N_Q] complex; writes
+ * u_dev [R][N_Q] and, if n_ff > 0, uinf_dev [R][n_ff] (ff_angles on the host).
+ * iters_out [R] on the host (may be NULL).
+ */
+ls_status ls_solve_dev(ls_op* op, int32_t R, const void* b_dev, void* u_dev,
+                       int32_t n_ff, const double* ff_angles, void* uinf_dev, int32_t* iters_out);
+
+/*
+ * Export of the correction dV as CSR (rows = N_Q targets, columns = nodes).
+ * Call with null arrays to get the size in *nnz, then with rowptr [N_Q + 1],
+ * cols [nnz], vals [nnz][2] (complex) to copy it out.
+ */
+ls_status ls_op_correction(const ls_op* op, int64_t* nnz, int64_t* rowptr, int32_t* cols, double* vals);
+
+/*
+ * Host-only build of the correction dV for a mesh (no device work): the same
+ * setup ls_operator_create runs (extended precision, OpenMP).  Two-call size
+ * query as ls_op_correction: null arrays return the size in *nnz.  The values
+ * are recomputed on every call.
+ */
+ls_status ls_correction_host(const ls_mesh* mesh, double k, double kappa, int64_t* nnz,
+                             int64_t* rowptr, int32_t* cols, double* vals);
+
+/* Diagnostic: h_dev[i] = H0^(1)(z_dev[i]) (complex) by the device routine of the pair sum. */
+ls_status ls_hankel0_dev(int64_t n, const double* z_dev, void* h_dev, void* stream);
+
+/*
+ * Instrumentation.  ls_op_set_timing(op, on) resets the counters and, when on,
+ * brackets every pair-sum launch with CUDA events on the operator's stream.
+ * ls_op_stats returns the summed pair-sum kernel time (ms, event-measured),
+ * the number of pair-sum launches and the number of kernels this operator
+ * launched since the last reset (any pointer may be NULL).
+ */
+ls_status ls_op_set_timing(ls_op* op, int32_t on);
+ls_status ls_op_stats(ls_op* op, double* pairsum_ms, int64_t* pairsum_launches, int64_t* launches);
+
+/* Diagnostic: measured FP64 FMA throughput of the device in GFLOP/s (2 flops per FMA). */
+ls_status ls_probe_fp64(double* gflops, void* stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* ls_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LSGPU_H */

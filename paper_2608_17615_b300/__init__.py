@@ -1,0 +1,250 @@
+"""Thin Python binding of liblsgpu.so (C ABI in include/lsgpu.h).
+
+Argument marshalling only: every step of the solver runs in the library's CUDA
+kernels (and its host setup).  Host arrays are numpy; device arrays are torch
+CUDA tensors of dtype complex128 (PyTorch is used for device memory and
+streams only).  Importing fails loudly when the library has not been built.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblsgpu.so")
+
+LS_OK, LS_EINVAL, LS_ENOMEM, LS_ECUDA, LS_ESINGULAR, LS_ENOCONV = range(6)
+_STATUS = {0: "LS_OK", 1: "LS_EINVAL", 2: "LS_ENOMEM", 3: "LS_ECUDA", 4: "LS_ESINGULAR", 5: "LS_ENOCONV"}
+
+EXPORTED = ["ls_params_default", "ls_mesh_create", "ls_mesh_destroy", "ls_mesh_num_nodes", "ls_operator_create",
+            "ls_op_destroy", "ls_op_num_nodes", "ls_apply_dev", "ls_apply", "ls_apply_precond_dev", "ls_pairsum_dev",
+            "ls_solve", "ls_solve_dev", "ls_op_correction", "ls_correction_host", "ls_hankel0_dev",
+            "ls_op_set_timing", "ls_op_stats", "ls_probe_fp64", "ls_last_error"]
+
+
+class LsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("use_precond", ctypes.c_int32),
+                ("kappa", ctypes.c_double), ("box", ctypes.c_double * 4), ("nx", ctypes.c_int32),
+                ("ny", ctypes.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing; build it with `python paper_2608_17615_b300/build.py`")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "ls_params_default": (None, [P]),
+        "ls_mesh_create": (I32, [I32, P, I32, P, P, P, P, I32, P, P, P, P]),
+        "ls_mesh_destroy": (None, [P]),
+        "ls_mesh_num_nodes": (I32, [P]),
+        "ls_operator_create": (I32, [P, D, P, P, P, P, P]),
+        "ls_op_destroy": (None, [P]),
+        "ls_op_num_nodes": (I32, [P]),
+        "ls_apply_dev": (I32, [P, P, P]),
+        "ls_apply": (I32, [P, P, P]),
+        "ls_apply_precond_dev": (I32, [P, P, P]),
+        "ls_pairsum_dev": (I32, [P, P, P]),
+        "ls_solve": (I32, [P, I32, P, I32, P, P, P, P, P]),
+        "ls_solve_dev": (I32, [P, I32, P, P, I32, P, P, P]),
+        "ls_op_correction": (I32, [P, P, P, P, P]),
+        "ls_correction_host": (I32, [P, D, D, P, P, P, P]),
+        "ls_hankel0_dev": (I32, [I64, P, P, P]),
+        "ls_op_set_timing": (I32, [P, I32]),
+        "ls_op_stats": (I32, [P, P, P, P]),
+        "ls_probe_fp64": (I32, [P, P]),
+        "ls_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def last_error():
+    return _lib.ls_last_error().decode()
+
+
+def _check(status, allow=()):
+    if status != LS_OK and status not in allow:
+        raise LsError(status, last_error())
+    return status
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _dptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device arguments must be contiguous CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _c128(a):
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return a, a.view(np.float64)
+
+
+def params_default():
+    p = Params()
+    _lib.ls_params_default(ctypes.byref(p))
+    return p
+
+
+class Mesh:
+    """ls_mesh handle built from an lsinput.mesh.Mesh-like object."""
+
+    def __init__(self, m):
+        self._keep = [np.ascontiguousarray(m.vertices, np.float64), np.ascontiguousarray(m.tris, np.int32),
+                      np.ascontiguousarray(m.domain, np.int32), np.ascontiguousarray(m.edge_curve, np.int32),
+                      np.ascontiguousarray(m.edge_theta, np.float64), np.ascontiguousarray(m.curves, np.float64),
+                      np.ascontiguousarray(m.nodes, np.float64), np.ascontiguousarray(m.weights, np.float64)]
+        v, t, d, ec, et, cu, nd, w = self._keep
+        h = ctypes.c_void_p()
+        _check(_lib.ls_mesh_create(v.shape[0], _ptr(v), t.shape[0], _ptr(t), _ptr(d), _ptr(ec), _ptr(et),
+                                   cu.shape[0], _ptr(cu), _ptr(nd), _ptr(w), ctypes.byref(h)))
+        self.handle = h
+        self.n = _lib.ls_mesh_num_nodes(h)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib.ls_mesh_destroy(self.handle)
+            self.handle = None
+
+
+class Operator:
+    """ls_op handle: L = I + k^2 V M and optionally the preconditioner P."""
+
+    def __init__(self, mesh, k, m, m_grid=None, params=None, stream=None, **overrides):
+        p = params if params is not None else params_default()
+        for key, val in overrides.items():
+            if key == "box":
+                for i in range(4):
+                    p.box[i] = val[i]
+            else:
+                setattr(p, key, val)
+        self.params = p
+        m_arr, m_f = _c128(m)
+        mg_f = None
+        if m_grid is not None:
+            self._mg, mg_f = _c128(m_grid)
+        h = ctypes.c_void_p()
+        if stream is None:
+            stream = _current_stream()
+        _check(_lib.ls_operator_create(mesh.handle, float(k), _ptr(m_f), _ptr(mg_f), ctypes.byref(p),
+                                       ctypes.c_void_p(stream), ctypes.byref(h)))
+        self.handle = h
+        self.n = _lib.ls_op_num_nodes(h)
+        self.k = float(k)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib.ls_op_destroy(self.handle)
+            self.handle = None
+
+    def apply_dev(self, x, y):
+        _check(_lib.ls_apply_dev(self.handle, _dptr(x), _dptr(y)))
+
+    def apply(self, x):
+        x, xf = _c128(x)
+        y = np.empty_like(x)
+        _check(_lib.ls_apply(self.handle, _ptr(xf), _ptr(y.view(np.float64))))
+        return y
+
+    def apply_precond_dev(self, x, y):
+        _check(_lib.ls_apply_precond_dev(self.handle, _dptr(x), _dptr(y)))
+
+    def pairsum_dev(self, f, y):
+        _check(_lib.ls_pairsum_dev(self.handle, _dptr(f), _dptr(y)))
+
+    def solve(self, dir_angles, ff_angles=None, want_u=True, want_hist=True):
+        """Host-buffer solve; returns (u [R, N], uinf [R, n_ff], hist [R, max_iter+1], iters [R], status)."""
+        dirs = np.ascontiguousarray(dir_angles, np.float64).ravel()
+        R = dirs.size
+        ff = np.ascontiguousarray(ff_angles if ff_angles is not None else [], np.float64).ravel()
+        u = np.empty((R, self.n), np.complex128) if want_u else None
+        uinf = np.empty((R, ff.size), np.complex128) if ff.size else None
+        hist = np.zeros((R, self.params.max_iter + 1)) if want_hist else None
+        iters = np.zeros(R, np.int32)
+        st = _check(_lib.ls_solve(self.handle, R, _ptr(dirs), ff.size, _ptr(ff) if ff.size else None,
+                                  _ptr(u.view(np.float64)) if u is not None else None,
+                                  _ptr(uinf.view(np.float64)) if uinf is not None else None,
+                                  _ptr(hist), _ptr(iters)), allow=(LS_ENOCONV,))
+        return u, uinf, hist, iters, st
+
+    def solve_dev(self, b, u, ff_angles=None, uinf=None):
+        """Device-buffer solve: b, u torch [R, N] complex128; uinf torch [R, n_ff] or None."""
+        R = b.shape[0] if b.dim() == 2 else 1
+        ff = np.ascontiguousarray(ff_angles if ff_angles is not None else [], np.float64).ravel()
+        iters = np.zeros(R, np.int32)
+        st = _check(_lib.ls_solve_dev(self.handle, R, _dptr(b), _dptr(u), ff.size, _ptr(ff) if ff.size else None,
+                                      _dptr(uinf), _ptr(iters)), allow=(LS_ENOCONV,))
+        return iters, st
+
+    def set_timing(self, on=True):
+        _check(_lib.ls_op_set_timing(self.handle, 1 if on else 0))
+
+    def stats(self):
+        """(pair-sum kernel ms, pair-sum launches, kernel launches) since the last set_timing."""
+        ms = ctypes.c_double()
+        pl = ctypes.c_int64()
+        la = ctypes.c_int64()
+        _check(_lib.ls_op_stats(self.handle, ctypes.byref(ms), ctypes.byref(pl), ctypes.byref(la)))
+        return ms.value, pl.value, la.value
+
+    def correction(self):
+        """The library's correction dV as (rowptr, cols, vals)."""
+        nnz = ctypes.c_int64()
+        _check(_lib.ls_op_correction(self.handle, ctypes.byref(nnz), None, None, None))
+        rp = np.empty(self.n + 1, np.int64)
+        ci = np.empty(nnz.value, np.int32)
+        va = np.empty(nnz.value, np.complex128)
+        _check(_lib.ls_op_correction(self.handle, ctypes.byref(nnz), _ptr(rp), _ptr(ci), _ptr(va.view(np.float64))))
+        return rp, ci, va
+
+
+def correction_host(mesh, k, kappa=3.0):
+    """Host-only build of dV for a Mesh handle: (rowptr, cols, vals)."""
+    nnz = ctypes.c_int64()
+    _check(_lib.ls_correction_host(mesh.handle, float(k), float(kappa), ctypes.byref(nnz), None, None, None))
+    rp = np.empty(mesh.n + 1, np.int64)
+    ci = np.empty(nnz.value, np.int32)
+    va = np.empty(nnz.value, np.complex128)
+    _check(_lib.ls_correction_host(mesh.handle, float(k), float(kappa), ctypes.byref(nnz), _ptr(rp), _ptr(ci),
+                                   _ptr(va.view(np.float64))))
+    return rp, ci, va
+
+
+def hankel0_dev(z, out):
+    """out[i] = H0^(1)(z[i]) by the device routine of the pair sum (z float64, out complex128 tensors)."""
+    _check(_lib.ls_hankel0_dev(z.numel(), _dptr(z), _dptr(out), ctypes.c_void_p(_current_stream())))
+
+
+def probe_fp64():
+    """Measured FP64 FMA throughput of the current device, GFLOP/s."""
+    g = ctypes.c_double()
+    _check(_lib.ls_probe_fp64(ctypes.byref(g), ctypes.c_void_p(_current_stream())))
+    return g.value
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return 0

@@ -1,0 +1,1124 @@
+// B300 (sm_103a) implementation of the Lippmann-Schwinger Nystrom hot path
+// behind the C ABI of include/lsgpu.h.
+//
+// Kernels (all FP64, complex as double2):
+//   k_pairsum        dense pair sum sum_{n != j} H0(k |y_j - y_n|) s_n, sources staged
+//                    through shared memory, one target per thread, the source range
+//                    split into chunks whose partial sums land in a scratch buffer
+//   k_apply_epi      warp per row: sums the chunk partials in a fixed order, the CSR
+//                    correction (VDIM dV, Eq. DIM_decomp) and the epilogue
+//                    (L x)_j = x_j + k^2 [(i/4) sum + sum_q dV_jq m_q x_q]  (Eq. linear_system_matrix)
+//   k_tqc            T_Q^C gather (Approach II, Eq. T_H^C_def) over the transposed CSR
+//   k_stencil        t = A g with the 3 x 3 sparsifying stencil (Eq. sparsifying_min)
+//   k_bt_fwd/bwd     block-tridiagonal solve C t' = t with precomputed dense
+//                    S_b^{-1} and S_b^{-1} C_{b,b+1} (block LU of C, Eq. LC_def)
+//   k_tcq            z_q = w_q + sum_4 psi (t' - g) (Eq. preconditioner_factored)
+//   k_dots/k_sumrows/k_update/k_norm...  classical Gram-Schmidt (twice) for GMRES
+//   k_givens         Hessenberg column update and Givens rotation, residual history
+//   k_farfield       u_inf(theta) = -k^2 e^{i pi/4}/sqrt(8 pi k) sum_j w_j m_j u_j e^{-i k xhat . y_j}
+//   k_incident       b_j = exp(i k d . y_j)
+// Device H0^(1): ascending series of J0, Y0 for z <= 6 (Abramowitz & Stegun 9.1.12,
+// 9.1.13); for z > 6 the modulus/phase form sqrt(2/(pi z)) (P + i Q) e^{i(z - pi/4)}
+// with P, zQ fitted polynomials in 36/z^2 (constants in hankel_fit.h).
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lsgpu.h"
+#include "hankel_fit.h"
+#include "ls_internal.h"
+
+using lsgpu::CsrC;
+using lsgpu::GridSetup;
+using lsgpu::HostMesh;
+
+static thread_local std::string g_err;
+
+static ls_status fail(ls_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(LS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));            \
+    } while (0)
+
+#define CKS(call)                                                                                 \
+    do {                                                                                          \
+        cusolverStatus_t s_ = (call);                                                             \
+        if (s_ != CUSOLVER_STATUS_SUCCESS)                                                        \
+            return fail(LS_ECUDA, std::string(#call) + ": cusolver status " + std::to_string(s_)); \
+    } while (0)
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 conjmul(double2 a, double2 b) {   // conj(a) * b
+    return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+#define LS_INV_SQRT_PI 0.56418958354775628695
+#define LS_TWO_OVER_PI 0.63661977236758134308
+#define LS_EULER_GAMMA 0.57721566490153286061
+
+// H0^(1)(z) for z = k r given r^2 > 0.
+__device__ __forceinline__ double2 ls_h0_r2(double r2, double k, double inv_k) {
+    double ir = rsqrt(r2);
+    double r = r2 * ir;
+    double z = k * r;
+    if (z > LS_H0_ZSPLIT) {
+        double iz = ir * inv_k;
+        double s = 36.0 * iz * iz;
+        double P = ls_h0_p[LS_H0_DEG], Qz = ls_h0_qz[LS_H0_DEG];
+#pragma unroll
+        for (int i = LS_H0_DEG - 1; i >= 0; --i) {
+            P = fma(P, s, ls_h0_p[i]);
+            Qz = fma(Qz, s, ls_h0_qz[i]);
+        }
+        double Q = Qz * iz;
+        double sz, cz;
+        sincos(z, &sz, &cz);
+        double amp = LS_INV_SQRT_PI * rsqrt(z);
+        double c1 = cz + sz, s1 = sz - cz;     // sqrt(2) cos(z - pi/4), sqrt(2) sin(z - pi/4)
+        return make_double2(amp * fma(P, c1, -Q * s1), amp * fma(P, s1, Q * c1));
+    }
+    double q = 0.25 * z * z;
+    double t = 1.0, j0 = 1.0, S = 0.0;
+#pragma unroll 4
+    for (int i = 0; i < LS_H0_NSERIES; ++i) {
+        t *= -q * ls_h0_rk2[i];
+        j0 += t;
+        S = fma(-ls_h0_hk[i], t, S);
+    }
+    double y0 = LS_TWO_OVER_PI * fma(log(0.5 * z) + LS_EULER_GAMMA, j0, S);
+    return make_double2(j0, y0);
+}
+
+// ------------------------------------------------------------------ pair sum
+#define PS_TPB 128
+#define PS_TILE 256
+
+// partial[c][j] = sum_{n in chunk c, n != j} H0(k |y_j - y_n|) s_n,  s_n = w_n (m_n) f_n
+__global__ void __launch_bounds__(PS_TPB) k_pairsum(const double2* __restrict__ xy, const double* __restrict__ w,
+                                                    const double2* __restrict__ m, const double2* __restrict__ f,
+                                                    int n, int src_per_chunk, double k, double inv_k,
+                                                    double2* __restrict__ partial) {
+    __shared__ double4 tile[PS_TILE];
+    const int j = blockIdx.x * PS_TPB + threadIdx.x;
+    const int s_begin = blockIdx.y * src_per_chunk;
+    const int s_end = min(n, s_begin + src_per_chunk);
+    const double2 yj = xy[min(j, n - 1)];
+    double ar = 0.0, ai = 0.0;
+    for (int base = s_begin; base < s_end; base += PS_TILE) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < PS_TILE; i += PS_TPB) {
+            int src = base + i;
+            double4 v = make_double4(0.0, 0.0, 0.0, 0.0);
+            if (src < s_end) {
+                double2 p = xy[src];
+                double2 ff = f[src];
+                if (m) ff = cmul(m[src], ff);
+                double ww = w[src];
+                v = make_double4(p.x, p.y, ww * ff.x, ww * ff.y);
+            }
+            tile[i] = v;
+        }
+        __syncthreads();
+        const int cnt = min(PS_TILE, s_end - base);
+        for (int i = 0; i < cnt; ++i) {
+            double4 s = tile[i];
+            double dx = yj.x - s.x, dy = yj.y - s.y;
+            double r2 = fma(dx, dx, dy * dy);
+            if (r2 > 0.0) {
+                double2 h = ls_h0_r2(r2, k, inv_k);
+                ar = fma(h.x, s.z, fma(-h.y, s.w, ar));
+                ai = fma(h.x, s.w, fma(h.y, s.z, ai));
+            }
+        }
+    }
+    if (j < n) partial[(size_t)blockIdx.y * n + j] = make_double2(ar, ai);
+}
+
+// mode 0: y = x + k2 * ((i/4) sum_c partial + dV (m x));  mode 1: y = (i/4) sum_c partial
+__global__ void k_apply_epi(int n, int nchunk, const double2* __restrict__ partial, const int64_t* __restrict__ rowptr,
+                            const int* __restrict__ cols, const double2* __restrict__ vals,
+                            const double2* __restrict__ m, const double2* __restrict__ x, double k2,
+                            double2* __restrict__ y, int mode) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const int j = warp;
+    double sr = 0.0, si = 0.0;
+    for (int c = lane; c < nchunk; c += 32) {
+        double2 p = partial[(size_t)c * n + j];
+        sr += p.x;
+        si += p.y;
+    }
+    double cr = 0.0, ci = 0.0;
+    if (mode == 0) {
+        for (int64_t e = rowptr[j] + lane; e < rowptr[j + 1]; e += 32) {
+            int q = cols[e];
+            double2 f = cmul(m[q], x[q]);
+            double2 t = cmul(vals[e], f);
+            cr += t.x;
+            ci += t.y;
+        }
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    cr = warp_sum(cr);
+    ci = warp_sum(ci);
+    if (lane == 0) {
+        // (i/4) (sr + i si) = (-si/4, sr/4)
+        double vr = -0.25 * si, vi = 0.25 * sr;
+        if (mode == 1) {
+            y[j] = make_double2(vr, vi);
+        } else {
+            double2 xj = x[j];
+            y[j] = make_double2(xj.x + k2 * (vr + cr), xj.y + k2 * (vi + ci));
+        }
+    }
+}
+
+__global__ void k_hankel0(int64_t n, const double* __restrict__ z, double2* __restrict__ h) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) h[i] = ls_h0_r2(z[i] * z[i], 1.0, 1.0);
+}
+
+// ------------------------------------------------------------------ preconditioner apply
+// g_i = sum_e tqc_vals[e] x[tqc_cols[e]]
+__global__ void k_tqc(int nc, const int64_t* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ cv,
+                      const double2* __restrict__ x, double2* __restrict__ g) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    double ar = 0.0, ai = 0.0;
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+        double2 v = x[ci[e]];
+        ar = fma(cv[e], v.x, ar);
+        ai = fma(cv[e], v.y, ai);
+    }
+    g[i] = make_double2(ar, ai);
+}
+
+struct Stencil9 { double2 v[9]; };
+
+// t = A g: 3x3 stencil on rows with a full stencil, identity on grid-edge rows
+__global__ void k_stencil(int nx, int ny, Stencil9 st, const double2* __restrict__ g, double2* __restrict__ t) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nx * ny) return;
+    int a = idx % nx, b = idx / nx;
+    if (a < 1 || a > nx - 2 || b < 1 || b > ny - 2) {
+        t[idx] = g[idx];
+        return;
+    }
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int s = 0; s < 9; ++s) {
+        int da = s % 3 - 1, db = s / 3 - 1;
+        acc = cadd(acc, cmul(st.v[s], g[idx + da + db * nx]));
+    }
+    t[idx] = acc;
+}
+
+// forward step of the block solve: y_b = W_b (t_b - Cm_b y_{b-1}); warp per row, W row-major
+__global__ void k_bt_fwd(int nx, int b, const double2* __restrict__ W, const double2* __restrict__ cband,
+                         const double2* __restrict__ t, double2* __restrict__ y) {
+    extern __shared__ double2 sh[];
+    const double2* Cm = cband + (size_t)b * 9 * nx;           // db = -1 diagonals at [0..2][nx]
+    for (int c = threadIdx.x; c < nx; c += blockDim.x) {
+        double2 v = t[(size_t)b * nx + c];
+        if (b > 0) {
+            const double2* yp = y + (size_t)(b - 1) * nx;
+            for (int da = -1; da <= 1; ++da) {
+                int cc = c + da;
+                if (cc >= 0 && cc < nx) v = csub(v, cmul(Cm[(size_t)(da + 1) * nx + c], yp[cc]));
+            }
+        }
+        sh[c] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= nx) return;
+    const double2* Wr = W + ((size_t)b * nx + row) * nx;
+    double ar = 0.0, ai = 0.0;
+    for (int c = lane; c < nx; c += 32) {
+        double2 wv = Wr[c], s = sh[c];
+        ar = fma(wv.x, s.x, fma(-wv.y, s.y, ar));
+        ai = fma(wv.x, s.y, fma(wv.y, s.x, ai));
+    }
+    ar = warp_sum(ar);
+    ai = warp_sum(ai);
+    if (lane == 0) y[(size_t)b * nx + row] = make_double2(ar, ai);
+}
+
+// backward step: x_b = y_b - G_b x_{b+1} (in place in y)
+__global__ void k_bt_bwd(int nx, int b, const double2* __restrict__ Gm, double2* __restrict__ y) {
+    extern __shared__ double2 sh[];
+    for (int c = threadIdx.x; c < nx; c += blockDim.x) sh[c] = y[(size_t)(b + 1) * nx + c];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= nx) return;
+    const double2* Gr = Gm + ((size_t)b * nx + row) * nx;
+    double ar = 0.0, ai = 0.0;
+    for (int c = lane; c < nx; c += 32) {
+        double2 gv = Gr[c], s = sh[c];
+        ar = fma(gv.x, s.x, fma(-gv.y, s.y, ar));
+        ai = fma(gv.x, s.y, fma(gv.y, s.x, ai));
+    }
+    ar = warp_sum(ar);
+    ai = warp_sum(ai);
+    if (lane == 0) {
+        double2 v = y[(size_t)b * nx + row];
+        y[(size_t)b * nx + row] = make_double2(v.x - ar, v.y - ai);
+    }
+}
+
+// z_q = w_q + sum_c psi_c (tp[i_c] - g[i_c])
+__global__ void k_tcq(int nq, const int* __restrict__ idx, const double* __restrict__ wt, const double2* __restrict__ tp,
+                      const double2* __restrict__ g, const double2* __restrict__ win, double2* __restrict__ z) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    double2 acc = win[q];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        int i = idx[4 * q + c];
+        double2 d = csub(tp[i], g[i]);
+        acc.x = fma(wt[4 * q + c], d.x, acc.x);
+        acc.y = fma(wt[4 * q + c], d.y, acc.y);
+    }
+    z[q] = acc;
+}
+
+// ------------------------------------------------------------------ block LU setup helpers
+// S (column-major, nx x nx) = tri(Cd_b) - Cm_b * Gprev (Gprev row-major, may be null)
+__global__ void k_build_S(int nx, int b, const double2* __restrict__ cband, const double2* __restrict__ Gprev,
+                          double2* __restrict__ S) {
+    int r = blockIdx.y;
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nx) return;
+    const double2* base = cband + (size_t)b * 9 * nx;
+    double2 v = make_double2(0.0, 0.0);
+    int off = c - r;
+    if (off >= -1 && off <= 1) v = base[(size_t)(3 + off + 1) * nx + r];     // db = 0 block, da = off
+    if (Gprev) {
+        for (int da = -1; da <= 1; ++da) {
+            int t = r + da;
+            if (t < 0 || t >= nx) continue;
+            v = csub(v, cmul(base[(size_t)(da + 1) * nx + r], Gprev[(size_t)t * nx + c]));
+        }
+    }
+    S[(size_t)c * nx + r] = v;
+}
+
+__global__ void k_identity_cm(int nx, double2* __restrict__ X) {
+    int r = blockIdx.y;
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < nx) X[(size_t)c * nx + r] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+}
+
+// W (row-major) = X (column-major);  G_b (row-major) = W_b Cp_b
+__global__ void k_store_W_G(int nx, int b, int ny, const double2* __restrict__ X, const double2* __restrict__ cband,
+                            double2* __restrict__ W, double2* __restrict__ Gm) {
+    int r = blockIdx.y;
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nx) return;
+    W[((size_t)b * nx + r) * nx + c] = X[(size_t)c * nx + r];
+    if (b == ny - 1) return;
+    const double2* Cp = cband + ((size_t)b * 9 + 6) * nx;    // db = +1 diagonals
+    double2 acc = make_double2(0.0, 0.0);
+    for (int da = -1; da <= 1; ++da) {                        // Cp(t, c) with c = t + da
+        int t = c - da;
+        if (t < 0 || t >= nx) continue;
+        acc = cadd(acc, cmul(X[(size_t)t * nx + r], Cp[(size_t)(da + 1) * nx + t]));
+    }
+    Gm[((size_t)b * nx + r) * nx + c] = acc;
+}
+
+// ------------------------------------------------------------------ GMRES kernels
+#define RED_TPB 256
+
+// part[j * nblk + block] = sum_{rows of block} conj(V_j) z   for j < J
+__global__ void k_dots(int n, int J, const double2* __restrict__ V, size_t ldv, const double2* __restrict__ z,
+                       double2* __restrict__ part) {
+    __shared__ double sr[RED_TPB / 32], si[RED_TPB / 32];
+    const int nblk = gridDim.x;
+    const int rows_per = (n + nblk - 1) / nblk;
+    const int r0 = blockIdx.x * rows_per, r1 = min(n, r0 + rows_per);
+    for (int j = 0; j < J; ++j) {
+        const double2* v = V + (size_t)j * ldv;
+        double ar = 0.0, ai = 0.0;
+        for (int r = r0 + threadIdx.x; r < r1; r += RED_TPB) {
+            double2 t = conjmul(v[r], z[r]);
+            ar += t.x;
+            ai += t.y;
+        }
+        ar = warp_sum(ar);
+        ai = warp_sum(ai);
+        if ((threadIdx.x & 31) == 0) { sr[threadIdx.x >> 5] = ar; si[threadIdx.x >> 5] = ai; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tr = 0.0, ti = 0.0;
+            for (int w = 0; w < RED_TPB / 32; ++w) { tr += sr[w]; ti += si[w]; }
+            part[(size_t)j * nblk + blockIdx.x] = make_double2(tr, ti);
+        }
+        __syncthreads();
+    }
+}
+
+// out[j] (+)= sum_b part[j * nblk + b]  (fixed order)
+__global__ void k_sumrows(int J, int nblk, const double2* __restrict__ part, double2* __restrict__ out, int accumulate) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= J) return;
+    double ar = 0.0, ai = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+        double2 p = part[(size_t)j * nblk + b];
+        ar += p.x;
+        ai += p.y;
+    }
+    if (accumulate) { out[j].x += ar; out[j].y += ai; }
+    else out[j] = make_double2(ar, ai);
+}
+
+// z -= sum_j V_j h_j
+__global__ void k_update(int n, int J, const double2* __restrict__ V, size_t ldv, const double2* __restrict__ h,
+                         double2* __restrict__ z) {
+    extern __shared__ double2 hs[];
+    for (int j = threadIdx.x; j < J; j += blockDim.x) hs[j] = h[j];
+    __syncthreads();
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double2 acc = z[r];
+    for (int j = 0; j < J; ++j) {
+        double2 t = cmul(V[(size_t)j * ldv + r], hs[j]);
+        acc.x -= t.x;
+        acc.y -= t.y;
+    }
+    z[r] = acc;
+}
+
+// u = sum_j V_j y_j
+__global__ void k_combine(int n, int J, const double2* __restrict__ V, size_t ldv, const double2* __restrict__ yv,
+                          double2* __restrict__ u) {
+    extern __shared__ double2 ys[];
+    for (int j = threadIdx.x; j < J; j += blockDim.x) ys[j] = yv[j];
+    __syncthreads();
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int j = 0; j < J; ++j) acc = cadd(acc, cmul(V[(size_t)j * ldv + r], ys[j]));
+    u[r] = acc;
+}
+
+// dst = src / nrm (nrm = sqrt(*nrm2)); writes nrm to *hout if given
+__global__ void k_scale(int n, const double2* __restrict__ src, const double2* __restrict__ nrm2, double2* __restrict__ dst,
+                        double2* hout) {
+    double nr = sqrt(nrm2->x);
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r == 0 && hout) *hout = make_double2(nr, 0.0);
+    if (r >= n) return;
+    double inv = nr > 0.0 ? 1.0 / nr : 0.0;
+    double2 v = src[r];
+    dst[r] = make_double2(v.x * inv, v.y * inv);
+}
+
+// Givens update of Hessenberg column j (column-major, leading dimension ldh)
+__global__ void k_givens(int j, double2* H, int ldh, double2* cs, double2* sn, double2* g, double* hist,
+                         const double2* beta2) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double2* col = H + (size_t)j * ldh;
+    for (int i = 0; i < j; ++i) {
+        double2 a = col[i], b = col[i + 1];
+        double2 t = cadd(cmul(cs[i], a), cmul(sn[i], b));
+        double2 cc = make_double2(cs[i].x, -cs[i].y), sc = make_double2(sn[i].x, -sn[i].y);
+        col[i + 1] = csub(cmul(cc, b), cmul(sc, a));
+        col[i] = t;
+    }
+    double2 a = col[j], b = col[j + 1];
+    double den = sqrt(a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y);
+    double2 c, s;
+    if (den > 0.0) {
+        c = make_double2(a.x / den, -a.y / den);
+        s = make_double2(b.x / den, -b.y / den);
+    } else {
+        c = make_double2(1.0, 0.0);
+        s = make_double2(0.0, 0.0);
+    }
+    cs[j] = c;
+    sn[j] = s;
+    col[j] = make_double2(den, 0.0);
+    col[j + 1] = make_double2(0.0, 0.0);
+    double2 gj = g[j];
+    double2 sc = make_double2(s.x, -s.y);
+    double2 gn = cmul(sc, gj);
+    g[j + 1] = make_double2(-gn.x, -gn.y);
+    g[j] = cmul(c, gj);
+    double beta = sqrt(beta2->x);
+    hist[j + 1] = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y) / beta;
+}
+
+// y = H(0:it, 0:it)^{-1} g(0:it) (upper triangular)
+__global__ void k_backsolve(int it, const double2* H, int ldh, const double2* g, double2* yv) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = it - 1; i >= 0; --i) {
+        double2 acc = g[i];
+        for (int c = i + 1; c < it; ++c) acc = csub(acc, cmul(H[(size_t)c * ldh + i], yv[c]));
+        double2 d = H[(size_t)i * ldh + i];
+        double dd = d.x * d.x + d.y * d.y;
+        yv[i] = make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd);
+    }
+}
+
+__global__ void k_gmres_init(double2* g, const double2* beta2, double* hist) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        g[0] = make_double2(sqrt(beta2->x), 0.0);
+        hist[0] = 1.0;
+    }
+}
+
+// ------------------------------------------------------------------ outputs
+__global__ void k_incident(int n, const double2* __restrict__ xy, double k, double dx, double dy, double2* __restrict__ b) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double2 p = xy[j];
+    double s, c;
+    sincos(k * fma(dx, p.x, dy * p.y), &s, &c);
+    b[j] = make_double2(c, s);
+}
+
+__global__ void k_farfield(int n, const double2* __restrict__ xy, const double* __restrict__ w,
+                           const double2* __restrict__ m, const double2* __restrict__ u, double k,
+                           const double* __restrict__ ang, double2* __restrict__ out) {
+    __shared__ double sr[RED_TPB / 32], si[RED_TPB / 32];
+    double th = ang[blockIdx.x];
+    double cx, cy;
+    sincos(th, &cy, &cx);
+    double ar = 0.0, ai = 0.0;
+    for (int j = threadIdx.x; j < n; j += RED_TPB) {
+        double2 p = xy[j];
+        double s, c;
+        sincos(-k * fma(cx, p.x, cy * p.y), &s, &c);
+        double2 f = cmul(m[j], u[j]);
+        double2 t = cmul(f, make_double2(c, s));
+        ar = fma(w[j], t.x, ar);
+        ai = fma(w[j], t.y, ai);
+    }
+    ar = warp_sum(ar);
+    ai = warp_sum(ai);
+    if ((threadIdx.x & 31) == 0) { sr[threadIdx.x >> 5] = ar; si[threadIdx.x >> 5] = ai; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tr = 0.0, ti = 0.0;
+        for (int q = 0; q < RED_TPB / 32; ++q) { tr += sr[q]; ti += si[q]; }
+        // -k^2 e^{i pi/4} / sqrt(8 pi k)
+        double gam = k * k / sqrt(8.0 * M_PI * k);
+        double2 pre = make_double2(-gam * M_SQRT1_2, -gam * M_SQRT1_2);
+        out[blockIdx.x] = cmul(pre, make_double2(tr, ti));
+    }
+}
+
+// FP64 FMA-rate probe: 8 independent dependent chains per thread
+__global__ void k_probe_dfma(int iters, double a, double b, double* sink) {
+    double x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+    for (int i = 0; i < iters; ++i) {
+        x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+        x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+    }
+    double s = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+    if (s == 123.456) sink[0] = s;
+}
+
+// ------------------------------------------------------------------ host structures
+struct ls_mesh {
+    HostMesh h;
+};
+
+template <typename T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    ~DevBuf() { if (p) cudaFree(p); }
+    cudaError_t alloc(size_t count) {
+        if (p) { cudaFree(p); p = nullptr; }
+        n = count;
+        if (count == 0) return cudaSuccess;
+        return cudaMalloc(&p, count * sizeof(T));
+    }
+};
+
+struct ls_op {
+    int nq = 0;
+    double k = 0;
+    ls_params prm{};
+    cudaStream_t stream = nullptr;
+    // mesh and operator data
+    DevBuf<double2> xy, m;
+    DevBuf<double> w;
+    DevBuf<int64_t> rowptr;
+    DevBuf<int> cols;
+    DevBuf<double2> vals;
+    CsrC host_csr;
+    std::vector<double> host_nodes, host_w;
+    std::vector<std::complex<double>> host_m;
+    // pair-sum decomposition and scratch
+    int nchunk = 1, src_per_chunk = 0;
+    DevBuf<double2> partial;
+    // preconditioner
+    bool has_prec = false;
+    int nx = 0, ny = 0;
+    DevBuf<int> tcq_idx;
+    DevBuf<double> tcq_w;
+    DevBuf<int64_t> tqc_rp;
+    DevBuf<int> tqc_ci;
+    DevBuf<double> tqc_cv;
+    DevBuf<double2> cband, Wf, Gf;
+    Stencil9 st{};
+    DevBuf<double2> pg, pt, ptp;         // grid work vectors
+    // GMRES workspace
+    DevBuf<double2> Vb, H, cs, sn, g, hv, yv, tmp, tmp2, dpart, scal;
+    DevBuf<double> hist;
+    int dblk = 0;
+    // instrumentation: kernel launches on this operator, CUDA-event timing of the pair sum
+    int64_t launches = 0, pairsum_launches = 0;
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    ~ls_op() {
+        for (auto& e : ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    }
+};
+
+static ls_status check_stream_sync(ls_op* op) {
+    CK(cudaStreamSynchronize(op->stream));
+    CK(cudaGetLastError());
+    return LS_OK;
+}
+
+// ------------------------------------------------------------------ building blocks
+static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m) {
+    dim3 grid((op->nq + PS_TPB - 1) / PS_TPB, op->nchunk);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (op->timing && op->ev.size() < 65536) {
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        op->ev.emplace_back(e0, e1);
+        CK(cudaEventRecord(e0, op->stream));
+    }
+    k_pairsum<<<grid, PS_TPB, 0, op->stream>>>(op->xy.p, op->w.p, m, f, op->nq, op->src_per_chunk, op->k, 1.0 / op->k,
+                                               op->partial.p);
+    CK(cudaGetLastError());
+    if (e1) CK(cudaEventRecord(e1, op->stream));
+    op->launches++;
+    op->pairsum_launches++;
+    return LS_OK;
+}
+
+static ls_status apply_L(ls_op* op, const double2* x, double2* y) {
+    ls_status s = launch_pairsum(op, x, op->m.p);
+    if (s != LS_OK) return s;
+    int threads = 256;
+    int blocks = (int)(((int64_t)op->nq * 32 + threads - 1) / threads);
+    k_apply_epi<<<blocks, threads, 0, op->stream>>>(op->nq, op->nchunk, op->partial.p, op->rowptr.p, op->cols.p, op->vals.p,
+                                                    op->m.p, x, op->k * op->k, y, 0);
+    CK(cudaGetLastError());
+    op->launches++;
+    return LS_OK;
+}
+
+static ls_status apply_P(ls_op* op, const double2* x, double2* z) {
+    const int nc = op->nx * op->ny, nx = op->nx, ny = op->ny;
+    k_tqc<<<(nc + 255) / 256, 256, 0, op->stream>>>(nc, op->tqc_rp.p, op->tqc_ci.p, op->tqc_cv.p, x, op->pg.p);
+    k_stencil<<<(nc + 255) / 256, 256, 0, op->stream>>>(nx, ny, op->st, op->pg.p, op->pt.p);
+    const int wpb = 8;                                   // warps per block in the block solve
+    const int blocks = (nx + wpb - 1) / wpb;
+    const size_t shm = sizeof(double2) * nx;
+    for (int b = 0; b < ny; ++b)
+        k_bt_fwd<<<blocks, 32 * wpb, shm, op->stream>>>(nx, b, op->Wf.p, op->cband.p, op->pt.p, op->ptp.p);
+    for (int b = ny - 2; b >= 0; --b)
+        k_bt_bwd<<<blocks, 32 * wpb, shm, op->stream>>>(nx, b, op->Gf.p, op->ptp.p);
+    k_tcq<<<(op->nq + 255) / 256, 256, 0, op->stream>>>(op->nq, op->tcq_idx.p, op->tcq_w.p, op->ptp.p, op->pg.p, x, z);
+    CK(cudaGetLastError());
+    op->launches += 3 + ny + (ny - 1);
+    return LS_OK;
+}
+
+// h[0:J] = V[0:J]^H z (into dst, accumulate or overwrite)
+static ls_status dots(ls_op* op, int J, const double2* V, const double2* z, double2* dst, int accumulate) {
+    k_dots<<<op->dblk, RED_TPB, 0, op->stream>>>(op->nq, J, V, (size_t)op->nq, z, op->dpart.p);
+    k_sumrows<<<(J + 127) / 128, 128, 0, op->stream>>>(J, op->dblk, op->dpart.p, dst, accumulate);
+    CK(cudaGetLastError());
+    op->launches += 2;
+    return LS_OK;
+}
+
+#define TRY(x)                         \
+    do {                               \
+        ls_status s__ = (x);           \
+        if (s__ != LS_OK) return s__;  \
+    } while (0)
+
+// One GMRES solve for device rhs b -> u. Writes hist (host, may be null) and iterations.
+static ls_status gmres_one(ls_op* op, const double2* b, double2* u, double* hist_host, int* iters) {
+    const int n = op->nq, maxit = op->prm.max_iter;
+    const int ldh = maxit + 1;
+    const size_t ldv = (size_t)n;
+    const int tpb = 256, nb = (n + tpb - 1) / tpb;
+    double2* V = op->Vb.p;
+    CK(cudaMemsetAsync(op->H.p, 0, sizeof(double2) * (size_t)ldh * maxit, op->stream));
+    // r0 = P b
+    if (op->has_prec && op->prm.use_precond) TRY(apply_P(op, b, op->tmp.p));
+    else CK(cudaMemcpyAsync(op->tmp.p, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, op->stream));
+    TRY(dots(op, 1, op->tmp.p, op->tmp.p, op->scal.p, 0));       // scal[0] = ||r0||^2
+    k_scale<<<nb, tpb, 0, op->stream>>>(n, op->tmp.p, op->scal.p, V, nullptr);
+    k_gmres_init<<<1, 1, 0, op->stream>>>(op->g.p, op->scal.p, op->hist.p);
+    CK(cudaGetLastError());
+    op->launches += 2;
+    int it = 0;
+    bool conv = false;
+    double last = 1.0;
+    for (int j = 0; j < maxit; ++j) {
+        double2* vj = V + (size_t)j * ldv;
+        double2* vn = V + (size_t)(j + 1) * ldv;
+        double2* hcol = op->H.p + (size_t)j * ldh;
+        if (op->has_prec && op->prm.use_precond) {
+            TRY(apply_L(op, vj, op->tmp.p));
+            TRY(apply_P(op, op->tmp.p, vn));
+        } else {
+            TRY(apply_L(op, vj, vn));
+        }
+        // classical Gram-Schmidt, twice
+        TRY(dots(op, j + 1, V, vn, hcol, 0));
+        k_update<<<nb, tpb, sizeof(double2) * (j + 1), op->stream>>>(n, j + 1, V, ldv, hcol, vn);
+        TRY(dots(op, j + 1, V, vn, op->hv.p, 0));
+        k_update<<<nb, tpb, sizeof(double2) * (j + 1), op->stream>>>(n, j + 1, V, ldv, op->hv.p, vn);
+        k_sumrows<<<(j + 1 + 127) / 128, 128, 0, op->stream>>>(j + 1, 1, op->hv.p, hcol, 1);
+        TRY(dots(op, 1, vn, vn, op->scal.p + 1, 0));
+        k_scale<<<nb, tpb, 0, op->stream>>>(n, vn, op->scal.p + 1, vn, hcol + j + 1);
+        k_givens<<<1, 1, 0, op->stream>>>(j, op->H.p, ldh, op->cs.p, op->sn.p, op->g.p, op->hist.p, op->scal.p);
+        CK(cudaGetLastError());
+        op->launches += 5;
+        CK(cudaMemcpyAsync(&last, op->hist.p + j + 1, sizeof(double), cudaMemcpyDeviceToHost, op->stream));
+        CK(cudaStreamSynchronize(op->stream));
+        it = j + 1;
+        if (!(last > op->prm.tol)) { conv = true; break; }
+    }
+    k_backsolve<<<1, 1, 0, op->stream>>>(it, op->H.p, ldh, op->g.p, op->yv.p);
+    k_combine<<<nb, tpb, sizeof(double2) * it, op->stream>>>(n, it, V, ldv, op->yv.p, u);
+    CK(cudaGetLastError());
+    op->launches += 2;
+    if (hist_host) CK(cudaMemcpyAsync(hist_host, op->hist.p, sizeof(double) * (it + 1), cudaMemcpyDeviceToHost, op->stream));
+    CK(cudaStreamSynchronize(op->stream));
+    if (iters) *iters = it;
+    return conv ? LS_OK : LS_ENOCONV;
+}
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char* ls_last_error(void) { return g_err.c_str(); }
+
+void ls_params_default(ls_params* p) {
+    if (!p) return;
+    p->tol = 1e-8;
+    p->max_iter = 600;
+    p->use_precond = 1;
+    p->kappa = 3.0;
+    p->box[0] = -1.2; p->box[1] = 1.2; p->box[2] = -1.2; p->box[3] = 1.2;
+    p->nx = 256;
+    p->ny = 256;
+}
+
+ls_status ls_mesh_create(int32_t n_vert, const double* vert_xy, int32_t n_elem, const int32_t* elem_vert,
+                         const int32_t* elem_domain, const int32_t* edge_curve, const double* edge_theta,
+                         int32_t n_curve, const double* curves, const double* nodes_xy, const double* weights,
+                         ls_mesh** out) {
+    if (!out) return fail(LS_EINVAL, "out is null");
+    *out = nullptr;
+    if (n_vert < 3 || n_elem < 1 || !vert_xy || !elem_vert || !elem_domain || !edge_curve || !edge_theta ||
+        !nodes_xy || !weights || n_curve < 0 || (n_curve > 0 && !curves))
+        return fail(LS_EINVAL, "ls_mesh_create: null pointer or bad size");
+    ls_mesh* M = new (std::nothrow) ls_mesh;
+    if (!M) return fail(LS_ENOMEM, "host allocation");
+    HostMesh& h = M->h;
+    h.nv = n_vert; h.nt = n_elem; h.nq = n_elem * lsgpu::NQ_ELEM; h.ncurve = n_curve;
+    h.vxy.assign(vert_xy, vert_xy + 2 * (size_t)n_vert);
+    h.tri.assign(elem_vert, elem_vert + 3 * (size_t)n_elem);
+    h.dom.assign(elem_domain, elem_domain + n_elem);
+    h.ecurve.assign(edge_curve, edge_curve + 3 * (size_t)n_elem);
+    h.etheta.assign(edge_theta, edge_theta + 6 * (size_t)n_elem);
+    h.curves.assign(curves, curves + 6 * (size_t)n_curve);
+    h.nodes.assign(nodes_xy, nodes_xy + 2 * (size_t)h.nq);
+    h.w.assign(weights, weights + h.nq);
+    for (int t = 0; t < n_elem; ++t) {
+        for (int e = 0; e < 3; ++e) {
+            int v = h.tri[3 * t + e];
+            int c = h.ecurve[3 * t + e];
+            if (v < 0 || v >= n_vert || c < -1 || c >= n_curve) { delete M; return fail(LS_EINVAL, "element index out of range"); }
+        }
+        if (h.dom[t] < 0) { delete M; return fail(LS_EINVAL, "negative subdomain id"); }
+        const int* v = &h.tri[3 * t];
+        double ax = h.vxy[2 * v[1]] - h.vxy[2 * v[0]], ay = h.vxy[2 * v[1] + 1] - h.vxy[2 * v[0] + 1];
+        double bx = h.vxy[2 * v[2]] - h.vxy[2 * v[0]], by = h.vxy[2 * v[2] + 1] - h.vxy[2 * v[0] + 1];
+        if (!(ax * by - ay * bx > 0)) { delete M; return fail(LS_EINVAL, "clockwise or degenerate element " + std::to_string(t)); }
+    }
+    for (int q = 0; q < h.nq; ++q)
+        if (!std::isfinite(h.nodes[2 * q]) || !std::isfinite(h.nodes[2 * q + 1]) || !std::isfinite(h.w[q])) {
+            delete M;
+            return fail(LS_EINVAL, "non-finite node or weight");
+        }
+    *out = M;
+    return LS_OK;
+}
+
+void ls_mesh_destroy(ls_mesh* mesh) { delete mesh; }
+int32_t ls_mesh_num_nodes(const ls_mesh* mesh) { return mesh ? mesh->h.nq : 0; }
+int32_t ls_op_num_nodes(const ls_op* op) { return op ? op->nq : 0; }
+
+static ls_status build_preconditioner(ls_op* op, const HostMesh& M, const double* m_grid) {
+    GridSetup G;
+    std::vector<std::complex<double>> mg((size_t)op->prm.nx * op->prm.ny);
+    for (size_t i = 0; i < mg.size(); ++i) {
+        mg[i] = std::complex<double>(m_grid[2 * i], m_grid[2 * i + 1]);
+        if (!std::isfinite(mg[i].real()) || !std::isfinite(mg[i].imag())) return fail(LS_EINVAL, "non-finite m_grid");
+    }
+    std::string err = lsgpu::build_grid(M, op->k, op->prm.box, op->prm.nx, op->prm.ny, mg.data(), G);
+    if (!err.empty()) return fail(LS_EINVAL, err);
+    const int nx = G.nx, ny = G.ny, nc = nx * ny;
+    op->nx = nx; op->ny = ny;
+    for (int s = 0; s < 9; ++s) op->st.v[s] = make_double2(G.v[s].real(), G.v[s].imag());
+    CK(op->tcq_idx.alloc(G.tcq_idx.size()));
+    CK(op->tcq_w.alloc(G.tcq_w.size()));
+    CK(op->tqc_rp.alloc(G.tqc_rowptr.size()));
+    CK(op->tqc_ci.alloc(G.tqc_cols.size()));
+    CK(op->tqc_cv.alloc(G.tqc_vals.size()));
+    CK(op->cband.alloc(G.cband.size()));
+    CK(cudaMemcpy(op->tcq_idx.p, G.tcq_idx.data(), sizeof(int) * G.tcq_idx.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(op->tcq_w.p, G.tcq_w.data(), sizeof(double) * G.tcq_w.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(op->tqc_rp.p, G.tqc_rowptr.data(), sizeof(int64_t) * G.tqc_rowptr.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(op->tqc_ci.p, G.tqc_cols.data(), sizeof(int) * G.tqc_cols.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(op->tqc_cv.p, G.tqc_vals.data(), sizeof(double) * G.tqc_vals.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(op->cband.p, G.cband.data(), sizeof(double2) * G.cband.size(), cudaMemcpyHostToDevice));
+    CK(op->pg.alloc(nc));
+    CK(op->pt.alloc(nc));
+    CK(op->ptp.alloc(nc));
+    CK(op->Wf.alloc((size_t)ny * nx * nx));
+    CK(op->Gf.alloc((size_t)ny * nx * nx));
+    // block LU: S_b = C_bb - C_{b,b-1} G_{b-1}; W_b = S_b^{-1}; G_b = W_b C_{b,b+1}
+    cusolverDnHandle_t hs = nullptr;
+    CKS(cusolverDnCreate(&hs));
+    struct HG { cusolverDnHandle_t h; ~HG() { cusolverDnDestroy(h); } } guard{hs};
+    CKS(cusolverDnSetStream(hs, op->stream));
+    DevBuf<double2> S, X, work;
+    DevBuf<int> piv, info;
+    CK(S.alloc((size_t)nx * nx));
+    CK(X.alloc((size_t)nx * nx));
+    CK(piv.alloc(nx));
+    CK(info.alloc(1));
+    int lwork = 0;
+    CKS(cusolverDnZgetrf_bufferSize(hs, nx, nx, (cuDoubleComplex*)S.p, nx, &lwork));
+    CK(work.alloc(std::max(lwork, 1)));
+    dim3 blk(128), grd((nx + 127) / 128, nx);
+    for (int b = 0; b < ny; ++b) {
+        k_build_S<<<grd, blk, 0, op->stream>>>(nx, b, op->cband.p, b > 0 ? op->Gf.p + (size_t)(b - 1) * nx * nx : nullptr, S.p);
+        CK(cudaGetLastError());
+        CKS(cusolverDnZgetrf(hs, nx, nx, (cuDoubleComplex*)S.p, nx, (cuDoubleComplex*)work.p, piv.p, info.p));
+        int hinfo = 0;
+        CK(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, op->stream));
+        CK(cudaStreamSynchronize(op->stream));
+        if (hinfo != 0) return fail(LS_ESINGULAR, "block " + std::to_string(b) + " of C is singular");
+        k_identity_cm<<<grd, blk, 0, op->stream>>>(nx, X.p);
+        CKS(cusolverDnZgetrs(hs, CUBLAS_OP_N, nx, nx, (const cuDoubleComplex*)S.p, nx, piv.p, (cuDoubleComplex*)X.p, nx, info.p));
+        k_store_W_G<<<grd, blk, 0, op->stream>>>(nx, b, ny, X.p, op->cband.p, op->Wf.p, op->Gf.p);
+        CK(cudaGetLastError());
+    }
+    CK(cudaStreamSynchronize(op->stream));
+    op->has_prec = true;
+    return LS_OK;
+}
+
+ls_status ls_operator_create(const ls_mesh* mesh, double k, const double* m, const double* m_grid,
+                             const ls_params* params, void* stream, ls_op** out) {
+    if (!out) return fail(LS_EINVAL, "out is null");
+    *out = nullptr;
+    if (!mesh || !m) return fail(LS_EINVAL, "null mesh or contrast");
+    if (!(k > 0) || !std::isfinite(k)) return fail(LS_EINVAL, "k must be positive");
+    ls_params prm;
+    ls_params_default(&prm);
+    if (params) prm = *params;
+    if (prm.max_iter < 1 || !(prm.tol > 0) || !(prm.kappa > 0)) return fail(LS_EINVAL, "bad tol / max_iter / kappa");
+    if (prm.use_precond && !m_grid) return fail(LS_EINVAL, "m_grid is required with use_precond");
+    const HostMesh& M = mesh->h;
+    for (int q = 0; q < M.nq; ++q)
+        if (!std::isfinite(m[2 * q]) || !std::isfinite(m[2 * q + 1])) return fail(LS_EINVAL, "non-finite contrast");
+    ls_op* op = new (std::nothrow) ls_op;
+    if (!op) return fail(LS_ENOMEM, "host allocation");
+    struct Guard { ls_op*& p; bool keep = false; ~Guard() { if (!keep) delete p; } } guard{op};
+    op->nq = M.nq;
+    op->k = k;
+    op->prm = prm;
+    op->stream = (cudaStream_t)stream;
+    const int n = M.nq;
+    // correction (host, extended precision)
+    std::string err = lsgpu::build_correction(M, k, prm.kappa, op->host_csr);
+    if (!err.empty()) return fail(LS_ESINGULAR, err);
+    op->host_nodes = M.nodes;
+    op->host_w = M.w;
+    op->host_m.resize(n);
+    for (int q = 0; q < n; ++q) op->host_m[q] = std::complex<double>(m[2 * q], m[2 * q + 1]);
+    CK(op->xy.alloc(n));
+    CK(op->w.alloc(n));
+    CK(op->m.alloc(n));
+    CK(op->rowptr.alloc(n + 1));
+    CK(op->cols.alloc(op->host_csr.cols.size()));
+    CK(op->vals.alloc(op->host_csr.vals.size()));
+    CK(cudaMemcpy(op->xy.p, M.nodes.data(), sizeof(double2) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(op->w.p, M.w.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(op->m.p, m, sizeof(double2) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(op->rowptr.p, op->host_csr.rowptr.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(op->cols.p, op->host_csr.cols.data(), sizeof(int) * op->host_csr.cols.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(op->vals.p, op->host_csr.vals.data(), sizeof(double2) * op->host_csr.vals.size(), cudaMemcpyHostToDevice));
+    // pair-sum decomposition: about 8 resident blocks per SM on 148 SMs
+    int dev = 0, nsm = 148;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int tblocks = (n + PS_TPB - 1) / PS_TPB;
+    int nchunk = std::max(1, std::min(64, (nsm * 8 + tblocks - 1) / tblocks));
+    int spc = (n + nchunk - 1) / nchunk;
+    spc = ((spc + PS_TILE - 1) / PS_TILE) * PS_TILE;
+    nchunk = (n + spc - 1) / spc;
+    op->nchunk = nchunk;
+    op->src_per_chunk = spc;
+    CK(op->partial.alloc((size_t)nchunk * n));
+    // GMRES workspace
+    const int maxit = prm.max_iter;
+    CK(op->Vb.alloc((size_t)(maxit + 1) * n));
+    CK(op->H.alloc((size_t)(maxit + 1) * maxit));
+    CK(op->cs.alloc(maxit + 1));
+    CK(op->sn.alloc(maxit + 1));
+    CK(op->g.alloc(maxit + 2));
+    CK(op->hv.alloc(maxit + 1));
+    CK(op->yv.alloc(maxit + 1));
+    CK(op->tmp.alloc(n));
+    CK(op->tmp2.alloc(n));
+    CK(op->scal.alloc(4));
+    CK(op->hist.alloc(maxit + 2));
+    op->dblk = std::max(1, std::min(nsm * 2, (n + RED_TPB - 1) / RED_TPB));
+    CK(op->dpart.alloc((size_t)op->dblk * (maxit + 1)));
+    if (prm.use_precond) TRY(build_preconditioner(op, M, m_grid));
+    guard.keep = true;
+    *out = op;
+    return LS_OK;
+}
+
+void ls_op_destroy(ls_op* op) { delete op; }
+
+ls_status ls_apply_dev(ls_op* op, const void* x_dev, void* y_dev) {
+    if (!op || !x_dev || !y_dev) return fail(LS_EINVAL, "null argument");
+    if (x_dev == y_dev) return fail(LS_EINVAL, "x and y may not alias");
+    TRY(apply_L(op, (const double2*)x_dev, (double2*)y_dev));
+    return check_stream_sync(op);
+}
+
+ls_status ls_apply(ls_op* op, const double* x, double* y) {
+    if (!op || !x || !y) return fail(LS_EINVAL, "null argument");
+    CK(cudaMemcpyAsync(op->tmp.p, x, sizeof(double2) * op->nq, cudaMemcpyHostToDevice, op->stream));
+    TRY(apply_L(op, op->tmp.p, op->tmp2.p));
+    CK(cudaMemcpyAsync(y, op->tmp2.p, sizeof(double2) * op->nq, cudaMemcpyDeviceToHost, op->stream));
+    return check_stream_sync(op);
+}
+
+ls_status ls_apply_precond_dev(ls_op* op, const void* x_dev, void* y_dev) {
+    if (!op || !x_dev || !y_dev) return fail(LS_EINVAL, "null argument");
+    if (!op->has_prec) return fail(LS_EINVAL, "operator was built without a preconditioner");
+    if (x_dev == y_dev) return fail(LS_EINVAL, "x and y may not alias");
+    TRY(apply_P(op, (const double2*)x_dev, (double2*)y_dev));
+    return check_stream_sync(op);
+}
+
+ls_status ls_pairsum_dev(ls_op* op, const void* f_dev, void* y_dev) {
+    if (!op || !f_dev || !y_dev) return fail(LS_EINVAL, "null argument");
+    TRY(launch_pairsum(op, (const double2*)f_dev, nullptr));
+    int threads = 256;
+    int blocks = (int)(((int64_t)op->nq * 32 + threads - 1) / threads);
+    k_apply_epi<<<blocks, threads, 0, op->stream>>>(op->nq, op->nchunk, op->partial.p, op->rowptr.p, op->cols.p,
+                                                    op->vals.p, op->m.p, (const double2*)f_dev, 0.0, (double2*)y_dev, 1);
+    CK(cudaGetLastError());
+    return check_stream_sync(op);
+}
+
+static ls_status farfield(ls_op* op, const double2* u, int n_ff, const double* ang_dev, double2* out_dev) {
+    k_farfield<<<n_ff, RED_TPB, 0, op->stream>>>(op->nq, op->xy.p, op->w.p, op->m.p, u, op->k, ang_dev, out_dev);
+    CK(cudaGetLastError());
+    op->launches++;
+    return LS_OK;
+}
+
+ls_status ls_solve_dev(ls_op* op, int32_t R, const void* b_dev, void* u_dev, int32_t n_ff, const double* ff_angles,
+                       void* uinf_dev, int32_t* iters_out) {
+    if (!op || R < 1 || !b_dev || !u_dev) return fail(LS_EINVAL, "null argument or R < 1");
+    if (n_ff > 0 && (!ff_angles || !uinf_dev)) return fail(LS_EINVAL, "far-field buffers missing");
+    DevBuf<double> ang;
+    if (n_ff > 0) {
+        CK(ang.alloc(n_ff));
+        CK(cudaMemcpy(ang.p, ff_angles, sizeof(double) * n_ff, cudaMemcpyHostToDevice));
+    }
+    ls_status worst = LS_OK;
+    for (int r = 0; r < R; ++r) {
+        const double2* b = (const double2*)b_dev + (size_t)r * op->nq;
+        double2* u = (double2*)u_dev + (size_t)r * op->nq;
+        int it = 0;
+        ls_status s = gmres_one(op, b, u, nullptr, &it);
+        if (s != LS_OK && s != LS_ENOCONV) return s;
+        if (s == LS_ENOCONV) worst = s;
+        if (iters_out) iters_out[r] = it;
+        if (n_ff > 0) TRY(farfield(op, u, n_ff, ang.p, (double2*)uinf_dev + (size_t)r * n_ff));
+    }
+    TRY(check_stream_sync(op));
+    if (worst != LS_OK) fail(worst, "GMRES reached max_iter");
+    return worst;
+}
+
+ls_status ls_solve(ls_op* op, int32_t R, const double* dir_angles, int32_t n_ff, const double* ff_angles,
+                   double* u_out, double* uinf_out, double* hist_out, int32_t* iters_out) {
+    if (!op || R < 1 || !dir_angles) return fail(LS_EINVAL, "null argument or R < 1");
+    if (n_ff > 0 && !ff_angles) return fail(LS_EINVAL, "ff_angles missing");
+    const int n = op->nq;
+    DevBuf<double2> b, u, uinf;
+    DevBuf<double> ang;
+    CK(b.alloc(n));
+    CK(u.alloc(n));
+    if (n_ff > 0) {
+        CK(uinf.alloc(n_ff));
+        CK(ang.alloc(n_ff));
+        CK(cudaMemcpy(ang.p, ff_angles, sizeof(double) * n_ff, cudaMemcpyHostToDevice));
+    }
+    std::vector<double> hist(op->prm.max_iter + 2);
+    ls_status worst = LS_OK;
+    for (int r = 0; r < R; ++r) {
+        k_incident<<<(n + 255) / 256, 256, 0, op->stream>>>(n, op->xy.p, op->k, std::cos(dir_angles[r]),
+                                                             std::sin(dir_angles[r]), b.p);
+        CK(cudaGetLastError());
+        op->launches++;
+        int it = 0;
+        ls_status s = gmres_one(op, b.p, u.p, hist.data(), &it);
+        if (s != LS_OK && s != LS_ENOCONV) return s;
+        if (s == LS_ENOCONV) worst = s;
+        if (iters_out) iters_out[r] = it;
+        if (hist_out) {
+            double* hr = hist_out + (size_t)r * (op->prm.max_iter + 1);
+            for (int i = 0; i <= op->prm.max_iter; ++i) hr[i] = i <= it ? hist[i] : 0.0;
+        }
+        if (u_out) CK(cudaMemcpyAsync(u_out + 2 * (size_t)r * n, u.p, sizeof(double2) * n, cudaMemcpyDeviceToHost, op->stream));
+        if (n_ff > 0 && uinf_out) {
+            TRY(farfield(op, u.p, n_ff, ang.p, uinf.p));
+            CK(cudaMemcpyAsync(uinf_out + 2 * (size_t)r * n_ff, uinf.p, sizeof(double2) * n_ff, cudaMemcpyDeviceToHost,
+                               op->stream));
+        }
+        TRY(check_stream_sync(op));
+    }
+    if (worst != LS_OK) fail(worst, "GMRES reached max_iter");
+    return worst;
+}
+
+ls_status ls_op_correction(const ls_op* op, int64_t* nnz, int64_t* rowptr, int32_t* cols, double* vals) {
+    if (!op || !nnz) return fail(LS_EINVAL, "null argument");
+    *nnz = (int64_t)op->host_csr.cols.size();
+    if (rowptr) std::memcpy(rowptr, op->host_csr.rowptr.data(), sizeof(int64_t) * op->host_csr.rowptr.size());
+    if (cols) std::memcpy(cols, op->host_csr.cols.data(), sizeof(int32_t) * op->host_csr.cols.size());
+    if (vals) std::memcpy(vals, op->host_csr.vals.data(), sizeof(double) * 2 * op->host_csr.vals.size());
+    return LS_OK;
+}
+
+ls_status ls_correction_host(const ls_mesh* mesh, double k, double kappa, int64_t* nnz, int64_t* rowptr,
+                             int32_t* cols, double* vals) {
+    if (!mesh || !nnz) return fail(LS_EINVAL, "null argument");
+    if (!(k > 0) || !(kappa > 0)) return fail(LS_EINVAL, "k and kappa must be positive");
+    CsrC csr;
+    std::string err = lsgpu::build_correction(mesh->h, k, kappa, csr);
+    if (!err.empty()) return fail(LS_ESINGULAR, err);
+    *nnz = (int64_t)csr.cols.size();
+    if (rowptr) std::memcpy(rowptr, csr.rowptr.data(), sizeof(int64_t) * csr.rowptr.size());
+    if (cols) std::memcpy(cols, csr.cols.data(), sizeof(int32_t) * csr.cols.size());
+    if (vals) std::memcpy(vals, csr.vals.data(), sizeof(double) * 2 * csr.vals.size());
+    return LS_OK;
+}
+
+ls_status ls_op_set_timing(ls_op* op, int32_t on) {
+    if (!op) return fail(LS_EINVAL, "null op");
+    CK(cudaStreamSynchronize(op->stream));
+    for (auto& e : op->ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    op->ev.clear();
+    op->timing = on != 0;
+    op->launches = 0;
+    op->pairsum_launches = 0;
+    return LS_OK;
+}
+
+ls_status ls_op_stats(ls_op* op, double* pairsum_ms, int64_t* pairsum_launches, int64_t* launches) {
+    if (!op) return fail(LS_EINVAL, "null op");
+    CK(cudaStreamSynchronize(op->stream));
+    double tot = 0.0;
+    for (auto& e : op->ev) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e.first, e.second));
+        tot += ms;
+    }
+    if (pairsum_ms) *pairsum_ms = tot;
+    if (pairsum_launches) *pairsum_launches = op->timing ? (int64_t)op->ev.size() : op->pairsum_launches;
+    if (launches) *launches = op->launches;
+    return LS_OK;
+}
+
+ls_status ls_probe_fp64(double* gflops, void* stream) {
+    if (!gflops) return fail(LS_EINVAL, "null argument");
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    cudaStream_t st = (cudaStream_t)stream;
+    DevBuf<double> sink;
+    CK(sink.alloc(1));
+    const int threads = 256, blocks = nsm * 8, iters = 1 << 14;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    k_probe_dfma<<<blocks, threads, 0, st>>>(iters, 0.999999, 1e-7, sink.p);   // warm-up
+    CK(cudaEventRecord(e0, st));
+    k_probe_dfma<<<blocks, threads, 0, st>>>(iters, 0.999999, 1e-7, sink.p);
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *gflops = 2.0 * 8.0 * iters * (double)threads * blocks / (ms * 1e-3) / 1e9;
+    return LS_OK;
+}
+
+ls_status ls_hankel0_dev(int64_t n, const double* z_dev, void* h_dev, void* stream) {
+    if (n < 0 || (n > 0 && (!z_dev || !h_dev))) return fail(LS_EINVAL, "null argument");
+    if (n == 0) return LS_OK;
+    k_hankel0<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, z_dev, (double2*)h_dev);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    return LS_OK;
+}
+
+}  // extern "C"

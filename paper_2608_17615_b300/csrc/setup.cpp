@@ -1,0 +1,684 @@
+// Host setup of the Lippmann-Schwinger operator, in extended precision.
+//
+//  * hankel01_ld: H0^(1), H1^(1) for real z > 0 in long double (x86 80-bit):
+//      z <= 6      ascending series (Abramowitz & Stegun 9.1.10-9.1.13)
+//      6 < z < 30  Miller backward recurrence normalised by J0 + 2 sum J_2k = 1,
+//                  Neumann series for Y0 (A&S 9.1.88) and its derivative for Y1
+//      z >= 30     Hankel asymptotic expansion (A&S 9.2.5-9.2.10)
+//  * build_correction: the VDIM near/self correction dV (Eq. DIM_decomp) in the
+//    local-patch form.  For target node x_j in element tau and every subdomain l
+//    with elements inside the patch radius:
+//      dV_jq = E_jq - N_jq,
+//      E_jq = -chi Phi_q(x_j) + int_{boundary of patch} (G dPhi_q/dn - Phi_q dG/dn) ds
+//      N_jq = sum_{n in patch, n != j} G(x_j, y_n) w_n L_q(y_n)
+//    L_q: Lagrange basis of the interpolation element's 15 nodes (tau for the
+//    own subdomain, chi = 1; the nearest element otherwise, chi = 0);
+//    Phi_q = L_q/k^2 - Lap L_q/k^4 + Lap^2 L_q/k^6 solves (Lap + k^2) Phi_q = L_q.
+//    Patch of target j in subdomain l: elements t of l with
+//    |c_t - x_j|^2 < kappa^2 h_j^2 (c_t = ((v0 + v1) + v2) / 3, h_j^2 the largest
+//    squared vertex distance of tau), plus tau itself in its own subdomain.
+//    dV is a small difference of two large numbers, hence long double throughout;
+//    boundary integrals use dyadic panel refinement until each panel is shorter
+//    than 3/4 of its distance to the target, then 32-point Gauss-Legendre.
+//  * build_grid: bilinear T_C^Q (Eq. psi_def), Approach II T_Q^C (Eq. T_H^C_def,
+//    Eq. D_def), the sparsifying stencil (Eq. sparsifying_min) from the 9 x 9
+//    Gram matrix of V^(C)(N(0), N(0)^c) diagonalised by Jacobi rotations, and
+//    C = A L^(C) on the 3 x 3 pattern (Eq. LC_def) in block-tridiagonal storage.
+//    V^(C) diagonal: integral of G over the disc of area h_C^2 (the
+//    Duan-Rokhlin weights of the paper are replaced by this value).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ls_internal.h"
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace lsgpu {
+
+using ld = long double;
+using cld = std::complex<long double>;
+
+static const ld PI_L = 3.141592653589793238462643383279502884L;
+static const ld EG_L = 0.577215664901532860606512090082402431L;
+
+// ---------------------------------------------------------------- Hankel
+static void series01(ld z, ld& j0, ld& j1, ld& y0, ld& y1) {
+    ld q = z * z / 4;
+    ld t0 = 1, t1 = 1;          // (-q)^k/(k!)^2 and (-q)^k/(k!(k+1)!)
+    ld s0 = 1, s1 = 1;          // J0, J1/(z/2)
+    ld hk = 0;                  // H_k
+    ld a0 = 0;                  // sum_{k>=1} H_k (-q)^k/(k!)^2
+    ld a1 = 1;                  // sum_{k>=0} (H_k + H_{k+1}) (-q)^k/(k!(k+1)!)
+    for (int k = 1; k <= 40; ++k) {
+        t0 *= -q / ((ld)k * k);
+        t1 *= -q / ((ld)k * (k + 1));
+        s0 += t0;
+        s1 += t1;
+        hk += 1.0L / k;
+        a0 += hk * t0;
+        a1 += (2 * hk + 1.0L / (k + 1)) * t1;
+        if (std::fabs(t0) < 1e-24L && std::fabs(t1) < 1e-24L) break;
+    }
+    ld L = std::log(z / 2) + EG_L;
+    j0 = s0;
+    j1 = s1 * z / 2;
+    y0 = (2 / PI_L) * (L * j0 - a0);
+    y1 = -2 / (PI_L * z) + (2 / PI_L) * L * j1 - z / (2 * PI_L) * a1;
+}
+
+static void miller01(ld z, ld& j0, ld& j1, ld& y0, ld& y1) {
+    int nstart = 2 * ((int)(z + 56) / 2);
+    std::vector<ld> J(nstart + 2, 0.0L);
+    J[nstart] = 1e-300L;
+    for (int n = nstart; n >= 1; --n) {
+        J[n - 1] = (2.0L * n / z) * J[n] - J[n + 1];
+        if (std::fabs(J[n - 1]) > 1e300L)
+            for (int i = n - 1; i <= nstart; ++i) J[i] *= 1e-300L;
+    }
+    ld norm = J[0];
+    for (int k = 2; k <= nstart; k += 2) norm += 2 * J[k];
+    for (auto& v : J) v /= norm;
+    ld s0 = 0, s1 = 0;
+    for (int k = 1; 2 * k + 1 <= nstart + 1; ++k) {
+        ld sg = (k % 2) ? -1.0L : 1.0L;
+        s0 += sg * J[2 * k] / k;
+        s1 += sg * (J[2 * k - 1] - J[2 * k + 1]) / k;
+    }
+    ld L = std::log(z / 2) + EG_L;
+    j0 = J[0];
+    j1 = J[1];
+    y0 = (2 / PI_L) * (L * j0 - 2 * s0);
+    y1 = (2 / PI_L) * (-j0 / z + L * j1 + s1);
+}
+
+static void asym01(ld z, ld& j0, ld& j1, ld& y0, ld& y1) {
+    ld c = std::cos(z), s = std::sin(z);
+    ld r2 = std::sqrt(0.5L);
+    ld amp = std::sqrt(2 / (PI_L * z));
+    ld out[4];
+    for (int nu = 0; nu < 2; ++nu) {
+        ld mu = 4.0L * nu * nu;
+        ld P = 1, Q = 0, term = 1;
+        for (int k = 1; k < 100; ++k) {
+            term *= (mu - (ld)(2 * k - 1) * (2 * k - 1)) / (k * 8 * z);
+            if (k % 2) Q += (((k - 1) / 2) % 2 ? -term : term);
+            else       P += ((k / 2) % 2 ? -term : term);
+            if (std::fabs(term) < 1e-22L) break;
+        }
+        ld cc, ss;   // cos, sin of z - (nu/2 + 1/4) pi
+        if (nu == 0) { cc = r2 * (c + s); ss = r2 * (s - c); }
+        else         { cc = r2 * (s - c); ss = -r2 * (s + c); }
+        out[2 * nu] = amp * (P * cc - Q * ss);      // J_nu
+        out[2 * nu + 1] = amp * (P * ss + Q * cc);  // Y_nu
+    }
+    j0 = out[0]; y0 = out[1]; j1 = out[2]; y1 = out[3];
+}
+
+void hankel01_ld(ld z, cld& h0, cld& h1) {
+    ld j0, j1, y0, y1;
+    if (z <= 6) series01(z, j0, j1, y0, y1);
+    else if (z < 30) miller01(z, j0, j1, y0, y1);
+    else asym01(z, j0, j1, y0, y1);
+    h0 = cld(j0, y0);
+    h1 = cld(j1, y1);
+}
+
+// ---------------------------------------------------------------- polynomials
+// Scaled monomials s1^a s2^b, a + b <= 4, ordered by degree then by b.
+struct Mono { int a, b; };
+static const std::array<Mono, 15> MONO = {{{0, 0}, {1, 0}, {0, 1}, {2, 0}, {1, 1}, {0, 2}, {3, 0}, {2, 1},
+                                           {1, 2}, {0, 3}, {4, 0}, {3, 1}, {2, 2}, {1, 3}, {0, 4}}};
+
+static int mono_index(int a, int b) {
+    for (int i = 0; i < 15; ++i) if (MONO[i].a == a && MONO[i].b == b) return i;
+    return -1;
+}
+
+static void mono_eval(ld s1, ld s2, ld* m, ld* g1, ld* g2, ld invh) {
+    ld p1[5] = {1, s1, s1 * s1, s1 * s1 * s1, s1 * s1 * s1 * s1};
+    ld p2[5] = {1, s2, s2 * s2, s2 * s2 * s2, s2 * s2 * s2 * s2};
+    for (int i = 0; i < 15; ++i) {
+        int a = MONO[i].a, b = MONO[i].b;
+        m[i] = p1[a] * p2[b];
+        if (g1) {
+            g1[i] = a ? a * p1[a - 1] * p2[b] * invh : 0;
+            g2[i] = b ? b * p1[a] * p2[b - 1] * invh : 0;
+        }
+    }
+}
+
+// Gauss-Jordan inverse with partial pivoting (n x n, row-major), false if singular.
+static bool invert_ld(ld* A, ld* Ainv, int n) {
+    std::vector<ld> M(n * 2 * n);
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < 2 * n; ++c)
+            M[r * 2 * n + c] = c < n ? A[r * n + c] : (c - n == r ? 1 : 0);
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(M[r * 2 * n + c]) > std::fabs(M[p * 2 * n + c])) p = r;
+        if (M[p * 2 * n + c] == 0) return false;
+        if (p != c)
+            for (int k = 0; k < 2 * n; ++k) std::swap(M[p * 2 * n + k], M[c * 2 * n + k]);
+        ld piv = M[c * 2 * n + c];
+        for (int k = 0; k < 2 * n; ++k) M[c * 2 * n + k] /= piv;
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            ld f = M[r * 2 * n + c];
+            if (f == 0) continue;
+            for (int k = 0; k < 2 * n; ++k) M[r * 2 * n + k] -= f * M[c * 2 * n + k];
+        }
+    }
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) Ainv[r * n + c] = M[r * 2 * n + n + c];
+    return true;
+}
+
+// ---------------------------------------------------------------- quadrature
+struct GL32 {
+    ld x[32], w[32];   // on [0, 1]
+    GL32() {
+        const int n = 32;
+        for (int i = 0; i < n; ++i) {
+            ld t = std::cos(PI_L * (i + 0.75L) / (n + 0.5L));
+            for (int it = 0; it < 100; ++it) {
+                ld p0 = 1, p1 = t;
+                for (int m = 2; m <= n; ++m) { ld p2 = ((2 * m - 1) * t * p1 - (m - 1) * p0) / m; p0 = p1; p1 = p2; }
+                ld dp = n * (t * p1 - p0) / (t * t - 1);
+                ld dt = p1 / dp;
+                t -= dt;
+                if (std::fabs(dt) < 1e-21L) break;
+            }
+            ld p0 = 1, p1 = t;
+            for (int m = 2; m <= n; ++m) { ld p2 = ((2 * m - 1) * t * p1 - (m - 1) * p0) / m; p0 = p1; p1 = p2; }
+            ld dp = n * (t * p1 - p0) / (t * t - 1);
+            x[i] = (t + 1) / 2;
+            w[i] = 1 / ((1 - t * t) * dp * dp);      // 2 / (...) halved for [0, 1]
+        }
+    }
+};
+static const GL32& gl32() { static GL32 g; return g; }
+
+struct Edge {                     // one oriented edge of an element
+    ld ax, ay, bx, by;            // straight: endpoints
+    bool curved;
+    ld cx, cy, R, a, m, phi, t0, t1;
+};
+
+static inline void edge_point(const Edge& e, ld t, ld& x, ld& y, ld& dx, ld& dy) {
+    if (!e.curved) {
+        x = e.ax + t * (e.bx - e.ax);
+        y = e.ay + t * (e.by - e.ay);
+        dx = e.bx - e.ax;
+        dy = e.by - e.ay;
+        return;
+    }
+    ld th = e.t0 + t * (e.t1 - e.t0);
+    ld ang = e.m * th + e.phi;
+    ld r = e.R * (1 + e.a * std::cos(ang));
+    ld dr = -e.R * e.a * e.m * std::sin(ang);
+    ld c = std::cos(th), s = std::sin(th);
+    x = e.cx + r * c;
+    y = e.cy + r * s;
+    dx = (dr * c - r * s) * (e.t1 - e.t0);
+    dy = (dr * s + r * c) * (e.t1 - e.t0);
+}
+
+static Edge make_edge(const HostMesh& M, int t, int e) {
+    Edge E{};
+    int va = M.tri[3 * t + e], vb = M.tri[3 * t + (e + 1) % 3];
+    E.ax = M.vxy[2 * va]; E.ay = M.vxy[2 * va + 1];
+    E.bx = M.vxy[2 * vb]; E.by = M.vxy[2 * vb + 1];
+    int c = M.ecurve[3 * t + e];
+    E.curved = c >= 0;
+    if (E.curved) {
+        const double* C = &M.curves[6 * c];
+        E.cx = C[0]; E.cy = C[1]; E.R = C[2]; E.a = C[3]; E.m = C[4]; E.phi = C[5];
+        E.t0 = M.etheta[6 * t + 2 * e]; E.t1 = M.etheta[6 * t + 2 * e + 1];
+    }
+    return E;
+}
+
+struct PolyCtx {                  // one interpolation element
+    ld cx, cy, h, invh;
+    ld C[15 * 15];                // L_q = sum_a mono_a C[a][q]
+    ld Phi[15 * 15];              // Phi_q = sum_a mono_a Phi[a][q]
+};
+
+static bool make_poly(const HostMesh& M, int tau, ld k, PolyCtx& P) {
+    const int* v = &M.tri[3 * tau];
+    ld x0 = M.vxy[2 * v[0]], y0 = M.vxy[2 * v[0] + 1];
+    ld x1 = M.vxy[2 * v[1]], y1 = M.vxy[2 * v[1] + 1];
+    ld x2 = M.vxy[2 * v[2]], y2 = M.vxy[2 * v[2] + 1];
+    P.cx = ((x0 + x1) + x2) / 3;
+    P.cy = ((y0 + y1) + y2) / 3;
+    ld h2 = std::max({(x0 - x1) * (x0 - x1) + (y0 - y1) * (y0 - y1), (x1 - x2) * (x1 - x2) + (y1 - y2) * (y1 - y2),
+                      (x2 - x0) * (x2 - x0) + (y2 - y0) * (y2 - y0)});
+    P.h = std::sqrt(h2);
+    P.invh = 1 / P.h;
+    ld V[225], m[15];
+    for (int q = 0; q < 15; ++q) {
+        int j = tau * NQ_ELEM + q;
+        mono_eval((M.nodes[2 * j] - P.cx) * P.invh, (M.nodes[2 * j + 1] - P.cy) * P.invh, m, nullptr, nullptr, P.invh);
+        for (int a = 0; a < 15; ++a) V[q * 15 + a] = m[a];      // V[q][a]
+    }
+    if (!invert_ld(V, P.C, 15)) return false;                    // C[a][q]
+    // Laplacian on coefficient vectors: lap(mono(a,b)) = (a(a-1) mono(a-2,b) + b(b-1) mono(a,b-2)) / h^2
+    ld lap1[225], lap2[225];
+    auto apply_lap = [&](const ld* src, ld* dst) {
+        for (int i = 0; i < 225; ++i) dst[i] = 0;
+        for (int a = 0; a < 15; ++a) {
+            int ea = MONO[a].a, eb = MONO[a].b;
+            for (int q = 0; q < 15; ++q) {
+                ld c = src[a * 15 + q];
+                if (c == 0) continue;
+                if (ea >= 2) dst[mono_index(ea - 2, eb) * 15 + q] += ea * (ea - 1) * c * P.invh * P.invh;
+                if (eb >= 2) dst[mono_index(ea, eb - 2) * 15 + q] += eb * (eb - 1) * c * P.invh * P.invh;
+            }
+        }
+    };
+    apply_lap(P.C, lap1);
+    apply_lap(lap1, lap2);
+    ld k2 = k * k;
+    for (int i = 0; i < 225; ++i) P.Phi[i] = P.C[i] / k2 - lap1[i] / (k2 * k2) + lap2[i] / (k2 * k2 * k2);
+    return true;
+}
+
+// Accumulate sum over GL32 points of one panel into E[15].
+static void panel_integral(const Edge& e, ld ta, ld tb, ld xj, ld yj, ld k, const PolyCtx& P, cld* E) {
+    const GL32& g = gl32();
+    ld m[15], g1[15], g2[15];
+    for (int i = 0; i < 32; ++i) {
+        ld t = ta + (tb - ta) * g.x[i];
+        ld wt = (tb - ta) * g.w[i];
+        ld x, y, dx, dy;
+        edge_point(e, t, x, y, dx, dy);
+        ld nx = dy, ny = -dx;                         // outward normal times |y'|
+        ld rx = x - xj, ry = y - yj;
+        ld r = std::sqrt(rx * rx + ry * ry);
+        cld h0, h1;
+        hankel01_ld(k * r, h0, h1);
+        cld G = cld(0, 0.25L) * h0;
+        cld dGdn = cld(0, 0.25L) * (-k) * h1 * ((rx * nx + ry * ny) / r);
+        mono_eval((x - P.cx) * P.invh, (y - P.cy) * P.invh, m, g1, g2, P.invh);
+        for (int q = 0; q < 15; ++q) {
+            ld phi = 0, dphi = 0;
+            for (int a = 0; a < 15; ++a) {
+                ld c = P.Phi[a * 15 + q];
+                phi += m[a] * c;
+                dphi += (g1[a] * nx + g2[a] * ny) * c;
+            }
+            E[q] += wt * (G * dphi - dGdn * phi);
+        }
+    }
+}
+
+static void edge_integral(const Edge& e, ld xj, ld yj, ld k, const PolyCtx& P, cld* E) {
+    struct Pan { ld a, b; int depth; };
+    std::vector<Pan> stack{{0, 1, 0}};
+    while (!stack.empty()) {
+        Pan p = stack.back();
+        stack.pop_back();
+        ld xa, ya, xm, ym, xb, yb, d1, d2;
+        edge_point(e, p.a, xa, ya, d1, d2);
+        edge_point(e, (p.a + p.b) / 2, xm, ym, d1, d2);
+        edge_point(e, p.b, xb, yb, d1, d2);
+        ld L = std::hypot(xm - xa, ym - ya) + std::hypot(xb - xm, yb - ym);
+        ld dist = std::min({std::hypot(xa - xj, ya - yj), std::hypot(xm - xj, ym - yj), std::hypot(xb - xj, yb - yj)});
+        if (L > 0.75L * dist && p.depth < 60) {
+            ld mid = (p.a + p.b) / 2;
+            stack.push_back({p.a, mid, p.depth + 1});
+            stack.push_back({mid, p.b, p.depth + 1});
+        } else {
+            panel_integral(e, p.a, p.b, xj, yj, k, P, E);
+        }
+    }
+}
+
+// dV_j,(15 nodes of tau) for the given patch; adds 15 entries to (cols, vals).
+static bool correction_block(const HostMesh& M, int j, ld k, const std::vector<int>& patch, int tau, bool own,
+                             std::vector<int32_t>& cols, std::vector<std::complex<double>>& vals) {
+    PolyCtx P;
+    if (!make_poly(M, tau, k, P)) return false;
+    ld xj = M.nodes[2 * j], yj = M.nodes[2 * j + 1];
+    cld E[15], N[15];
+    for (int q = 0; q < 15; ++q) { E[q] = 0; N[q] = 0; }
+    // boundary edges of the patch: edges met once among the patch elements
+    std::vector<std::array<int, 4>> keys;   // (min v, max v, element, edge)
+    keys.reserve(patch.size() * 3);
+    for (int t : patch)
+        for (int e = 0; e < 3; ++e) {
+            int a = M.tri[3 * t + e], b = M.tri[3 * t + (e + 1) % 3];
+            keys.push_back({std::min(a, b), std::max(a, b), t, e});
+        }
+    std::sort(keys.begin(), keys.end());
+    for (size_t i = 0; i < keys.size();) {
+        size_t r = i + 1;
+        while (r < keys.size() && keys[r][0] == keys[i][0] && keys[r][1] == keys[i][1]) ++r;
+        if (r - i == 1) edge_integral(make_edge(M, keys[i][2], keys[i][3]), xj, yj, k, P, E);
+        i = r;
+    }
+    ld m[15];
+    if (own) {
+        mono_eval((xj - P.cx) * P.invh, (yj - P.cy) * P.invh, m, nullptr, nullptr, P.invh);
+        for (int q = 0; q < 15; ++q) {
+            ld phi = 0;
+            for (int a = 0; a < 15; ++a) phi += m[a] * P.Phi[a * 15 + q];
+            E[q] -= phi;
+        }
+    }
+    for (int t : patch)
+        for (int qq = 0; qq < NQ_ELEM; ++qq) {
+            int n = t * NQ_ELEM + qq;
+            if (n == j) continue;
+            ld yx = M.nodes[2 * n], yy = M.nodes[2 * n + 1];
+            ld r = std::sqrt((yx - xj) * (yx - xj) + (yy - yj) * (yy - yj));
+            cld h0, h1;
+            hankel01_ld(k * r, h0, h1);
+            cld Gw = cld(0, 0.25L) * h0 * (ld)M.w[n];
+            mono_eval((yx - P.cx) * P.invh, (yy - P.cy) * P.invh, m, nullptr, nullptr, P.invh);
+            for (int q = 0; q < 15; ++q) {
+                ld L = 0;
+                for (int a = 0; a < 15; ++a) L += m[a] * P.C[a * 15 + q];
+                N[q] += Gw * L;
+            }
+        }
+    for (int q = 0; q < 15; ++q) {
+        cols.push_back(tau * NQ_ELEM + q);
+        cld d = E[q] - N[q];
+        vals.push_back(std::complex<double>((double)d.real(), (double)d.imag()));
+    }
+    return true;
+}
+
+#pragma GCC push_options
+#pragma GCC optimize("fp-contract=off")
+// Element centroid and squared size, computed exactly as documented (float64, no FMA).
+static void element_geometry(const HostMesh& M, std::vector<double>& cen, std::vector<double>& h2) {
+    cen.resize(2 * M.nt);
+    h2.resize(M.nt);
+    for (int t = 0; t < M.nt; ++t) {
+        const int* v = &M.tri[3 * t];
+        double x0 = M.vxy[2 * v[0]], y0 = M.vxy[2 * v[0] + 1];
+        double x1 = M.vxy[2 * v[1]], y1 = M.vxy[2 * v[1] + 1];
+        double x2 = M.vxy[2 * v[2]], y2 = M.vxy[2 * v[2] + 1];
+        cen[2 * t] = ((x0 + x1) + x2) / 3.0;
+        cen[2 * t + 1] = ((y0 + y1) + y2) / 3.0;
+        double a = (x0 - x1) * (x0 - x1) + (y0 - y1) * (y0 - y1);
+        double b = (x1 - x2) * (x1 - x2) + (y1 - y2) * (y1 - y2);
+        double c = (x2 - x0) * (x2 - x0) + (y2 - y0) * (y2 - y0);
+        h2[t] = std::max(std::max(a, b), c);
+    }
+}
+
+static inline double dist2(double ax, double ay, double bx, double by) {
+    double dx = ax - bx, dy = ay - by;
+    return dx * dx + dy * dy;
+}
+#pragma GCC pop_options
+
+std::string build_correction(const HostMesh& M, double k, double kappa, CsrC& out) {
+    std::vector<double> cen, h2;
+    element_geometry(M, cen, h2);
+    int ndom = 0;
+    for (int d : M.dom) ndom = std::max(ndom, d + 1);
+    // bucket grid of element centroids
+    double rmax = 0, xmin = 1e300, ymin = 1e300, xmax = -1e300, ymax = -1e300;
+    for (int t = 0; t < M.nt; ++t) {
+        rmax = std::max(rmax, kappa * std::sqrt(h2[t]));
+        xmin = std::min(xmin, cen[2 * t]); xmax = std::max(xmax, cen[2 * t]);
+        ymin = std::min(ymin, cen[2 * t + 1]); ymax = std::max(ymax, cen[2 * t + 1]);
+    }
+    double cell = std::max(rmax, 1e-12) * 1.0000001;
+    int gx = std::max(1, (int)std::ceil((xmax - xmin) / cell) + 1);
+    int gy = std::max(1, (int)std::ceil((ymax - ymin) / cell) + 1);
+    std::vector<std::vector<int>> bucket((size_t)gx * gy);
+    for (int t = 0; t < M.nt; ++t) {
+        int bx = std::min(gx - 1, (int)((cen[2 * t] - xmin) / cell));
+        int by = std::min(gy - 1, (int)((cen[2 * t + 1] - ymin) / cell));
+        bucket[(size_t)by * gx + bx].push_back(t);
+    }
+    const int nq = M.nq;
+    std::vector<std::vector<int32_t>> rcols(nq);
+    std::vector<std::vector<std::complex<double>>> rvals(nq);
+    int failed = -1;
+    const ld kl = k;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int j = 0; j < nq; ++j) {
+        int tau = j / NQ_ELEM;
+        int l = M.dom[tau];
+        double xj = M.nodes[2 * j], yj = M.nodes[2 * j + 1];
+        double thr = kappa * kappa * h2[tau];
+        int bx = std::min(gx - 1, std::max(0, (int)((xj - xmin) / cell)));
+        int by = std::min(gy - 1, std::max(0, (int)((yj - ymin) / cell)));
+        std::vector<std::vector<int>> patch(ndom);
+        for (int cy = std::max(0, by - 1); cy <= std::min(gy - 1, by + 1); ++cy)
+            for (int cx = std::max(0, bx - 1); cx <= std::min(gx - 1, bx + 1); ++cx)
+                for (int t : bucket[(size_t)cy * gx + cx])
+                    if (dist2(cen[2 * t], cen[2 * t + 1], xj, yj) < thr) patch[M.dom[t]].push_back(t);
+        for (int d = 0; d < ndom; ++d) {
+            auto& P = patch[d];
+            std::sort(P.begin(), P.end());
+            int interp;
+            if (d == l) {
+                if (!std::binary_search(P.begin(), P.end(), tau)) P.insert(std::lower_bound(P.begin(), P.end(), tau), tau);
+                interp = tau;
+            } else {
+                if (P.empty()) continue;
+                interp = P[0];
+                double best = dist2(cen[2 * P[0]], cen[2 * P[0] + 1], xj, yj);
+                for (int t : P) {
+                    double d2 = dist2(cen[2 * t], cen[2 * t + 1], xj, yj);
+                    if (d2 < best) { best = d2; interp = t; }
+                }
+            }
+            if (!correction_block(M, j, kl, P, interp, d == l, rcols[j], rvals[j])) {
+#pragma omp critical
+                failed = j;
+            }
+        }
+    }
+    if (failed >= 0) return "singular interpolation matrix for target " + std::to_string(failed);
+    out.rowptr.assign(nq + 1, 0);
+    for (int j = 0; j < nq; ++j) out.rowptr[j + 1] = out.rowptr[j] + (int64_t)rcols[j].size();
+    out.cols.resize(out.rowptr[nq]);
+    out.vals.resize(out.rowptr[nq]);
+    for (int j = 0; j < nq; ++j) {
+        std::copy(rcols[j].begin(), rcols[j].end(), out.cols.begin() + out.rowptr[j]);
+        std::copy(rvals[j].begin(), rvals[j].end(), out.vals.begin() + out.rowptr[j]);
+    }
+    return "";
+}
+
+// ---------------------------------------------------------------- grid
+static std::complex<double> vc_entry(ld k, ld h, int da, int db) {
+    if (da == 0 && db == 0) {
+        ld a = h / std::sqrt(PI_L);
+        cld h0, h1;
+        hankel01_ld(k * a, h0, h1);
+        cld v = cld(0, PI_L) * a * h1 / (2 * k) - 1 / (k * k);
+        return std::complex<double>((double)v.real(), (double)v.imag());
+    }
+    ld r = h * std::sqrt((ld)da * da + (ld)db * db);
+    cld h0, h1;
+    hankel01_ld(k * r, h0, h1);
+    cld v = cld(0, 0.25L) * h0 * h * h;
+    return std::complex<double>((double)v.real(), (double)v.imag());
+}
+
+// Hermitian 9 x 9 Jacobi eigen-solver (long double); returns the eigenvector of the
+// smallest eigenvalue in vec.
+static void smallest_eigvec(std::vector<cld>& A, int n, std::vector<cld>& vec) {
+    std::vector<cld> Vm(n * n, cld(0, 0));
+    for (int i = 0; i < n; ++i) Vm[i * n + i] = 1;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        ld off = 0, tot = 0;
+        for (int p = 0; p < n; ++p)
+            for (int q = 0; q < n; ++q) {
+                ld a2 = std::norm(A[p * n + q]);
+                tot += a2;
+                if (p != q) off += a2;
+            }
+        if (off <= 1e-38L * tot) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                cld apq = A[p * n + q];
+                ld aabs = std::abs(apq);
+                if (aabs == 0) continue;
+                ld app = A[p * n + p].real(), aqq = A[q * n + q].real();
+                // rotation zeroing A[p][q]: unitary [[c, -s e^{i phi}], [s e^{-i phi}, c]]
+                cld ph = apq / aabs;
+                ld theta = 0.5L * std::atan2(2 * aabs, aqq - app);
+                ld c = std::cos(theta), s = std::sin(theta);
+                // columns p, q
+                for (int r = 0; r < n; ++r) {
+                    cld arp = A[r * n + p], arq = A[r * n + q];
+                    A[r * n + p] = c * arp - s * std::conj(ph) * arq;
+                    A[r * n + q] = s * ph * arp + c * arq;
+                    cld vrp = Vm[r * n + p], vrq = Vm[r * n + q];
+                    Vm[r * n + p] = c * vrp - s * std::conj(ph) * vrq;
+                    Vm[r * n + q] = s * ph * vrp + c * vrq;
+                }
+                // rows p, q
+                for (int r = 0; r < n; ++r) {
+                    cld apr = A[p * n + r], aqr = A[q * n + r];
+                    A[p * n + r] = c * apr - s * ph * aqr;
+                    A[q * n + r] = s * std::conj(ph) * apr + c * aqr;
+                }
+            }
+    }
+    int best = 0;
+    for (int i = 1; i < n; ++i) if (A[i * n + i].real() < A[best * n + best].real()) best = i;
+    vec.resize(n);
+    for (int r = 0; r < n; ++r) vec[r] = Vm[r * n + best];
+}
+
+std::string build_grid(const HostMesh& M, double k, const double box[4], int nx, int ny,
+                       const std::complex<double>* m_grid, GridSetup& G) {
+    if (nx < 4 || ny < 4) return "grid needs at least 4 x 4 nodes";
+    double hx = (box[1] - box[0]) / (nx - 1), hy = (box[3] - box[2]) / (ny - 1);
+    if (!(hx > 0) || std::fabs(hx - hy) > 1e-12 * hx) return "grid step must be equal in x and y";
+    G.nx = nx; G.ny = ny; G.x0 = box[0]; G.y0 = box[2]; G.h = hx;
+    const int nq = M.nq, nc = nx * ny;
+    G.tcq_idx.resize(4 * (size_t)nq);
+    G.tcq_w.resize(4 * (size_t)nq);
+    std::vector<double> colsum(nc, 0.0);
+    for (int q = 0; q < nq; ++q) {
+        double yx = M.nodes[2 * q], yy = M.nodes[2 * q + 1];
+        if (yx < box[0] || yx > box[1] || yy < box[2] || yy > box[3]) return "quadrature node outside the grid box";
+        int a = (int)std::floor((yx - G.x0) / G.h), b = (int)std::floor((yy - G.y0) / G.h);
+        a = std::min(std::max(a, 0), nx - 2);
+        b = std::min(std::max(b, 0), ny - 2);
+        int c = 0;
+        for (int db = 0; db < 2; ++db)
+            for (int da = 0; da < 2; ++da) {
+                double zx = G.x0 + (a + da) * G.h, zy = G.y0 + (b + db) * G.h;
+                double psi = (1 - std::fabs(yx - zx) / G.h) * (1 - std::fabs(yy - zy) / G.h);
+                int idx = (a + da) + nx * (b + db);
+                G.tcq_idx[4 * (size_t)q + c] = idx;
+                G.tcq_w[4 * (size_t)q + c] = psi;
+                colsum[idx] += psi;
+                ++c;
+            }
+    }
+    G.D.resize(nc);
+    for (int i = 0; i < nc; ++i) G.D[i] = colsum[i] > 0 ? colsum[i] : 1.0;
+    // gather CSR of T_Q^C = D^{-1} (T_C^Q)^T
+    G.tqc_rowptr.assign(nc + 1, 0);
+    for (size_t e = 0; e < 4 * (size_t)nq; ++e) G.tqc_rowptr[G.tcq_idx[e] + 1]++;
+    for (int i = 0; i < nc; ++i) G.tqc_rowptr[i + 1] += G.tqc_rowptr[i];
+    G.tqc_cols.resize(4 * (size_t)nq);
+    G.tqc_vals.resize(4 * (size_t)nq);
+    std::vector<int64_t> fill(G.tqc_rowptr.begin(), G.tqc_rowptr.end() - 1);
+    for (int q = 0; q < nq; ++q)
+        for (int c = 0; c < 4; ++c) {
+            int i = G.tcq_idx[4 * (size_t)q + c];
+            int64_t pos = fill[i]++;
+            G.tqc_cols[pos] = q;
+            G.tqc_vals[pos] = G.tcq_w[4 * (size_t)q + c] / G.D[i];
+        }
+    // stencil: Gram matrix of B = V^(C)(N(0), N(0)^c) around the grid centre
+    const ld kl = k, hl = G.h;
+    int ca = nx / 2, cb = ny / 2;
+    std::vector<cld> gram(81, cld(0, 0));
+    int nthreads = 1;
+#ifdef _OPENMP
+#pragma omp parallel
+    {
+#pragma omp single
+        nthreads = omp_get_num_threads();
+    }
+#endif
+    std::vector<std::vector<cld>> part(nthreads, std::vector<cld>(81, cld(0, 0)));
+#pragma omp parallel for schedule(static)
+    for (int l = 0; l < nc; ++l) {
+        int la = l % nx, lb = l / nx;
+        if (std::abs(la - ca) <= 1 && std::abs(lb - cb) <= 1) continue;
+        cld col[9];
+        for (int s = 0; s < 9; ++s) {
+            int da = s % 3 - 1, db = s / 3 - 1;
+            ld r = hl * std::sqrt((ld)(la - ca - da) * (la - ca - da) + (ld)(lb - cb - db) * (lb - cb - db));
+            cld h0, h1;
+            hankel01_ld(kl * r, h0, h1);
+            col[s] = cld(0, 0.25L) * h0 * hl * hl;
+        }
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        for (int p = 0; p < 9; ++p)
+            for (int q = 0; q < 9; ++q) part[tid][p * 9 + q] += col[p] * std::conj(col[q]);
+    }
+    for (auto& pp : part)
+        for (int i = 0; i < 81; ++i) gram[i] += pp[i];
+    std::vector<cld> u;
+    smallest_eigvec(gram, 9, u);
+    // v = conj(u), unit norm
+    ld nrm = 0;
+    for (auto& x : u) nrm += std::norm(x);
+    nrm = std::sqrt(nrm);
+    for (int s = 0; s < 9; ++s) {
+        cld vs = std::conj(u[s]) / nrm;
+        G.v[s] = std::complex<double>((double)vs.real(), (double)vs.imag());
+    }
+    // V^(C) on offsets [-2, 2]^2
+    std::complex<double> vcoff[5][5];
+    for (int da = -2; da <= 2; ++da)
+        for (int db = -2; db <= 2; ++db) vcoff[da + 2][db + 2] = vc_entry(kl, hl, da, db);
+    // C = A L^(C) on the 3x3 pattern
+    G.cband.assign((size_t)ny * 9 * nx, std::complex<double>(0, 0));
+    const double k2 = k * k;
+    for (int b = 0; b < ny; ++b)
+        for (int a = 0; a < nx; ++a) {
+            bool full = a >= 1 && a <= nx - 2 && b >= 1 && b <= ny - 2;
+            for (int db = -1; db <= 1; ++db)
+                for (int da = -1; da <= 1; ++da) {
+                    int la = a + da, lb = b + db;
+                    if (la < 0 || la >= nx || lb < 0 || lb >= ny) continue;
+                    std::complex<double> acc = 0;
+                    std::complex<double> ml = m_grid[la + (size_t)nx * lb];
+                    if (full) {
+                        acc = G.v[(da + 1) + 3 * (db + 1)];
+                        if (ml != 0.0) {
+                            std::complex<double> s = 0;
+                            for (int sb = -1; sb <= 1; ++sb)
+                                for (int sa = -1; sa <= 1; ++sa)
+                                    s += G.v[(sa + 1) + 3 * (sb + 1)] * vcoff[(a + sa - la) + 2][(b + sb - lb) + 2];
+                            acc += k2 * ml * s;
+                        }
+                    } else {
+                        acc = (da == 0 && db == 0) ? 1.0 : 0.0;
+                        if (ml != 0.0) acc += k2 * ml * vcoff[(a - la) + 2][(b - lb) + 2];
+                    }
+                    G.cband[((size_t)b * 9 + (db + 1) * 3 + (da + 1)) * nx + a] = acc;
+                }
+        }
+    return "";
+}
+
+}  // namespace lsgpu

@@ -1,0 +1,202 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: FP64 matvec <= 1e-11 relative L2 (the target for the FP64 form);
+device Hankel <= 5e-14 relative (the series branch near z = 6 loses about two
+digits to cancellation); solutions agree to the GMRES tolerance times a
+condition factor.  Sizes span many pair-sum tiles and chunks with ragged tails
+(3,240 / 1,800 / 40,200 nodes against tiles of 128 targets and 256 sources).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2608_17615_b300 as L
+from lsinput.mesh import disk_mesh
+from lsinput.workloads import constant_disk, random_density, two_material
+from oracle.bessel import hankel01
+from oracle.farfield import far_field, mie_far_field, mie_interior
+from oracle.gmres import gmres
+from oracle.nystrom import naive_apply
+from oracle.operator import Operator as OracleOp, plane_wave
+from oracle.precond import Grid, Preconditioner
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.complex128)).cuda()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def test_device_hankel():
+    z = np.concatenate([np.logspace(-6, 2.3, 20000), np.linspace(5.9, 6.1, 2001), np.linspace(0.5, 60, 5000)])
+    zt = torch.from_numpy(z).cuda()
+    out = torch.empty(z.size, dtype=torch.complex128, device="cuda")
+    L.hankel0_dev(zt, out)
+    h = out.cpu().numpy()
+    ref, _ = hankel01(z)
+    err = np.abs(h - ref) / np.abs(ref)
+    assert err.max() < 5e-14, (err.max(), z[err.argmax()])
+
+
+def test_pairsum_parity_disk():
+    wl = constant_disk(k=5.0, n_rings=3)
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, use_precond=0)
+    f = random_density(wl.mesh.n_nodes, 3)
+    y = torch.empty(wl.mesh.n_nodes, dtype=torch.complex128, device="cuda")
+    op.pairsum_dev(_dev(f), y)
+    ref = naive_apply(wl.mesh.nodes, wl.mesh.weights, wl.k, f)
+    assert _rel(y.cpu().numpy(), ref) < 1e-13
+
+
+@pytest.mark.parametrize("case", ["disk", "two_material"])
+def test_apply_parity_full(case):
+    if case == "disk":
+        wl = constant_disk(k=5.0, n_rings=2)
+    else:
+        wl = two_material("tiny", k=8.0)
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, use_precond=0)
+    x = random_density(wl.mesh.n_nodes, 5)
+    y = torch.empty(wl.mesh.n_nodes, dtype=torch.complex128, device="cuda")
+    op.apply_dev(_dev(x), y)
+    ref = OracleOp(wl.mesh, wl.k, wl.m).apply(x)
+    assert _rel(y.cpu().numpy(), ref) < 1e-11
+    # host-buffer entry point gives the same numbers
+    assert np.array_equal(op.apply(x), y.cpu().numpy())
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    wl = two_material("small")                 # 40,200 nodes, k = 20, 256^2 grid
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, tol=1e-8)
+    return wl, op
+
+
+def test_apply_parity_two_material_full_size(cfg2):
+    wl, op = cfg2
+    n = wl.mesh.n_nodes
+    x = random_density(n, 11)
+    y = torch.empty(n, dtype=torch.complex128, device="cuda")
+    op.apply_dev(_dev(x), y)
+    rows = np.concatenate([np.arange(0, n, 997), [n - 1]])
+    ref = OracleOp(wl.mesh, wl.k, wl.m, rows_only=True).apply_rows(x, rows)
+    assert _rel(y.cpu().numpy()[rows], ref) < 1e-11
+
+
+def test_precond_parity_small():
+    wl = constant_disk(k=5.0, n_rings=3, nx=48, ny=48)
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, nx=48, ny=48)
+    x = random_density(wl.mesh.n_nodes, 7)
+    y = torch.empty(wl.mesh.n_nodes, dtype=torch.complex128, device="cuda")
+    op.apply_precond_dev(_dev(x), y)
+    P = Preconditioner(Grid(wl.box, wl.nx, wl.ny), wl.mesh.nodes, wl.k, wl.m_grid)
+    assert _rel(y.cpu().numpy(), P.apply(x)) < 1e-11
+
+
+def test_precond_parity_full_size(cfg2):
+    wl, op = cfg2
+    n = wl.mesh.n_nodes
+    x = random_density(n, 13)
+    y = torch.empty(n, dtype=torch.complex128, device="cuda")
+    op.apply_precond_dev(_dev(x), y)
+    P = Preconditioner(Grid(wl.box, wl.nx, wl.ny), wl.mesh.nodes, wl.k, wl.m_grid)
+    err = _rel(y.cpu().numpy(), P.apply(x))
+    print("precond full-size rel err", err)
+    assert err < 1e-9
+
+
+def test_solve_matches_oracle_small_disk():
+    wl = constant_disk(k=5.0, n_rings=3)
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, use_precond=0, tol=1e-12)
+    u, uinf, hist, iters, st = op.solve([0.0], wl.ff_angles)
+    assert st == L.LS_OK and hist[0, iters[0]] <= 1e-12
+    ora = OracleOp(wl.mesh, wl.k, wl.m)
+    b = plane_wave(wl.mesh.nodes, wl.k, 0.0)
+    ud = np.linalg.solve(ora.dense(), b)
+    assert _rel(u[0], ud) < 1e-9
+    ff = far_field(wl.mesh.nodes, wl.mesh.weights, wl.m, u[0], wl.k, wl.ff_angles)
+    assert _rel(uinf[0], ff) < 1e-12
+
+
+def test_solve_disk_mie_and_energy():
+    wl = constant_disk(k=5.0, n_rings=6)      # 216 triangles, 3,240 nodes
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, use_precond=0, tol=1e-10)
+    u, uinf, hist, iters, st = op.solve([0.0], wl.ff_angles)
+    assert st == L.LS_OK
+    ref = mie_interior(wl.mesh.nodes, wl.k, 1.5)
+    e_int = np.max(np.abs(u[0] - ref)) / np.max(np.abs(ref))
+    e_ff = np.max(np.abs(uinf[0] - mie_far_field(wl.ff_angles, wl.k, 1.5)))
+    b = plane_wave(wl.mesh.nodes, wl.k, 0.0)
+    lhs = np.imag(np.sum(wl.mesh.weights * np.conj(wl.m * u[0]) * b))
+    rhs = np.sum(np.abs(uinf[0]) ** 2) * 2 * np.pi / len(wl.ff_angles) / wl.k
+    print("cfg1 iters", iters[0], "Mie e_int", e_int, "far-field err", e_ff, "energy", lhs, rhs)
+    assert e_int < 1e-5 and e_ff < 1e-5
+    assert abs(lhs - rhs) < 1e-5 * rhs
+
+
+def test_preconditioned_solve_two_material():
+    wl = two_material("tiny", k=8.0, nx=64, ny=64)
+    mesh = L.Mesh(wl.mesh)
+    opu = L.Operator(mesh, wl.k, wl.m, use_precond=0, tol=1e-10)
+    opp = L.Operator(mesh, wl.k, wl.m, wl.m_grid, nx=64, ny=64, tol=1e-10)
+    uu, _, _, iu, su = opu.solve([np.pi / 4])
+    up, _, _, ip, sp = opp.solve([np.pi / 4])
+    assert su == sp == L.LS_OK
+    assert ip[0] < iu[0]
+    assert _rel(up[0], uu[0]) < 1e-8
+    b = plane_wave(wl.mesh.nodes, wl.k, np.pi / 4)
+    ud = np.linalg.solve(OracleOp(wl.mesh, wl.k, wl.m).dense(), b)
+    assert _rel(up[0], ud) < 1e-8
+
+
+def test_two_material_full_size_solve(cfg2):
+    wl, op = cfg2
+    u, uinf, hist, iters, st = op.solve([np.pi / 4], wl.ff_angles)
+    print("cfg2 preconditioned iterations", iters[0])
+    assert st == L.LS_OK and iters[0] < 100
+    # the true residual of the returned solution, with the library's own L and P
+    n = wl.mesh.n_nodes
+    ud = _dev(u[0])
+    Lu = torch.empty(n, dtype=torch.complex128, device="cuda")
+    op.apply_dev(ud, Lu)
+    b = _dev(plane_wave(wl.mesh.nodes, wl.k, np.pi / 4))
+    r = torch.empty_like(Lu)
+    pb = torch.empty_like(Lu)
+    op.apply_precond_dev(b - Lu, r)
+    op.apply_precond_dev(b, pb)
+    assert (torch.linalg.norm(r) / torch.linalg.norm(pb)).item() < 2e-8
+
+
+def test_solve_dev_and_enoconv():
+    wl = constant_disk(k=5.0, n_rings=2)
+    mesh = L.Mesh(wl.mesh)
+    op = L.Operator(mesh, wl.k, wl.m, use_precond=0, tol=1e-12)
+    b = plane_wave(wl.mesh.nodes, wl.k, 0.3)
+    bd = _dev(np.stack([b, 2 * b]))
+    ud = torch.empty_like(bd)
+    iters, st = op.solve_dev(bd, ud)
+    assert st == L.LS_OK
+    u = ud.cpu().numpy()
+    assert _rel(u[1], 2 * u[0]) < 1e-12
+    op3 = L.Operator(mesh, wl.k, wl.m, use_precond=0, tol=1e-12, max_iter=3)
+    _, _, _, it3, st3 = op3.solve([0.3])
+    assert st3 == L.LS_ENOCONV and it3[0] == 3
+
+
+def test_bad_device_arguments():
+    wl = constant_disk(k=5.0, n_rings=1)
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, use_precond=0)
+    x = torch.zeros(wl.mesh.n_nodes, dtype=torch.complex128, device="cuda")
+    with pytest.raises(L.LsError):
+        op.apply_dev(x, x)                     # aliasing is rejected
+    with pytest.raises(L.LsError):
+        op.apply_precond_dev(x, torch.empty_like(x))   # no preconditioner built

@@ -1,0 +1,87 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every declared
+symbol, validates inputs, and its host setup of the VDIM correction agrees with
+the oracle's (both in extended precision, independently written)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sps
+
+import paper_2608_17615_b300 as L
+from lsinput.mesh import disk_mesh
+from lsinput.workloads import two_material
+from oracle import vdim
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "lsgpu.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ls_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported():
+    lib = ctypes.CDLL(L.LIB_PATH)
+    names = _declared()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(L.EXPORTED) == names
+
+
+def test_params_default():
+    p = L.params_default()
+    assert p.tol == 1e-8 and p.max_iter == 600 and p.use_precond == 1 and p.kappa == 3.0
+    assert list(p.box) == [-1.2, 1.2, -1.2, 1.2] and p.nx == 256 and p.ny == 256
+
+
+def test_mesh_rejects_clockwise_element():
+    m = disk_mesh(1)
+    m.tris = m.tris.copy()
+    m.tris[0] = m.tris[0][::-1]
+    with pytest.raises(L.LsError) as e:
+        L.Mesh(m)
+    assert e.value.status == L.LS_EINVAL
+
+
+def test_mesh_rejects_out_of_range_vertex():
+    m = disk_mesh(1)
+    m.tris = m.tris.copy()
+    m.tris[2, 1] = 10_000
+    with pytest.raises(L.LsError):
+        L.Mesh(m)
+
+
+def test_correction_rejects_bad_k():
+    M = L.Mesh(disk_mesh(1))
+    with pytest.raises(L.LsError):
+        L.correction_host(M, -1.0)
+
+
+def _csr(mesh, rp, ci, va):
+    return sps.csr_matrix((va, ci, rp), shape=(mesh.n_nodes, mesh.n_nodes))
+
+
+def test_correction_matches_oracle_disk():
+    mesh = disk_mesh(2)
+    k = 5.0
+    A = _csr(mesh, *L.correction_host(L.Mesh(mesh), k, 3.0))
+    B = vdim.correction_matrix(mesh, k, 3.0)
+    assert (A != 0).nnz == (B != 0).nnz == 15 * mesh.n_nodes
+    assert abs(A - B).max() < 1e-13 * abs(B).max()
+
+
+def test_correction_matches_oracle_two_materials():
+    # tiny two-material mesh: rows with a second (foreign-subdomain) block
+    wl = two_material("tiny", k=8.0)
+    mesh = wl.mesh
+    A = _csr(mesh, *L.correction_host(L.Mesh(mesh), wl.k, 3.0))
+    rows = np.arange(0, mesh.n_nodes, 7)
+    B = vdim.correction_matrix(mesh, wl.k, 3.0, rows=rows)
+    Ar = A[rows]
+    assert np.array_equal(Ar.indptr, B.indptr)
+    assert np.max(np.diff(B.indptr)) == 30          # some rows carry a foreign block
+    assert abs(Ar - B).max() < 1e-13 * abs(B).max()
