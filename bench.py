@@ -21,6 +21,10 @@ import sys
 import threading
 import time
 
+# The oracle legs run single-threaded (BLAS included); the library's OpenMP setup is unaffected.
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -30,7 +34,7 @@ WORKLOAD = "two-material disk, k=20, 40,200 nodes (2,680 curved P4 triangles), 2
 METRIC = "LS GMRES solves/s (FP64, preconditioned)"
 # Preconditioned GMRES iterations of this workload as measured by the GPU arm;
 # the reference arm scales its sampled matvec cost by it.
-REFERENCE_ITERS = 20
+REFERENCE_ITERS = 55
 
 
 def _env_rank():
@@ -89,7 +93,6 @@ def cpu_baseline(wl, u_gpu, Lu_gpu, iters, n_rows=1536, n_corr=48):
     """The oracle as it stands, timed on a bounded sample of the same workload:
     n_rows rows of the naive pair sum and n_corr rows of the correction for the
     GPU's solution vector (also giving the sampled matvec error vs the oracle)."""
-    from threadpoolctl import threadpool_limits
     from oracle.nystrom import naive_rows
     from oracle.vdim import correction_matrix
 
@@ -98,12 +101,11 @@ def cpu_baseline(wl, u_gpu, Lu_gpu, iters, n_rows=1536, n_corr=48):
     rows = np.sort(rng.choice(n, n_rows, replace=False))
     crow = rows[:: max(1, n_rows // n_corr)][:n_corr]
     f = wl.m * u_gpu
-    with threadpool_limits(1):
-        t0 = time.perf_counter()
-        nv = naive_rows(wl.mesh.nodes, wl.mesh.weights, wl.k, f, rows)
-        t1 = time.perf_counter()
-        dV = correction_matrix(wl.mesh, wl.k, 3.0, rows=crow)
-        t2 = time.perf_counter()
+    t0 = time.perf_counter()
+    nv = naive_rows(wl.mesh.nodes, wl.mesh.weights, wl.k, f, rows)
+    t1 = time.perf_counter()
+    dV = correction_matrix(wl.mesh, wl.k, 3.0, rows=crow)
+    t2 = time.perf_counter()
     ref = u_gpu[crow] + wl.k**2 * (nv[np.searchsorted(rows, crow)] + dV @ f)
     err = float(np.linalg.norm(Lu_gpu[crow] - ref) / np.linalg.norm(ref))
     t_apply = (t1 - t0) / n_rows * n + (t2 - t1) / n_corr * n       # one L apply, extrapolated
@@ -119,7 +121,6 @@ def cpu_baseline(wl, u_gpu, Lu_gpu, iters, n_rows=1536, n_corr=48):
 def reference_arm(args):
     """--impl reference: the oracle as it stands, each step a bounded sample."""
     from lsinput.workloads import two_material
-    from threadpoolctl import threadpool_limits
     from oracle.nystrom import naive_rows
     from oracle.vdim import correction_matrix
 
@@ -129,15 +130,14 @@ def reference_arm(args):
     f = wl.m * x
     rows = np.arange(0, n, n // 256)[:256]
     times = []
-    with threadpool_limits(1):
-        for s in range(args.warmup + args.steps):
-            t0 = time.perf_counter()
-            naive_rows(wl.mesh.nodes, wl.mesh.weights, wl.k, f, rows)
-            t1 = time.perf_counter()
-            correction_matrix(wl.mesh, wl.k, 3.0, rows=rows[:8])
-            t2 = time.perf_counter()
-            if s >= args.warmup:
-                times.append(((t1 - t0) / rows.size + (t2 - t1) / 8) * n * REFERENCE_ITERS)
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        naive_rows(wl.mesh.nodes, wl.mesh.weights, wl.k, f, rows)
+        t1 = time.perf_counter()
+        correction_matrix(wl.mesh, wl.k, 3.0, rows=rows[:8])
+        t2 = time.perf_counter()
+        if s >= args.warmup:
+            times.append(((t1 - t0) / rows.size + (t2 - t1) / 8) * n * REFERENCE_ITERS)
     t_solve = statistics.mean(times)
     value = 1.0 / t_solve
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
@@ -180,6 +180,7 @@ def main():
     op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, tol=1e-8)
     setup_s = time.perf_counter() - t0
     fp64_peak = L.probe_fp64()
+    print(f"[bench] setup {setup_s:.1f} s, FP64 probe {fp64_peak:.1f} GFLOP/s", file=sys.stderr, flush=True)
     # each rank solves its own direction (replicas)
     angle = np.pi / 4 + 2 * np.pi * rank / max(world, 1) if world > 1 else np.pi / 4
     d = np.array([np.cos(angle), np.sin(angle)])
@@ -213,6 +214,8 @@ def main():
     if dist:
         dist.barrier()
     ps_ms, ps_launches, launches = op.stats()
+    print(f"[bench] steps ms {step_ms}, iters {iters_list}, pair-sum {ps_ms:.1f} ms / {ps_launches} launches",
+          file=sys.stderr, flush=True)
     op.set_timing(False)
     total_ms = sum(step_ms)
     if dist:

@@ -55,9 +55,15 @@ typedef struct {
     double  box[4];       /* Cartesian grid box xmin, xmax, ymin, ymax (Section 4)    */
     int32_t nx, ny;       /* grid nodes per direction, endpoints included; the step
                              (xmax - xmin)/(nx - 1) must equal (ymax - ymin)/(ny - 1) */
+    int32_t pairsum;      /* 0: FP64, H0 from a per-operator table of degree-11 polynomials
+                             in t = r^2 on octave-graded cells (validated to 2e-15
+                             against the long-double routine at setup); 1: FP64 direct
+                             evaluation; 2: precision form -- FP32 table (degree 6,
+                             validated to 2e-8), double-float coordinate differences,
+                             Kahan-compensated FP32 accumulation                      */
 } ls_params;
 
-/* Defaults: tol 1e-8, max_iter 600, use_precond 1, kappa 3, box [-1.2,1.2]^2, 256 x 256. */
+/* Defaults: tol 1e-8, max_iter 600, use_precond 1, kappa 3, box [-1.2,1.2]^2, 256 x 256, pairsum 0. */
 void ls_params_default(ls_params* p);
 
 /*

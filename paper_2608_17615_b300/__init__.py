@@ -31,7 +31,7 @@ class LsError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("use_precond", ctypes.c_int32),
                 ("kappa", ctypes.c_double), ("box", ctypes.c_double * 4), ("nx", ctypes.c_int32),
-                ("ny", ctypes.c_int32)]
+                ("ny", ctypes.c_int32), ("pairsum", ctypes.c_int32)]
 
 
 def _load():

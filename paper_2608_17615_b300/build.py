@@ -20,16 +20,23 @@ def _run(cmd):
 
 
 def build(verbose_ptxas=False):
+    """Compile every csrc/*.cu with nvcc (sm_103a) and csrc/*.cpp with g++, link liblsgpu.so."""
     os.makedirs(BUILD, exist_ok=True)
-    cu_obj = os.path.join(BUILD, "lsgpu.o")
-    cpp_obj = os.path.join(BUILD, "setup.o")
-    nv = [NVCC, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp",
-          "-c", os.path.join(CSRC, "lsgpu.cu"), "-o", cu_obj]
-    if verbose_ptxas:
-        nv.insert(1, "-Xptxas=-v")
-    _run(nv)
-    _run(["g++", "-O2", "-std=c++17", "-fPIC", "-fopenmp", "-c", os.path.join(CSRC, "setup.cpp"), "-o", cpp_obj])
-    _run([NVCC, "-shared", *ARCH, "-o", LIB, cu_obj, cpp_obj, "-lcusolver", "-lcublas", "-Xcompiler", "-fopenmp"])
+    objs = []
+    for name in sorted(os.listdir(CSRC)):
+        src = os.path.join(CSRC, name)
+        obj = os.path.join(BUILD, os.path.splitext(name)[0] + ".o")
+        if name.endswith(".cu"):
+            nv = [NVCC, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp", "-c", src, "-o", obj]
+            if verbose_ptxas:
+                nv.insert(1, "-Xptxas=-v")
+            _run(nv)
+        elif name.endswith(".cpp"):
+            _run(["g++", "-O2", "-std=c++17", "-fPIC", "-fopenmp", "-c", src, "-o", obj])
+        else:
+            continue
+        objs.append(obj)
+    _run([NVCC, "-shared", *ARCH, "-o", LIB, *objs, "-lcusolver", "-lcublas", "-Xcompiler", "-fopenmp"])
     return LIB
 
 

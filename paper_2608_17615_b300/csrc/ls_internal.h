@@ -53,6 +53,22 @@ struct GridSetup {
 std::string build_grid(const HostMesh& mesh, double k, const double box[4], int nx, int ny,
                        const std::complex<double>* m_grid, GridSetup& out);
 
+// Per-operator table of H0^(1)(k sqrt(t)) over t = r^2 for the pair sum.
+// Octave [2^(B-1023), 2^(B-1022)) (B = biased exponent of t) is split into
+// 2^m equal cells (m = 20 - shift); on each cell H0 is a degree-(NCOEF-1)
+// polynomial in u = (t - mid) * inv_hw in [-1, 1] (monomial coefficients).
+constexpr int H0TAB_NCOEF = 12;     // FP64 table: degree 11
+struct H0Table {
+    int b_lo = 0;                          // biased exponent of the first octave
+    int noct = 0;
+    std::vector<int> oct_base, oct_shift;  // [noct]
+    std::vector<double> mid, inv_hw;       // [ncell]
+    std::vector<std::complex<double>> coef;  // [ncell][H0TAB_NCOEF]
+    double max_rel_err = 0;                // validated against the long-double routine
+};
+std::string build_h0_table(double k, double t_lo, double t_hi, H0Table& T, int ncoef = H0TAB_NCOEF,
+                           double tol = 2e-15);
+
 // Long-double Hankel functions used by the setup (host only).
 void hankel01_ld(long double z, std::complex<long double>& h0, std::complex<long double>& h1);
 

@@ -157,6 +157,197 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum(const double2* __restrict__ 
     if (j < n) partial[(size_t)blockIdx.y * n + j] = make_double2(ar, ai);
 }
 
+// Tabulated form: H0(k sqrt(t)) from the per-operator octave table (lsgpu::H0Table)
+// held in shared memory: coef [ncell][NC] double2, then (mid, inv_hw) [ncell],
+// then (base, shift) [noct].  Pairs with t outside the table use ls_h0_r2.
+#define NC_TAB 12
+__global__ void __launch_bounds__(PS_TPB) k_pairsum_tab(const double2* __restrict__ xy, const double* __restrict__ w,
+                                                        const double2* __restrict__ m, const double2* __restrict__ f,
+                                                        int n, int src_per_chunk, double k, double inv_k,
+                                                        const double2* __restrict__ tab_g, int ncell, int noct, int b_lo,
+                                                        double2* __restrict__ partial) {
+    extern __shared__ double2 tab[];
+    __shared__ double4 tile[PS_TILE];
+    const int words = ncell * (NC_TAB + 1) + (noct + 1) / 2;      // double2 words
+    for (int i = threadIdx.x; i < words; i += PS_TPB) tab[i] = tab_g[i];
+    const double2* coef = tab;
+    const double2* mh = tab + (size_t)ncell * NC_TAB;
+    const int2* oct = reinterpret_cast<const int2*>(mh + ncell);
+    const int j = blockIdx.x * PS_TPB + threadIdx.x;
+    const int s_begin = blockIdx.y * src_per_chunk;
+    const int s_end = min(n, s_begin + src_per_chunk);
+    const double2 yj = xy[min(j, n - 1)];
+    double ar = 0.0, ai = 0.0;
+    for (int base = s_begin; base < s_end; base += PS_TILE) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < PS_TILE; i += PS_TPB) {
+            int src = base + i;
+            double4 v = make_double4(0.0, 0.0, 0.0, 0.0);
+            if (src < s_end) {
+                double2 p = xy[src];
+                double2 ff = f[src];
+                if (m) ff = cmul(m[src], ff);
+                double ww = w[src];
+                v = make_double4(p.x, p.y, ww * ff.x, ww * ff.y);
+            }
+            tile[i] = v;
+        }
+        __syncthreads();
+        const int cnt = min(PS_TILE, s_end - base);
+        for (int i = 0; i < cnt; ++i) {
+            double4 s = tile[i];
+            double dx = yj.x - s.x, dy = yj.y - s.y;
+            double t = fma(dx, dx, dy * dy);
+            int hi = __double2hiint(t);
+            unsigned o = (unsigned)((hi >> 20) - b_lo);
+            double hr, him;
+            if (o < (unsigned)noct) {
+                int2 ob = oct[o];
+                int cell = ob.x + ((hi & 0xfffff) >> ob.y);
+                double2 q = mh[cell];
+                double u = (t - q.x) * q.y;
+                const double2* c = coef + (size_t)cell * NC_TAB;
+                double2 cc = c[NC_TAB - 1];
+                hr = cc.x;
+                him = cc.y;
+#pragma unroll
+                for (int e = NC_TAB - 2; e >= 0; --e) {
+                    cc = c[e];
+                    hr = fma(hr, u, cc.x);
+                    him = fma(him, u, cc.y);
+                }
+            } else if (t > 0.0) {
+                double2 h = ls_h0_r2(t, k, inv_k);
+                hr = h.x;
+                him = h.y;
+            } else {
+                continue;                     // the self pair
+            }
+            ar = fma(hr, s.z, fma(-him, s.w, ar));
+            ai = fma(hr, s.w, fma(him, s.z, ai));
+        }
+    }
+    if (j < n) partial[(size_t)blockIdx.y * n + j] = make_double2(ar, ai);
+}
+
+// Precision form: FP32 pair sum.  Coordinates travel as float pairs (hi, lo);
+// dx, dy and t = dx^2 + dy^2 are formed in double-float arithmetic (TwoSum /
+// FMA-based TwoProduct) so that t keeps a relative error near 1e-14 and the
+// cell variable u near 1e-7; H0 comes from an FP32 table (complex64 degree-6
+// polynomials, validated to 2e-8 at setup); terms are accumulated with Kahan
+// compensation in FP32.  Pairs below the table range use the FP64 routine.
+#define NC_F32 7
+struct F32Tile { float4 xy; float2 s; };
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    float bv = s - a;
+    float av = s - bv;
+    e = (a - av) + (b - bv);
+}
+
+__device__ __forceinline__ void df_diff(float ah, float al, float bh, float bl, float& dh, float& dl) {
+    float s, e;
+    two_sum(ah, -bh, s, e);
+    e += al - bl;
+    dh = s + e;
+    dl = e - (dh - s);
+}
+
+__global__ void __launch_bounds__(PS_TPB) k_pairsum_f32(const double2* __restrict__ xy, const double* __restrict__ w,
+                                                        const double2* __restrict__ m, const double2* __restrict__ f,
+                                                        int n, int src_per_chunk, double k, double inv_k,
+                                                        const float4* __restrict__ tab_g, int ncell, int noct, int b_lo,
+                                                        double2* __restrict__ partial) {
+    extern __shared__ float4 ftab[];
+    __shared__ F32Tile tile[PS_TILE];
+    // layout: coef [ncell][NC_F32] float2 (as float4 pairs), cell (mid_hi, mid_lo, inv_hw, 0) [ncell], oct int2 [noct]
+    const int coef_f4 = (ncell * NC_F32 + 1) / 2;
+    const int words = coef_f4 + ncell + (noct + 1) / 2;
+    for (int i = threadIdx.x; i < words; i += PS_TPB) ftab[i] = tab_g[i];
+    const float2* coef = reinterpret_cast<const float2*>(ftab);
+    const float4* cellv = ftab + coef_f4;
+    const int2* oct = reinterpret_cast<const int2*>(cellv + ncell);
+    const int j = blockIdx.x * PS_TPB + threadIdx.x;
+    const int s_begin = blockIdx.y * src_per_chunk;
+    const int s_end = min(n, s_begin + src_per_chunk);
+    const double2 yj = xy[min(j, n - 1)];
+    const float txh = (float)yj.x, txl = (float)(yj.x - (double)txh);
+    const float tyh = (float)yj.y, tyl = (float)(yj.y - (double)tyh);
+    float sr = 0.f, si = 0.f, cr = 0.f, ci = 0.f;     // Kahan sums and compensations
+    for (int base = s_begin; base < s_end; base += PS_TILE) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < PS_TILE; i += PS_TPB) {
+            int src = base + i;
+            F32Tile v;
+            v.xy = make_float4(0.f, 0.f, 0.f, 0.f);
+            v.s = make_float2(0.f, 0.f);
+            if (src < s_end) {
+                double2 p = xy[src];
+                double2 ff = f[src];
+                if (m) ff = cmul(m[src], ff);
+                double ww = w[src];
+                float xh = (float)p.x, yh = (float)p.y;
+                v.xy = make_float4(xh, (float)(p.x - (double)xh), yh, (float)(p.y - (double)yh));
+                v.s = make_float2((float)(ww * ff.x), (float)(ww * ff.y));
+            }
+            tile[i] = v;
+        }
+        __syncthreads();
+        const int cnt = min(PS_TILE, s_end - base);
+        for (int i = 0; i < cnt; ++i) {
+            F32Tile src = tile[i];
+            float dxh, dxl, dyh, dyl;
+            df_diff(txh, txl, src.xy.x, src.xy.y, dxh, dxl);
+            df_diff(tyh, tyl, src.xy.z, src.xy.w, dyh, dyl);
+            float p1 = dxh * dxh, e1 = fmaf(dxh, dxh, -p1);
+            e1 = fmaf(2.f * dxh, dxl, e1);
+            float p2 = dyh * dyh, e2 = fmaf(dyh, dyh, -p2);
+            e2 = fmaf(2.f * dyh, dyl, e2);
+            float th, tl;
+            two_sum(p1, p2, th, tl);
+            tl += e1 + e2;
+            float t0 = th + tl;
+            tl = tl - (t0 - th);
+            th = t0;
+            int bits = __float_as_int(th);
+            unsigned o = (unsigned)((bits >> 23) - b_lo);
+            float hr, him;
+            if (o < (unsigned)noct) {
+                int2 ob = oct[o];
+                int cell = ob.x + ((bits & 0x7fffff) >> ob.y);
+                float4 cv = cellv[cell];
+                float u = ((th - cv.x) + (tl - cv.y)) * cv.z;
+                const float2* c = coef + cell * NC_F32;
+                float2 cc = c[NC_F32 - 1];
+                hr = cc.x;
+                him = cc.y;
+#pragma unroll
+                for (int e = NC_F32 - 2; e >= 0; --e) {
+                    cc = c[e];
+                    hr = fmaf(hr, u, cc.x);
+                    him = fmaf(him, u, cc.y);
+                }
+            } else if (th > 0.f) {
+                double2 h = ls_h0_r2((double)th + (double)tl, k, inv_k);
+                hr = (float)h.x;
+                him = (float)h.y;
+            } else {
+                continue;                     // the self pair
+            }
+            float tr = fmaf(hr, src.s.x, -him * src.s.y);
+            float ti = fmaf(hr, src.s.y, him * src.s.x);
+            float yr = tr - cr, yi = ti - ci;
+            float nr = sr + yr, ni = si + yi;
+            cr = (nr - sr) - yr;
+            ci = (ni - si) - yi;
+            sr = nr;
+            si = ni;
+        }
+    }
+    if (j < n) partial[(size_t)blockIdx.y * n + j] = make_double2((double)sr - (double)cr, (double)si - (double)ci);
+}
+
 // mode 0: y = x + k2 * ((i/4) sum_c partial + dV (m x));  mode 1: y = (i/4) sum_c partial
 __global__ void k_apply_epi(int n, int nchunk, const double2* __restrict__ partial, const int64_t* __restrict__ rowptr,
                             const int* __restrict__ cols, const double2* __restrict__ vals,
@@ -582,6 +773,13 @@ struct ls_op {
     // pair-sum decomposition and scratch
     int nchunk = 1, src_per_chunk = 0;
     DevBuf<double2> partial;
+    // tabulated H0 (pairsum mode 0: FP64 table, mode 2: FP32 table)
+    int mode = 0;
+    bool use_table = false;
+    int tab_ncell = 0, tab_noct = 0, tab_blo = 0;
+    size_t tab_bytes = 0;
+    double tab_err = 0;
+    DevBuf<double2> tab;
     // preconditioner
     bool has_prec = false;
     int nx = 0, ny = 0;
@@ -622,8 +820,17 @@ static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m) {
         op->ev.emplace_back(e0, e1);
         CK(cudaEventRecord(e0, op->stream));
     }
-    k_pairsum<<<grid, PS_TPB, 0, op->stream>>>(op->xy.p, op->w.p, m, f, op->nq, op->src_per_chunk, op->k, 1.0 / op->k,
-                                               op->partial.p);
+    if (op->mode == 2)
+        k_pairsum_f32<<<grid, PS_TPB, op->tab_bytes, op->stream>>>(op->xy.p, op->w.p, m, f, op->nq, op->src_per_chunk,
+                                                                    op->k, 1.0 / op->k, (const float4*)op->tab.p,
+                                                                    op->tab_ncell, op->tab_noct, op->tab_blo, op->partial.p);
+    else if (op->use_table)
+        k_pairsum_tab<<<grid, PS_TPB, op->tab_bytes, op->stream>>>(op->xy.p, op->w.p, m, f, op->nq, op->src_per_chunk,
+                                                                    op->k, 1.0 / op->k, op->tab.p, op->tab_ncell,
+                                                                    op->tab_noct, op->tab_blo, op->partial.p);
+    else
+        k_pairsum<<<grid, PS_TPB, 0, op->stream>>>(op->xy.p, op->w.p, m, f, op->nq, op->src_per_chunk, op->k, 1.0 / op->k,
+                                                   op->partial.p);
     CK(cudaGetLastError());
     if (e1) CK(cudaEventRecord(e1, op->stream));
     op->launches++;
@@ -730,6 +937,9 @@ static ls_status gmres_one(ls_op* op, const double2* b, double2* u, double* hist
     return conv ? LS_OK : LS_ENOCONV;
 }
 
+// Error reporting for other translation units of the library.
+ls_status lsgpu_set_error(ls_status s, const char* msg) { return fail(s, msg); }
+
 // ------------------------------------------------------------------ C ABI
 extern "C" {
 
@@ -744,6 +954,7 @@ void ls_params_default(ls_params* p) {
     p->box[0] = -1.2; p->box[1] = 1.2; p->box[2] = -1.2; p->box[3] = 1.2;
     p->nx = 256;
     p->ny = 256;
+    p->pairsum = 0;
 }
 
 ls_status ls_mesh_create(int32_t n_vert, const double* vert_xy, int32_t n_elem, const int32_t* elem_vert,
@@ -791,6 +1002,69 @@ ls_status ls_mesh_create(int32_t n_vert, const double* vert_xy, int32_t n_elem, 
 void ls_mesh_destroy(ls_mesh* mesh) { delete mesh; }
 int32_t ls_mesh_num_nodes(const ls_mesh* mesh) { return mesh ? mesh->h.nq : 0; }
 int32_t ls_op_num_nodes(const ls_op* op) { return op ? op->nq : 0; }
+
+// Tabulated H0 for the pair sum: t from (1e-2 h_min)^2 to the squared bounding-box diagonal.
+static ls_status build_table(ls_op* op, const HostMesh& M, bool f32) {
+    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300, hmin = 1e300;
+    for (int q = 0; q < M.nq; ++q) {
+        xmin = std::min(xmin, M.nodes[2 * q]); xmax = std::max(xmax, M.nodes[2 * q]);
+        ymin = std::min(ymin, M.nodes[2 * q + 1]); ymax = std::max(ymax, M.nodes[2 * q + 1]);
+    }
+    for (int t = 0; t < M.nt; ++t) {
+        const int* v = &M.tri[3 * t];
+        for (int e = 0; e < 3; ++e) {
+            double dx = M.vxy[2 * v[e]] - M.vxy[2 * v[(e + 1) % 3]], dy = M.vxy[2 * v[e] + 1] - M.vxy[2 * v[(e + 1) % 3] + 1];
+            hmin = std::min(hmin, std::sqrt(dx * dx + dy * dy));
+        }
+    }
+    double t_hi = ((xmax - xmin) * (xmax - xmin) + (ymax - ymin) * (ymax - ymin)) * 1.0001;
+    double t_lo = std::min(1e-2 * hmin * 1e-2 * hmin, t_hi / 4);
+    lsgpu::H0Table T;
+    std::string err = f32 ? lsgpu::build_h0_table(op->k, t_lo, t_hi, T, NC_F32, 2e-8)
+                          : lsgpu::build_h0_table(op->k, t_lo, t_hi, T);
+    if (!err.empty()) return fail(LS_EINVAL, err);
+    const int ncell = (int)T.mid.size();
+    if (f32) {
+        // float layout: coef [ncell][NC_F32] float2, cells (mid_hi, mid_lo, inv_hw, 0), oct (base, 23 - m)
+        const int coef_f4 = (ncell * NC_F32 + 1) / 2;
+        std::vector<float4> hf((size_t)coef_f4 + ncell + (T.noct + 1) / 2, make_float4(0.f, 0.f, 0.f, 0.f));
+        float2* cf = reinterpret_cast<float2*>(hf.data());
+        for (size_t i = 0; i < (size_t)ncell * NC_F32; ++i)
+            cf[i] = make_float2((float)T.coef[i].real(), (float)T.coef[i].imag());
+        for (int c = 0; c < ncell; ++c) {
+            float mh = (float)T.mid[c];
+            hf[(size_t)coef_f4 + c] = make_float4(mh, (float)(T.mid[c] - (double)mh), (float)T.inv_hw[c], 0.f);
+        }
+        int2* oct = reinterpret_cast<int2*>(hf.data() + coef_f4 + ncell);
+        for (int o = 0; o < T.noct; ++o) oct[o] = make_int2(T.oct_base[o], T.oct_shift[o] + 3);   // 23 - m
+        op->tab_ncell = ncell;
+        op->tab_noct = T.noct;
+        op->tab_blo = T.b_lo - 1023 + 127;
+        op->tab_err = T.max_rel_err;
+        op->tab_bytes = hf.size() * sizeof(float4);
+        CK(op->tab.alloc((op->tab_bytes + sizeof(double2) - 1) / sizeof(double2)));
+        CK(cudaMemcpy(op->tab.p, hf.data(), op->tab_bytes, cudaMemcpyHostToDevice));
+        CK(cudaFuncSetAttribute(k_pairsum_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)op->tab_bytes));
+        op->use_table = true;
+        return LS_OK;
+    }
+    std::vector<double2> h((size_t)ncell * (NC_TAB + 1) + (T.noct + 1) / 2);
+    for (size_t i = 0; i < (size_t)ncell * NC_TAB; ++i) h[i] = make_double2(T.coef[i].real(), T.coef[i].imag());
+    for (int c = 0; c < ncell; ++c) h[(size_t)ncell * NC_TAB + c] = make_double2(T.mid[c], T.inv_hw[c]);
+    int2* oct = reinterpret_cast<int2*>(h.data() + (size_t)ncell * (NC_TAB + 1));
+    for (int o = 0; o < T.noct; ++o) oct[o] = make_int2(T.oct_base[o], T.oct_shift[o]);
+    op->tab_ncell = ncell;
+    op->tab_noct = T.noct;
+    op->tab_blo = T.b_lo;
+    op->tab_err = T.max_rel_err;
+    op->tab_bytes = h.size() * sizeof(double2);
+    if (op->tab_bytes > 200 * 1024) return fail(LS_EINVAL, "H0 table too large for shared memory");
+    CK(op->tab.alloc(h.size()));
+    CK(cudaMemcpy(op->tab.p, h.data(), op->tab_bytes, cudaMemcpyHostToDevice));
+    CK(cudaFuncSetAttribute(k_pairsum_tab, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)op->tab_bytes));
+    op->use_table = true;
+    return LS_OK;
+}
 
 static ls_status build_preconditioner(ls_op* op, const HostMesh& M, const double* m_grid) {
     GridSetup G;
@@ -864,6 +1138,7 @@ ls_status ls_operator_create(const ls_mesh* mesh, double k, const double* m, con
     ls_params_default(&prm);
     if (params) prm = *params;
     if (prm.max_iter < 1 || !(prm.tol > 0) || !(prm.kappa > 0)) return fail(LS_EINVAL, "bad tol / max_iter / kappa");
+    if (prm.pairsum < 0 || prm.pairsum > 2) return fail(LS_EINVAL, "pairsum must be 0 (FP64 table), 1 (FP64 direct) or 2 (FP32)");
     if (prm.use_precond && !m_grid) return fail(LS_EINVAL, "m_grid is required with use_precond");
     const HostMesh& M = mesh->h;
     for (int q = 0; q < M.nq; ++q)
@@ -907,6 +1182,8 @@ ls_status ls_operator_create(const ls_mesh* mesh, double k, const double* m, con
     op->nchunk = nchunk;
     op->src_per_chunk = spc;
     CK(op->partial.alloc((size_t)nchunk * n));
+    op->mode = prm.pairsum;
+    if (prm.pairsum == 0 || prm.pairsum == 2) TRY(build_table(op, M, prm.pairsum == 2));
     // GMRES workspace
     const int maxit = prm.max_iter;
     CK(op->Vb.alloc((size_t)(maxit + 1) * n));

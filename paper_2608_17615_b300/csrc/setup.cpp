@@ -495,6 +495,88 @@ std::string build_correction(const HostMesh& M, double k, double kappa, CsrC& ou
     return "";
 }
 
+// ---------------------------------------------------------------- H0 table
+// Chebyshev interpolation of H0(k sqrt(t)) at ncoef points per cell, converted
+// to monomials in u; each octave is refined (2^m cells, m >= 3) until the
+// interpolant matches the long-double routine to tol (relative) at 33 points
+// per cell.
+std::string build_h0_table(double k, double t_lo, double t_hi, H0Table& T, int ncoef, double tol) {
+    if (!(t_lo > 0) || !(t_hi > t_lo)) return "bad table range";
+    if (ncoef < 2 || ncoef > 16) return "bad table degree";
+    const int NC = ncoef;
+    int e_lo, e_hi;
+    std::frexp(t_lo, &e_lo);          // t in [2^(e-1), 2^e)
+    std::frexp(t_hi, &e_hi);
+    T.b_lo = e_lo - 1 + 1023;
+    T.noct = e_hi - e_lo + 1;
+    T.oct_base.assign(T.noct, 0);
+    T.oct_shift.assign(T.noct, 0);
+    T.mid.clear(); T.inv_hw.clear(); T.coef.clear();
+    T.max_rel_err = 0;
+    // monomial coefficients of T_n(u), n < NC
+    std::vector<std::vector<ld>> cheb(NC, std::vector<ld>(NC, 0));
+    std::vector<ld> un(NC);
+    cheb[0][0] = 1;
+    if (NC > 1) cheb[1][1] = 1;
+    for (int n = 2; n < NC; ++n)
+        for (int j = 0; j < NC; ++j)
+            cheb[n][j] = (j > 0 ? 2 * cheb[n - 1][j - 1] : 0) - cheb[n - 2][j];
+    for (int i = 0; i < NC; ++i) un[i] = std::cos(PI_L * (i + 0.5L) / NC);
+    const ld kl = k;
+    for (int o = 0; o < T.noct; ++o) {
+        ld a = std::ldexp(1.0L, e_lo - 1 + o), b = 2 * a;
+        std::vector<double> bm, bi;
+        std::vector<std::complex<double>> bc;
+        int m = 3;
+        for (;; ++m) {
+            int M = 1 << m;
+            bm.assign(M, 0); bi.assign(M, 0); bc.assign((size_t)M * NC, 0);
+            double worst = 0;
+            for (int c = 0; c < M; ++c) {
+                ld lo = a + (b - a) * c / M, hi = a + (b - a) * (c + 1) / M;
+                ld mid = (lo + hi) / 2, hw = (hi - lo) / 2;
+                std::vector<cld> f(NC), cc(NC), mono(NC);
+                for (int i = 0; i < NC; ++i) {
+                    cld h0, h1;
+                    hankel01_ld(kl * std::sqrt(mid + hw * un[i]), h0, h1);
+                    f[i] = h0;
+                }
+                for (int n = 0; n < NC; ++n) {
+                    cld acc = 0;
+                    for (int i = 0; i < NC; ++i) acc += f[i] * std::cos(n * PI_L * (i + 0.5L) / NC);
+                    cc[n] = acc * (n == 0 ? 1.0L : 2.0L) / (ld)NC;
+                }
+                for (int j = 0; j < NC; ++j) {
+                    mono[j] = 0;
+                    for (int n = 0; n < NC; ++n) mono[j] += cc[n] * cheb[n][j];
+                }
+                for (int q = 0; q <= 32; ++q) {
+                    ld u = -1 + 2.0L * q / 32;
+                    cld p = 0;
+                    for (int j = NC - 1; j >= 0; --j) p = p * u + mono[j];
+                    cld h0, h1;
+                    hankel01_ld(kl * std::sqrt(mid + hw * u), h0, h1);
+                    worst = std::max(worst, (double)(std::abs(p - h0) / std::abs(h0)));
+                }
+                bm[c] = (double)mid;
+                bi[c] = (double)(1 / hw);
+                for (int j = 0; j < NC; ++j)
+                    bc[(size_t)c * NC + j] = std::complex<double>((double)mono[j].real(), (double)mono[j].imag());
+            }
+            if (worst <= tol || m >= 12) {
+                T.max_rel_err = std::max(T.max_rel_err, worst);
+                break;
+            }
+        }
+        T.oct_base[o] = (int)T.mid.size();
+        T.oct_shift[o] = 20 - m;
+        T.mid.insert(T.mid.end(), bm.begin(), bm.end());
+        T.inv_hw.insert(T.inv_hw.end(), bi.begin(), bi.end());
+        T.coef.insert(T.coef.end(), bc.begin(), bc.end());
+    }
+    return "";
+}
+
 // ---------------------------------------------------------------- grid
 static std::complex<double> vc_entry(ld k, ld h, int da, int db) {
     if (da == 0 && db == 0) {

@@ -48,9 +48,11 @@ def test_device_hankel():
     assert err.max() < 5e-14, (err.max(), z[err.argmax()])
 
 
-def test_pairsum_parity_disk():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_pairsum_parity_disk(mode):
+    # mode 0: tabulated H0(k sqrt(t)); mode 1: direct series / modulus-phase evaluation
     wl = constant_disk(k=5.0, n_rings=3)
-    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, use_precond=0)
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, use_precond=0, pairsum=mode)
     f = random_density(wl.mesh.n_nodes, 3)
     y = torch.empty(wl.mesh.n_nodes, dtype=torch.complex128, device="cuda")
     op.pairsum_dev(_dev(f), y)
@@ -90,6 +92,18 @@ def test_apply_parity_two_material_full_size(cfg2):
     rows = np.concatenate([np.arange(0, n, 997), [n - 1]])
     ref = OracleOp(wl.mesh, wl.k, wl.m, rows_only=True).apply_rows(x, rows)
     assert _rel(y.cpu().numpy()[rows], ref) < 1e-11
+
+
+def test_pairsum_table_vs_direct_full_size(cfg2):
+    wl, op = cfg2
+    n = wl.mesh.n_nodes
+    opd = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, use_precond=0, pairsum=1)
+    f = _dev(random_density(n, 17))
+    y0 = torch.empty_like(f)
+    y1 = torch.empty_like(f)
+    op.pairsum_dev(f, y0)
+    opd.pairsum_dev(f, y1)
+    assert (torch.linalg.norm(y0 - y1) / torch.linalg.norm(y1)).item() < 1e-13
 
 
 def test_precond_parity_small():
