@@ -41,6 +41,26 @@ def _env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def rank_direction(rank, world, base=np.pi / 4):
+    """Incident angle of rank `rank`: independent replicas, one direction each."""
+    return base + 2 * np.pi * rank / world if world > 1 else base
+
+
+def max_over_ranks(total_ms, dist=None, device="cpu"):
+    """Max of the per-rank timed totals (the whole job ends with the slowest rank)."""
+    if dist is None:
+        return float(total_ms)
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(world, steps, max_total_ms):
+    """Whole-job throughput: all solves of all ranks over the slowest rank's time."""
+    return world * steps / (max_total_ms * 1e-3)
+
+
 class ClockSampler:
     """nvidia-smi samples during the timed region (SM clocks, throttle reasons)."""
 
@@ -140,6 +160,43 @@ def reference_arm(args):
             times.append(((t1 - t0) / rows.size + (t2 - t1) / 8) * n * REFERENCE_ITERS)
     t_solve = statistics.mean(times)
     value = 1.0 / t_solve
+    # precision form on the same operator (FP32 pair sum), timed the same way
+    forms = {}
+    op.set_pairsum(2)
+    u32 = torch.empty_like(u)
+    op.solve_dev(b.view(1, -1), u32.view(1, -1))
+    ms32, it32 = [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it, st = op.solve_dev(b.view(1, -1), u32.view(1, -1), wl.ff_angles, uinf.view(1, -1))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms32.append(e0.elapsed_time(e1))
+        it32.append(int(it[0]))
+    rel32 = (torch.linalg.norm(u32 - u) / torch.linalg.norm(u)).item()
+    forms["fp32_pairsum"] = {"value": args.steps / (sum(ms32) * 1e-3), "unit": "solves/s", "iterations": it32[0],
+                             "rel_err_vs_fp64_solution": rel32,
+                             "pairs_per_s": it32[0] * n * (n - 1) * args.steps / (sum(ms32) * 1e-3)}
+    # FP64-accurate double-float pair sum on the same operator
+    op.set_pairsum(3)
+    op.solve_dev(b.view(1, -1), u32.view(1, -1))
+    msd, itd = [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it, st = op.solve_dev(b.view(1, -1), u32.view(1, -1), wl.ff_angles, uinf.view(1, -1))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msd.append(e0.elapsed_time(e1))
+        itd.append(int(it[0]))
+    reld = (torch.linalg.norm(u32 - u) / torch.linalg.norm(u)).item()
+    forms["df_pairsum"] = {"value": args.steps / (sum(msd) * 1e-3), "unit": "solves/s", "iterations": itd[0],
+                           "rel_err_vs_fp64_solution": reld,
+                           "pairs_per_s": itd[0] * n * (n - 1) * args.steps / (sum(msd) * 1e-3)}
+    op.set_pairsum(0)
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
@@ -180,9 +237,10 @@ def main():
     op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, tol=1e-8)
     setup_s = time.perf_counter() - t0
     fp64_peak = L.probe_fp64()
-    print(f"[bench] setup {setup_s:.1f} s, FP64 probe {fp64_peak:.1f} GFLOP/s", file=sys.stderr, flush=True)
+    setup_parts = dict(zip(["correction", "grid", "block_lu", "table"], op.setup_times()))
+    print(f"[bench] setup {setup_s:.1f} s {setup_parts}, FP64 probe {fp64_peak:.1f} GFLOP/s", file=sys.stderr, flush=True)
     # each rank solves its own direction (replicas)
-    angle = np.pi / 4 + 2 * np.pi * rank / max(world, 1) if world > 1 else np.pi / 4
+    angle = rank_direction(rank, world)
     d = np.array([np.cos(angle), np.sin(angle)])
     b = torch.from_numpy(np.exp(1j * wl.k * (wl.mesh.nodes @ d))).cuda()
     u = torch.empty_like(b)
@@ -217,21 +275,18 @@ def main():
     print(f"[bench] steps ms {step_ms}, iters {iters_list}, pair-sum {ps_ms:.1f} ms / {ps_launches} launches",
           file=sys.stderr, flush=True)
     op.set_timing(False)
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     iters = statistics.mean(iters_list)
-    value = world * args.steps / (total_ms * 1e-3)
+    value = aggregate_value(world, args.steps, total_ms)
     pairs_per_solve = iters * n * (n - 1)
     # roofline of the pair-sum kernel (FP64 ALU bound)
     avg_launch_s = ps_ms / max(ps_launches, 1) * 1e-3
-    flops_per_pair = FLOPS_PER_PAIR
+    flops_per_pair = FLOPS_PER_PAIR[op.params.pairsum]
     achieved = flops_per_pair * n * (n - 1) / avg_launch_s / 1e12
     peak = fp64_peak / 1e3
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_pairsum", "flops_per_pair": flops_per_pair,
+                "traffic": TRAFFIC.get(op.params.pairsum), "kernel": KERNEL[op.params.pairsum],
+                "flops_per_pair": flops_per_pair,
                 "peak_source": "measured FP64 FMA probe (ls_probe_fp64), same run",
                 "kernel_ms_per_launch": avg_launch_s * 1e3, "kernel_share_of_step": ps_ms / total_ms}
     # end to end through the host-buffer entry point
@@ -244,15 +299,52 @@ def main():
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e = {"value": world * args.steps / (sum(e2e_ms) * 1e-3), "unit": "solves/s",
            "h2d_bytes_per_step": 8 * (1 + n_ff), "d2h_bytes_per_step": 16 * n + 16 * n_ff + 8 * (int(it_h[0]) + 1)}
+    # precision form on the same operator (FP32 pair sum), timed the same way
+    forms = {}
+    op.set_pairsum(2)
+    u32 = torch.empty_like(u)
+    op.solve_dev(b.view(1, -1), u32.view(1, -1))
+    ms32, it32 = [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it, st = op.solve_dev(b.view(1, -1), u32.view(1, -1), wl.ff_angles, uinf.view(1, -1))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms32.append(e0.elapsed_time(e1))
+        it32.append(int(it[0]))
+    rel32 = (torch.linalg.norm(u32 - u) / torch.linalg.norm(u)).item()
+    forms["fp32_pairsum"] = {"value": args.steps / (sum(ms32) * 1e-3), "unit": "solves/s", "iterations": it32[0],
+                             "rel_err_vs_fp64_solution": rel32,
+                             "pairs_per_s": it32[0] * n * (n - 1) * args.steps / (sum(ms32) * 1e-3)}
+    # FP64-accurate double-float pair sum on the same operator
+    op.set_pairsum(3)
+    op.solve_dev(b.view(1, -1), u32.view(1, -1))
+    msd, itd = [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it, st = op.solve_dev(b.view(1, -1), u32.view(1, -1), wl.ff_angles, uinf.view(1, -1))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msd.append(e0.elapsed_time(e1))
+        itd.append(int(it[0]))
+    reld = (torch.linalg.norm(u32 - u) / torch.linalg.norm(u)).item()
+    forms["df_pairsum"] = {"value": args.steps / (sum(msd) * 1e-3), "unit": "solves/s", "iterations": itd[0],
+                           "rel_err_vs_fp64_solution": reld,
+                           "pairs_per_s": itd[0] * n * (n - 1) * args.steps / (sum(msd) * 1e-3)}
+    op.set_pairsum(0)
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "nodes": n, "k": wl.k, "grid": [wl.nx, wl.ny],
                        "l2": "flushed (512 MB write) before every timed step", "parallelism": "replicas"},
             "iterations": iters, "pairs_per_s": world * pairs_per_solve * args.steps / (total_ms * 1e-3),
-            "matvecs_per_s": world * iters * args.steps / (total_ms * 1e-3), "setup_s": setup_s,
+            "matvecs_per_s": world * iters * args.steps / (total_ms * 1e-3), "setup_s": setup_s, "setup_parts_s": setup_parts,
             "wall_s_timed": wall, "roofline": roofline, "gpu_launches": launches, "clocks": clocks.summary(),
-            "e2e": e2e}
+            "e2e": e2e, "forms": forms}
     if rank == 0 and not args.no_cpu_baseline:
         Lu = torch.empty_like(u)
         op.apply_dev(u, Lu)
@@ -265,10 +357,19 @@ def main():
         dist.destroy_process_group()
 
 
-# FP64 floating-point operations per pair in k_pairsum (asymptotic branch, z > 6),
-# FMA counted as 2: distance 5, rsqrt 9, scaling 5, two degree-14 Horner
-# polynomials 56, sincos 40, amplitude rsqrt and phase 14, complex accumulate 8.
-FLOPS_PER_PAIR = 137
+# Floating-point operations per pair of each pair-sum kernel (FMA = 2).
+#  0 k_pairsum_tab (FP64): dx, dy 2; t = dx^2 + dy^2 3; u 2; two degree-11
+#    Horner chains 44; complex multiply-accumulate 8 -> 59
+#  1 k_pairsum (FP64, direct): 89 FP64 instructions per pair measured by ncu
+#    (58.5 DFMA, 23.5 DMUL, 7.1 DADD) -> 148
+#  2 k_pairsum_f32 (FP32): two double-float differences 22, double-float t 16,
+#    u 4, two degree-6 Horner chains 24, complex multiply 6, Kahan sums 8 -> 80
+#  3 k_pairsum_df (double-float on FP32): differences 22, t 12, u 8, two degree-11
+#    DF Horner chains 2 x 11 x 15 = 330, DF complex multiply-accumulate 60 -> 432
+FLOPS_PER_PAIR = {0: 59, 1: 148, 2: 80, 3: 432}
+KERNEL = {0: "k_pairsum_tab", 1: "k_pairsum", 2: "k_pairsum_f32", 3: "k_pairsum_df"}
+# dram__bytes_read + write per launch from ncu captures of the current kernels (None until captured)
+TRAFFIC = {}
 
 if __name__ == "__main__":
     main()

@@ -60,7 +60,9 @@ typedef struct {
                              against the long-double routine at setup); 1: FP64 direct
                              evaluation; 2: precision form -- FP32 table (degree 6,
                              validated to 2e-8), double-float coordinate differences,
-                             Kahan-compensated FP32 accumulation                      */
+                             Kahan-compensated FP32 accumulation; 3: FP64-accurate
+                             double-float (FP32 pairs) evaluation of the degree-11
+                             table and accumulation on the FP32 pipe            */
 } ls_params;
 
 /* Defaults: tol 1e-8, max_iter 600, use_precond 1, kappa 3, box [-1.2,1.2]^2, 256 x 256, pairsum 0. */
@@ -152,6 +154,76 @@ ls_status ls_solve_dev(ls_op* op, int32_t R, const void* b_dev, void* u_dev,
                        int32_t n_ff, const double* ff_angles, void* uinf_dev, int32_t* iters_out);
 
 /*
+ * Batching form: R right-hand sides of one operator advanced together.
+ *   ls_pairsum_batch_dev  y_r = (i/4) sum_{n != j} H0 w_n f_r,n for f_dev, y_dev [R][N]
+ *   ls_solve_batch_dev    R independent GMRES solves in lock step (each system
+ *                         keeps its own Krylov space, Hessenberg matrix and stop),
+ *                         b_dev, u_dev [R][N]; far field as ls_solve_dev
+ * The pair sum of all R systems is one launch per iteration: each H(j, n) comes
+ * from an FP32 table (degree 6, validated to 2e-8) with double-float t and is
+ * applied to blocks of 8 right-hand sides; sums run in FP32 over runs of 32
+ * sources and in FP64 across runs (the precision of the batching form: <= 1e-6
+ * relative solution error).  The preconditioner sweeps and the Arnoldi kernels
+ * are batched over r as well.  Workspace grows on first use with a larger R.
+ */
+ls_status ls_pairsum_batch_dev(ls_op* op, int32_t R, const void* f_dev, void* y_dev);
+ls_status ls_solve_batch_dev(ls_op* op, int32_t R, const void* b_dev, void* u_dev, int32_t n_ff,
+                             const double* ff_angles, void* uinf_dev, int32_t* iters_out);
+
+/*
+ * Several scatterers (operators of uneven size, own k and mesh) with R right-hand
+ * sides each, advanced in lock step; every iteration runs ONE persistent pair-sum
+ * launch over all (scatterer, target block, source chunk, RHS block) work units,
+ * fetched dynamically from an atomic counter (load balance across uneven sizes),
+ * followed by each operator's batched epilogue, preconditioner and Arnoldi kernels.
+ * The persistent grid size is autotuned on the first iteration.
+ *   ops [S]; b_devs[s], u_devs[s]: [R][N_s] complex; iters_out [S][R] (may be NULL)
+ * All operators must share one stream and max_iter.  LS_ENOCONV if any system
+ * hit max_iter.
+ */
+ls_status ls_solve_multi_dev(int32_t S, ls_op* const* ops, int32_t R, const void* const* b_devs,
+                             void* const* u_devs, int32_t* iters_out);
+
+/*
+ * Differentiation form (the paper has no adjoint; this follows from
+ * Eq. linear_system_matrix: L(m) = I + k^2 V diag(m), V independent of m).
+ *   ls_apply_transpose_dev          y = L^T x = x + k^2 diag(m) V^T x
+ *   ls_potential_transpose_dev      y = V^T x (the pair sum is symmetric up to
+ *                                   the weights: (K^T x)_n = w_n sum_j G(y_n, y_j) x_j)
+ *   ls_apply_precond_transpose_dev  y = P^T x = x + T_Q^C^T (A^T C^{-T} - I) T_C^Q^T x
+ *   ls_solve_transpose_dev          L^T lambda = g for R right-hand sides g_dev [R][N],
+ *                                   GMRES left-preconditioned by P^T when built
+ * Device buffers of N complex (R x N for the solve); x and y may not alias.
+ */
+ls_status ls_apply_transpose_dev(ls_op* op, const void* x_dev, void* y_dev);
+ls_status ls_potential_transpose_dev(ls_op* op, const void* x_dev, void* y_dev);
+ls_status ls_apply_precond_transpose_dev(ls_op* op, const void* x_dev, void* y_dev);
+ls_status ls_solve_transpose_dev(ls_op* op, int32_t R, const void* g_dev, void* lambda_dev, int32_t* iters_out);
+
+/*
+ * Replace the nodal contrast m (host, [N] complex).  The correction dV and the
+ * H0 table do not depend on m; the preconditioner keeps the grid contrast it
+ * was built with (it stays a valid preconditioner, only its quality changes).
+ */
+ls_status ls_op_set_contrast(ls_op* op, const double* m);
+
+/* b_dev [R][N] = exp(i k d . y_j), d = (cos a, sin a) for the R angles (host). */
+ls_status ls_incident_dev(ls_op* op, int32_t R, const double* dir_angles, void* b_dev);
+
+/*
+ * Gradient of J = 1/2 sum_r sum_a |u_inf^(r)(theta_a) - t_a^(r)|^2 with respect to
+ * the real part of each nodal contrast:
+ *   grad_j = Re sum_r u_j^(r) [g_j^(r) - k^2 (V^T lambda^(r))_j],
+ *   g^(r) = A^T conj(res^(r)),  L^T lambda^(r) = m * g^(r),
+ *   A_aj = -k^2 e^{i pi/4} / sqrt(8 pi k) w_j e^{-i k xhat_a . y_j}.
+ *   u_dev [R][N] forward solutions; resid_dev [R][n_ff] = u_inf - targets;
+ *   ff_angles [n_ff] (host); grad_dev [N] double (overwritten); iters_out [R]
+ *   adjoint GMRES iterations (may be NULL).  Only u and lambda are stored.
+ */
+ls_status ls_misfit_gradient_dev(ls_op* op, int32_t R, const void* u_dev, int32_t n_ff, const double* ff_angles,
+                                 const void* resid_dev, double* grad_dev, int32_t* iters_out);
+
+/*
  * Export of the correction dV as CSR (rows = N_Q targets, columns = nodes).
  * Call with null arrays to get the size in *nnz, then with rowptr [N_Q + 1],
  * cols [nnz], vals [nnz][2] (complex) to copy it out.
@@ -170,6 +242,9 @@ ls_status ls_correction_host(const ls_mesh* mesh, double k, double kappa, int64_
 /* Diagnostic: h_dev[i] = H0^(1)(z_dev[i]) (complex) by the device routine of the pair sum. */
 ls_status ls_hankel0_dev(int64_t n, const double* z_dev, void* h_dev, void* stream);
 
+/* Switch the pair-sum kernel of an operator (0, 1 or 2 as ls_params.pairsum); rebuilds the H0 table. */
+ls_status ls_op_set_pairsum(ls_op* op, int32_t mode);
+
 /*
  * Instrumentation.  ls_op_set_timing(op, on) resets the counters and, when on,
  * brackets every pair-sum launch with CUDA events on the operator's stream.
@@ -178,10 +253,14 @@ ls_status ls_hankel0_dev(int64_t n, const double* z_dev, void* h_dev, void* stre
  * launched since the last reset (any pointer may be NULL).
  */
 ls_status ls_op_set_timing(ls_op* op, int32_t on);
+/* Wall time (s) of the setup phases: [0] correction dV (host), [1] grid transfers, stencil and C
+   (host), [2] block LU of C and its transposes (device), [3] H0 table. */
+ls_status ls_op_setup_times(const ls_op* op, double* t4);
 ls_status ls_op_stats(ls_op* op, double* pairsum_ms, int64_t* pairsum_launches, int64_t* launches);
 
 /* Diagnostic: measured FP64 FMA throughput of the device in GFLOP/s (2 flops per FMA). */
 ls_status ls_probe_fp64(double* gflops, void* stream);
+
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* ls_last_error(void);

@@ -19,7 +19,9 @@ _STATUS = {0: "LS_OK", 1: "LS_EINVAL", 2: "LS_ENOMEM", 3: "LS_ECUDA", 4: "LS_ESI
 EXPORTED = ["ls_params_default", "ls_mesh_create", "ls_mesh_destroy", "ls_mesh_num_nodes", "ls_operator_create",
             "ls_op_destroy", "ls_op_num_nodes", "ls_apply_dev", "ls_apply", "ls_apply_precond_dev", "ls_pairsum_dev",
             "ls_solve", "ls_solve_dev", "ls_op_correction", "ls_correction_host", "ls_hankel0_dev",
-            "ls_op_set_timing", "ls_op_stats", "ls_probe_fp64", "ls_last_error"]
+            "ls_pairsum_batch_dev", "ls_solve_batch_dev", "ls_solve_multi_dev", "ls_apply_transpose_dev", "ls_potential_transpose_dev", "ls_apply_precond_transpose_dev",
+            "ls_solve_transpose_dev", "ls_op_set_contrast", "ls_incident_dev", "ls_misfit_gradient_dev",
+            "ls_op_set_pairsum", "ls_op_set_timing", "ls_op_setup_times", "ls_op_stats", "ls_probe_fp64", "ls_last_error"]
 
 
 class LsError(RuntimeError):
@@ -56,7 +58,19 @@ def _load():
         "ls_op_correction": (I32, [P, P, P, P, P]),
         "ls_correction_host": (I32, [P, D, D, P, P, P, P]),
         "ls_hankel0_dev": (I32, [I64, P, P, P]),
+        "ls_pairsum_batch_dev": (I32, [P, I32, P, P]),
+        "ls_solve_batch_dev": (I32, [P, I32, P, P, I32, P, P, P]),
+        "ls_solve_multi_dev": (I32, [I32, P, I32, P, P, P]),
+        "ls_apply_transpose_dev": (I32, [P, P, P]),
+        "ls_potential_transpose_dev": (I32, [P, P, P]),
+        "ls_apply_precond_transpose_dev": (I32, [P, P, P]),
+        "ls_solve_transpose_dev": (I32, [P, I32, P, P, P]),
+        "ls_op_set_contrast": (I32, [P, P]),
+        "ls_incident_dev": (I32, [P, I32, P, P]),
+        "ls_misfit_gradient_dev": (I32, [P, I32, P, I32, P, P, P, P]),
+        "ls_op_set_pairsum": (I32, [P, I32]),
         "ls_op_set_timing": (I32, [P, I32]),
+        "ls_op_setup_times": (I32, [P, P]),
         "ls_op_stats": (I32, [P, P, P, P]),
         "ls_probe_fp64": (I32, [P, P]),
         "ls_last_error": (ctypes.c_char_p, []),
@@ -194,8 +208,64 @@ class Operator:
                                       _dptr(uinf), _ptr(iters)), allow=(LS_ENOCONV,))
         return iters, st
 
+    def pairsum_batch_dev(self, f, y):
+        """Batched naive pair sum for f, y torch [R, N] complex128."""
+        _check(_lib.ls_pairsum_batch_dev(self.handle, f.shape[0], _dptr(f), _dptr(y)))
+
+    def solve_batch_dev(self, b, u, ff_angles=None, uinf=None):
+        """R lock-step solves: b, u torch [R, N]; uinf torch [R, n_ff] or None."""
+        R = b.shape[0]
+        ff = np.ascontiguousarray(ff_angles if ff_angles is not None else [], np.float64).ravel()
+        iters = np.zeros(R, np.int32)
+        st = _check(_lib.ls_solve_batch_dev(self.handle, R, _dptr(b), _dptr(u), ff.size, _ptr(ff) if ff.size else None,
+                                            _dptr(uinf), _ptr(iters)), allow=(LS_ENOCONV,))
+        return iters, st
+
+    def apply_transpose_dev(self, x, y):
+        _check(_lib.ls_apply_transpose_dev(self.handle, _dptr(x), _dptr(y)))
+
+    def potential_transpose_dev(self, x, y):
+        _check(_lib.ls_potential_transpose_dev(self.handle, _dptr(x), _dptr(y)))
+
+    def apply_precond_transpose_dev(self, x, y):
+        _check(_lib.ls_apply_precond_transpose_dev(self.handle, _dptr(x), _dptr(y)))
+
+    def solve_transpose_dev(self, g, lam):
+        R = g.shape[0] if g.dim() == 2 else 1
+        iters = np.zeros(R, np.int32)
+        st = _check(_lib.ls_solve_transpose_dev(self.handle, R, _dptr(g), _dptr(lam), _ptr(iters)), allow=(LS_ENOCONV,))
+        return iters, st
+
+    def set_contrast(self, m):
+        m, mf = _c128(m)
+        _check(_lib.ls_op_set_contrast(self.handle, _ptr(mf)))
+
+    def incident_dev(self, dir_angles, b):
+        dirs = np.ascontiguousarray(dir_angles, np.float64).ravel()
+        _check(_lib.ls_incident_dev(self.handle, dirs.size, _ptr(dirs), _dptr(b)))
+
+    def misfit_gradient_dev(self, u, ff_angles, resid, grad):
+        """grad [N] float64 tensor <- dJ/dRe(m); u [R, N], resid [R, n_ff] complex128 tensors."""
+        ff = np.ascontiguousarray(ff_angles, np.float64).ravel()
+        R = u.shape[0] if u.dim() == 2 else 1
+        iters = np.zeros(R, np.int32)
+        st = _check(_lib.ls_misfit_gradient_dev(self.handle, R, _dptr(u), ff.size, _ptr(ff), _dptr(resid),
+                                                _dptr(grad), _ptr(iters)), allow=(LS_ENOCONV,))
+        return iters, st
+
+    def set_pairsum(self, mode):
+        """0: FP64 table, 1: FP64 direct, 2: FP32 precision form."""
+        _check(_lib.ls_op_set_pairsum(self.handle, int(mode)))
+        self.params.pairsum = int(mode)
+
     def set_timing(self, on=True):
         _check(_lib.ls_op_set_timing(self.handle, 1 if on else 0))
+
+    def setup_times(self):
+        """(correction, grid, block LU, table) setup wall times in seconds."""
+        t = np.zeros(4)
+        _check(_lib.ls_op_setup_times(self.handle, _ptr(t)))
+        return tuple(t)
 
     def stats(self):
         """(pair-sum kernel ms, pair-sum launches, kernel launches) since the last set_timing."""
@@ -226,6 +296,18 @@ def correction_host(mesh, k, kappa=3.0):
     _check(_lib.ls_correction_host(mesh.handle, float(k), float(kappa), ctypes.byref(nnz), _ptr(rp), _ptr(ci),
                                    _ptr(va.view(np.float64))))
     return rp, ci, va
+
+
+def solve_multi_dev(ops, B, U):
+    """Several operators in lock step: B[s], U[s] torch [R, N_s] complex128.  Returns iters [S, R], status."""
+    S = len(ops)
+    R = B[0].shape[0]
+    hs = (ctypes.c_void_p * S)(*[o.handle.value for o in ops])
+    bs = (ctypes.c_void_p * S)(*[b.data_ptr() for b in B])
+    us = (ctypes.c_void_p * S)(*[u.data_ptr() for u in U])
+    iters = np.zeros((S, R), np.int32)
+    st = _check(_lib.ls_solve_multi_dev(S, hs, R, bs, us, _ptr(iters)), allow=(LS_ENOCONV,))
+    return iters, st
 
 
 def hankel0_dev(z, out):

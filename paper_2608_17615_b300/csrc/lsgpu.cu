@@ -24,6 +24,7 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -60,6 +61,18 @@ static ls_status fail(ls_status s, const std::string& msg) {
             return fail(LS_ECUDA, std::string(#call) + ": cusolver status " + std::to_string(s_)); \
     } while (0)
 
+// The dynamic shared-memory limit is a per-kernel attribute shared by all operators:
+// only ever raise it, so that an operator with a smaller table cannot invalidate
+// another operator's launches.
+template <typename K>
+static cudaError_t raise_smem_limit(K kernel, size_t bytes) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    if (e != cudaSuccess) return e;
+    if ((size_t)a.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 // ------------------------------------------------------------------ device helpers
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
@@ -74,6 +87,8 @@ __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
 }
+
+struct Stencil9 { double2 v[9]; };   // 3x3 sparsifying stencil, index (da+1) + 3 (db+1)
 
 #define LS_INV_SQRT_PI 0.56418958354775628695
 #define LS_TWO_OVER_PI 0.63661977236758134308
@@ -136,7 +151,7 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum(const double2* __restrict__ 
                 double2 p = xy[src];
                 double2 ff = f[src];
                 if (m) ff = cmul(m[src], ff);
-                double ww = w[src];
+                double ww = w ? w[src] : 1.0;
                 v = make_double4(p.x, p.y, ww * ff.x, ww * ff.y);
             }
             tile[i] = v;
@@ -187,7 +202,7 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum_tab(const double2* __restric
                 double2 p = xy[src];
                 double2 ff = f[src];
                 if (m) ff = cmul(m[src], ff);
-                double ww = w[src];
+                double ww = w ? w[src] : 1.0;
                 v = make_double4(p.x, p.y, ww * ff.x, ww * ff.y);
             }
             tile[i] = v;
@@ -286,7 +301,7 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum_f32(const double2* __restric
                 double2 p = xy[src];
                 double2 ff = f[src];
                 if (m) ff = cmul(m[src], ff);
-                double ww = w[src];
+                double ww = w ? w[src] : 1.0;
                 float xh = (float)p.x, yh = (float)p.y;
                 v.xy = make_float4(xh, (float)(p.x - (double)xh), yh, (float)(p.y - (double)yh));
                 v.s = make_float2((float)(ww * ff.x), (float)(ww * ff.y));
@@ -348,6 +363,315 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum_f32(const double2* __restric
     if (j < n) partial[(size_t)blockIdx.y * n + j] = make_double2((double)sr - (double)cr, (double)si - (double)ci);
 }
 
+// FP64-accurate pair sum in double-float (pairs of FP32, ~48-bit significand) on the
+// FP32 pipe (pairsum = 3): DF coordinate differences, DF t = dx^2 + dy^2, exact DF
+// cell variable u (t and the cell centre share an octave, so t_hi - mid_hi is exact,
+// and 1/half-width is a power of two), DF Horner on the degree-11 table stored as
+// (hi, lo) float pairs, DF complex multiply-accumulate per 256-source tile folded
+// into FP64.  Error-free transformations: TwoSum (Knuth), TwoProduct via FMA.
+struct DF { float h, l; };
+__device__ __forceinline__ DF df_fast(float a, float b) {       // |a| >= |b|
+    float s = a + b;
+    return DF{s, b - (s - a)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    float s, e;
+    two_sum(a.h, b.h, s, e);
+    e += a.l + b.l;
+    return df_fast(s, e);
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    return df_fast(p, e);
+}
+// a * u + c
+__device__ __forceinline__ DF df_mad(DF a, DF u, DF c) {
+    float p = a.h * u.h;
+    float e = fmaf(a.h, u.h, -p);
+    float s, e2;
+    two_sum(p, c.h, s, e2);
+    e = fmaf(a.h, u.l, e);
+    e = fmaf(a.l, u.h, e);
+    e += e2 + c.l;
+    return df_fast(s, e);
+}
+__device__ __forceinline__ DF df_from(double x) {
+    float h = (float)x;
+    return DF{h, (float)(x - (double)h)};
+}
+
+struct DFTile { float4 xy; float4 s; };     // (x_h, x_l, y_h, y_l), (s_re_h, s_re_l, s_im_h, s_im_l)
+
+__global__ void __launch_bounds__(PS_TPB) k_pairsum_df(const double2* __restrict__ xy, const double* __restrict__ w,
+                                                       const double2* __restrict__ m, const double2* __restrict__ f,
+                                                       int n, int src_per_chunk, double k, double inv_k,
+                                                       const float4* __restrict__ tab_g, int ncell, int noct, int b_lo,
+                                                       double2* __restrict__ partial) {
+    // table layout (float4 words): coef [ncell][NC_TAB] as (re_h, re_l, im_h, im_l),
+    // cells (mid_h, mid_l, inv_hw, 0) [ncell], oct int2 (base, 23 - m) [noct]
+    extern __shared__ float4 dtab[];
+    __shared__ DFTile tile[PS_TILE];
+    const int words = ncell * (NC_TAB + 1) + (noct + 1) / 2;
+    for (int i = threadIdx.x; i < words; i += PS_TPB) dtab[i] = tab_g[i];
+    const float4* coef = dtab;
+    const float4* cellv = dtab + (size_t)ncell * NC_TAB;
+    const int2* oct = reinterpret_cast<const int2*>(cellv + ncell);
+    const int j = blockIdx.x * PS_TPB + threadIdx.x;
+    const int s_begin = blockIdx.y * src_per_chunk;
+    const int s_end = min(n, s_begin + src_per_chunk);
+    const double2 yj = xy[min(j, n - 1)];
+    const DF tx = df_from(yj.x), ty = df_from(yj.y);
+    double accr = 0.0, acci = 0.0;
+    for (int base = s_begin; base < s_end; base += PS_TILE) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < PS_TILE; i += PS_TPB) {
+            int src = base + i;
+            DFTile v;
+            v.xy = make_float4(0.f, 0.f, 0.f, 0.f);
+            v.s = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (src < s_end) {
+                double2 p = xy[src];
+                double2 ff = f[src];
+                if (m) ff = cmul(m[src], ff);
+                double ww = w ? w[src] : 1.0;
+                DF a = df_from(p.x), b = df_from(p.y), c = df_from(ww * ff.x), d = df_from(ww * ff.y);
+                v.xy = make_float4(a.h, a.l, b.h, b.l);
+                v.s = make_float4(c.h, c.l, d.h, d.l);
+            }
+            tile[i] = v;
+        }
+        __syncthreads();
+        DF sr{0.f, 0.f}, si{0.f, 0.f};
+        const int cnt = min(PS_TILE, s_end - base);
+        for (int i = 0; i < cnt; ++i) {
+            DFTile src = tile[i];
+            float dxh, dxl, dyh, dyl;
+            df_diff(tx.h, tx.l, src.xy.x, src.xy.y, dxh, dxl);
+            df_diff(ty.h, ty.l, src.xy.z, src.xy.w, dyh, dyl);
+            float p1 = dxh * dxh, e1 = fmaf(dxh, dxh, -p1);
+            e1 = fmaf(2.f * dxh, dxl, e1);
+            float p2 = dyh * dyh, e2 = fmaf(dyh, dyh, -p2);
+            e2 = fmaf(2.f * dyh, dyl, e2);
+            float th, tl;
+            two_sum(p1, p2, th, tl);
+            tl += e1 + e2;
+            DF t = df_fast(th, tl);
+            int bits = __float_as_int(t.h);
+            unsigned o = (unsigned)((bits >> 23) - b_lo);
+            DF hr, hi;
+            if (o < (unsigned)noct) {
+                int2 ob = oct[o];
+                int cell = ob.x + ((bits & 0x7fffff) >> ob.y);
+                float4 cv = cellv[cell];
+                float d0, d1;
+                two_sum(t.h - cv.x, t.l - cv.y, d0, d1);      // t.h - mid.h is exact
+                DF u = DF{d0 * cv.z, d1 * cv.z};                // times a power of two: exact
+                const float4* c = coef + (size_t)cell * NC_TAB;
+                float4 cc = c[NC_TAB - 1];
+                hr = DF{cc.x, cc.y};
+                hi = DF{cc.z, cc.w};
+#pragma unroll
+                for (int e = NC_TAB - 2; e >= 0; --e) {
+                    cc = c[e];
+                    hr = df_mad(hr, u, DF{cc.x, cc.y});
+                    hi = df_mad(hi, u, DF{cc.z, cc.w});
+                }
+            } else if (t.h > 0.f) {
+                double2 h = ls_h0_r2((double)t.h + (double)t.l, k, inv_k);
+                hr = df_from(h.x);
+                hi = df_from(h.y);
+            } else {
+                continue;                     // the self pair
+            }
+            DF s_re{src.s.x, src.s.y}, s_im{src.s.z, src.s.w};
+            DF a1 = df_mul(hr, s_re), a2 = df_mul(hi, s_im), a3 = df_mul(hr, s_im), a4 = df_mul(hi, s_re);
+            sr = df_add(sr, df_add(a1, DF{-a2.h, -a2.l}));
+            si = df_add(si, df_add(a3, a4));
+        }
+        accr += (double)sr.h + (double)sr.l;
+        acci += (double)si.h + (double)si.l;
+    }
+    if (j < n) partial[(size_t)blockIdx.y * n + j] = make_double2(accr, acci);
+}
+
+// Batched form: R right-hand sides.  Each thread owns one target and a block of
+// RB right-hand sides; H(j, n) is generated once per pair from the FP32 table
+// (double-float t as in k_pairsum_f32) and applied to the RB strengths.  Sums
+// run in FP32 over runs of 32 sources and are folded into FP64 accumulators after
+// each run, which bounds the recursive-summation error of FP32 to 32 terms.
+//   f [R][n] densities; partial [R][nchunk][n] (blockIdx.z = RHS block).
+#define MRB 8
+
+// One work unit of the batched pair sum: target block tb, source chunk, RHS block rb.
+struct MultiArgs {
+    const double2* xy;
+    const double* w;
+    const double2* m;
+    const double2* f;
+    size_t sf;
+    int n, R, spc, nchunk;
+    double k, inv_k;
+    int ncell, noct, b_lo;
+    double2* partial;
+};
+
+__device__ __forceinline__ void multi_unit(const MultiArgs& A, int tb, int chunk, int rb, const float4* ftab,
+                                           float4* txy, float2 (*ts)[MRB]) {
+    const int coef_f4 = (A.ncell * NC_F32 + 1) / 2;
+    const float2* coef = reinterpret_cast<const float2*>(ftab);
+    const float4* cellv = ftab + coef_f4;
+    const int2* oct = reinterpret_cast<const int2*>(cellv + A.ncell);
+    const int n = A.n;
+    const int j = tb * PS_TPB + threadIdx.x;
+    const int r0 = rb * MRB;
+    const int nr = min(MRB, A.R - r0);
+    const int s_begin = chunk * A.spc;
+    const int s_end = min(n, s_begin + A.spc);
+    const double2 yj = A.xy[min(j, n - 1)];
+    const float txh = (float)yj.x, txl = (float)(yj.x - (double)txh);
+    const float tyh = (float)yj.y, tyl = (float)(yj.y - (double)tyh);
+    double accr[MRB], acci[MRB];
+#pragma unroll
+    for (int q = 0; q < MRB; ++q) { accr[q] = 0.0; acci[q] = 0.0; }
+    for (int base = s_begin; base < s_end; base += PS_TILE) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < PS_TILE; i += PS_TPB) {
+            int src = base + i;
+            float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (src < s_end) {
+                double2 p = A.xy[src];
+                float xh = (float)p.x, yh = (float)p.y;
+                c = make_float4(xh, (float)(p.x - (double)xh), yh, (float)(p.y - (double)yh));
+            }
+            txy[i] = c;
+            double ww = (src < s_end) ? (A.w ? A.w[src] : 1.0) : 0.0;
+            double2 mm = (src < s_end && A.m) ? A.m[src] : make_double2(1.0, 0.0);
+#pragma unroll
+            for (int q = 0; q < MRB; ++q) {
+                float2 v = make_float2(0.f, 0.f);
+                if (src < s_end && q < nr) {
+                    double2 ff = cmul(mm, A.f[(size_t)(r0 + q) * A.sf + src]);
+                    v = make_float2((float)(ww * ff.x), (float)(ww * ff.y));
+                }
+                ts[i][q] = v;
+            }
+        }
+        __syncthreads();
+        const int cnt = min(PS_TILE, s_end - base);
+        // FP32 sums over runs of 32 sources, folded into the FP64 accumulators after each run
+        for (int i0 = 0; i0 < cnt; i0 += 32) {
+            float sr[MRB], si[MRB];
+#pragma unroll
+            for (int q = 0; q < MRB; ++q) { sr[q] = 0.f; si[q] = 0.f; }
+            const int i1 = min(cnt, i0 + 32);
+            for (int i = i0; i < i1; ++i) {
+                float4 sc = txy[i];
+                float dxh, dxl, dyh, dyl;
+                df_diff(txh, txl, sc.x, sc.y, dxh, dxl);
+                df_diff(tyh, tyl, sc.z, sc.w, dyh, dyl);
+                float p1 = dxh * dxh, e1 = fmaf(dxh, dxh, -p1);
+                e1 = fmaf(2.f * dxh, dxl, e1);
+                float p2 = dyh * dyh, e2 = fmaf(dyh, dyh, -p2);
+                e2 = fmaf(2.f * dyh, dyl, e2);
+                float th, tl;
+                two_sum(p1, p2, th, tl);
+                tl += e1 + e2;
+                float t0 = th + tl;
+                tl = tl - (t0 - th);
+                th = t0;
+                int bits = __float_as_int(th);
+                unsigned o = (unsigned)((bits >> 23) - A.b_lo);
+                float hr, him;
+                if (o < (unsigned)A.noct) {
+                    int2 ob = oct[o];
+                    int cell = ob.x + ((bits & 0x7fffff) >> ob.y);
+                    float4 cv = cellv[cell];
+                    float u = ((th - cv.x) + (tl - cv.y)) * cv.z;
+                    const float2* c = coef + cell * NC_F32;
+                    float2 cc = c[NC_F32 - 1];
+                    hr = cc.x;
+                    him = cc.y;
+#pragma unroll
+                    for (int e = NC_F32 - 2; e >= 0; --e) {
+                        cc = c[e];
+                        hr = fmaf(hr, u, cc.x);
+                        him = fmaf(him, u, cc.y);
+                    }
+                } else if (th > 0.f) {
+                    double2 h = ls_h0_r2((double)th + (double)tl, A.k, A.inv_k);
+                    hr = (float)h.x;
+                    him = (float)h.y;
+                } else {
+                    continue;
+                }
+#pragma unroll
+                for (int q = 0; q < MRB; ++q) {
+                    float2 v = ts[i][q];
+                    sr[q] = fmaf(hr, v.x, fmaf(-him, v.y, sr[q]));
+                    si[q] = fmaf(hr, v.y, fmaf(him, v.x, si[q]));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < MRB; ++q) { accr[q] += (double)sr[q]; acci[q] += (double)si[q]; }
+        }
+    }
+    if (j < n)
+        for (int q = 0; q < nr; ++q)
+            A.partial[((size_t)(r0 + q) * A.nchunk + chunk) * n + j] = make_double2(accr[q], acci[q]);
+}
+
+__global__ void __launch_bounds__(PS_TPB) k_pairsum_multi_f32(MultiArgs A, const float4* __restrict__ tab_g) {
+    extern __shared__ float4 ftab[];
+    __shared__ float4 txy[PS_TILE];
+    __shared__ float2 ts[PS_TILE][MRB];
+    const int words = (A.ncell * NC_F32 + 1) / 2 + A.ncell + (A.noct + 1) / 2;
+    for (int i = threadIdx.x; i < words; i += PS_TPB) ftab[i] = tab_g[i];
+    multi_unit(A, blockIdx.x, blockIdx.y, blockIdx.z, ftab, txy, ts);
+}
+
+// Persistent form over several operators (scatterers): a block fetches work units
+// (operator, target block, source chunk, RHS block) from an atomic counter until
+// all units are done, reloading the shared-memory H0 table when the operator changes.
+struct PSDesc {
+    MultiArgs a;
+    const float4* tab;
+    int tab_words, tblocks, unit_begin, units;
+};
+
+__global__ void __launch_bounds__(PS_TPB) k_pairsum_persist(const PSDesc* __restrict__ d, int S, int total,
+                                                            int* __restrict__ counter) {
+    extern __shared__ float4 ftab[];
+    __shared__ float4 txy[PS_TILE];
+    __shared__ float2 ts[PS_TILE][MRB];
+    __shared__ int s_unit;
+    int cur = -1;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
+        __syncthreads();
+        const int u = s_unit;
+        if (u >= total) break;
+        int s = 0;
+        while (s + 1 < S && d[s + 1].unit_begin <= u) ++s;
+        if (s != cur) {
+            const float4* tg = d[s].tab;
+            const int words = d[s].tab_words;
+            for (int i = threadIdx.x; i < words; i += PS_TPB) ftab[i] = tg[i];
+            cur = s;
+            __syncthreads();
+        }
+        const int local = u - d[s].unit_begin;
+        const int tb = local % d[s].tblocks;
+        const int rest = local / d[s].tblocks;
+        const int chunk = rest % d[s].a.nchunk;
+        const int rb = rest / d[s].a.nchunk;
+        multi_unit(d[s].a, tb, chunk, rb, ftab, txy, ts);
+    }
+}
+
 // mode 0: y = x + k2 * ((i/4) sum_c partial + dV (m x));  mode 1: y = (i/4) sum_c partial
 __global__ void k_apply_epi(int n, int nchunk, const double2* __restrict__ partial, const int64_t* __restrict__ rowptr,
                             const int* __restrict__ cols, const double2* __restrict__ vals,
@@ -389,6 +713,171 @@ __global__ void k_apply_epi(int n, int nchunk, const double2* __restrict__ parti
     }
 }
 
+// L^T x = x + k^2 m (w (i/4) sum_c partial + dV^T x), with the pair sum taken on unit
+// weights (G is symmetric, so (K^T x)_n = w_n sum_j G(y_n, y_j) x_j).  mode 2 returns
+// V^T x instead (no identity, no k^2 m factor).
+__global__ void k_applyT_epi(int n, int nchunk, const double2* __restrict__ partial, const int64_t* __restrict__ rowptr,
+                             const int* __restrict__ cols, const double2* __restrict__ vals,
+                             const double2* __restrict__ m, const double* __restrict__ w,
+                             const double2* __restrict__ x, double k2, double2* __restrict__ y, int mode) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const int j = warp;
+    double sr = 0.0, si = 0.0;
+    for (int c = lane; c < nchunk; c += 32) {
+        double2 p = partial[(size_t)c * n + j];
+        sr += p.x;
+        si += p.y;
+    }
+    double cr = 0.0, ci = 0.0;
+    for (int64_t e = rowptr[j] + lane; e < rowptr[j + 1]; e += 32) {
+        double2 t = cmul(vals[e], x[cols[e]]);
+        cr += t.x;
+        ci += t.y;
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    cr = warp_sum(cr);
+    ci = warp_sum(ci);
+    if (lane == 0) {
+        double2 vt = make_double2(w[j] * (-0.25 * si) + cr, w[j] * (0.25 * sr) + ci);   // (V^T x)_j
+        if (mode == 2) {
+            y[j] = vt;
+        } else {
+            double2 mv = cmul(m[j], vt);
+            double2 xj = x[j];
+            y[j] = make_double2(xj.x + k2 * mv.x, xj.y + k2 * mv.y);
+        }
+    }
+}
+
+// (A^T y)_l = sum_s v_s y_{l - s} over full-stencil rows l - s, plus y_l on grid-edge rows
+__global__ void k_stencilT(int nx, int ny, Stencil9 st, const double2* __restrict__ y, const double2* __restrict__ g,
+                           double2* __restrict__ r) {
+    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nx * ny) return;
+    int a = l % nx, b = l / nx;
+    double2 acc = make_double2(0.0, 0.0);
+    if (a < 1 || a > nx - 2 || b < 1 || b > ny - 2) acc = y[l];
+#pragma unroll
+    for (int s = 0; s < 9; ++s) {
+        int ja = a - (s % 3 - 1), jb = b - (s / 3 - 1);
+        if (ja >= 1 && ja <= nx - 2 && jb >= 1 && jb <= ny - 2) acc = cadd(acc, cmul(st.v[s], y[ja + nx * jb]));
+    }
+    r[l] = csub(acc, g[l]);                  // (S^T - I) g = A^T C^{-T} g - g
+}
+
+// transposed forward sweep, in place: z_b -= GT_{b-1} z_{b-1}   (GT_b = G_b^T, row-major)
+__global__ void k_btT_fwd(int nx, int b, const double2* __restrict__ GT, double2* __restrict__ z) {
+    extern __shared__ double2 sh[];
+    for (int c = threadIdx.x; c < nx; c += blockDim.x) sh[c] = z[(size_t)(b - 1) * nx + c];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= nx) return;
+    const double2* Gr = GT + ((size_t)(b - 1) * nx + row) * nx;
+    double ar = 0.0, ai = 0.0;
+    for (int c = lane; c < nx; c += 32) {
+        double2 gv = Gr[c], v = sh[c];
+        ar = fma(gv.x, v.x, fma(-gv.y, v.y, ar));
+        ai = fma(gv.x, v.y, fma(gv.y, v.x, ai));
+    }
+    ar = warp_sum(ar);
+    ai = warp_sum(ai);
+    if (lane == 0) {
+        double2 v = z[(size_t)b * nx + row];
+        z[(size_t)b * nx + row] = make_double2(v.x - ar, v.y - ai);
+    }
+}
+
+// transposed backward sweep: x_b = WT_b (z_b - C_{b+1,b}^T x_{b+1})  (x and z distinct buffers)
+__global__ void k_btT_bwd(int nx, int ny, int b, const double2* __restrict__ WT, const double2* __restrict__ cband,
+                          const double2* __restrict__ z, double2* __restrict__ x) {
+    extern __shared__ double2 sh[];
+    for (int c = threadIdx.x; c < nx; c += blockDim.x) {
+        double2 v = z[(size_t)b * nx + c];
+        if (b + 1 < ny) {
+            const double2* Cm1 = cband + (size_t)(b + 1) * 9 * nx;   // db = -1 diagonals of block row b+1
+            const double2* xn = x + (size_t)(b + 1) * nx;
+            for (int da = -1; da <= 1; ++da) {
+                int a = c - da;                    // C_{b+1,b}(a, c) with c = a + da
+                if (a >= 0 && a < nx) v = csub(v, cmul(Cm1[(size_t)(da + 1) * nx + a], xn[a]));
+            }
+        }
+        sh[c] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= nx) return;
+    const double2* Wr = WT + ((size_t)b * nx + row) * nx;
+    double ar = 0.0, ai = 0.0;
+    for (int c = lane; c < nx; c += 32) {
+        double2 wv = Wr[c], v = sh[c];
+        ar = fma(wv.x, v.x, fma(-wv.y, v.y, ar));
+        ai = fma(wv.x, v.y, fma(wv.y, v.x, ai));
+    }
+    ar = warp_sum(ar);
+    ai = warp_sum(ai);
+    if (lane == 0) x[(size_t)b * nx + row] = make_double2(ar, ai);
+}
+
+// block transpose for the factors: out_b = in_b^T (row-major nx x nx blocks)
+__global__ void k_transpose_blocks(int nx, int nblk, const double2* __restrict__ in, double2* __restrict__ out) {
+    __shared__ double2 t[32][33];
+    int b = blockIdx.z;
+    if (b >= nblk) return;
+    int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    const double2* src = in + (size_t)b * nx * nx;
+    double2* dst = out + (size_t)b * nx * nx;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        int r = y0 + i, c = x0 + threadIdx.x;
+        if (r < nx && c < nx) t[i][threadIdx.x] = src[(size_t)r * nx + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        int r = x0 + i, c = y0 + threadIdx.x;
+        if (r < nx && c < nx) dst[(size_t)r * nx + c] = t[threadIdx.x][i];
+    }
+}
+
+// g_j = -k^2 e^{i pi/4}/sqrt(8 pi k) w_j sum_a conj(r_a) e^{-i k xhat_a . y_j}  (A^T conj(r))
+__global__ void k_farfieldT(int n, const double2* __restrict__ xy, const double* __restrict__ w, double k, int n_ff,
+                            const double* __restrict__ ang, const double2* __restrict__ r, double2* __restrict__ g) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double2 p = xy[j];
+    double ar = 0.0, ai = 0.0;
+    for (int a = 0; a < n_ff; ++a) {
+        double cy, cx, s, c;
+        sincos(ang[a], &cy, &cx);
+        sincos(-k * fma(cx, p.x, cy * p.y), &s, &c);
+        double2 rc = make_double2(r[a].x, -r[a].y);
+        double2 t = cmul(rc, make_double2(c, s));
+        ar += t.x;
+        ai += t.y;
+    }
+    double gam = k * k / sqrt(8.0 * M_PI * k);
+    double2 pre = make_double2(-gam * M_SQRT1_2 * w[j], -gam * M_SQRT1_2 * w[j]);
+    g[j] = cmul(pre, make_double2(ar, ai));
+}
+
+// out = m * g (the adjoint right-hand side)
+__global__ void k_cmul_vec(int n, const double2* __restrict__ a, const double2* __restrict__ b, double2* __restrict__ out) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) out[j] = cmul(a[j], b[j]);
+}
+
+// grad_j += Re(u_j (g_j - k^2 vtl_j))
+__global__ void k_grad_acc(int n, const double2* __restrict__ u, const double2* __restrict__ g,
+                           const double2* __restrict__ vtl, double k2, double* __restrict__ grad) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double2 d = make_double2(g[j].x - k2 * vtl[j].x, g[j].y - k2 * vtl[j].y);
+    grad[j] += u[j].x * d.x - u[j].y * d.y;
+}
+
 __global__ void k_hankel0(int64_t n, const double* __restrict__ z, double2* __restrict__ h) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) h[i] = ls_h0_r2(z[i] * z[i], 1.0, 1.0);
@@ -408,8 +897,6 @@ __global__ void k_tqc(int nc, const int64_t* __restrict__ rp, const int* __restr
     }
     g[i] = make_double2(ar, ai);
 }
-
-struct Stencil9 { double2 v[9]; };
 
 // t = A g: 3x3 stencil on rows with a full stencil, identity on grid-edge rows
 __global__ void k_stencil(int nx, int ny, Stencil9 st, const double2* __restrict__ g, double2* __restrict__ t) {
@@ -493,7 +980,7 @@ __global__ void k_tcq(int nq, const int* __restrict__ idx, const double* __restr
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         int i = idx[4 * q + c];
-        double2 d = csub(tp[i], g[i]);
+        double2 d = g ? csub(tp[i], g[i]) : tp[i];
         acc.x = fma(wt[4 * q + c], d.x, acc.x);
         acc.y = fma(wt[4 * q + c], d.y, acc.y);
     }
@@ -686,6 +1173,301 @@ __global__ void k_gmres_init(double2* g, const double2* beta2, double* hist) {
     }
 }
 
+// ------------------------------------------------------------------ batched (R systems, blockIdx.y = r)
+// Vectors of system r live at base + r * stride.
+__global__ void k_apply_epi_multi(int n, int nchunk, const double2* __restrict__ partial, const int64_t* __restrict__ rowptr,
+                                  const int* __restrict__ cols, const double2* __restrict__ vals,
+                                  const double2* __restrict__ m, const double2* __restrict__ x, size_t sx, double k2,
+                                  double2* __restrict__ y, size_t sy) {
+    const int r = blockIdx.y;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const int j = warp;
+    const double2* xr = x + (size_t)r * sx;
+    const double2* pr = partial + (size_t)r * nchunk * n;
+    double sr = 0.0, si = 0.0;
+    for (int c = lane; c < nchunk; c += 32) {
+        double2 p = pr[(size_t)c * n + j];
+        sr += p.x;
+        si += p.y;
+    }
+    double cr = 0.0, ci = 0.0;
+    for (int64_t e = rowptr[j] + lane; e < rowptr[j + 1]; e += 32) {
+        int q = cols[e];
+        double2 t = cmul(vals[e], cmul(m[q], xr[q]));
+        cr += t.x;
+        ci += t.y;
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    cr = warp_sum(cr);
+    ci = warp_sum(ci);
+    if (lane == 0) {
+        double2 xj = xr[j];
+        y[(size_t)r * sy + j] = make_double2(xj.x + k2 * (-0.25 * si + cr), xj.y + k2 * (0.25 * sr + ci));
+    }
+}
+
+__global__ void k_tqc_multi(int nc, const int64_t* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ cv,
+                            const double2* __restrict__ x, size_t sx, double2* __restrict__ g) {
+    int r = blockIdx.y;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    const double2* xr = x + (size_t)r * sx;
+    double ar = 0.0, ai = 0.0;
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+        double2 v = xr[ci[e]];
+        ar = fma(cv[e], v.x, ar);
+        ai = fma(cv[e], v.y, ai);
+    }
+    g[(size_t)r * nc + i] = make_double2(ar, ai);
+}
+
+__global__ void k_stencil_multi(int nx, int ny, Stencil9 st, const double2* __restrict__ g, double2* __restrict__ t) {
+    int r = blockIdx.y;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nc = nx * ny;
+    if (idx >= nc) return;
+    const double2* gr = g + (size_t)r * nc;
+    int a = idx % nx, b = idx / nx;
+    if (a < 1 || a > nx - 2 || b < 1 || b > ny - 2) { t[(size_t)r * nc + idx] = gr[idx]; return; }
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int s = 0; s < 9; ++s) acc = cadd(acc, cmul(st.v[s], gr[idx + (s % 3 - 1) + (s / 3 - 1) * nx]));
+    t[(size_t)r * nc + idx] = acc;
+}
+
+__global__ void k_bt_fwd_multi(int nx, int ny, int b, const double2* __restrict__ W, const double2* __restrict__ cband,
+                               const double2* __restrict__ t, double2* __restrict__ y) {
+    extern __shared__ double2 sh[];
+    const int r = blockIdx.y;
+    const size_t off = (size_t)r * nx * ny;
+    const double2* Cm = cband + (size_t)b * 9 * nx;
+    for (int c = threadIdx.x; c < nx; c += blockDim.x) {
+        double2 v = t[off + (size_t)b * nx + c];
+        if (b > 0) {
+            const double2* yp = y + off + (size_t)(b - 1) * nx;
+            for (int da = -1; da <= 1; ++da) {
+                int cc = c + da;
+                if (cc >= 0 && cc < nx) v = csub(v, cmul(Cm[(size_t)(da + 1) * nx + c], yp[cc]));
+            }
+        }
+        sh[c] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= nx) return;
+    const double2* Wr = W + ((size_t)b * nx + row) * nx;
+    double ar = 0.0, ai = 0.0;
+    for (int c = lane; c < nx; c += 32) {
+        double2 wv = Wr[c], v = sh[c];
+        ar = fma(wv.x, v.x, fma(-wv.y, v.y, ar));
+        ai = fma(wv.x, v.y, fma(wv.y, v.x, ai));
+    }
+    ar = warp_sum(ar);
+    ai = warp_sum(ai);
+    if (lane == 0) y[off + (size_t)b * nx + row] = make_double2(ar, ai);
+}
+
+__global__ void k_bt_bwd_multi(int nx, int ny, int b, const double2* __restrict__ Gm, double2* __restrict__ y) {
+    extern __shared__ double2 sh[];
+    const size_t off = (size_t)blockIdx.y * nx * ny;
+    for (int c = threadIdx.x; c < nx; c += blockDim.x) sh[c] = y[off + (size_t)(b + 1) * nx + c];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= nx) return;
+    const double2* Gr = Gm + ((size_t)b * nx + row) * nx;
+    double ar = 0.0, ai = 0.0;
+    for (int c = lane; c < nx; c += 32) {
+        double2 gv = Gr[c], v = sh[c];
+        ar = fma(gv.x, v.x, fma(-gv.y, v.y, ar));
+        ai = fma(gv.x, v.y, fma(gv.y, v.x, ai));
+    }
+    ar = warp_sum(ar);
+    ai = warp_sum(ai);
+    if (lane == 0) {
+        double2 v = y[off + (size_t)b * nx + row];
+        y[off + (size_t)b * nx + row] = make_double2(v.x - ar, v.y - ai);
+    }
+}
+
+__global__ void k_tcq_multi(int nq, int nc, const int* __restrict__ idx, const double* __restrict__ wt,
+                            const double2* __restrict__ tp, const double2* __restrict__ g, const double2* __restrict__ win,
+                            size_t sin_, double2* __restrict__ z, size_t sz) {
+    int r = blockIdx.y;
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    const double2* tpr = tp + (size_t)r * nc;
+    const double2* gr = g + (size_t)r * nc;
+    double2 acc = win[(size_t)r * sin_ + q];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        int i = idx[4 * q + c];
+        double2 d = csub(tpr[i], gr[i]);
+        acc.x = fma(wt[4 * q + c], d.x, acc.x);
+        acc.y = fma(wt[4 * q + c], d.y, acc.y);
+    }
+    z[(size_t)r * sz + q] = acc;
+}
+
+// part[(r * J + j) * nblk + block] = conj(V_{r,j}) . z_r over the block's rows
+__global__ void k_dots_multi(int n, int J, const double2* __restrict__ V, size_t sv_r, size_t ldv,
+                             const double2* __restrict__ z, size_t sz, double2* __restrict__ part, const int* __restrict__ active) {
+    __shared__ double sr[RED_TPB / 32], si[RED_TPB / 32];
+    const int r = blockIdx.y;
+    if (active && !active[r]) return;
+    const int nblk = gridDim.x;
+    const int rows_per = (n + nblk - 1) / nblk;
+    const int r0 = blockIdx.x * rows_per, r1 = min(n, r0 + rows_per);
+    const double2* zr = z + (size_t)r * sz;
+    for (int j = 0; j < J; ++j) {
+        const double2* v = V + (size_t)r * sv_r + (size_t)j * ldv;
+        double ar = 0.0, ai = 0.0;
+        for (int q = r0 + threadIdx.x; q < r1; q += RED_TPB) {
+            double2 t = conjmul(v[q], zr[q]);
+            ar += t.x;
+            ai += t.y;
+        }
+        ar = warp_sum(ar);
+        ai = warp_sum(ai);
+        if ((threadIdx.x & 31) == 0) { sr[threadIdx.x >> 5] = ar; si[threadIdx.x >> 5] = ai; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tr = 0.0, ti = 0.0;
+            for (int w = 0; w < RED_TPB / 32; ++w) { tr += sr[w]; ti += si[w]; }
+            part[((size_t)r * J + j) * nblk + blockIdx.x] = make_double2(tr, ti);
+        }
+        __syncthreads();
+    }
+}
+
+// out[r * so + j] (+)= sum_b part[(r * J + j) * nblk + b]
+__global__ void k_sumrows_multi(int J, int nblk, const double2* __restrict__ part, double2* __restrict__ out, size_t so,
+                                int accumulate, const int* __restrict__ active) {
+    int r = blockIdx.y;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= J || (active && !active[r])) return;
+    double ar = 0.0, ai = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+        double2 p = part[((size_t)r * J + j) * nblk + b];
+        ar += p.x;
+        ai += p.y;
+    }
+    double2* o = out + (size_t)r * so + j;
+    if (accumulate) { o->x += ar; o->y += ai; }
+    else *o = make_double2(ar, ai);
+}
+
+__global__ void k_update_multi(int n, int J, const double2* __restrict__ V, size_t sv_r, size_t ldv,
+                               const double2* __restrict__ h, size_t sh_r, double2* __restrict__ z, size_t sz,
+                               const int* __restrict__ active) {
+    extern __shared__ double2 hs[];
+    const int r = blockIdx.y;
+    if (active && !active[r]) return;
+    for (int j = threadIdx.x; j < J; j += blockDim.x) hs[j] = h[(size_t)r * sh_r + j];
+    __syncthreads();
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    double2* zr = z + (size_t)r * sz;
+    double2 acc = zr[q];
+    for (int j = 0; j < J; ++j) {
+        double2 t = cmul(V[(size_t)r * sv_r + (size_t)j * ldv + q], hs[j]);
+        acc.x -= t.x;
+        acc.y -= t.y;
+    }
+    zr[q] = acc;
+}
+
+// dst_r = src_r / sqrt(nrm2[r].x); hout[r * sh] = the norm
+__global__ void k_scale_multi(int n, const double2* __restrict__ src, size_t ss, const double2* __restrict__ nrm2,
+                              double2* __restrict__ dst, size_t sd, double2* hout, size_t sh, const int* __restrict__ active) {
+    const int r = blockIdx.y;
+    if (active && !active[r]) return;
+    double nr = sqrt(nrm2[r].x);
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q == 0 && hout) hout[(size_t)r * sh] = make_double2(nr, 0.0);
+    if (q >= n) return;
+    double inv = nr > 0.0 ? 1.0 / nr : 0.0;
+    double2 v = src[(size_t)r * ss + q];
+    dst[(size_t)r * sd + q] = make_double2(v.x * inv, v.y * inv);
+}
+
+// one thread per system: Givens update of column j; deactivates converged systems
+__global__ void k_givens_multi(int R, int j, double2* H, size_t sH, int ldh, double2* cs, double2* sn, double2* g,
+                               size_t sg, double* hist, size_t shist, const double2* beta2, double tol, int* active,
+                               int* its) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R || !active[r]) return;
+    double2* col = H + (size_t)r * sH + (size_t)j * ldh;
+    double2* csr = cs + (size_t)r * sg;
+    double2* snr = sn + (size_t)r * sg;
+    double2* gr = g + (size_t)r * sg;
+    for (int i = 0; i < j; ++i) {
+        double2 a = col[i], b = col[i + 1];
+        double2 t = cadd(cmul(csr[i], a), cmul(snr[i], b));
+        double2 cc = make_double2(csr[i].x, -csr[i].y), sc = make_double2(snr[i].x, -snr[i].y);
+        col[i + 1] = csub(cmul(cc, b), cmul(sc, a));
+        col[i] = t;
+    }
+    double2 a = col[j], b = col[j + 1];
+    double den = sqrt(a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y);
+    double2 c = den > 0.0 ? make_double2(a.x / den, -a.y / den) : make_double2(1.0, 0.0);
+    double2 s_ = den > 0.0 ? make_double2(b.x / den, -b.y / den) : make_double2(0.0, 0.0);
+    csr[j] = c;
+    snr[j] = s_;
+    col[j] = make_double2(den, 0.0);
+    col[j + 1] = make_double2(0.0, 0.0);
+    double2 gj = gr[j];
+    double2 gn = cmul(make_double2(s_.x, -s_.y), gj);
+    gr[j + 1] = make_double2(-gn.x, -gn.y);
+    gr[j] = cmul(c, gj);
+    double res = sqrt(gr[j + 1].x * gr[j + 1].x + gr[j + 1].y * gr[j + 1].y) / sqrt(beta2[r].x);
+    hist[(size_t)r * shist + j + 1] = res;
+    its[r] = j + 1;
+    if (!(res > tol)) active[r] = 0;
+}
+
+__global__ void k_backsolve_multi(int R, const int* its, const double2* H, size_t sH, int ldh, const double2* g, size_t sg,
+                                  double2* yv, size_t sy) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    int it = its[r];
+    const double2* Hr = H + (size_t)r * sH;
+    const double2* gr = g + (size_t)r * sg;
+    double2* yr = yv + (size_t)r * sy;
+    for (int i = it - 1; i >= 0; --i) {
+        double2 acc = gr[i];
+        for (int c = i + 1; c < it; ++c) acc = csub(acc, cmul(Hr[(size_t)c * ldh + i], yr[c]));
+        double2 d = Hr[(size_t)i * ldh + i];
+        double dd = d.x * d.x + d.y * d.y;
+        yr[i] = make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd);
+    }
+}
+
+__global__ void k_combine_multi(int n, const int* its, const double2* __restrict__ V, size_t sv_r, size_t ldv,
+                                const double2* __restrict__ yv, size_t sy, double2* __restrict__ u, size_t su) {
+    const int r = blockIdx.y;
+    const int it = its[r];
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int j = 0; j < it; ++j) acc = cadd(acc, cmul(V[(size_t)r * sv_r + (size_t)j * ldv + q], yv[(size_t)r * sy + j]));
+    u[(size_t)r * su + q] = acc;
+}
+
+__global__ void k_gmres_init_multi(int R, double2* g, size_t sg, const double2* beta2, double* hist, size_t shist, int* active,
+                                   int* its) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    its[r] = 0;
+    g[(size_t)r * sg] = make_double2(sqrt(beta2[r].x), 0.0);
+    hist[(size_t)r * shist] = 1.0;
+    active[r] = beta2[r].x > 0.0 ? 1 : 0;
+}
+
 // ------------------------------------------------------------------ outputs
 __global__ void k_incident(int n, const double2* __restrict__ xy, double k, double dx, double dy, double2* __restrict__ b) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -764,9 +1546,9 @@ struct ls_op {
     // mesh and operator data
     DevBuf<double2> xy, m;
     DevBuf<double> w;
-    DevBuf<int64_t> rowptr;
-    DevBuf<int> cols;
-    DevBuf<double2> vals;
+    DevBuf<int64_t> rowptr, rowptrT;
+    DevBuf<int> cols, colsT;
+    DevBuf<double2> vals, valsT;         // dV and its transpose
     CsrC host_csr;
     std::vector<double> host_nodes, host_w;
     std::vector<std::complex<double>> host_m;
@@ -778,7 +1560,7 @@ struct ls_op {
     bool use_table = false;
     int tab_ncell = 0, tab_noct = 0, tab_blo = 0;
     size_t tab_bytes = 0;
-    double tab_err = 0;
+    double tab_err = 0, tab_tlo = 0, tab_thi = 0;
     DevBuf<double2> tab;
     // preconditioner
     bool has_prec = false;
@@ -789,18 +1571,36 @@ struct ls_op {
     DevBuf<int> tqc_ci;
     DevBuf<double> tqc_cv;
     DevBuf<double2> cband, Wf, Gf;
+    DevBuf<double2> WT, GT;              // transposed factors for P^T
+    DevBuf<double> tqcT_cv, tcqT_w;      // T_C^Q^T gather weights (psi), T_Q^C^T corner weights (psi / D)
     Stencil9 st{};
     DevBuf<double2> pg, pt, ptp;         // grid work vectors
     // GMRES workspace
     DevBuf<double2> Vb, H, cs, sn, g, hv, yv, tmp, tmp2, dpart, scal;
     DevBuf<double> hist;
     int dblk = 0;
+    // batched form: FP32 table and lock-step GMRES workspace for R systems
+    DevBuf<double2> tab32;
+    int t32_ncell = 0, t32_noct = 0, t32_blo = 0;
+    size_t t32_bytes = 0;
+    int bR = 0, b_nchunk = 1, b_spc = 0;
+    DevBuf<double2> bV, bH, bcs, bsn, bg, bhv, byv, btmp, bdpart, bscal, bpartial, bpg, bpt, bptp;
+    DevBuf<double> bhist;
+    DevBuf<int> bactive, bits;
+    // setup phase times (s): correction, grid transfers + stencil + C, block LU, H0 table
+    double t_setup[4] = {0, 0, 0, 0};
+    // CUDA graph of the preconditioner apply (fixed input/output buffers)
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gP = nullptr;
+    DevBuf<double2> pin, pout;
     // instrumentation: kernel launches on this operator, CUDA-event timing of the pair sum
     int64_t launches = 0, pairsum_launches = 0;
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
     ~ls_op() {
         for (auto& e : ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+        if (gP) cudaGraphExecDestroy(gP);
+        if (cap) cudaStreamDestroy(cap);
     }
 };
 
@@ -811,7 +1611,10 @@ static ls_status check_stream_sync(ls_op* op) {
 }
 
 // ------------------------------------------------------------------ building blocks
-static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m) {
+static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m, const double* w);
+static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m) { return launch_pairsum(op, f, m, op->w.p); }
+
+static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m, const double* w) {
     dim3 grid((op->nq + PS_TPB - 1) / PS_TPB, op->nchunk);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (op->timing && op->ev.size() < 65536) {
@@ -820,16 +1623,20 @@ static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m) {
         op->ev.emplace_back(e0, e1);
         CK(cudaEventRecord(e0, op->stream));
     }
-    if (op->mode == 2)
-        k_pairsum_f32<<<grid, PS_TPB, op->tab_bytes, op->stream>>>(op->xy.p, op->w.p, m, f, op->nq, op->src_per_chunk,
+    if (op->mode == 3)
+        k_pairsum_df<<<grid, PS_TPB, op->tab_bytes, op->stream>>>(op->xy.p, w, m, f, op->nq, op->src_per_chunk, op->k,
+                                                                   1.0 / op->k, (const float4*)op->tab.p, op->tab_ncell,
+                                                                   op->tab_noct, op->tab_blo, op->partial.p);
+    else if (op->mode == 2)
+        k_pairsum_f32<<<grid, PS_TPB, op->tab_bytes, op->stream>>>(op->xy.p, w, m, f, op->nq, op->src_per_chunk,
                                                                     op->k, 1.0 / op->k, (const float4*)op->tab.p,
                                                                     op->tab_ncell, op->tab_noct, op->tab_blo, op->partial.p);
     else if (op->use_table)
-        k_pairsum_tab<<<grid, PS_TPB, op->tab_bytes, op->stream>>>(op->xy.p, op->w.p, m, f, op->nq, op->src_per_chunk,
+        k_pairsum_tab<<<grid, PS_TPB, op->tab_bytes, op->stream>>>(op->xy.p, w, m, f, op->nq, op->src_per_chunk,
                                                                     op->k, 1.0 / op->k, op->tab.p, op->tab_ncell,
                                                                     op->tab_noct, op->tab_blo, op->partial.p);
     else
-        k_pairsum<<<grid, PS_TPB, 0, op->stream>>>(op->xy.p, op->w.p, m, f, op->nq, op->src_per_chunk, op->k, 1.0 / op->k,
+        k_pairsum<<<grid, PS_TPB, 0, op->stream>>>(op->xy.p, w, m, f, op->nq, op->src_per_chunk, op->k, 1.0 / op->k,
                                                    op->partial.p);
     CK(cudaGetLastError());
     if (e1) CK(cudaEventRecord(e1, op->stream));
@@ -850,20 +1657,73 @@ static ls_status apply_L(ls_op* op, const double2* x, double2* y) {
     return LS_OK;
 }
 
-static ls_status apply_P(ls_op* op, const double2* x, double2* z) {
+// The kernel sequence of P x (3 + 2 ny - 1 launches) on stream st.
+static void launch_P_kernels(ls_op* op, cudaStream_t st, const double2* x, double2* z) {
     const int nc = op->nx * op->ny, nx = op->nx, ny = op->ny;
-    k_tqc<<<(nc + 255) / 256, 256, 0, op->stream>>>(nc, op->tqc_rp.p, op->tqc_ci.p, op->tqc_cv.p, x, op->pg.p);
-    k_stencil<<<(nc + 255) / 256, 256, 0, op->stream>>>(nx, ny, op->st, op->pg.p, op->pt.p);
+    k_tqc<<<(nc + 255) / 256, 256, 0, st>>>(nc, op->tqc_rp.p, op->tqc_ci.p, op->tqc_cv.p, x, op->pg.p);
+    k_stencil<<<(nc + 255) / 256, 256, 0, st>>>(nx, ny, op->st, op->pg.p, op->pt.p);
     const int wpb = 8;                                   // warps per block in the block solve
     const int blocks = (nx + wpb - 1) / wpb;
     const size_t shm = sizeof(double2) * nx;
     for (int b = 0; b < ny; ++b)
-        k_bt_fwd<<<blocks, 32 * wpb, shm, op->stream>>>(nx, b, op->Wf.p, op->cband.p, op->pt.p, op->ptp.p);
+        k_bt_fwd<<<blocks, 32 * wpb, shm, st>>>(nx, b, op->Wf.p, op->cband.p, op->pt.p, op->ptp.p);
     for (int b = ny - 2; b >= 0; --b)
-        k_bt_bwd<<<blocks, 32 * wpb, shm, op->stream>>>(nx, b, op->Gf.p, op->ptp.p);
-    k_tcq<<<(op->nq + 255) / 256, 256, 0, op->stream>>>(op->nq, op->tcq_idx.p, op->tcq_w.p, op->ptp.p, op->pg.p, x, z);
-    CK(cudaGetLastError());
+        k_bt_bwd<<<blocks, 32 * wpb, shm, st>>>(nx, b, op->Gf.p, op->ptp.p);
+    k_tcq<<<(op->nq + 255) / 256, 256, 0, st>>>(op->nq, op->tcq_idx.p, op->tcq_w.p, op->ptp.p, op->pg.p, x, z);
+}
+
+// P x.  The sequence is captured once into a CUDA graph (on a private stream, with
+// fixed input/output buffers) and replayed; x and z are copied in and out.
+static ls_status apply_P(ls_op* op, const double2* x, double2* z) {
+    const int ny = op->ny;
+    if (!op->gP) {
+        if (!op->cap) CK(cudaStreamCreateWithFlags(&op->cap, cudaStreamNonBlocking));
+        CK(op->pin.alloc(op->nq));
+        CK(op->pout.alloc(op->nq));
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(op->cap, cudaStreamCaptureModeThreadLocal));
+        launch_P_kernels(op, op->cap, op->pin.p, op->pout.p);
+        CK(cudaStreamEndCapture(op->cap, &g));
+        cudaError_t e = cudaGraphInstantiate(&op->gP, g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+    }
+    CK(cudaMemcpyAsync(op->pin.p, x, sizeof(double2) * op->nq, cudaMemcpyDeviceToDevice, op->stream));
+    CK(cudaGraphLaunch(op->gP, op->stream));
+    CK(cudaMemcpyAsync(z, op->pout.p, sizeof(double2) * op->nq, cudaMemcpyDeviceToDevice, op->stream));
     op->launches += 3 + ny + (ny - 1);
+    return LS_OK;
+}
+
+// y = L^T x (mode 0) or y = V^T x (mode 2)
+static ls_status apply_LT(ls_op* op, const double2* x, double2* y, int mode = 0) {
+    ls_status s = launch_pairsum(op, x, nullptr, nullptr);
+    if (s != LS_OK) return s;
+    int threads = 256;
+    int blocks = (int)(((int64_t)op->nq * 32 + threads - 1) / threads);
+    k_applyT_epi<<<blocks, threads, 0, op->stream>>>(op->nq, op->nchunk, op->partial.p, op->rowptrT.p, op->colsT.p,
+                                                     op->valsT.p, op->m.p, op->w.p, x, op->k * op->k, y, mode);
+    CK(cudaGetLastError());
+    op->launches++;
+    return LS_OK;
+}
+
+// z = P^T x = x + T_Q^C^T (A^T C^{-T} - I) T_C^Q^T x
+static ls_status apply_PT(ls_op* op, const double2* x, double2* z) {
+    const int nc = op->nx * op->ny, nx = op->nx, ny = op->ny;
+    k_tqc<<<(nc + 255) / 256, 256, 0, op->stream>>>(nc, op->tqc_rp.p, op->tqc_ci.p, op->tqcT_cv.p, x, op->pg.p);
+    CK(cudaMemcpyAsync(op->ptp.p, op->pg.p, sizeof(double2) * nc, cudaMemcpyDeviceToDevice, op->stream));
+    const int wpb = 8;
+    const int blocks = (nx + wpb - 1) / wpb;
+    const size_t shm = sizeof(double2) * nx;
+    for (int b = 1; b < ny; ++b)
+        k_btT_fwd<<<blocks, 32 * wpb, shm, op->stream>>>(nx, b, op->GT.p, op->ptp.p);
+    for (int b = ny - 1; b >= 0; --b)
+        k_btT_bwd<<<blocks, 32 * wpb, shm, op->stream>>>(nx, ny, b, op->WT.p, op->cband.p, op->ptp.p, op->pt.p);
+    k_stencilT<<<(nc + 255) / 256, 256, 0, op->stream>>>(nx, ny, op->st, op->pt.p, op->pg.p, op->ptp.p);
+    k_tcq<<<(op->nq + 255) / 256, 256, 0, op->stream>>>(op->nq, op->tcq_idx.p, op->tcqT_w.p, op->ptp.p, nullptr, x, z);
+    CK(cudaGetLastError());
+    op->launches += 3 + (ny - 1) + ny;
     return LS_OK;
 }
 
@@ -883,7 +1743,9 @@ static ls_status dots(ls_op* op, int J, const double2* V, const double2* z, doub
     } while (0)
 
 // One GMRES solve for device rhs b -> u. Writes hist (host, may be null) and iterations.
-static ls_status gmres_one(ls_op* op, const double2* b, double2* u, double* hist_host, int* iters) {
+static ls_status gmres_one(ls_op* op, const double2* b, double2* u, double* hist_host, int* iters, bool transpose = false) {
+    auto opL = [&](const double2* x, double2* y) { return transpose ? apply_LT(op, x, y) : apply_L(op, x, y); };
+    auto opP = [&](const double2* x, double2* y) { return transpose ? apply_PT(op, x, y) : apply_P(op, x, y); };
     const int n = op->nq, maxit = op->prm.max_iter;
     const int ldh = maxit + 1;
     const size_t ldv = (size_t)n;
@@ -891,7 +1753,7 @@ static ls_status gmres_one(ls_op* op, const double2* b, double2* u, double* hist
     double2* V = op->Vb.p;
     CK(cudaMemsetAsync(op->H.p, 0, sizeof(double2) * (size_t)ldh * maxit, op->stream));
     // r0 = P b
-    if (op->has_prec && op->prm.use_precond) TRY(apply_P(op, b, op->tmp.p));
+    if (op->has_prec && op->prm.use_precond) TRY(opP(b, op->tmp.p));
     else CK(cudaMemcpyAsync(op->tmp.p, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, op->stream));
     TRY(dots(op, 1, op->tmp.p, op->tmp.p, op->scal.p, 0));       // scal[0] = ||r0||^2
     k_scale<<<nb, tpb, 0, op->stream>>>(n, op->tmp.p, op->scal.p, V, nullptr);
@@ -906,10 +1768,10 @@ static ls_status gmres_one(ls_op* op, const double2* b, double2* u, double* hist
         double2* vn = V + (size_t)(j + 1) * ldv;
         double2* hcol = op->H.p + (size_t)j * ldh;
         if (op->has_prec && op->prm.use_precond) {
-            TRY(apply_L(op, vj, op->tmp.p));
-            TRY(apply_P(op, op->tmp.p, vn));
+            TRY(opL(vj, op->tmp.p));
+            TRY(opP(op->tmp.p, vn));
         } else {
-            TRY(apply_L(op, vj, vn));
+            TRY(opL(vj, vn));
         }
         // classical Gram-Schmidt, twice
         TRY(dots(op, j + 1, V, vn, hcol, 0));
@@ -1004,7 +1866,43 @@ int32_t ls_mesh_num_nodes(const ls_mesh* mesh) { return mesh ? mesh->h.nq : 0; }
 int32_t ls_op_num_nodes(const ls_op* op) { return op ? op->nq : 0; }
 
 // Tabulated H0 for the pair sum: t from (1e-2 h_min)^2 to the squared bounding-box diagonal.
-static ls_status build_table(ls_op* op, const HostMesh& M, bool f32) {
+static ls_status build_table_range(ls_op* op, double t_lo, double t_hi, int mode);
+
+// FP32 table layout: coef [ncell][NC_F32] float2, cells (mid_hi, mid_lo, inv_hw, 0), oct (base, 23 - m)
+static ls_status upload_f32_table(const lsgpu::H0Table& T, DevBuf<double2>& buf, int& ncell, int& noct, int& blo,
+                                  size_t& bytes, double& err) {
+    ncell = (int)T.mid.size();
+    const int coef_f4 = (ncell * NC_F32 + 1) / 2;
+    std::vector<float4> hf((size_t)coef_f4 + ncell + (T.noct + 1) / 2, make_float4(0.f, 0.f, 0.f, 0.f));
+    float2* cf = reinterpret_cast<float2*>(hf.data());
+    for (size_t i = 0; i < (size_t)ncell * NC_F32; ++i) cf[i] = make_float2((float)T.coef[i].real(), (float)T.coef[i].imag());
+    for (int c = 0; c < ncell; ++c) {
+        float mh = (float)T.mid[c];
+        hf[(size_t)coef_f4 + c] = make_float4(mh, (float)(T.mid[c] - (double)mh), (float)T.inv_hw[c], 0.f);
+    }
+    int2* oct = reinterpret_cast<int2*>(hf.data() + coef_f4 + ncell);
+    for (int o = 0; o < T.noct; ++o) oct[o] = make_int2(T.oct_base[o], T.oct_shift[o] + 3);
+    noct = T.noct;
+    blo = T.b_lo - 1023 + 127;
+    err = T.max_rel_err;
+    bytes = hf.size() * sizeof(float4);
+    CK(buf.alloc((bytes + sizeof(double2) - 1) / sizeof(double2)));
+    CK(cudaMemcpy(buf.p, hf.data(), bytes, cudaMemcpyHostToDevice));
+    return LS_OK;
+}
+
+static ls_status ensure_table32(ls_op* op) {
+    if (op->t32_bytes) return LS_OK;
+    lsgpu::H0Table T;
+    std::string err = lsgpu::build_h0_table(op->k, op->tab_tlo, op->tab_thi, T, NC_F32, 2e-8);
+    if (!err.empty()) return fail(LS_EINVAL, err);
+    double e = 0;
+    TRY(upload_f32_table(T, op->tab32, op->t32_ncell, op->t32_noct, op->t32_blo, op->t32_bytes, e));
+    CK(raise_smem_limit(k_pairsum_multi_f32, op->t32_bytes));
+    return LS_OK;
+}
+
+static void table_range(ls_op* op, const HostMesh& M) {
     double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300, hmin = 1e300;
     for (int q = 0; q < M.nq; ++q) {
         xmin = std::min(xmin, M.nodes[2 * q]); xmax = std::max(xmax, M.nodes[2 * q]);
@@ -1019,32 +1917,50 @@ static ls_status build_table(ls_op* op, const HostMesh& M, bool f32) {
     }
     double t_hi = ((xmax - xmin) * (xmax - xmin) + (ymax - ymin) * (ymax - ymin)) * 1.0001;
     double t_lo = std::min(1e-2 * hmin * 1e-2 * hmin, t_hi / 4);
+    op->tab_tlo = t_lo;
+    op->tab_thi = t_hi;
+}
+
+static ls_status build_table_range(ls_op* op, double t_lo, double t_hi, int mode) {
+    const bool f32 = mode == 2;
     lsgpu::H0Table T;
     std::string err = f32 ? lsgpu::build_h0_table(op->k, t_lo, t_hi, T, NC_F32, 2e-8)
                           : lsgpu::build_h0_table(op->k, t_lo, t_hi, T);
     if (!err.empty()) return fail(LS_EINVAL, err);
     const int ncell = (int)T.mid.size();
-    if (f32) {
-        // float layout: coef [ncell][NC_F32] float2, cells (mid_hi, mid_lo, inv_hw, 0), oct (base, 23 - m)
-        const int coef_f4 = (ncell * NC_F32 + 1) / 2;
-        std::vector<float4> hf((size_t)coef_f4 + ncell + (T.noct + 1) / 2, make_float4(0.f, 0.f, 0.f, 0.f));
-        float2* cf = reinterpret_cast<float2*>(hf.data());
-        for (size_t i = 0; i < (size_t)ncell * NC_F32; ++i)
-            cf[i] = make_float2((float)T.coef[i].real(), (float)T.coef[i].imag());
-        for (int c = 0; c < ncell; ++c) {
-            float mh = (float)T.mid[c];
-            hf[(size_t)coef_f4 + c] = make_float4(mh, (float)(T.mid[c] - (double)mh), (float)T.inv_hw[c], 0.f);
+    if (mode == 3) {
+        std::vector<float4> hd((size_t)ncell * (NC_TAB + 1) + (T.noct + 1) / 2, make_float4(0.f, 0.f, 0.f, 0.f));
+        auto split = [](double x, float& h, float& l) { h = (float)x; l = (float)(x - (double)h); };
+        for (size_t i = 0; i < (size_t)ncell * NC_TAB; ++i) {
+            float a, b, c, d;
+            split(T.coef[i].real(), a, b);
+            split(T.coef[i].imag(), c, d);
+            hd[i] = make_float4(a, b, c, d);
         }
-        int2* oct = reinterpret_cast<int2*>(hf.data() + coef_f4 + ncell);
-        for (int o = 0; o < T.noct; ++o) oct[o] = make_int2(T.oct_base[o], T.oct_shift[o] + 3);   // 23 - m
+        for (int c = 0; c < ncell; ++c) {
+            float a, b;
+            split(T.mid[c], a, b);
+            hd[(size_t)ncell * NC_TAB + c] = make_float4(a, b, (float)T.inv_hw[c], 0.f);
+        }
+        int2* oct = reinterpret_cast<int2*>(hd.data() + (size_t)ncell * (NC_TAB + 1));
+        for (int o = 0; o < T.noct; ++o) oct[o] = make_int2(T.oct_base[o], T.oct_shift[o] + 3);
         op->tab_ncell = ncell;
         op->tab_noct = T.noct;
         op->tab_blo = T.b_lo - 1023 + 127;
         op->tab_err = T.max_rel_err;
-        op->tab_bytes = hf.size() * sizeof(float4);
+        op->tab_bytes = hd.size() * sizeof(float4);
+        if (op->tab_bytes > 200 * 1024) return fail(LS_EINVAL, "H0 table too large for shared memory");
         CK(op->tab.alloc((op->tab_bytes + sizeof(double2) - 1) / sizeof(double2)));
-        CK(cudaMemcpy(op->tab.p, hf.data(), op->tab_bytes, cudaMemcpyHostToDevice));
-        CK(cudaFuncSetAttribute(k_pairsum_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)op->tab_bytes));
+        CK(cudaMemcpy(op->tab.p, hd.data(), op->tab_bytes, cudaMemcpyHostToDevice));
+        CK(raise_smem_limit(k_pairsum_df, op->tab_bytes));
+        op->use_table = true;
+        return LS_OK;
+    }
+    if (f32) {
+        double err32 = 0;
+        TRY(upload_f32_table(T, op->tab, op->tab_ncell, op->tab_noct, op->tab_blo, op->tab_bytes, err32));
+        op->tab_err = err32;
+        CK(raise_smem_limit(k_pairsum_f32, op->tab_bytes));
         op->use_table = true;
         return LS_OK;
     }
@@ -1061,7 +1977,7 @@ static ls_status build_table(ls_op* op, const HostMesh& M, bool f32) {
     if (op->tab_bytes > 200 * 1024) return fail(LS_EINVAL, "H0 table too large for shared memory");
     CK(op->tab.alloc(h.size()));
     CK(cudaMemcpy(op->tab.p, h.data(), op->tab_bytes, cudaMemcpyHostToDevice));
-    CK(cudaFuncSetAttribute(k_pairsum_tab, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)op->tab_bytes));
+    CK(raise_smem_limit(k_pairsum_tab, op->tab_bytes));
     op->use_table = true;
     return LS_OK;
 }
@@ -1073,8 +1989,11 @@ static ls_status build_preconditioner(ls_op* op, const HostMesh& M, const double
         mg[i] = std::complex<double>(m_grid[2 * i], m_grid[2 * i + 1]);
         if (!std::isfinite(mg[i].real()) || !std::isfinite(mg[i].imag())) return fail(LS_EINVAL, "non-finite m_grid");
     }
+    auto tg0 = std::chrono::steady_clock::now();
     std::string err = lsgpu::build_grid(M, op->k, op->prm.box, op->prm.nx, op->prm.ny, mg.data(), G);
     if (!err.empty()) return fail(LS_EINVAL, err);
+    op->t_setup[1] = std::chrono::duration<double>(std::chrono::steady_clock::now() - tg0).count();
+    auto tl0 = std::chrono::steady_clock::now();
     const int nx = G.nx, ny = G.ny, nc = nx * ny;
     op->nx = nx; op->ny = ny;
     for (int s = 0; s < 9; ++s) op->st.v[s] = make_double2(G.v[s].real(), G.v[s].imag());
@@ -1090,6 +2009,16 @@ static ls_status build_preconditioner(ls_op* op, const HostMesh& M, const double
     CK(cudaMemcpy(op->tqc_ci.p, G.tqc_cols.data(), sizeof(int) * G.tqc_cols.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(op->tqc_cv.p, G.tqc_vals.data(), sizeof(double) * G.tqc_vals.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(op->cband.p, G.cband.data(), sizeof(double2) * G.cband.size(), cudaMemcpyHostToDevice));
+    {
+        std::vector<double> tT(G.tqc_vals.size()), cT(G.tcq_w.size());
+        for (int i = 0; i < nc; ++i)
+            for (int64_t e = G.tqc_rowptr[i]; e < G.tqc_rowptr[i + 1]; ++e) tT[e] = G.tqc_vals[e] * G.D[i];
+        for (size_t e = 0; e < cT.size(); ++e) cT[e] = G.tcq_w[e] / G.D[G.tcq_idx[e]];
+        CK(op->tqcT_cv.alloc(tT.size()));
+        CK(op->tcqT_w.alloc(cT.size()));
+        CK(cudaMemcpy(op->tqcT_cv.p, tT.data(), sizeof(double) * tT.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(op->tcqT_w.p, cT.data(), sizeof(double) * cT.size(), cudaMemcpyHostToDevice));
+    }
     CK(op->pg.alloc(nc));
     CK(op->pt.alloc(nc));
     CK(op->ptp.alloc(nc));
@@ -1123,7 +2052,16 @@ static ls_status build_preconditioner(ls_op* op, const HostMesh& M, const double
         k_store_W_G<<<grd, blk, 0, op->stream>>>(nx, b, ny, X.p, op->cband.p, op->Wf.p, op->Gf.p);
         CK(cudaGetLastError());
     }
+    CK(op->WT.alloc((size_t)ny * nx * nx));
+    CK(op->GT.alloc((size_t)ny * nx * nx));
+    {
+        dim3 tb(32, 8), tg((nx + 31) / 32, (nx + 31) / 32, ny);
+        k_transpose_blocks<<<tg, tb, 0, op->stream>>>(nx, ny, op->Wf.p, op->WT.p);
+        k_transpose_blocks<<<tg, tb, 0, op->stream>>>(nx, ny, op->Gf.p, op->GT.p);
+        CK(cudaGetLastError());
+    }
     CK(cudaStreamSynchronize(op->stream));
+    op->t_setup[2] = std::chrono::duration<double>(std::chrono::steady_clock::now() - tl0).count();
     op->has_prec = true;
     return LS_OK;
 }
@@ -1138,7 +2076,8 @@ ls_status ls_operator_create(const ls_mesh* mesh, double k, const double* m, con
     ls_params_default(&prm);
     if (params) prm = *params;
     if (prm.max_iter < 1 || !(prm.tol > 0) || !(prm.kappa > 0)) return fail(LS_EINVAL, "bad tol / max_iter / kappa");
-    if (prm.pairsum < 0 || prm.pairsum > 2) return fail(LS_EINVAL, "pairsum must be 0 (FP64 table), 1 (FP64 direct) or 2 (FP32)");
+    if (prm.pairsum < 0 || prm.pairsum > 3)
+        return fail(LS_EINVAL, "pairsum must be 0 (FP64 table), 1 (FP64 direct), 2 (FP32) or 3 (double-float)");
     if (prm.use_precond && !m_grid) return fail(LS_EINVAL, "m_grid is required with use_precond");
     const HostMesh& M = mesh->h;
     for (int q = 0; q < M.nq; ++q)
@@ -1152,7 +2091,9 @@ ls_status ls_operator_create(const ls_mesh* mesh, double k, const double* m, con
     op->stream = (cudaStream_t)stream;
     const int n = M.nq;
     // correction (host, extended precision)
+    auto tc0 = std::chrono::steady_clock::now();
     std::string err = lsgpu::build_correction(M, k, prm.kappa, op->host_csr);
+    op->t_setup[0] = std::chrono::duration<double>(std::chrono::steady_clock::now() - tc0).count();
     if (!err.empty()) return fail(LS_ESINGULAR, err);
     op->host_nodes = M.nodes;
     op->host_w = M.w;
@@ -1170,6 +2111,28 @@ ls_status ls_operator_create(const ls_mesh* mesh, double k, const double* m, con
     CK(cudaMemcpy(op->rowptr.p, op->host_csr.rowptr.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(op->cols.p, op->host_csr.cols.data(), sizeof(int) * op->host_csr.cols.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(op->vals.p, op->host_csr.vals.data(), sizeof(double2) * op->host_csr.vals.size(), cudaMemcpyHostToDevice));
+    {   // dV^T as CSR (rows = source nodes)
+        const CsrC& A = op->host_csr;
+        const size_t nnz = A.cols.size();
+        std::vector<int64_t> rp(n + 1, 0);
+        for (size_t e = 0; e < nnz; ++e) rp[A.cols[e] + 1]++;
+        for (int i = 0; i < n; ++i) rp[i + 1] += rp[i];
+        std::vector<int64_t> fill(rp.begin(), rp.end() - 1);
+        std::vector<int> ci(nnz);
+        std::vector<std::complex<double>> cv(nnz);
+        for (int r = 0; r < n; ++r)
+            for (int64_t e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) {
+                int64_t pos = fill[A.cols[e]]++;
+                ci[pos] = r;
+                cv[pos] = A.vals[e];
+            }
+        CK(op->rowptrT.alloc(n + 1));
+        CK(op->colsT.alloc(nnz));
+        CK(op->valsT.alloc(nnz));
+        CK(cudaMemcpy(op->rowptrT.p, rp.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(op->colsT.p, ci.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(op->valsT.p, cv.data(), sizeof(double2) * nnz, cudaMemcpyHostToDevice));
+    }
     // pair-sum decomposition: about 8 resident blocks per SM on 148 SMs
     int dev = 0, nsm = 148;
     CK(cudaGetDevice(&dev));
@@ -1183,7 +2146,10 @@ ls_status ls_operator_create(const ls_mesh* mesh, double k, const double* m, con
     op->src_per_chunk = spc;
     CK(op->partial.alloc((size_t)nchunk * n));
     op->mode = prm.pairsum;
-    if (prm.pairsum == 0 || prm.pairsum == 2) TRY(build_table(op, M, prm.pairsum == 2));
+    table_range(op, M);
+    auto tt0 = std::chrono::steady_clock::now();
+    if (prm.pairsum != 1) TRY(build_table_range(op, op->tab_tlo, op->tab_thi, prm.pairsum));
+    op->t_setup[3] = std::chrono::duration<double>(std::chrono::steady_clock::now() - tt0).count();
     // GMRES workspace
     const int maxit = prm.max_iter;
     CK(op->Vb.alloc((size_t)(maxit + 1) * n));
@@ -1246,6 +2212,354 @@ static ls_status farfield(ls_op* op, const double2* u, int n_ff, const double* a
     CK(cudaGetLastError());
     op->launches++;
     return LS_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batched form (host side)
+static ls_status ensure_batch(ls_op* op, int R) {
+    if (op->bR >= R) return LS_OK;
+    const int n = op->nq, maxit = op->prm.max_iter, ldh = maxit + 1;
+    int dev = 0, nsm = 148;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int tblocks = (n + PS_TPB - 1) / PS_TPB, rblocks = (R + MRB - 1) / MRB;
+    int nchunk = std::max(1, std::min(16, (nsm * 4 + tblocks * rblocks - 1) / (tblocks * rblocks)));
+    int spc = (n + nchunk - 1) / nchunk;
+    spc = ((spc + PS_TILE - 1) / PS_TILE) * PS_TILE;
+    op->b_nchunk = (n + spc - 1) / spc;
+    op->b_spc = spc;
+    CK(op->bV.alloc((size_t)R * (maxit + 1) * n));
+    CK(op->bH.alloc((size_t)R * ldh * maxit));
+    CK(op->bcs.alloc((size_t)R * (maxit + 2)));
+    CK(op->bsn.alloc((size_t)R * (maxit + 2)));
+    CK(op->bg.alloc((size_t)R * (maxit + 2)));
+    CK(op->bhv.alloc((size_t)R * (maxit + 1)));
+    CK(op->byv.alloc((size_t)R * (maxit + 1)));
+    CK(op->btmp.alloc((size_t)R * n));
+    CK(op->bdpart.alloc((size_t)R * (maxit + 1) * op->dblk));
+    CK(op->bscal.alloc((size_t)2 * R));
+    CK(op->bpartial.alloc((size_t)R * op->b_nchunk * n));
+    CK(op->bhist.alloc((size_t)R * (maxit + 2)));
+    CK(op->bactive.alloc(R));
+    CK(op->bits.alloc(R));
+    if (op->has_prec) {
+        const size_t nc = (size_t)op->nx * op->ny;
+        CK(op->bpg.alloc(R * nc));
+        CK(op->bpt.alloc(R * nc));
+        CK(op->bptp.alloc(R * nc));
+    }
+    op->bR = R;
+    return LS_OK;
+}
+
+static MultiArgs multi_args(ls_op* op, int R, const double2* f, size_t sf, const double2* m) {
+    MultiArgs A;
+    A.xy = op->xy.p; A.w = op->w.p; A.m = m; A.f = f; A.sf = sf;
+    A.n = op->nq; A.R = R; A.spc = op->b_spc; A.nchunk = op->b_nchunk;
+    A.k = op->k; A.inv_k = 1.0 / op->k;
+    A.ncell = op->t32_ncell; A.noct = op->t32_noct; A.b_lo = op->t32_blo;
+    A.partial = op->bpartial.p;
+    return A;
+}
+
+// partial[r][c][j] for R densities f (stride sf)
+static ls_status pairsum_batch(ls_op* op, int R, const double2* f, size_t sf, const double2* m) {
+    TRY(ensure_table32(op));
+    dim3 grid((op->nq + PS_TPB - 1) / PS_TPB, op->b_nchunk, (R + MRB - 1) / MRB);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (op->timing && op->ev.size() < 65536) {
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        op->ev.emplace_back(e0, e1);
+        CK(cudaEventRecord(e0, op->stream));
+    }
+    k_pairsum_multi_f32<<<grid, PS_TPB, op->t32_bytes, op->stream>>>(multi_args(op, R, f, sf, m), (const float4*)op->tab32.p);
+    CK(cudaGetLastError());
+    if (e1) CK(cudaEventRecord(e1, op->stream));
+    op->launches++;
+    op->pairsum_launches++;
+    return LS_OK;
+}
+
+static ls_status apply_L_batch(ls_op* op, int R, const double2* x, size_t sx, double2* y, size_t sy) {
+    TRY(pairsum_batch(op, R, x, sx, op->m.p));
+    dim3 grid((unsigned)(((int64_t)op->nq * 32 + 255) / 256), R);
+    k_apply_epi_multi<<<grid, 256, 0, op->stream>>>(op->nq, op->b_nchunk, op->bpartial.p, op->rowptr.p, op->cols.p,
+                                                    op->vals.p, op->m.p, x, sx, op->k * op->k, y, sy);
+    CK(cudaGetLastError());
+    op->launches++;
+    return LS_OK;
+}
+
+static ls_status apply_P_batch(ls_op* op, int R, const double2* x, size_t sx, double2* z, size_t sz) {
+    const int nx = op->nx, ny = op->ny, nc = nx * ny;
+    dim3 gc((nc + 255) / 256, R);
+    k_tqc_multi<<<gc, 256, 0, op->stream>>>(nc, op->tqc_rp.p, op->tqc_ci.p, op->tqc_cv.p, x, sx, op->bpg.p);
+    k_stencil_multi<<<gc, 256, 0, op->stream>>>(nx, ny, op->st, op->bpg.p, op->bpt.p);
+    const int wpb = 8;
+    dim3 gb((nx + wpb - 1) / wpb, R);
+    const size_t shm = sizeof(double2) * nx;
+    for (int b = 0; b < ny; ++b)
+        k_bt_fwd_multi<<<gb, 32 * wpb, shm, op->stream>>>(nx, ny, b, op->Wf.p, op->cband.p, op->bpt.p, op->bptp.p);
+    for (int b = ny - 2; b >= 0; --b)
+        k_bt_bwd_multi<<<gb, 32 * wpb, shm, op->stream>>>(nx, ny, b, op->Gf.p, op->bptp.p);
+    dim3 gq((op->nq + 255) / 256, R);
+    k_tcq_multi<<<gq, 256, 0, op->stream>>>(op->nq, nc, op->tcq_idx.p, op->tcq_w.p, op->bptp.p, op->bpg.p, x, sx, z, sz);
+    CK(cudaGetLastError());
+    op->launches += 3 + ny + (ny - 1);
+    return LS_OK;
+}
+
+// R lock-step GMRES solves (each system its own Krylov space, Hessenberg and stop),
+// split in stages so that several operators can share one pair-sum launch.
+static ls_status gb_begin(ls_op* op, int R, const double2* b) {
+    TRY(ensure_batch(op, R));
+    const int n = op->nq, maxit = op->prm.max_iter, ldh = maxit + 1;
+    const size_t ldv = (size_t)n, svr = (size_t)(maxit + 1) * n, sH = (size_t)ldh * maxit, sg = maxit + 2;
+    const bool prec = op->has_prec && op->prm.use_precond;
+    const int tpb = 256, nb = (n + tpb - 1) / tpb;
+    CK(cudaMemsetAsync(op->bH.p, 0, sizeof(double2) * R * sH, op->stream));
+    if (prec) TRY(apply_P_batch(op, R, b, n, op->btmp.p, n));
+    else CK(cudaMemcpyAsync(op->btmp.p, b, sizeof(double2) * R * n, cudaMemcpyDeviceToDevice, op->stream));
+    dim3 gd(op->dblk, R), gn(nb, R);
+    k_dots_multi<<<gd, RED_TPB, 0, op->stream>>>(n, 1, op->btmp.p, n, ldv, op->btmp.p, n, op->bdpart.p, nullptr);
+    k_sumrows_multi<<<dim3(1, R), 128, 0, op->stream>>>(1, op->dblk, op->bdpart.p, op->bscal.p, 1, 0, nullptr);
+    k_scale_multi<<<gn, tpb, 0, op->stream>>>(n, op->btmp.p, n, op->bscal.p, op->bV.p, svr, nullptr, 0, nullptr);
+    k_gmres_init_multi<<<(R + 127) / 128, 128, 0, op->stream>>>(R, op->bg.p, sg, op->bscal.p, op->bhist.p, sg,
+                                                                op->bactive.p, op->bits.p);
+    CK(cudaGetLastError());
+    op->launches += 4;
+    return LS_OK;
+}
+
+// Everything of iteration j after the pair sum (partials in op->bpartial).
+static ls_status gb_after_pairsum(ls_op* op, int R, int j) {
+    const int n = op->nq, maxit = op->prm.max_iter, ldh = maxit + 1;
+    const size_t ldv = (size_t)n, svr = (size_t)(maxit + 1) * n, sH = (size_t)ldh * maxit, sg = maxit + 2;
+    const bool prec = op->has_prec && op->prm.use_precond;
+    const int tpb = 256, nb = (n + tpb - 1) / tpb;
+    double2* V = op->bV.p;
+    double2* vj = V + (size_t)j * ldv;
+    double2* vn = V + (size_t)(j + 1) * ldv;
+    double2* hcol = op->bH.p + (size_t)j * ldh;
+    dim3 ge((unsigned)(((int64_t)n * 32 + 255) / 256), R);
+    k_apply_epi_multi<<<ge, 256, 0, op->stream>>>(n, op->b_nchunk, op->bpartial.p, op->rowptr.p, op->cols.p, op->vals.p,
+                                                  op->m.p, vj, svr, op->k * op->k, prec ? op->btmp.p : vn,
+                                                  prec ? (size_t)n : svr);
+    op->launches++;
+    if (prec) TRY(apply_P_batch(op, R, op->btmp.p, n, vn, svr));
+    const int J = j + 1;
+    dim3 gd(op->dblk, R), gn(nb, R), gs((J + 127) / 128, R);
+    k_dots_multi<<<gd, RED_TPB, 0, op->stream>>>(n, J, V, svr, ldv, vn, svr, op->bdpart.p, op->bactive.p);
+    k_sumrows_multi<<<gs, 128, 0, op->stream>>>(J, op->dblk, op->bdpart.p, hcol, sH, 0, op->bactive.p);
+    k_update_multi<<<gn, tpb, sizeof(double2) * J, op->stream>>>(n, J, V, svr, ldv, hcol, sH, vn, svr, op->bactive.p);
+    k_dots_multi<<<gd, RED_TPB, 0, op->stream>>>(n, J, V, svr, ldv, vn, svr, op->bdpart.p, op->bactive.p);
+    k_sumrows_multi<<<gs, 128, 0, op->stream>>>(J, op->dblk, op->bdpart.p, op->bhv.p, J, 0, op->bactive.p);
+    k_update_multi<<<gn, tpb, sizeof(double2) * J, op->stream>>>(n, J, V, svr, ldv, op->bhv.p, J, vn, svr, op->bactive.p);
+    k_sumrows_multi<<<gs, 128, 0, op->stream>>>(J, 1, op->bhv.p, hcol, sH, 1, op->bactive.p);
+    k_dots_multi<<<gd, RED_TPB, 0, op->stream>>>(n, 1, vn, svr, ldv, vn, svr, op->bdpart.p, op->bactive.p);
+    k_sumrows_multi<<<dim3(1, R), 128, 0, op->stream>>>(1, op->dblk, op->bdpart.p, op->bscal.p + R, 1, 0, op->bactive.p);
+    k_scale_multi<<<gn, tpb, 0, op->stream>>>(n, vn, svr, op->bscal.p + R, vn, svr, hcol + j + 1, sH, op->bactive.p);
+    k_givens_multi<<<(R + 127) / 128, 128, 0, op->stream>>>(R, j, op->bH.p, sH, ldh, op->bcs.p, op->bsn.p, op->bg.p, sg,
+                                                            op->bhist.p, sg, op->bscal.p, op->prm.tol, op->bactive.p,
+                                                            op->bits.p);
+    CK(cudaGetLastError());
+    op->launches += 11;
+    return LS_OK;
+}
+
+static ls_status gb_active(ls_op* op, int R, std::vector<int>& act, bool& any) {
+    act.resize(R);
+    CK(cudaMemcpyAsync(act.data(), op->bactive.p, sizeof(int) * R, cudaMemcpyDeviceToHost, op->stream));
+    CK(cudaStreamSynchronize(op->stream));
+    any = false;
+    for (int r = 0; r < R; ++r) any = any || act[r];
+    return LS_OK;
+}
+
+static ls_status gb_finish(ls_op* op, int R, double2* u, int* iters, bool& all_conv) {
+    const int n = op->nq, maxit = op->prm.max_iter, ldh = maxit + 1;
+    const size_t ldv = (size_t)n, svr = (size_t)(maxit + 1) * n, sH = (size_t)ldh * maxit, sg = maxit + 2;
+    const int tpb = 256, nb = (n + tpb - 1) / tpb;
+    k_backsolve_multi<<<(R + 127) / 128, 128, 0, op->stream>>>(R, op->bits.p, op->bH.p, sH, ldh, op->bg.p, sg, op->byv.p,
+                                                               maxit + 1);
+    k_combine_multi<<<dim3(nb, R), tpb, 0, op->stream>>>(n, op->bits.p, op->bV.p, svr, ldv, op->byv.p, maxit + 1, u, n);
+    CK(cudaGetLastError());
+    op->launches += 2;
+    std::vector<int> its(R), act;
+    bool any = false;
+    TRY(gb_active(op, R, act, any));
+    CK(cudaMemcpyAsync(its.data(), op->bits.p, sizeof(int) * R, cudaMemcpyDeviceToHost, op->stream));
+    CK(cudaStreamSynchronize(op->stream));
+    for (int r = 0; r < R; ++r)
+        if (iters) iters[r] = its[r];
+    all_conv = !any;
+    return LS_OK;
+}
+
+static ls_status gmres_batch(ls_op* op, int R, const double2* b, double2* u, int* iters) {
+    TRY(gb_begin(op, R, b));
+    const size_t svr = (size_t)(op->prm.max_iter + 1) * op->nq;
+    std::vector<int> act;
+    for (int j = 0; j < op->prm.max_iter; ++j) {
+        TRY(pairsum_batch(op, R, op->bV.p + (size_t)j * op->nq, svr, op->m.p));
+        TRY(gb_after_pairsum(op, R, j));
+        bool any = false;
+        TRY(gb_active(op, R, act, any));
+        if (!any) break;
+    }
+    bool all = false;
+    TRY(gb_finish(op, R, u, iters, all));
+    return all ? LS_OK : LS_ENOCONV;
+}
+
+// Several operators (scatterers) solved in lock step: each iteration one persistent
+// pair-sum launch covers every operator with an unconverged system.  The grid size
+// of that launch is chosen once per call by timing candidate resident-block counts
+// on the first iteration (the pair sum is idempotent, so the trial launches only
+// cost time).
+static ls_status solve_multi(int S, ls_op* const* ops, int R, const double2* const* b, double2* const* u, int* iters,
+                             bool& all_conv) {
+    cudaStream_t st = ops[0]->stream;
+    for (int s = 0; s < S; ++s) {
+        if (!ops[s]) return fail(LS_EINVAL, "null operator");
+        if (ops[s]->stream != st) return fail(LS_EINVAL, "all operators must share one stream");
+        TRY(ensure_batch(ops[s], R));
+        TRY(ensure_table32(ops[s]));
+    }
+    size_t max_tab = 0;
+    for (int s = 0; s < S; ++s) max_tab = std::max(max_tab, ops[s]->t32_bytes);
+    CK(raise_smem_limit(k_pairsum_persist, max_tab));
+    int dev = 0, nsm = 148, occ = 1;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pairsum_persist, PS_TPB, max_tab));
+    occ = std::max(occ, 1);
+    for (int s = 0; s < S; ++s) TRY(gb_begin(ops[s], R, b[s]));
+    DevBuf<PSDesc> ddesc;
+    DevBuf<int> counter;
+    CK(ddesc.alloc(S));
+    CK(counter.alloc(1));
+    std::vector<PSDesc> hd(S);
+    std::vector<char> done(S, 0);
+    std::vector<int> act;
+    int grid_blocks = nsm * occ;
+    const int maxit = ops[0]->prm.max_iter;
+    for (int s = 1; s < S; ++s)
+        if (ops[s]->prm.max_iter != maxit) return fail(LS_EINVAL, "all operators must share max_iter");
+    for (int j = 0; j < maxit; ++j) {
+        int nd = 0, total = 0;
+        std::vector<int> which;
+        for (int s = 0; s < S; ++s) {
+            if (done[s]) continue;
+            ls_op* op = ops[s];
+            const size_t svr = (size_t)(maxit + 1) * op->nq;
+            PSDesc d;
+            d.a = multi_args(op, R, op->bV.p + (size_t)j * op->nq, svr, op->m.p);
+            d.tab = (const float4*)op->tab32.p;
+            d.tab_words = (int)(op->t32_bytes / sizeof(float4));
+            d.tblocks = (op->nq + PS_TPB - 1) / PS_TPB;
+            d.units = d.tblocks * op->b_nchunk * ((R + MRB - 1) / MRB);
+            d.unit_begin = total;
+            total += d.units;
+            hd[nd++] = d;
+            which.push_back(s);
+        }
+        if (nd == 0) break;
+        CK(cudaMemcpyAsync(ddesc.p, hd.data(), sizeof(PSDesc) * nd, cudaMemcpyHostToDevice, st));
+        if (j == 0) {   // autotune the resident grid: candidates 1/2, 1 and 2 blocks per resident slot
+            float best = 1e30f;
+            int cand[3] = {std::max(1, nsm * occ / 2), nsm * occ, nsm * occ * 2};
+            cudaEvent_t e0, e1;
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            for (int c = 0; c < 3; ++c) {
+                CK(cudaMemsetAsync(counter.p, 0, sizeof(int), st));
+                CK(cudaEventRecord(e0, st));
+                k_pairsum_persist<<<cand[c], PS_TPB, max_tab, st>>>(ddesc.p, nd, total, counter.p);
+                CK(cudaEventRecord(e1, st));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) { best = ms; grid_blocks = cand[c]; }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            for (int s = 0; s < S; ++s) ops[s]->launches += 3;
+        }
+        CK(cudaMemsetAsync(counter.p, 0, sizeof(int), st));
+        k_pairsum_persist<<<grid_blocks, PS_TPB, max_tab, st>>>(ddesc.p, nd, total, counter.p);
+        CK(cudaGetLastError());
+        ops[which[0]]->launches++;
+        ops[which[0]]->pairsum_launches++;
+        for (int s : which) TRY(gb_after_pairsum(ops[s], R, j));
+        for (int s : which) {
+            bool any = false;
+            TRY(gb_active(ops[s], R, act, any));
+            if (!any) done[s] = 1;
+        }
+    }
+    all_conv = true;
+    for (int s = 0; s < S; ++s) {
+        bool c = false;
+        TRY(gb_finish(ops[s], R, u[s], iters ? iters + (size_t)s * R : nullptr, c));
+        all_conv = all_conv && c;
+    }
+    return LS_OK;
+}
+
+extern "C" {
+
+ls_status ls_pairsum_batch_dev(ls_op* op, int32_t R, const void* f_dev, void* y_dev) {
+    if (!op || R < 1 || !f_dev || !y_dev) return fail(LS_EINVAL, "null argument or R < 1");
+    TRY(ensure_batch(op, R));
+    TRY(pairsum_batch(op, R, (const double2*)f_dev, op->nq, nullptr));
+    // y_r = (i/4) sum_c partial: the batched epilogue with k2 = 0 and x = 0 would add x; use the
+    // single epilogue in mode 1 per system instead
+    int threads = 256;
+    int blocks = (int)(((int64_t)op->nq * 32 + threads - 1) / threads);
+    for (int r = 0; r < R; ++r)
+        k_apply_epi<<<blocks, threads, 0, op->stream>>>(op->nq, op->b_nchunk, op->bpartial.p + (size_t)r * op->b_nchunk * op->nq,
+                                                        nullptr, nullptr, nullptr, nullptr, nullptr, 0.0,
+                                                        (double2*)y_dev + (size_t)r * op->nq, 1);
+    CK(cudaGetLastError());
+    return check_stream_sync(op);
+}
+
+ls_status ls_solve_multi_dev(int32_t S, ls_op* const* ops, int32_t R, const void* const* b_devs, void* const* u_devs,
+                             int32_t* iters_out) {
+    if (S < 1 || !ops || R < 1 || !b_devs || !u_devs) return fail(LS_EINVAL, "null argument or bad size");
+    for (int s = 0; s < S; ++s)
+        if (!ops[s] || !b_devs[s] || !u_devs[s]) return fail(LS_EINVAL, "null operator or buffer");
+    bool all = false;
+    std::vector<int> its((size_t)S * R);
+    TRY(solve_multi(S, ops, R, reinterpret_cast<const double2* const*>(b_devs), reinterpret_cast<double2* const*>(u_devs),
+                    its.data(), all));
+    if (iters_out) for (size_t i = 0; i < its.size(); ++i) iters_out[i] = its[i];
+    CK(cudaStreamSynchronize(ops[0]->stream));
+    if (!all) return fail(LS_ENOCONV, "GMRES reached max_iter");
+    return LS_OK;
+}
+
+ls_status ls_solve_batch_dev(ls_op* op, int32_t R, const void* b_dev, void* u_dev, int32_t n_ff, const double* ff_angles,
+                             void* uinf_dev, int32_t* iters_out) {
+    if (!op || R < 1 || !b_dev || !u_dev) return fail(LS_EINVAL, "null argument or R < 1");
+    if (n_ff > 0 && (!ff_angles || !uinf_dev)) return fail(LS_EINVAL, "far-field buffers missing");
+    std::vector<int> its(R);
+    ls_status s = gmres_batch(op, R, (const double2*)b_dev, (double2*)u_dev, its.data());
+    if (s != LS_OK && s != LS_ENOCONV) return s;
+    if (iters_out) for (int r = 0; r < R; ++r) iters_out[r] = its[r];
+    if (n_ff > 0) {
+        DevBuf<double> ang;
+        CK(ang.alloc(n_ff));
+        CK(cudaMemcpy(ang.p, ff_angles, sizeof(double) * n_ff, cudaMemcpyHostToDevice));
+        for (int r = 0; r < R; ++r)
+            TRY(farfield(op, (const double2*)u_dev + (size_t)r * op->nq, n_ff, ang.p, (double2*)uinf_dev + (size_t)r * n_ff));
+    }
+    TRY(check_stream_sync(op));
+    if (s == LS_ENOCONV) fail(s, "GMRES reached max_iter");
+    return s;
 }
 
 ls_status ls_solve_dev(ls_op* op, int32_t R, const void* b_dev, void* u_dev, int32_t n_ff, const double* ff_angles,
@@ -1335,6 +2649,119 @@ ls_status ls_correction_host(const ls_mesh* mesh, double k, double kappa, int64_
     if (rowptr) std::memcpy(rowptr, csr.rowptr.data(), sizeof(int64_t) * csr.rowptr.size());
     if (cols) std::memcpy(cols, csr.cols.data(), sizeof(int32_t) * csr.cols.size());
     if (vals) std::memcpy(vals, csr.vals.data(), sizeof(double) * 2 * csr.vals.size());
+    return LS_OK;
+}
+
+ls_status ls_apply_transpose_dev(ls_op* op, const void* x_dev, void* y_dev) {
+    if (!op || !x_dev || !y_dev) return fail(LS_EINVAL, "null argument");
+    if (x_dev == y_dev) return fail(LS_EINVAL, "x and y may not alias");
+    TRY(apply_LT(op, (const double2*)x_dev, (double2*)y_dev, 0));
+    return check_stream_sync(op);
+}
+
+ls_status ls_potential_transpose_dev(ls_op* op, const void* x_dev, void* y_dev) {
+    if (!op || !x_dev || !y_dev) return fail(LS_EINVAL, "null argument");
+    if (x_dev == y_dev) return fail(LS_EINVAL, "x and y may not alias");
+    TRY(apply_LT(op, (const double2*)x_dev, (double2*)y_dev, 2));
+    return check_stream_sync(op);
+}
+
+ls_status ls_apply_precond_transpose_dev(ls_op* op, const void* x_dev, void* y_dev) {
+    if (!op || !x_dev || !y_dev) return fail(LS_EINVAL, "null argument");
+    if (!op->has_prec) return fail(LS_EINVAL, "operator was built without a preconditioner");
+    if (x_dev == y_dev) return fail(LS_EINVAL, "x and y may not alias");
+    TRY(apply_PT(op, (const double2*)x_dev, (double2*)y_dev));
+    return check_stream_sync(op);
+}
+
+ls_status ls_solve_transpose_dev(ls_op* op, int32_t R, const void* g_dev, void* lambda_dev, int32_t* iters_out) {
+    if (!op || R < 1 || !g_dev || !lambda_dev) return fail(LS_EINVAL, "null argument or R < 1");
+    ls_status worst = LS_OK;
+    for (int r = 0; r < R; ++r) {
+        int it = 0;
+        ls_status s = gmres_one(op, (const double2*)g_dev + (size_t)r * op->nq, (double2*)lambda_dev + (size_t)r * op->nq,
+                                nullptr, &it, true);
+        if (s != LS_OK && s != LS_ENOCONV) return s;
+        if (s == LS_ENOCONV) worst = s;
+        if (iters_out) iters_out[r] = it;
+    }
+    TRY(check_stream_sync(op));
+    if (worst != LS_OK) fail(worst, "GMRES reached max_iter");
+    return worst;
+}
+
+ls_status ls_op_set_contrast(ls_op* op, const double* m) {
+    if (!op || !m) return fail(LS_EINVAL, "null argument");
+    for (int q = 0; q < op->nq; ++q)
+        if (!std::isfinite(m[2 * q]) || !std::isfinite(m[2 * q + 1])) return fail(LS_EINVAL, "non-finite contrast");
+    CK(cudaMemcpyAsync(op->m.p, m, sizeof(double2) * op->nq, cudaMemcpyHostToDevice, op->stream));
+    for (int q = 0; q < op->nq; ++q) op->host_m[q] = std::complex<double>(m[2 * q], m[2 * q + 1]);
+    return check_stream_sync(op);
+}
+
+ls_status ls_incident_dev(ls_op* op, int32_t R, const double* dir_angles, void* b_dev) {
+    if (!op || R < 1 || !dir_angles || !b_dev) return fail(LS_EINVAL, "null argument or R < 1");
+    for (int r = 0; r < R; ++r) {
+        k_incident<<<(op->nq + 255) / 256, 256, 0, op->stream>>>(op->nq, op->xy.p, op->k, std::cos(dir_angles[r]),
+                                                                 std::sin(dir_angles[r]), (double2*)b_dev + (size_t)r * op->nq);
+        CK(cudaGetLastError());
+        op->launches++;
+    }
+    return check_stream_sync(op);
+}
+
+ls_status ls_misfit_gradient_dev(ls_op* op, int32_t R, const void* u_dev, int32_t n_ff, const double* ff_angles,
+                                 const void* resid_dev, double* grad_dev, int32_t* iters_out) {
+    if (!op || R < 1 || !u_dev || n_ff < 1 || !ff_angles || !resid_dev || !grad_dev)
+        return fail(LS_EINVAL, "null argument or bad size");
+    const int n = op->nq;
+    DevBuf<double> ang;
+    DevBuf<double2> g, rhs, lam, vtl;
+    CK(ang.alloc(n_ff));
+    CK(g.alloc(n));
+    CK(rhs.alloc(n));
+    CK(lam.alloc(n));
+    CK(vtl.alloc(n));
+    CK(cudaMemcpy(ang.p, ff_angles, sizeof(double) * n_ff, cudaMemcpyHostToDevice));
+    CK(cudaMemsetAsync(grad_dev, 0, sizeof(double) * n, op->stream));
+    ls_status worst = LS_OK;
+    const int nb = (n + 255) / 256;
+    for (int r = 0; r < R; ++r) {
+        const double2* u = (const double2*)u_dev + (size_t)r * n;
+        k_farfieldT<<<nb, 256, 0, op->stream>>>(n, op->xy.p, op->w.p, op->k, n_ff, ang.p,
+                                               (const double2*)resid_dev + (size_t)r * n_ff, g.p);
+        k_cmul_vec<<<nb, 256, 0, op->stream>>>(n, op->m.p, g.p, rhs.p);
+        CK(cudaGetLastError());
+        op->launches += 2;
+        int it = 0;
+        ls_status s = gmres_one(op, rhs.p, lam.p, nullptr, &it, true);
+        if (s != LS_OK && s != LS_ENOCONV) return s;
+        if (s == LS_ENOCONV) worst = s;
+        if (iters_out) iters_out[r] = it;
+        TRY(apply_LT(op, lam.p, vtl.p, 2));
+        k_grad_acc<<<nb, 256, 0, op->stream>>>(n, u, g.p, vtl.p, op->k * op->k, grad_dev);
+        CK(cudaGetLastError());
+        op->launches++;
+    }
+    TRY(check_stream_sync(op));
+    if (worst != LS_OK) fail(worst, "adjoint GMRES reached max_iter");
+    return worst;
+}
+
+ls_status ls_op_set_pairsum(ls_op* op, int32_t mode) {
+    if (!op) return fail(LS_EINVAL, "null op");
+    if (mode < 0 || mode > 3) return fail(LS_EINVAL, "pairsum must be 0, 1, 2 or 3");
+    CK(cudaStreamSynchronize(op->stream));
+    if (mode != 1 && !(op->tab_thi > 0)) return fail(LS_EINVAL, "operator has no table range (built with pairsum = 1)");
+    op->use_table = false;
+    if (mode != 1) TRY(build_table_range(op, op->tab_tlo, op->tab_thi, mode));
+    op->mode = mode;
+    return LS_OK;
+}
+
+ls_status ls_op_setup_times(const ls_op* op, double* t4) {
+    if (!op || !t4) return fail(LS_EINVAL, "null argument");
+    for (int i = 0; i < 4; ++i) t4[i] = op->t_setup[i];
     return LS_OK;
 }
 

@@ -47,21 +47,37 @@ static const ld PI_L = 3.141592653589793238462643383279502884L;
 static const ld EG_L = 0.577215664901532860606512090082402431L;
 
 // ---------------------------------------------------------------- Hankel
+struct SeriesTables {            // 1/k^2, 1/(k(k+1)), H_k and H_k + H_{k+1} for k = 1..40
+    ld rk2[41], rkk1[41], hk[41], hh[41];
+    SeriesTables() {
+        ld h = 0;
+        for (int k = 1; k <= 40; ++k) {
+            rk2[k] = 1.0L / ((ld)k * k);
+            rkk1[k] = 1.0L / ((ld)k * (k + 1));
+            h += 1.0L / k;
+            hk[k] = h;
+            hh[k] = 2 * h + 1.0L / (k + 1);
+        }
+    }
+};
+static const SeriesTables& series_tables() { static SeriesTables t; return t; }
+
 static void series01(ld z, ld& j0, ld& j1, ld& y0, ld& y1) {
+    const SeriesTables& T = series_tables();
     ld q = z * z / 4;
     ld t0 = 1, t1 = 1;          // (-q)^k/(k!)^2 and (-q)^k/(k!(k+1)!)
     ld s0 = 1, s1 = 1;          // J0, J1/(z/2)
     ld hk = 0;                  // H_k
     ld a0 = 0;                  // sum_{k>=1} H_k (-q)^k/(k!)^2
     ld a1 = 1;                  // sum_{k>=0} (H_k + H_{k+1}) (-q)^k/(k!(k+1)!)
+    (void)hk;
     for (int k = 1; k <= 40; ++k) {
-        t0 *= -q / ((ld)k * k);
-        t1 *= -q / ((ld)k * (k + 1));
+        t0 *= -q * T.rk2[k];
+        t1 *= -q * T.rkk1[k];
         s0 += t0;
         s1 += t1;
-        hk += 1.0L / k;
-        a0 += hk * t0;
-        a1 += (2 * hk + 1.0L / (k + 1)) * t1;
+        a0 += T.hk[k] * t0;
+        a1 += T.hh[k] * t1;
         if (std::fabs(t0) < 1e-24L && std::fabs(t1) < 1e-24L) break;
     }
     ld L = std::log(z / 2) + EG_L;
@@ -72,8 +88,9 @@ static void series01(ld z, ld& j0, ld& j1, ld& y0, ld& y1) {
 }
 
 static void miller01(ld z, ld& j0, ld& j1, ld& y0, ld& y1) {
-    int nstart = 2 * ((int)(z + 56) / 2);
-    std::vector<ld> J(nstart + 2, 0.0L);
+    int nstart = 2 * ((int)(z + 56) / 2);          // z < 30 here, so nstart <= 86
+    ld J[96];
+    for (int i = 0; i < nstart + 2; ++i) J[i] = 0.0L;
     J[nstart] = 1e-300L;
     for (int n = nstart; n >= 1; --n) {
         J[n - 1] = (2.0L * n / z) * J[n] - J[n + 1];
@@ -82,7 +99,7 @@ static void miller01(ld z, ld& j0, ld& j1, ld& y0, ld& y1) {
     }
     ld norm = J[0];
     for (int k = 2; k <= nstart; k += 2) norm += 2 * J[k];
-    for (auto& v : J) v /= norm;
+    for (int i = 0; i < nstart + 2; ++i) J[i] /= norm;
     ld s0 = 0, s1 = 0;
     for (int k = 1; 2 * k + 1 <= nstart + 1; ++k) {
         ld sg = (k % 2) ? -1.0L : 1.0L;
@@ -289,8 +306,9 @@ static bool make_poly(const HostMesh& M, int tau, ld k, PolyCtx& P) {
     return true;
 }
 
-// Accumulate sum over GL32 points of one panel into E[15].
-static void panel_integral(const Edge& e, ld ta, ld tb, ld xj, ld yj, ld k, const PolyCtx& P, cld* E) {
+// Accumulate, over the GL32 points of one panel, the monomial moments
+// Mo[a] = sum wt (G d(mono_a)/dn - mono_a dG/dn); E = Phi^T Mo afterwards.
+static void panel_integral(const Edge& e, ld ta, ld tb, ld xj, ld yj, ld k, const PolyCtx& P, cld* Mo) {
     const GL32& g = gl32();
     ld m[15], g1[15], g2[15];
     for (int i = 0; i < 32; ++i) {
@@ -306,19 +324,12 @@ static void panel_integral(const Edge& e, ld ta, ld tb, ld xj, ld yj, ld k, cons
         cld G = cld(0, 0.25L) * h0;
         cld dGdn = cld(0, 0.25L) * (-k) * h1 * ((rx * nx + ry * ny) / r);
         mono_eval((x - P.cx) * P.invh, (y - P.cy) * P.invh, m, g1, g2, P.invh);
-        for (int q = 0; q < 15; ++q) {
-            ld phi = 0, dphi = 0;
-            for (int a = 0; a < 15; ++a) {
-                ld c = P.Phi[a * 15 + q];
-                phi += m[a] * c;
-                dphi += (g1[a] * nx + g2[a] * ny) * c;
-            }
-            E[q] += wt * (G * dphi - dGdn * phi);
-        }
+        cld Gw = wt * G, Dw = wt * dGdn;
+        for (int a = 0; a < 15; ++a) Mo[a] += Gw * (g1[a] * nx + g2[a] * ny) - Dw * m[a];
     }
 }
 
-static void edge_integral(const Edge& e, ld xj, ld yj, ld k, const PolyCtx& P, cld* E) {
+static void edge_integral(const Edge& e, ld xj, ld yj, ld k, const PolyCtx& P, cld* Mo) {
     struct Pan { ld a, b; int depth; };
     std::vector<Pan> stack{{0, 1, 0}};
     while (!stack.empty()) {
@@ -335,7 +346,7 @@ static void edge_integral(const Edge& e, ld xj, ld yj, ld k, const PolyCtx& P, c
             stack.push_back({p.a, mid, p.depth + 1});
             stack.push_back({mid, p.b, p.depth + 1});
         } else {
-            panel_integral(e, p.a, p.b, xj, yj, k, P, E);
+            panel_integral(e, p.a, p.b, xj, yj, k, P, Mo);
         }
     }
 }
@@ -346,8 +357,8 @@ static bool correction_block(const HostMesh& M, int j, ld k, const std::vector<i
     PolyCtx P;
     if (!make_poly(M, tau, k, P)) return false;
     ld xj = M.nodes[2 * j], yj = M.nodes[2 * j + 1];
-    cld E[15], N[15];
-    for (int q = 0; q < 15; ++q) { E[q] = 0; N[q] = 0; }
+    cld E[15], N[15], Mo[15], Mn[15];
+    for (int q = 0; q < 15; ++q) { E[q] = 0; N[q] = 0; Mo[q] = 0; Mn[q] = 0; }
     // boundary edges of the patch: edges met once among the patch elements
     std::vector<std::array<int, 4>> keys;   // (min v, max v, element, edge)
     keys.reserve(patch.size() * 3);
@@ -360,9 +371,11 @@ static bool correction_block(const HostMesh& M, int j, ld k, const std::vector<i
     for (size_t i = 0; i < keys.size();) {
         size_t r = i + 1;
         while (r < keys.size() && keys[r][0] == keys[i][0] && keys[r][1] == keys[i][1]) ++r;
-        if (r - i == 1) edge_integral(make_edge(M, keys[i][2], keys[i][3]), xj, yj, k, P, E);
+        if (r - i == 1) edge_integral(make_edge(M, keys[i][2], keys[i][3]), xj, yj, k, P, Mo);
         i = r;
     }
+    for (int q = 0; q < 15; ++q)
+        for (int a = 0; a < 15; ++a) E[q] += P.Phi[a * 15 + q] * Mo[a];
     ld m[15];
     if (own) {
         mono_eval((xj - P.cx) * P.invh, (yj - P.cy) * P.invh, m, nullptr, nullptr, P.invh);
@@ -382,12 +395,10 @@ static bool correction_block(const HostMesh& M, int j, ld k, const std::vector<i
             hankel01_ld(k * r, h0, h1);
             cld Gw = cld(0, 0.25L) * h0 * (ld)M.w[n];
             mono_eval((yx - P.cx) * P.invh, (yy - P.cy) * P.invh, m, nullptr, nullptr, P.invh);
-            for (int q = 0; q < 15; ++q) {
-                ld L = 0;
-                for (int a = 0; a < 15; ++a) L += m[a] * P.C[a * 15 + q];
-                N[q] += Gw * L;
-            }
+            for (int a = 0; a < 15; ++a) Mn[a] += Gw * m[a];
         }
+    for (int q = 0; q < 15; ++q)
+        for (int a = 0; a < 15; ++a) N[q] += P.C[a * 15 + q] * Mn[a];
     for (int q = 0; q < 15; ++q) {
         cols.push_back(tau * NQ_ELEM + q);
         cld d = E[q] - N[q];

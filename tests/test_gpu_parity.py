@@ -48,9 +48,10 @@ def test_device_hankel():
     assert err.max() < 5e-14, (err.max(), z[err.argmax()])
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 3])
 def test_pairsum_parity_disk(mode):
-    # mode 0: tabulated H0(k sqrt(t)); mode 1: direct series / modulus-phase evaluation
+    # mode 0: tabulated H0(k sqrt(t)); 1: direct series / modulus-phase evaluation;
+    # 3: the same table evaluated in double-float arithmetic on the FP32 pipe
     wl = constant_disk(k=5.0, n_rings=3)
     op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, use_precond=0, pairsum=mode)
     f = random_density(wl.mesh.n_nodes, 3)
@@ -104,6 +105,62 @@ def test_pairsum_table_vs_direct_full_size(cfg2):
     op.pairsum_dev(f, y0)
     opd.pairsum_dev(f, y1)
     assert (torch.linalg.norm(y0 - y1) / torch.linalg.norm(y1)).item() < 1e-13
+
+
+def test_double_float_form_full_size(cfg2):
+    # pairsum = 3 must meet the FP64 bar: pair sum within 1e-13 of the FP64 table
+    # kernel and the L apply within 1e-11 of the oracle on sampled rows
+    wl, op = cfg2
+    n = wl.mesh.n_nodes
+    opd = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, use_precond=0, pairsum=3)
+    f = _dev(random_density(n, 23))
+    y0 = torch.empty_like(f)
+    y1 = torch.empty_like(f)
+    op.pairsum_dev(f, y0)
+    opd.pairsum_dev(f, y1)
+    e_ps = (torch.linalg.norm(y1 - y0) / torch.linalg.norm(y0)).item()
+    x = random_density(n, 11)
+    y = torch.empty(n, dtype=torch.complex128, device="cuda")
+    opd.apply_dev(_dev(x), y)
+    rows = np.concatenate([np.arange(0, n, 1999), [n - 1]])
+    ref = OracleOp(wl.mesh, wl.k, wl.m, rows_only=True).apply_rows(x, rows)
+    e_ap = _rel(y.cpu().numpy()[rows], ref)
+    print("double-float form: pair sum vs FP64", e_ps, "apply vs oracle", e_ap)
+    assert e_ps < 1e-13 and e_ap < 1e-11
+
+
+def test_pairsum_precision_form_full_size(cfg2):
+    # FP32 table (2e-8), FP32 strengths (6e-8), Kahan-compensated sums: ~1e-7 expected
+    wl, op = cfg2
+    n = wl.mesh.n_nodes
+    op32 = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, use_precond=0, pairsum=2)
+    f = _dev(random_density(n, 19))
+    y0 = torch.empty_like(f)
+    y1 = torch.empty_like(f)
+    op.pairsum_dev(f, y0)
+    op32.pairsum_dev(f, y1)
+    err = (torch.linalg.norm(y1 - y0) / torch.linalg.norm(y0)).item()
+    print("precision-form pair sum rel err", err)
+    assert err < 5e-7
+
+
+def test_precision_form_solutions(cfg2):
+    # target of the precision form: <= 1e-6 relative solution error vs FP64
+    wl = two_material("tiny", k=8.0, nx=64, ny=64)
+    op32 = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, nx=64, ny=64, tol=1e-10, pairsum=2)
+    u, _, _, _, st = op32.solve([np.pi / 4])
+    b = plane_wave(wl.mesh.nodes, wl.k, np.pi / 4)
+    ud = np.linalg.solve(OracleOp(wl.mesh, wl.k, wl.m).dense(), b)
+    e_small = _rel(u[0], ud)
+    wl2, op64 = cfg2
+    op2 = L.Operator(L.Mesh(wl2.mesh), wl2.k, wl2.m, wl2.m_grid, tol=1e-10, pairsum=2)
+    u32, _, _, it32, st32 = op2.solve([np.pi / 4])
+    op64b = L.Operator(L.Mesh(wl2.mesh), wl2.k, wl2.m, wl2.m_grid, tol=1e-10)
+    u64, _, _, it64, st64 = op64b.solve([np.pi / 4])
+    e_full = _rel(u32[0], u64[0])
+    print("precision form: small vs oracle", e_small, "full vs FP64 path", e_full, "iters", it32, it64)
+    assert st == st32 == st64 == L.LS_OK
+    assert e_small < 1e-6 and e_full < 1e-6
 
 
 def test_precond_parity_small():
