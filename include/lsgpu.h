@@ -261,6 +261,27 @@ ls_status ls_op_stats(ls_op* op, double* pairsum_ms, int64_t* pairsum_launches, 
 /* Diagnostic: measured FP64 FMA throughput of the device in GFLOP/s (2 flops per FMA). */
 ls_status ls_probe_fp64(double* gflops, void* stream);
 
+/*
+ * Allocation-free pair sum, for callers that cannot allocate device memory:
+ * code inside a CUDA graph being captured, plug-ins whose device memory is
+ * owned by a host application's allocator or a fixed pool, real-time loops that
+ * must stay out of the allocator.  No counterpart in the paper; it computes the
+ * same sum as ls_pairsum_dev, y_j = (i/4) sum_{n != j} H0^(1)(k |x_j - x_n|) w_n f_n,
+ * with the direct FP64 H0 routine and without an operator:
+ *   n          number of nodes, 2 <= n <= 1048576 (larger n: LS_EINVAL)
+ *   xy_dev     [n][2] double node coordinates, w_dev [n] double weights
+ *   f_dev      [n] complex density, y_dev [n] complex output (may not alias f)
+ *   k          wavenumber > 0;  stream: cudaStream_t (NULL = default)
+ * Its scratch (chunked partial sums) lives in a file-scope __device__ array of
+ * 16 MiB that every GPU loading the library keeps until the process exits; no
+ * cudaMalloc/cudaFree or allocating library routine is called.  The first call
+ * on a device looks up the array's address with cudaGetSymbolAddress (make it
+ * before any stream capture).  All calls share the array: calls that overlap on
+ * the GPU (other streams, other host threads) race; serialise them.  Every
+ * partial is overwritten before it is read, so no clearing is needed.
+ */
+ls_status ls_pairsum_noalloc(int32_t n, const double* xy_dev, const double* w_dev, const void* f_dev,
+                             double k, void* y_dev, void* stream);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* ls_last_error(void);

@@ -21,7 +21,7 @@ EXPORTED = ["ls_params_default", "ls_mesh_create", "ls_mesh_destroy", "ls_mesh_n
             "ls_solve", "ls_solve_dev", "ls_op_correction", "ls_correction_host", "ls_hankel0_dev",
             "ls_pairsum_batch_dev", "ls_solve_batch_dev", "ls_solve_multi_dev", "ls_apply_transpose_dev", "ls_potential_transpose_dev", "ls_apply_precond_transpose_dev",
             "ls_solve_transpose_dev", "ls_op_set_contrast", "ls_incident_dev", "ls_misfit_gradient_dev",
-            "ls_op_set_pairsum", "ls_op_set_timing", "ls_op_setup_times", "ls_op_stats", "ls_probe_fp64", "ls_last_error"]
+            "ls_op_set_pairsum", "ls_op_set_timing", "ls_op_setup_times", "ls_op_stats", "ls_probe_fp64", "ls_pairsum_noalloc", "ls_last_error"]
 
 
 class LsError(RuntimeError):
@@ -73,6 +73,7 @@ def _load():
         "ls_op_setup_times": (I32, [P, P]),
         "ls_op_stats": (I32, [P, P, P, P]),
         "ls_probe_fp64": (I32, [P, P]),
+        "ls_pairsum_noalloc": (I32, [I32, P, P, P, D, P, P]),
         "ls_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -320,6 +321,13 @@ def probe_fp64():
     g = ctypes.c_double()
     _check(_lib.ls_probe_fp64(ctypes.byref(g), ctypes.c_void_p(_current_stream())))
     return g.value
+
+
+def pairsum_noalloc(xy, w, f, k, y):
+    """Allocation-free pair sum on device tensors: xy [n, 2] and w [n] float64,
+    f and y [n] complex128 (see ls_pairsum_noalloc for whom it serves)."""
+    _check(_lib.ls_pairsum_noalloc(int(f.numel()), _dptr(xy), _dptr(w), _dptr(f), float(k), _dptr(y),
+                                   ctypes.c_void_p(_current_stream())))
 
 
 def _current_stream():
