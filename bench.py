@@ -208,6 +208,59 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def precision_report(args):
+    """--workload precision: the precision form on its own configuration (two-material
+    disk at k = 40, 13,042 triangles = 195,630 nodes, 512^2 preconditioner): one FP32
+    solve and one FP64-accurate double-float solve (the reference for the error),
+    both timed with CUDA events, plus the FP32 matvec against the FP64 oracle on
+    sampled rows.  One JSON line; not part of the default run."""
+    import torch
+    import paper_2608_17615_b300 as L
+    from lsinput.workloads import two_material
+
+    torch.cuda.set_device(0)
+    wl = two_material("medium", k=40.0, nx=512, ny=512)
+    n = wl.mesh.n_nodes
+    t0 = time.perf_counter()
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, tol=1e-8, pairsum=2)
+    setup_s = time.perf_counter() - t0
+    d = np.array([np.cos(np.pi / 4), np.sin(np.pi / 4)])
+    b = torch.from_numpy(np.exp(1j * wl.k * (wl.mesh.nodes @ d))).cuda().view(1, -1)
+    out = {}
+    sols = {}
+    for mode, name in ((2, "fp32"), (3, "double_float")):
+        op.set_pairsum(mode)
+        u = torch.empty_like(b)
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it, st = op.solve_dev(b, u)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        sols[name] = u
+        out[name] = {"solve_ms": ms, "solves_per_s": 1e3 / ms, "iterations": int(it[0]), "status": int(st),
+                     "pairs_per_s": int(it[0]) * n * (n - 1) / (ms * 1e-3)}
+    out["fp32"]["rel_err_vs_double_float_solution"] = (
+        torch.linalg.norm(sols["fp32"] - sols["double_float"]) / torch.linalg.norm(sols["double_float"])).item()
+    # FP32 matvec against the oracle on sampled rows
+    from oracle.operator import Operator as OracleOp
+    op.set_pairsum(2)
+    x = np.exp(1j * np.arange(n) * 0.37)
+    y = torch.empty(n, dtype=torch.complex128, device="cuda")
+    op.apply_dev(torch.from_numpy(x).cuda(), y)
+    rows = np.arange(0, n, n // 24)[:24]
+    ref = OracleOp(wl.mesh, wl.k, wl.m, rows_only=True).apply_rows(x, rows)
+    yv = y.cpu().numpy()[rows]
+    out["fp32"]["matvec_rel_err_vs_oracle"] = float(np.linalg.norm(yv - ref) / np.linalg.norm(ref))
+    line = {"report": "precision form", "config": {"workload": "two-material disk, k=40, 195,630 nodes "
+            "(13,042 curved P4 triangles), 512^2 Cartesian preconditioner, tol 1e-8", "nodes": n},
+            "setup_s": setup_s, "setup_parts_s": dict(zip(["correction", "grid", "block_lu", "table"],
+                                                         [round(float(t), 3) for t in op.setup_times()])),
+            "forms": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -215,8 +268,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="default", choices=["default", "precision"])
     args = ap.parse_args()
     rank, world, local = _env_rank()
+    if args.workload == "precision":
+        if rank == 0:
+            precision_report(args)
+        return
     if args.impl == "reference":
         if rank == 0:
             reference_arm(args)
@@ -237,7 +295,7 @@ def main():
     op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, tol=1e-8)
     setup_s = time.perf_counter() - t0
     fp64_peak = L.probe_fp64()
-    setup_parts = dict(zip(["correction", "grid", "block_lu", "table"], op.setup_times()))
+    setup_parts = {k: round(float(v), 3) for k, v in zip(["correction", "grid", "block_lu", "table"], op.setup_times())}
     print(f"[bench] setup {setup_s:.1f} s {setup_parts}, FP64 probe {fp64_peak:.1f} GFLOP/s", file=sys.stderr, flush=True)
     # each rank solves its own direction (replicas)
     angle = rank_direction(rank, world)
@@ -281,12 +339,13 @@ def main():
     pairs_per_solve = iters * n * (n - 1)
     # roofline of the pair-sum kernel (FP64 ALU bound)
     avg_launch_s = ps_ms / max(ps_launches, 1) * 1e-3
-    flops_per_pair = FLOPS_PER_PAIR[op.params.pairsum]
+    nc_tab, tune_ms = op.tuning()
+    flops_per_pair = flops_per_pair_of(op.params.pairsum, nc_tab)
     achieved = flops_per_pair * n * (n - 1) / avg_launch_s / 1e12
     peak = fp64_peak / 1e3
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": TRAFFIC.get(op.params.pairsum), "kernel": KERNEL[op.params.pairsum],
-                "flops_per_pair": flops_per_pair,
+                "flops_per_pair": flops_per_pair, "table_ncoef": nc_tab, "tuning_ms": list(tune_ms),
                 "peak_source": "measured FP64 FMA probe (ls_probe_fp64), same run",
                 "kernel_ms_per_launch": avg_launch_s * 1e3, "kernel_share_of_step": ps_ms / total_ms}
     # end to end through the host-buffer entry point
@@ -367,6 +426,15 @@ def main():
 #  3 k_pairsum_df (double-float on FP32): differences 22, t 12, u 8, two degree-11
 #    DF Horner chains 2 x 11 x 15 = 330, DF complex multiply-accumulate 60 -> 432
 FLOPS_PER_PAIR = {0: 59, 1: 148, 2: 80, 3: 432}
+
+
+def flops_per_pair_of(mode, nc):
+    """Source count for the table degree in use (nc coefficients per cell)."""
+    if mode == 0:
+        return 15 + 4 * (nc - 1)            # 59 at nc = 12
+    if mode == 3:
+        return 102 + 30 * (nc - 1)          # 432 at nc = 12
+    return FLOPS_PER_PAIR[mode]
 KERNEL = {0: "k_pairsum_tab", 1: "k_pairsum", 2: "k_pairsum_f32", 3: "k_pairsum_df"}
 # dram__bytes_read + write per launch from ncu captures of the current kernels (None until captured)
 TRAFFIC = {}

@@ -55,14 +55,15 @@ typedef struct {
     double  box[4];       /* Cartesian grid box xmin, xmax, ymin, ymax (Section 4)    */
     int32_t nx, ny;       /* grid nodes per direction, endpoints included; the step
                              (xmax - xmin)/(nx - 1) must equal (ymax - ymin)/(ny - 1) */
-    int32_t pairsum;      /* 0: FP64, H0 from a per-operator table of degree-11 polynomials
-                             in t = r^2 on octave-graded cells (validated to 2e-15
-                             against the long-double routine at setup); 1: FP64 direct
+    int32_t pairsum;      /* 0: FP64, H0 from a per-operator table of polynomials in
+                             t = r^2 on octave-graded cells (each table validated to
+                             2e-15 against the long-double routine at setup; degree 11,
+                             9 or 8 chosen by timing at setup); 1: FP64 direct
                              evaluation; 2: precision form -- FP32 table (degree 6,
                              validated to 2e-8), double-float coordinate differences,
                              Kahan-compensated FP32 accumulation; 3: FP64-accurate
-                             double-float (FP32 pairs) evaluation of the degree-11
-                             table and accumulation on the FP32 pipe            */
+                             double-float (FP32 pairs) evaluation of the mode-0 table
+                             and accumulation on the FP32 pipe                   */
 } ls_params;
 
 /* Defaults: tol 1e-8, max_iter 600, use_precond 1, kappa 3, box [-1.2,1.2]^2, 256 x 256, pairsum 0. */
@@ -161,8 +162,8 @@ ls_status ls_solve_dev(ls_op* op, int32_t R, const void* b_dev, void* u_dev,
  *                         b_dev, u_dev [R][N]; far field as ls_solve_dev
  * The pair sum of all R systems is one launch per iteration: each H(j, n) comes
  * from an FP32 table (degree 6, validated to 2e-8) with double-float t and is
- * applied to blocks of 8 right-hand sides; sums run in FP32 over runs of 32
- * sources and in FP64 across runs (the precision of the batching form: <= 1e-6
+ * applied to blocks of 8 right-hand sides; sums are Kahan-compensated FP32 over
+ * runs of 64 sources and FP64 across runs (the precision of the batching form: <= 1e-6
  * relative solution error).  The preconditioner sweeps and the Arnoldi kernels
  * are batched over r as well.  Workspace grows on first use with a larger R.
  */
@@ -256,6 +257,9 @@ ls_status ls_op_set_timing(ls_op* op, int32_t on);
 /* Wall time (s) of the setup phases: [0] correction dV (host), [1] grid transfers, stencil and C
    (host), [2] block LU of C and its transposes (device), [3] H0 table. */
 ls_status ls_op_setup_times(const ls_op* op, double* t4);
+/* Pair-sum autotuner result: coefficients per cell of the H0 table in use and the timed
+   pair-sum launch (ms) of the 12-, 10- and 9-coefficient candidates (0 = not tried). */
+ls_status ls_op_tuning(const ls_op* op, int32_t* table_ncoef, double* cand_ms);
 ls_status ls_op_stats(ls_op* op, double* pairsum_ms, int64_t* pairsum_launches, int64_t* launches);
 
 /* Diagnostic: measured FP64 FMA throughput of the device in GFLOP/s (2 flops per FMA). */

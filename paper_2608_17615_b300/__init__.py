@@ -21,7 +21,7 @@ EXPORTED = ["ls_params_default", "ls_mesh_create", "ls_mesh_destroy", "ls_mesh_n
             "ls_solve", "ls_solve_dev", "ls_op_correction", "ls_correction_host", "ls_hankel0_dev",
             "ls_pairsum_batch_dev", "ls_solve_batch_dev", "ls_solve_multi_dev", "ls_apply_transpose_dev", "ls_potential_transpose_dev", "ls_apply_precond_transpose_dev",
             "ls_solve_transpose_dev", "ls_op_set_contrast", "ls_incident_dev", "ls_misfit_gradient_dev",
-            "ls_op_set_pairsum", "ls_op_set_timing", "ls_op_setup_times", "ls_op_stats", "ls_probe_fp64", "ls_pairsum_noalloc", "ls_last_error"]
+            "ls_op_set_pairsum", "ls_op_set_timing", "ls_op_setup_times", "ls_op_tuning", "ls_op_stats", "ls_probe_fp64", "ls_pairsum_noalloc", "ls_last_error"]
 
 
 class LsError(RuntimeError):
@@ -71,6 +71,7 @@ def _load():
         "ls_op_set_pairsum": (I32, [P, I32]),
         "ls_op_set_timing": (I32, [P, I32]),
         "ls_op_setup_times": (I32, [P, P]),
+        "ls_op_tuning": (I32, [P, P, P]),
         "ls_op_stats": (I32, [P, P, P, P]),
         "ls_probe_fp64": (I32, [P, P]),
         "ls_pairsum_noalloc": (I32, [I32, P, P, P, D, P, P]),
@@ -267,6 +268,13 @@ class Operator:
         t = np.zeros(4)
         _check(_lib.ls_op_setup_times(self.handle, _ptr(t)))
         return tuple(t)
+
+    def tuning(self):
+        """(table coefficients per cell in use, timed ms of the 12/10/9-coefficient candidates)."""
+        nc = ctypes.c_int32()
+        ms = np.zeros(3)
+        _check(_lib.ls_op_tuning(self.handle, ctypes.byref(nc), _ptr(ms)))
+        return nc.value, tuple(ms)
 
     def stats(self):
         """(pair-sum kernel ms, pair-sum launches, kernel launches) since the last set_timing."""

@@ -175,7 +175,8 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum(const double2* __restrict__ 
 // Tabulated form: H0(k sqrt(t)) from the per-operator octave table (lsgpu::H0Table)
 // held in shared memory: coef [ncell][NC] double2, then (mid, inv_hw) [ncell],
 // then (base, shift) [noct].  Pairs with t outside the table use ls_h0_r2.
-#define NC_TAB 12
+// NC = polynomial degree + 1; the autotuner of the operator setup picks NC.
+template <int NC_TAB>
 __global__ void __launch_bounds__(PS_TPB) k_pairsum_tab(const double2* __restrict__ xy, const double* __restrict__ w,
                                                         const double2* __restrict__ m, const double2* __restrict__ f,
                                                         int n, int src_per_chunk, double k, double inv_k,
@@ -405,6 +406,7 @@ __device__ __forceinline__ DF df_from(double x) {
 
 struct DFTile { float4 xy; float4 s; };     // (x_h, x_l, y_h, y_l), (s_re_h, s_re_l, s_im_h, s_im_l)
 
+template <int NC_TAB>
 __global__ void __launch_bounds__(PS_TPB) k_pairsum_df(const double2* __restrict__ xy, const double* __restrict__ w,
                                                        const double2* __restrict__ m, const double2* __restrict__ f,
                                                        int n, int src_per_chunk, double k, double inv_k,
@@ -500,8 +502,8 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum_df(const double2* __restrict
 // Batched form: R right-hand sides.  Each thread owns one target and a block of
 // RB right-hand sides; H(j, n) is generated once per pair from the FP32 table
 // (double-float t as in k_pairsum_f32) and applied to the RB strengths.  Sums
-// run in FP32 over runs of 32 sources and are folded into FP64 accumulators after
-// each run, which bounds the recursive-summation error of FP32 to 32 terms.
+// are Kahan-compensated FP32 over runs of 64 sources, folded into FP64
+// accumulators after each run.
 //   f [R][n] densities; partial [R][nchunk][n] (blockIdx.z = RHS block).
 #define MRB 8
 
@@ -561,12 +563,13 @@ __device__ __forceinline__ void multi_unit(const MultiArgs& A, int tb, int chunk
         }
         __syncthreads();
         const int cnt = min(PS_TILE, s_end - base);
-        // FP32 sums over runs of 32 sources, folded into the FP64 accumulators after each run
-        for (int i0 = 0; i0 < cnt; i0 += 32) {
-            float sr[MRB], si[MRB];
+        // Kahan-compensated FP32 sums over runs of 64 sources, folded into the FP64
+        // accumulators after each run
+        for (int i0 = 0; i0 < cnt; i0 += 64) {
+            float sr[MRB], si[MRB], cr[MRB], ci[MRB];
 #pragma unroll
-            for (int q = 0; q < MRB; ++q) { sr[q] = 0.f; si[q] = 0.f; }
-            const int i1 = min(cnt, i0 + 32);
+            for (int q = 0; q < MRB; ++q) { sr[q] = 0.f; si[q] = 0.f; cr[q] = 0.f; ci[q] = 0.f; }
+            const int i1 = min(cnt, i0 + 64);
             for (int i = i0; i < i1; ++i) {
                 float4 sc = txy[i];
                 float dxh, dxl, dyh, dyl;
@@ -610,12 +613,20 @@ __device__ __forceinline__ void multi_unit(const MultiArgs& A, int tb, int chunk
 #pragma unroll
                 for (int q = 0; q < MRB; ++q) {
                     float2 v = ts[i][q];
-                    sr[q] = fmaf(hr, v.x, fmaf(-him, v.y, sr[q]));
-                    si[q] = fmaf(hr, v.y, fmaf(him, v.x, si[q]));
+                    float tr = fmaf(hr, v.x, -him * v.y) - cr[q];
+                    float ti = fmaf(hr, v.y, him * v.x) - ci[q];
+                    float nr = sr[q] + tr, ni = si[q] + ti;
+                    cr[q] = (nr - sr[q]) - tr;
+                    ci[q] = (ni - si[q]) - ti;
+                    sr[q] = nr;
+                    si[q] = ni;
                 }
             }
 #pragma unroll
-            for (int q = 0; q < MRB; ++q) { accr[q] += (double)sr[q]; acci[q] += (double)si[q]; }
+            for (int q = 0; q < MRB; ++q) {
+                accr[q] += (double)sr[q] - (double)cr[q];
+                acci[q] += (double)si[q] - (double)ci[q];
+            }
         }
     }
     if (j < n)
@@ -1558,6 +1569,8 @@ struct ls_op {
     // tabulated H0 (pairsum mode 0: FP64 table, mode 2: FP32 table)
     int mode = 0;
     bool use_table = false;
+    int tab_nc = 12;                     // table degree + 1 chosen by the setup autotuner
+    float tune_ms[3] = {0, 0, 0};        // pair-sum time of the NC = 12, 10, 9 candidates (0: not tried)
     int tab_ncell = 0, tab_noct = 0, tab_blo = 0;
     size_t tab_bytes = 0;
     double tab_err = 0, tab_tlo = 0, tab_thi = 0;
@@ -1611,6 +1624,36 @@ static ls_status check_stream_sync(ls_op* op) {
 }
 
 // ------------------------------------------------------------------ building blocks
+static void launch_tab(int nc, dim3 grid, size_t smem, cudaStream_t st, const double2* xy, const double* w,
+                       const double2* m, const double2* f, int n, int spc, double k, const double2* tab, int ncell,
+                       int noct, int blo, double2* partial) {
+    const double ik = 1.0 / k;
+    if (nc == 9) k_pairsum_tab<9><<<grid, PS_TPB, smem, st>>>(xy, w, m, f, n, spc, k, ik, tab, ncell, noct, blo, partial);
+    else if (nc == 10) k_pairsum_tab<10><<<grid, PS_TPB, smem, st>>>(xy, w, m, f, n, spc, k, ik, tab, ncell, noct, blo, partial);
+    else k_pairsum_tab<12><<<grid, PS_TPB, smem, st>>>(xy, w, m, f, n, spc, k, ik, tab, ncell, noct, blo, partial);
+}
+
+static void launch_df(int nc, dim3 grid, size_t smem, cudaStream_t st, const double2* xy, const double* w,
+                      const double2* m, const double2* f, int n, int spc, double k, const float4* tab, int ncell,
+                      int noct, int blo, double2* partial) {
+    const double ik = 1.0 / k;
+    if (nc == 9) k_pairsum_df<9><<<grid, PS_TPB, smem, st>>>(xy, w, m, f, n, spc, k, ik, tab, ncell, noct, blo, partial);
+    else if (nc == 10) k_pairsum_df<10><<<grid, PS_TPB, smem, st>>>(xy, w, m, f, n, spc, k, ik, tab, ncell, noct, blo, partial);
+    else k_pairsum_df<12><<<grid, PS_TPB, smem, st>>>(xy, w, m, f, n, spc, k, ik, tab, ncell, noct, blo, partial);
+}
+
+static cudaError_t raise_tab_limits(int mode, size_t bytes) {
+    cudaError_t e = cudaSuccess;
+    if (mode == 3) {
+        if ((e = raise_smem_limit(k_pairsum_df<9>, bytes)) != cudaSuccess) return e;
+        if ((e = raise_smem_limit(k_pairsum_df<10>, bytes)) != cudaSuccess) return e;
+        return raise_smem_limit(k_pairsum_df<12>, bytes);
+    }
+    if ((e = raise_smem_limit(k_pairsum_tab<9>, bytes)) != cudaSuccess) return e;
+    if ((e = raise_smem_limit(k_pairsum_tab<10>, bytes)) != cudaSuccess) return e;
+    return raise_smem_limit(k_pairsum_tab<12>, bytes);
+}
+
 static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m, const double* w);
 static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m) { return launch_pairsum(op, f, m, op->w.p); }
 
@@ -1624,17 +1667,15 @@ static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m, c
         CK(cudaEventRecord(e0, op->stream));
     }
     if (op->mode == 3)
-        k_pairsum_df<<<grid, PS_TPB, op->tab_bytes, op->stream>>>(op->xy.p, w, m, f, op->nq, op->src_per_chunk, op->k,
-                                                                   1.0 / op->k, (const float4*)op->tab.p, op->tab_ncell,
-                                                                   op->tab_noct, op->tab_blo, op->partial.p);
+        launch_df(op->tab_nc, grid, op->tab_bytes, op->stream, op->xy.p, w, m, f, op->nq, op->src_per_chunk, op->k,
+                  (const float4*)op->tab.p, op->tab_ncell, op->tab_noct, op->tab_blo, op->partial.p);
     else if (op->mode == 2)
         k_pairsum_f32<<<grid, PS_TPB, op->tab_bytes, op->stream>>>(op->xy.p, w, m, f, op->nq, op->src_per_chunk,
                                                                     op->k, 1.0 / op->k, (const float4*)op->tab.p,
                                                                     op->tab_ncell, op->tab_noct, op->tab_blo, op->partial.p);
     else if (op->use_table)
-        k_pairsum_tab<<<grid, PS_TPB, op->tab_bytes, op->stream>>>(op->xy.p, w, m, f, op->nq, op->src_per_chunk,
-                                                                    op->k, 1.0 / op->k, op->tab.p, op->tab_ncell,
-                                                                    op->tab_noct, op->tab_blo, op->partial.p);
+        launch_tab(op->tab_nc, grid, op->tab_bytes, op->stream, op->xy.p, w, m, f, op->nq, op->src_per_chunk, op->k,
+                   op->tab.p, op->tab_ncell, op->tab_noct, op->tab_blo, op->partial.p);
     else
         k_pairsum<<<grid, PS_TPB, 0, op->stream>>>(op->xy.p, w, m, f, op->nq, op->src_per_chunk, op->k, 1.0 / op->k,
                                                    op->partial.p);
@@ -1921,17 +1962,13 @@ static void table_range(ls_op* op, const HostMesh& M) {
     op->tab_thi = t_hi;
 }
 
-static ls_status build_table_range(ls_op* op, double t_lo, double t_hi, int mode) {
-    const bool f32 = mode == 2;
-    lsgpu::H0Table T;
-    std::string err = f32 ? lsgpu::build_h0_table(op->k, t_lo, t_hi, T, NC_F32, 2e-8)
-                          : lsgpu::build_h0_table(op->k, t_lo, t_hi, T);
-    if (!err.empty()) return fail(LS_EINVAL, err);
+// Upload an FP64 (mode 0) or double-float (mode 3) table with nc coefficients per cell.
+static ls_status upload_table(ls_op* op, const lsgpu::H0Table& T, int nc, int mode) {
     const int ncell = (int)T.mid.size();
     if (mode == 3) {
-        std::vector<float4> hd((size_t)ncell * (NC_TAB + 1) + (T.noct + 1) / 2, make_float4(0.f, 0.f, 0.f, 0.f));
+        std::vector<float4> hd((size_t)ncell * (nc + 1) + (T.noct + 1) / 2, make_float4(0.f, 0.f, 0.f, 0.f));
         auto split = [](double x, float& h, float& l) { h = (float)x; l = (float)(x - (double)h); };
-        for (size_t i = 0; i < (size_t)ncell * NC_TAB; ++i) {
+        for (size_t i = 0; i < (size_t)ncell * nc; ++i) {
             float a, b, c, d;
             split(T.coef[i].real(), a, b);
             split(T.coef[i].imag(), c, d);
@@ -1940,23 +1977,42 @@ static ls_status build_table_range(ls_op* op, double t_lo, double t_hi, int mode
         for (int c = 0; c < ncell; ++c) {
             float a, b;
             split(T.mid[c], a, b);
-            hd[(size_t)ncell * NC_TAB + c] = make_float4(a, b, (float)T.inv_hw[c], 0.f);
+            hd[(size_t)ncell * nc + c] = make_float4(a, b, (float)T.inv_hw[c], 0.f);
         }
-        int2* oct = reinterpret_cast<int2*>(hd.data() + (size_t)ncell * (NC_TAB + 1));
+        int2* oct = reinterpret_cast<int2*>(hd.data() + (size_t)ncell * (nc + 1));
         for (int o = 0; o < T.noct; ++o) oct[o] = make_int2(T.oct_base[o], T.oct_shift[o] + 3);
-        op->tab_ncell = ncell;
-        op->tab_noct = T.noct;
         op->tab_blo = T.b_lo - 1023 + 127;
-        op->tab_err = T.max_rel_err;
         op->tab_bytes = hd.size() * sizeof(float4);
-        if (op->tab_bytes > 200 * 1024) return fail(LS_EINVAL, "H0 table too large for shared memory");
         CK(op->tab.alloc((op->tab_bytes + sizeof(double2) - 1) / sizeof(double2)));
         CK(cudaMemcpy(op->tab.p, hd.data(), op->tab_bytes, cudaMemcpyHostToDevice));
-        CK(raise_smem_limit(k_pairsum_df, op->tab_bytes));
-        op->use_table = true;
-        return LS_OK;
+    } else {
+        std::vector<double2> h((size_t)ncell * (nc + 1) + (T.noct + 1) / 2);
+        for (size_t i = 0; i < (size_t)ncell * nc; ++i) h[i] = make_double2(T.coef[i].real(), T.coef[i].imag());
+        for (int c = 0; c < ncell; ++c) h[(size_t)ncell * nc + c] = make_double2(T.mid[c], T.inv_hw[c]);
+        int2* oct = reinterpret_cast<int2*>(h.data() + (size_t)ncell * (nc + 1));
+        for (int o = 0; o < T.noct; ++o) oct[o] = make_int2(T.oct_base[o], T.oct_shift[o]);
+        op->tab_blo = T.b_lo;
+        op->tab_bytes = h.size() * sizeof(double2);
+        CK(op->tab.alloc(h.size()));
+        CK(cudaMemcpy(op->tab.p, h.data(), op->tab_bytes, cudaMemcpyHostToDevice));
     }
-    if (f32) {
+    op->tab_ncell = ncell;
+    op->tab_noct = T.noct;
+    op->tab_err = T.max_rel_err;
+    op->tab_nc = nc;
+    CK(raise_tab_limits(mode, op->tab_bytes));
+    return LS_OK;
+}
+
+// Tables for the pair sum.  Modes 0 and 3 autotune the polynomial degree: every
+// candidate (12, 10 or 9 coefficients per cell, each validated to 2e-15 at build
+// time, with fewer cells for higher degree) whose table fits in shared memory is
+// timed on one pair-sum launch over the operator's own nodes; the fastest is kept.
+static ls_status build_table_range(ls_op* op, double t_lo, double t_hi, int mode) {
+    if (mode == 2) {
+        lsgpu::H0Table T;
+        std::string err = lsgpu::build_h0_table(op->k, t_lo, t_hi, T, NC_F32, 2e-8);
+        if (!err.empty()) return fail(LS_EINVAL, err);
         double err32 = 0;
         TRY(upload_f32_table(T, op->tab, op->tab_ncell, op->tab_noct, op->tab_blo, op->tab_bytes, err32));
         op->tab_err = err32;
@@ -1964,24 +2020,52 @@ static ls_status build_table_range(ls_op* op, double t_lo, double t_hi, int mode
         op->use_table = true;
         return LS_OK;
     }
-    std::vector<double2> h((size_t)ncell * (NC_TAB + 1) + (T.noct + 1) / 2);
-    for (size_t i = 0; i < (size_t)ncell * NC_TAB; ++i) h[i] = make_double2(T.coef[i].real(), T.coef[i].imag());
-    for (int c = 0; c < ncell; ++c) h[(size_t)ncell * NC_TAB + c] = make_double2(T.mid[c], T.inv_hw[c]);
-    int2* oct = reinterpret_cast<int2*>(h.data() + (size_t)ncell * (NC_TAB + 1));
-    for (int o = 0; o < T.noct; ++o) oct[o] = make_int2(T.oct_base[o], T.oct_shift[o]);
-    op->tab_ncell = ncell;
-    op->tab_noct = T.noct;
-    op->tab_blo = T.b_lo;
-    op->tab_err = T.max_rel_err;
-    op->tab_bytes = h.size() * sizeof(double2);
-    if (op->tab_bytes > 200 * 1024) return fail(LS_EINVAL, "H0 table too large for shared memory");
-    CK(op->tab.alloc(h.size()));
-    CK(cudaMemcpy(op->tab.p, h.data(), op->tab_bytes, cudaMemcpyHostToDevice));
-    CK(raise_smem_limit(k_pairsum_tab, op->tab_bytes));
+    const int cand[3] = {12, 10, 9};
+    const size_t smem_cap = 160 * 1024;
+    DevBuf<double2> fdum;
+    CK(fdum.alloc(op->nq));
+    CK(cudaMemsetAsync(fdum.p, 0, sizeof(double2) * op->nq, op->stream));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int best_nc = 12;
+    float best = 1e30f;
+    dim3 grid((op->nq + PS_TPB - 1) / PS_TPB, op->nchunk);
+    for (int c = 0; c < 3; ++c) {
+        lsgpu::H0Table T;
+        std::string err = lsgpu::build_h0_table(op->k, t_lo, t_hi, T, cand[c], 2e-15);
+        op->tune_ms[c] = 0.f;
+        if (!err.empty() || T.max_rel_err > 2e-15) continue;
+        size_t words = T.mid.size() * (cand[c] + 1) + (T.noct + 1) / 2;
+        if (words * 16 > smem_cap) continue;
+        TRY(upload_table(op, T, cand[c], mode));
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {          // first launch warms up, second is timed
+            CK(cudaEventRecord(e0, op->stream));
+            if (mode == 3)
+                launch_df(cand[c], grid, op->tab_bytes, op->stream, op->xy.p, op->w.p, nullptr, fdum.p, op->nq,
+                          op->src_per_chunk, op->k, (const float4*)op->tab.p, op->tab_ncell, op->tab_noct, op->tab_blo,
+                          op->partial.p);
+            else
+                launch_tab(cand[c], grid, op->tab_bytes, op->stream, op->xy.p, op->w.p, nullptr, fdum.p, op->nq,
+                           op->src_per_chunk, op->k, op->tab.p, op->tab_ncell, op->tab_noct, op->tab_blo, op->partial.p);
+            CK(cudaGetLastError());
+            CK(cudaEventRecord(e1, op->stream));
+            CK(cudaEventSynchronize(e1));
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+        }
+        op->tune_ms[c] = ms;
+        if (ms < best) { best = ms; best_nc = cand[c]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    lsgpu::H0Table T;
+    std::string err = lsgpu::build_h0_table(op->k, t_lo, t_hi, T, best_nc, 2e-15);
+    if (!err.empty()) return fail(LS_EINVAL, err);
+    TRY(upload_table(op, T, best_nc, mode));
     op->use_table = true;
     return LS_OK;
 }
-
 static ls_status build_preconditioner(ls_op* op, const HostMesh& M, const double* m_grid) {
     GridSetup G;
     std::vector<std::complex<double>> mg((size_t)op->prm.nx * op->prm.ny);
@@ -2756,6 +2840,13 @@ ls_status ls_op_set_pairsum(ls_op* op, int32_t mode) {
     op->use_table = false;
     if (mode != 1) TRY(build_table_range(op, op->tab_tlo, op->tab_thi, mode));
     op->mode = mode;
+    return LS_OK;
+}
+
+ls_status ls_op_tuning(const ls_op* op, int32_t* table_ncoef, double* cand_ms) {
+    if (!op) return fail(LS_EINVAL, "null op");
+    if (table_ncoef) *table_ncoef = op->tab_nc;
+    if (cand_ms) for (int i = 0; i < 3; ++i) cand_ms[i] = op->tune_ms[i];
     return LS_OK;
 }
 
