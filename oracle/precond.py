@@ -10,11 +10,15 @@
   Reading: the Duan-Rokhlin corrected weights are not available, the diagonal
   is the integral of G over the disc of area h_C^2,
   (i pi a H1(k a)) / (2k) - 1/k^2 with pi a^2 = h_C^2.
-* Stencil (Eq. sparsifying_min): B = V^(C)(N(0), N(0)^c) for the 3x3 stencil
-  around the grid node (n_x // 2, n_y // 2) against every other grid node;
+* Stencil (Eq. sparsifying_min, Eq. cart_neighbors_LS): the neighbourhood
+  N(j) = {i : |i - j|_inf <= 1, z_i in D} is the 3x3 block truncated to the
+  grid, so a row's stencil depends on its class c = ca + 3 cb (ca = 0 at the
+  first column, 1 inside, 2 at the last column; cb likewise for rows): interior
+  (9 points), edge (6) or corner (4).  By translation invariance one
+  representative per class suffices (the grid centre, the middle of an edge, the
+  corner itself): B = V^(C)(N(j), N(j)^c) against every other grid node,
   v = conj of the left singular vector of the smallest singular value.
-  A(j, N(j)) = v for rows with a full 3x3 stencil inside the grid; other rows of
-  A are identity rows (reading: the paper only treats the full stencil).
+  A(j, N(j)) = v_c(j) on every row.
 * C (Eq. LC_def): A L^(C) kept on the 3x3 pattern of each row, with
   L^(C) = I + k^2 V^(C) M^(C), M^(C) = diag(m(z_j)).  S = C^{-1} A, applied
   with a sparse LU (SuperLU from scipy).
@@ -88,16 +92,33 @@ def cartesian_kernel(k, h, da, db):
     return out
 
 
-def stencil_vector(grid, k):
-    """v (9 entries, STENCIL order) minimising ||v V^(C)(N(0), N(0)^c)||, ||v|| = 1."""
-    ca, cb = grid.nx // 2, grid.ny // 2
+def row_class(grid, a, b):
+    """Class of grid row (a, b): ca + 3 cb with 0 / 1 / 2 = first / inner / last index."""
+    ca = 0 if a == 0 else (2 if a == grid.nx - 1 else 1)
+    cb = 0 if b == 0 else (2 if b == grid.ny - 1 else 1)
+    return ca + 3 * cb
+
+
+def stencil_vectors(grid, k):
+    """v[c] (9 entries in STENCIL order, zero outside the grid) minimising
+    ||v V^(C)(N(j), N(j)^c)||, ||v|| = 1, at the representative node j of each
+    class c; also the singular values of each B."""
     A, B = np.meshgrid(np.arange(grid.nx), np.arange(grid.ny))
     A, B = A.ravel(), B.ravel()
-    keep = ~((np.abs(A - ca) <= 1) & (np.abs(B - cb) <= 1))
-    rows = [cartesian_kernel(k, grid.h, A[keep] - (ca + da), B[keep] - (cb + db)) for da, db in STENCIL]
-    Bm = np.stack(rows, axis=0)
-    U, s, _ = np.linalg.svd(Bm, full_matrices=False)
-    return np.conj(U[:, -1]), s
+    rep_a = (0, grid.nx // 2, grid.nx - 1)
+    rep_b = (0, grid.ny // 2, grid.ny - 1)
+    vs, svs = np.zeros((9, 9), np.complex128), []
+    for c in range(9):
+        ca, cb = rep_a[c % 3], rep_b[c // 3]
+        offs = [s for s, (da, db) in enumerate(STENCIL)
+                if 0 <= ca + da < grid.nx and 0 <= cb + db < grid.ny]
+        keep = ~((np.abs(A - ca) <= 1) & (np.abs(B - cb) <= 1))
+        rows = [cartesian_kernel(k, grid.h, A[keep] - (ca + STENCIL[s][0]), B[keep] - (cb + STENCIL[s][1]))
+                for s in offs]
+        U, sv, _ = np.linalg.svd(np.stack(rows, axis=0), full_matrices=False)
+        vs[c, offs] = np.conj(U[:, -1])
+        svs.append(sv)
+    return vs, svs
 
 
 class Preconditioner:
@@ -105,7 +126,7 @@ class Preconditioner:
         self.grid, self.k = grid, float(k)
         self.T = transfer_CQ(grid, nodes)
         self.TQC, self.D = transfer_QC_II(self.T)
-        self.v, self.sv = stencil_vector(grid, k)
+        self.v, self.sv = stencil_vectors(grid, k)
         self.m_grid = np.asarray(m_grid, np.complex128)
         self.A, self.C = self._assemble()
         self.lu = spla.splu(self.C.tocsc())
@@ -120,13 +141,11 @@ class Preconditioner:
         for b in range(ny):
             for a in range(nx):
                 j = a + nx * b
-                full = 1 <= a <= nx - 2 and 1 <= b <= ny - 2
+                vc = v[row_class(g, a, b)]
                 arow = {}
-                if full:
-                    for s, (da, db) in enumerate(STENCIL):
-                        arow[(a + da, b + db)] = v[s]
-                else:
-                    arow[(a, b)] = 1.0
+                for s, (da, db) in enumerate(STENCIL):
+                    if 0 <= a + da < nx and 0 <= b + db < ny:
+                        arow[(a + da, b + db)] = vc[s]
                 for (ia, ib), av in arow.items():
                     Ar.append(j); Ac.append(ia + nx * ib); Av.append(av)
                 # C_jl = sum_i A_ji (delta_il + k^2 V^(C)_il m_l), l in the 3x3 pattern of j
