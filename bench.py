@@ -261,6 +261,133 @@ def precision_report(args):
     print(json.dumps(line), flush=True)
 
 
+def batched_pairsum_report(args):
+    """--workload batched: the batched pair sum alone (two-material disk, k = 20, 40,200 nodes,
+    64 right-hand sides), tensor-core GEMM (k_pairsum_tc) against the CUDA-core kernel
+    (k_pairsum_multi_f32), each timed with CUDA events over --steps launches after
+    --warmup, with its error against the FP64 pair sum on 4 sampled right-hand sides.
+    Also the launch to profile the tensor-core kernel.  One JSON line."""
+    import torch
+    import paper_2608_17615_b300 as L
+    from lsinput.workloads import random_density, two_material
+
+    torch.cuda.set_device(0)
+    wl = two_material("small")
+    n = wl.mesh.n_nodes
+    R = 64
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, use_precond=0)
+    F = torch.from_numpy(np.stack([random_density(n, 900 + r) for r in range(R)])).cuda()
+    Y = torch.empty_like(F)
+    sample = (0, 21, 42, 63)
+    ref = {}
+    for r in sample:
+        y1 = torch.empty_like(F[r])
+        op.pairsum_dev(F[r].contiguous(), y1)
+        ref[r] = y1
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    tf32_peak = peaks.get("bf16_tflops", 1800.0) * (1.1 / 2.25)
+    out = {}
+    for kind, name in ((1, "tensor_cores"), (0, "cuda_cores")):
+        op.set_batch_kernel(kind, 4)
+        for _ in range(max(1, args.warmup)):
+            op.pairsum_batch_dev(F, Y)
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            op.pairsum_batch_dev(F, Y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        err = max((torch.linalg.norm(Y[r] - ref[r]) / torch.linalg.norm(ref[r])).item() for r in sample)
+        pairs = R * n * (n - 1)
+        out[name] = {"ms_per_launch_incl_epilogue": ms, "pair_rhs_interactions_per_s": pairs / (ms * 1e-3),
+                     "rel_err_vs_fp64_max_of_4": err}
+        if kind == 1:
+            flops = 24.0 * pairs                       # 3 split products x 2 K-slots x 2 columns x 2 flops
+            out[name]["tensor_pipe"] = {"executed_tf32_tflops": flops / (ms * 1e-3) / 1e12,
+                                        "peak_tf32_tflops": tf32_peak,
+                                        "peak_source": "measured bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"}
+    line = {"report": "batched pair sum", "config": {"workload": "two-material disk, k=20, 40,200 nodes, "
+            "64 right-hand sides, tensor-core run length 4 stages", "nodes": n, "rhs": R},
+            "speedup_tensor_vs_cuda_cores": out["cuda_cores"]["ms_per_launch_incl_epilogue"]
+            / out["tensor_cores"]["ms_per_launch_incl_epilogue"], "forms": out}
+    print(json.dumps(line), flush=True)
+
+
+BATCH_NODES = (5000, 8000, 14000, 22000, 34000, 50000, 72000, 100000)
+
+
+def batching_report(args):
+    """--workload batching: the batching form's configuration, 8 star-shaped scatterers of
+    uneven size (5k-100k nodes, k = 10, 20, 40 in turn, grids at k h_C ~ 0.19), 64 incident
+    directions each, all solved in lock step with one persistent pair-sum launch per
+    iteration (ls_solve_multi_dev), once on the tensor cores and once on the CUDA cores;
+    error of direction 0 of every scatterer against its FP64-accurate double-float solve.
+    One JSON line; not part of the default run."""
+    import torch
+    import paper_2608_17615_b300 as L
+    from lsinput.workloads import star_scatterer
+
+    torch.cuda.set_device(0)
+    R = 64
+    ops, B, wls, setup = [], [], [], 0.0
+    for s, nn in enumerate(BATCH_NODES):
+        k = (10.0, 20.0, 40.0)[s % 3]
+        nx = int(round(2.9 * k / 0.19)) + 1
+        wl = star_scatterer(s, nn, k=k, nx=nx, ny=nx, n_dirs=R)
+        t0 = time.perf_counter()
+        op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, box=wl.box, nx=wl.nx, ny=wl.ny, tol=1e-8,
+                        max_iter=100)
+        setup += time.perf_counter() - t0
+        b = torch.empty((R, wl.mesh.n_nodes), dtype=torch.complex128, device="cuda")
+        op.incident_dev(wl.directions, b)
+        ops.append(op)
+        B.append(b)
+        wls.append(wl)
+        print(f"[batching] scatterer {s}: {wl.mesh.n_nodes} nodes, k={k}, grid {nx}^2", file=sys.stderr, flush=True)
+    n_s = [w.mesh.n_nodes for w in wls]
+    out = {}
+    sols = {}
+    for kind, name in ((1, "tensor_cores"), (0, "cuda_cores")):
+        for op in ops:
+            op.set_batch_kernel(kind)
+        U = [torch.empty_like(b) for b in B]
+        L.solve_multi_dev(ops, B, U)                   # warm-up (grid autotune, buffers)
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        iters, st = L.solve_multi_dev(ops, B, U)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        it = np.asarray(iters)
+        pairs = float(sum(int(it[s].max()) * R * n * (n - 1) for s, n in enumerate(n_s)))
+        out[name] = {"ms": ms, "solves_per_s": len(ops) * R / (ms * 1e-3), "status": int(st),
+                     "iterations_max_per_scatterer": [int(x.max()) for x in it],
+                     "pair_interactions_per_s": pairs / (ms * 1e-3)}
+        sols[name] = [u[0].clone() for u in U]
+    errs = []
+    for s, op in enumerate(ops):
+        op.set_pairsum(3)
+        u1 = torch.empty_like(B[s][0]).view(1, -1)
+        op.solve_dev(B[s][0].contiguous().view(1, -1), u1)
+        ref = u1[0]
+        errs.append({name: (torch.linalg.norm(sols[name][s] - ref) / torch.linalg.norm(ref)).item() for name in sols})
+    for name in sols:
+        out[name]["rel_err_vs_fp64_accurate_dir0_max"] = max(e[name] for e in errs)
+    line = {"report": "batching form", "config": {"workload": "8 star scatterers (r = 1 + 0.2 cos(5 theta + phi)), "
+            f"nodes {n_s}, k = 10/20/40, 64 directions each, tol 1e-8", "nodes": n_s, "rhs_per_scatterer": R},
+            "setup_s": setup, "forms": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -268,12 +395,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="default", choices=["default", "precision"])
+    ap.add_argument("--workload", default="default", choices=["default", "precision", "batching", "batched"])
     args = ap.parse_args()
     rank, world, local = _env_rank()
     if args.workload == "precision":
         if rank == 0:
             precision_report(args)
+        return
+    if args.workload == "batching":
+        if rank == 0:
+            batching_report(args)
+        return
+    if args.workload == "batched":
+        if rank == 0:
+            batched_pairsum_report(args)
         return
     if args.impl == "reference":
         if rank == 0:

@@ -40,7 +40,8 @@ typedef enum {
     LS_ENOMEM = 2,      /* device or host allocation failed */
     LS_ECUDA = 3,       /* a CUDA runtime / library call failed */
     LS_ESINGULAR = 4,   /* a block of the Cartesian matrix C could not be factored */
-    LS_ENOCONV = 5      /* GMRES hit max_iter; outputs hold the last iterate */
+    LS_ENOCONV = 5,     /* GMRES hit max_iter; outputs hold the last iterate */
+    LS_ETIMEOUT = 6     /* a bounded device wait ran out (tensor-core pipeline); the context stays usable */
 } ls_status;
 
 typedef struct ls_mesh ls_mesh;
@@ -223,6 +224,49 @@ ls_status ls_incident_dev(ls_op* op, int32_t R, const double* dir_angles, void* 
  */
 ls_status ls_misfit_gradient_dev(ls_op* op, int32_t R, const void* u_dev, int32_t n_ff, const double* ff_angles,
                                  const void* resid_dev, double* grad_dev, int32_t* iters_out);
+
+/*
+ * Batched versions for many incident directions: the R transposed systems advance
+ * in lock step with one batched pair-sum launch per iteration (the FP32 batched
+ * kernel of ls_solve_batch_dev on unit weights, P^T batched likewise).
+ *   ls_solve_transpose_batch_dev   L^T lambda_r = g_r, g_dev, lambda_dev [R][N]
+ *   ls_misfit_gradient_batch_dev   as ls_misfit_gradient_dev with the batched adjoint solve
+ */
+ls_status ls_solve_transpose_batch_dev(ls_op* op, int32_t R, const void* g_dev, void* lambda_dev, int32_t* iters_out);
+
+/*
+ * Kernel of the batched pair sum (ls_pairsum_batch_dev, ls_solve_batch_dev,
+ * ls_solve_multi_dev and the batched transposed solves):
+ *   kind 0  CUDA cores: FP32 H0 table, Kahan-compensated FP32 sums per (target, RHS)
+ *           (pair sum within ~1e-7 of the FP64 one)
+ *   kind 1  tensor cores (default): the sum over sources as a GEMM on tcgen05
+ *           kind::tf32 with 3-term TF32 splits of H and of the densities, FP32
+ *           accumulation in tensor memory restarted every `fold` stages of 16
+ *           sources, run totals Kahan-folded, chunks summed in FP64.  The tensor
+ *           memory accumulation truncates, so the pair sum carries ~3e-7 x fold
+ *           relative error; batched solves on kind 1 are therefore followed by up
+ *           to `refine` steps of iterative refinement whose residuals use the
+ *           kind 0 operator, which restores the kind 0 accuracy (refine = 0: none).
+ *           Refinement stops when ||P r|| <= max(tol, 2e-7) ||P b|| (the kind 0
+ *           operator's rounding level) or when a correction no longer halves the
+ *           residual; LS_ENOCONV if neither happens within `refine` steps.
+ * Defaults: kind 1, fold 4, refine 4.
+ * Errors: LS_EINVAL for kind outside {0, 1}, fold < 1 or refine < 0.  A stalled
+ * tensor-core pipeline (every wait in the kernel is bounded) makes the next call
+ * that synchronises return LS_ETIMEOUT.
+ */
+ls_status ls_op_set_batch_kernel(ls_op* op, int32_t kind, int32_t fold, int32_t refine);
+
+/*
+ * Self-check of the tensor-core MMA path (no counterpart in the paper): one
+ * 128 x N x 32 product of exactly representable values through the shared-memory
+ * layouts, descriptors and tcgen05.mma / tcgen05.ld sequence of the batched pair
+ * sum, compared with the host product.  *max_abs_err = 0 when the path is right.
+ * N a multiple of 16 in [16, 256].  Synchronises the device.
+ */
+ls_status ls_tc_gemm_check(int32_t N, double* max_abs_err);
+ls_status ls_misfit_gradient_batch_dev(ls_op* op, int32_t R, const void* u_dev, int32_t n_ff, const double* ff_angles,
+                                       const void* resid_dev, double* grad_dev, int32_t* iters_out);
 
 /*
  * Export of the correction dV as CSR (rows = N_Q targets, columns = nodes).

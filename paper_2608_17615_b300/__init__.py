@@ -13,7 +13,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblsgpu.so")
 
-LS_OK, LS_EINVAL, LS_ENOMEM, LS_ECUDA, LS_ESINGULAR, LS_ENOCONV = range(6)
+LS_OK, LS_EINVAL, LS_ENOMEM, LS_ECUDA, LS_ESINGULAR, LS_ENOCONV, LS_ETIMEOUT = range(7)
 _STATUS = {0: "LS_OK", 1: "LS_EINVAL", 2: "LS_ENOMEM", 3: "LS_ECUDA", 4: "LS_ESINGULAR", 5: "LS_ENOCONV"}
 
 EXPORTED = ["ls_params_default", "ls_mesh_create", "ls_mesh_destroy", "ls_mesh_num_nodes", "ls_operator_create",
@@ -21,6 +21,8 @@ EXPORTED = ["ls_params_default", "ls_mesh_create", "ls_mesh_destroy", "ls_mesh_n
             "ls_solve", "ls_solve_dev", "ls_op_correction", "ls_correction_host", "ls_hankel0_dev",
             "ls_pairsum_batch_dev", "ls_solve_batch_dev", "ls_solve_multi_dev", "ls_apply_transpose_dev", "ls_potential_transpose_dev", "ls_apply_precond_transpose_dev",
             "ls_solve_transpose_dev", "ls_op_set_contrast", "ls_incident_dev", "ls_misfit_gradient_dev",
+            "ls_solve_transpose_batch_dev", "ls_misfit_gradient_batch_dev",
+            "ls_op_set_batch_kernel", "ls_tc_gemm_check",
             "ls_op_set_pairsum", "ls_op_set_timing", "ls_op_setup_times", "ls_op_tuning", "ls_op_stats", "ls_probe_fp64", "ls_pairsum_noalloc", "ls_last_error"]
 
 
@@ -68,6 +70,10 @@ def _load():
         "ls_op_set_contrast": (I32, [P, P]),
         "ls_incident_dev": (I32, [P, I32, P, P]),
         "ls_misfit_gradient_dev": (I32, [P, I32, P, I32, P, P, P, P]),
+        "ls_solve_transpose_batch_dev": (I32, [P, I32, P, P, P]),
+        "ls_op_set_batch_kernel": (I32, [P, I32, I32, I32]),
+        "ls_tc_gemm_check": (I32, [I32, P]),
+        "ls_misfit_gradient_batch_dev": (I32, [P, I32, P, I32, P, P, P, P]),
         "ls_op_set_pairsum": (I32, [P, I32]),
         "ls_op_set_timing": (I32, [P, I32]),
         "ls_op_setup_times": (I32, [P, P]),
@@ -255,10 +261,30 @@ class Operator:
                                                 _dptr(grad), _ptr(iters)), allow=(LS_ENOCONV,))
         return iters, st
 
+    def solve_transpose_batch_dev(self, g, lam):
+        R = g.shape[0]
+        iters = np.zeros(R, np.int32)
+        st = _check(_lib.ls_solve_transpose_batch_dev(self.handle, R, _dptr(g), _dptr(lam), _ptr(iters)),
+                    allow=(LS_ENOCONV,))
+        return iters, st
+
+    def misfit_gradient_batch_dev(self, u, ff_angles, resid, grad):
+        ff = np.ascontiguousarray(ff_angles, np.float64).ravel()
+        R = u.shape[0]
+        iters = np.zeros(R, np.int32)
+        st = _check(_lib.ls_misfit_gradient_batch_dev(self.handle, R, _dptr(u), ff.size, _ptr(ff), _dptr(resid),
+                                                      _dptr(grad), _ptr(iters)), allow=(LS_ENOCONV,))
+        return iters, st
+
     def set_pairsum(self, mode):
         """0: FP64 table, 1: FP64 direct, 2: FP32 precision form."""
         _check(_lib.ls_op_set_pairsum(self.handle, int(mode)))
         self.params.pairsum = int(mode)
+
+    def set_batch_kernel(self, kind, fold=4, refine=4):
+        """Batched pair sum on 0: CUDA cores, 1: tensor cores (accumulator restarted every fold
+        stages; batched solves refined up to `refine` times against the kind-0 operator)."""
+        _check(_lib.ls_op_set_batch_kernel(self.handle, int(kind), int(fold), int(refine)))
 
     def set_timing(self, on=True):
         _check(_lib.ls_op_set_timing(self.handle, 1 if on else 0))
@@ -322,6 +348,13 @@ def solve_multi_dev(ops, B, U):
 def hankel0_dev(z, out):
     """out[i] = H0^(1)(z[i]) by the device routine of the pair sum (z float64, out complex128 tensors)."""
     _check(_lib.ls_hankel0_dev(z.numel(), _dptr(z), _dptr(out), ctypes.c_void_p(_current_stream())))
+
+
+def tc_gemm_check(N=128):
+    """Max abs error of one exact 128 x N x 32 product through the tensor-core path (0 when right)."""
+    e = ctypes.c_double()
+    _check(_lib.ls_tc_gemm_check(int(N), ctypes.byref(e)))
+    return e.value
 
 
 def probe_fp64():

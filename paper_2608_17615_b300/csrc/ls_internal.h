@@ -43,8 +43,9 @@ struct GridSetup {
     std::vector<int32_t> tqc_cols;
     std::vector<double> tqc_vals;
     std::vector<double> D;            // [nx*ny]
-    // sparsifying stencil v (3x3, index (da+1) + 3 (db+1))
-    std::complex<double> v[9];
+    // sparsifying stencils v[c][(da+1) + 3 (db+1)] per grid-row class c = ca + 3 cb
+    // (0 / 1 / 2 = first / inner / last column or row); zero at offsets outside the grid
+    std::complex<double> v[9][9];
     // C in block-tridiagonal form: [ny][3 (db)][3 (da)][nx]; entry C(j=(a,b), l=(a+da,b+db))
     std::vector<std::complex<double>> cband;
 };

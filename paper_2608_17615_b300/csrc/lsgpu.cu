@@ -9,7 +9,8 @@
 //                    correction (VDIM dV, Eq. DIM_decomp) and the epilogue
 //                    (L x)_j = x_j + k^2 [(i/4) sum + sum_q dV_jq m_q x_q]  (Eq. linear_system_matrix)
 //   k_tqc            T_Q^C gather (Approach II, Eq. T_H^C_def) over the transposed CSR
-//   k_stencil        t = A g with the 3 x 3 sparsifying stencil (Eq. sparsifying_min)
+//   k_stencil        t = A g with the 3 x 3 sparsifying stencils (Eq. sparsifying_min), one per
+//                    grid-row class (interior, edges, corners; Eq. cart_neighbors_LS)
 //   k_bt_fwd/bwd     block-tridiagonal solve C t' = t with precomputed dense
 //                    S_b^{-1} and S_b^{-1} C_{b,b+1} (block LU of C, Eq. LC_def)
 //   k_tcq            z_q = w_q + sum_4 psi (t' - g) (Eq. preconditioner_factored)
@@ -17,6 +18,7 @@
 //   k_givens         Hessenberg column update and Givens rotation, residual history
 //   k_farfield       u_inf(theta) = -k^2 e^{i pi/4}/sqrt(8 pi k) sum_j w_j m_j u_j e^{-i k xhat . y_j}
 //   k_incident       b_j = exp(i k d . y_j)
+//   k_pairsum_tc     batched pair sum as a tcgen05 (kind::tf32) GEMM, tc_pairsum.cuh
 // Device H0^(1): ascending series of J0, Y0 for z <= 6 (Abramowitz & Stegun 9.1.12,
 // 9.1.13); for z > 6 the modulus/phase form sqrt(2/(pi z)) (P + i Q) e^{i(z - pi/4)}
 // with P, zQ fitted polynomials in 36/z^2 (constants in hankel_fit.h).
@@ -88,7 +90,14 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-struct Stencil9 { double2 v[9]; };   // 3x3 sparsifying stencil, index (da+1) + 3 (db+1)
+// Sparsifying stencils (Eq. sparsifying_min) per grid-row class c = ca + 3 cb (ca = 0 on the
+// first column, 1 inside, 2 on the last; cb likewise): st[9 c + (da+1) + 3 (db+1)], zero at
+// offsets that leave the grid (Eq. cart_neighbors_LS truncates the neighbourhood to D).
+__device__ __forceinline__ int grid_row_class(int a, int b, int nx, int ny) {
+    const int ca = a == 0 ? 0 : (a == nx - 1 ? 2 : 1);
+    const int cb = b == 0 ? 0 : (b == ny - 1 ? 2 : 1);
+    return ca + 3 * cb;
+}
 
 #define LS_INV_SQRT_PI 0.56418958354775628695
 #define LS_TWO_OVER_PI 0.63661977236758134308
@@ -683,6 +692,8 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum_persist(const PSDesc* __rest
     }
 }
 
+#include "tc_pairsum.cuh"
+
 // mode 0: y = x + k2 * ((i/4) sum_c partial + dV (m x));  mode 1: y = (i/4) sum_c partial
 __global__ void k_apply_epi(int n, int nchunk, const double2* __restrict__ partial, const int64_t* __restrict__ rowptr,
                             const int* __restrict__ cols, const double2* __restrict__ vals,
@@ -763,18 +774,18 @@ __global__ void k_applyT_epi(int n, int nchunk, const double2* __restrict__ part
     }
 }
 
-// (A^T y)_l = sum_s v_s y_{l - s} over full-stencil rows l - s, plus y_l on grid-edge rows
-__global__ void k_stencilT(int nx, int ny, Stencil9 st, const double2* __restrict__ y, const double2* __restrict__ g,
-                           double2* __restrict__ r) {
+// (A^T y)_l = sum_s A(l - s, l) y_{l - s} over grid rows l - s, A(j, j + s) = st[9 c(j) + s]
+__global__ void k_stencilT(int nx, int ny, const double2* __restrict__ st, const double2* __restrict__ y,
+                           const double2* __restrict__ g, double2* __restrict__ r) {
     int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= nx * ny) return;
     int a = l % nx, b = l / nx;
     double2 acc = make_double2(0.0, 0.0);
-    if (a < 1 || a > nx - 2 || b < 1 || b > ny - 2) acc = y[l];
 #pragma unroll
     for (int s = 0; s < 9; ++s) {
         int ja = a - (s % 3 - 1), jb = b - (s / 3 - 1);
-        if (ja >= 1 && ja <= nx - 2 && jb >= 1 && jb <= ny - 2) acc = cadd(acc, cmul(st.v[s], y[ja + nx * jb]));
+        if (ja >= 0 && ja < nx && jb >= 0 && jb < ny)
+            acc = cadd(acc, cmul(st[9 * grid_row_class(ja, jb, nx, ny) + s], y[ja + nx * jb]));
     }
     r[l] = csub(acc, g[l]);                  // (S^T - I) g = A^T C^{-T} g - g
 }
@@ -909,20 +920,18 @@ __global__ void k_tqc(int nc, const int64_t* __restrict__ rp, const int* __restr
     g[i] = make_double2(ar, ai);
 }
 
-// t = A g: 3x3 stencil on rows with a full stencil, identity on grid-edge rows
-__global__ void k_stencil(int nx, int ny, Stencil9 st, const double2* __restrict__ g, double2* __restrict__ t) {
+// t = A g: row (a, b) takes the stencil of its class over the in-grid offsets
+__global__ void k_stencil(int nx, int ny, const double2* __restrict__ st, const double2* __restrict__ g,
+                          double2* __restrict__ t) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= nx * ny) return;
     int a = idx % nx, b = idx / nx;
-    if (a < 1 || a > nx - 2 || b < 1 || b > ny - 2) {
-        t[idx] = g[idx];
-        return;
-    }
+    const double2* v = st + 9 * grid_row_class(a, b, nx, ny);
     double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
     for (int s = 0; s < 9; ++s) {
-        int da = s % 3 - 1, db = s / 3 - 1;
-        acc = cadd(acc, cmul(st.v[s], g[idx + da + db * nx]));
+        int la = a + s % 3 - 1, lb = b + s / 3 - 1;
+        if (la >= 0 && la < nx && lb >= 0 && lb < ny) acc = cadd(acc, cmul(v[s], g[la + nx * lb]));
     }
     t[idx] = acc;
 }
@@ -1235,17 +1244,21 @@ __global__ void k_tqc_multi(int nc, const int64_t* __restrict__ rp, const int* _
     g[(size_t)r * nc + i] = make_double2(ar, ai);
 }
 
-__global__ void k_stencil_multi(int nx, int ny, Stencil9 st, const double2* __restrict__ g, double2* __restrict__ t) {
+__global__ void k_stencil_multi(int nx, int ny, const double2* __restrict__ st, const double2* __restrict__ g,
+                                double2* __restrict__ t) {
     int r = blockIdx.y;
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     const int nc = nx * ny;
     if (idx >= nc) return;
     const double2* gr = g + (size_t)r * nc;
     int a = idx % nx, b = idx / nx;
-    if (a < 1 || a > nx - 2 || b < 1 || b > ny - 2) { t[(size_t)r * nc + idx] = gr[idx]; return; }
+    const double2* v = st + 9 * grid_row_class(a, b, nx, ny);
     double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
-    for (int s = 0; s < 9; ++s) acc = cadd(acc, cmul(st.v[s], gr[idx + (s % 3 - 1) + (s / 3 - 1) * nx]));
+    for (int s = 0; s < 9; ++s) {
+        int la = a + s % 3 - 1, lb = b + s / 3 - 1;
+        if (la >= 0 && la < nx && lb >= 0 && lb < ny) acc = cadd(acc, cmul(v[s], gr[la + nx * lb]));
+    }
     t[(size_t)r * nc + idx] = acc;
 }
 
@@ -1312,12 +1325,12 @@ __global__ void k_tcq_multi(int nq, int nc, const int* __restrict__ idx, const d
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq) return;
     const double2* tpr = tp + (size_t)r * nc;
-    const double2* gr = g + (size_t)r * nc;
+    const double2* gr = g ? g + (size_t)r * nc : nullptr;
     double2 acc = win[(size_t)r * sin_ + q];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         int i = idx[4 * q + c];
-        double2 d = csub(tpr[i], gr[i]);
+        double2 d = g ? csub(tpr[i], gr[i]) : tpr[i];
         acc.x = fma(wt[4 * q + c], d.x, acc.x);
         acc.y = fma(wt[4 * q + c], d.y, acc.y);
     }
@@ -1469,6 +1482,126 @@ __global__ void k_combine_multi(int n, const int* its, const double2* __restrict
     u[(size_t)r * su + q] = acc;
 }
 
+// batched L^T epilogue: y_r = x_r + k^2 m (w (i/4) sum_c partial_r + dV^T x_r)
+__global__ void k_applyT_epi_multi(int n, int nchunk, const double2* __restrict__ partial, const int64_t* __restrict__ rowptr,
+                                   const int* __restrict__ cols, const double2* __restrict__ vals,
+                                   const double2* __restrict__ m, const double* __restrict__ w,
+                                   const double2* __restrict__ x, size_t sx, double k2, double2* __restrict__ y, size_t sy) {
+    const int r = blockIdx.y;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const int j = warp;
+    const double2* xr = x + (size_t)r * sx;
+    const double2* pr = partial + (size_t)r * nchunk * n;
+    double sr = 0.0, si = 0.0;
+    for (int c = lane; c < nchunk; c += 32) {
+        double2 p = pr[(size_t)c * n + j];
+        sr += p.x;
+        si += p.y;
+    }
+    double cr = 0.0, ci = 0.0;
+    for (int64_t e = rowptr[j] + lane; e < rowptr[j + 1]; e += 32) {
+        double2 t = cmul(vals[e], xr[cols[e]]);
+        cr += t.x;
+        ci += t.y;
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    cr = warp_sum(cr);
+    ci = warp_sum(ci);
+    if (lane == 0) {
+        double2 vt = make_double2(w[j] * (-0.25 * si) + cr, w[j] * (0.25 * sr) + ci);
+        double2 mv = cmul(m[j], vt);
+        double2 xj = xr[j];
+        y[(size_t)r * sy + j] = make_double2(xj.x + k2 * mv.x, xj.y + k2 * mv.y);
+    }
+}
+
+__global__ void k_btT_fwd_multi(int nx, int ny, int b, const double2* __restrict__ GT, double2* __restrict__ z) {
+    extern __shared__ double2 sh[];
+    const size_t off = (size_t)blockIdx.y * nx * ny;
+    for (int c = threadIdx.x; c < nx; c += blockDim.x) sh[c] = z[off + (size_t)(b - 1) * nx + c];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= nx) return;
+    const double2* Gr = GT + ((size_t)(b - 1) * nx + row) * nx;
+    double ar = 0.0, ai = 0.0;
+    for (int c = lane; c < nx; c += 32) {
+        double2 gv = Gr[c], v = sh[c];
+        ar = fma(gv.x, v.x, fma(-gv.y, v.y, ar));
+        ai = fma(gv.x, v.y, fma(gv.y, v.x, ai));
+    }
+    ar = warp_sum(ar);
+    ai = warp_sum(ai);
+    if (lane == 0) {
+        double2 v = z[off + (size_t)b * nx + row];
+        z[off + (size_t)b * nx + row] = make_double2(v.x - ar, v.y - ai);
+    }
+}
+
+__global__ void k_btT_bwd_multi(int nx, int ny, int b, const double2* __restrict__ WT, const double2* __restrict__ cband,
+                                const double2* __restrict__ z, double2* __restrict__ x) {
+    extern __shared__ double2 sh[];
+    const size_t off = (size_t)blockIdx.y * nx * ny;
+    for (int c = threadIdx.x; c < nx; c += blockDim.x) {
+        double2 v = z[off + (size_t)b * nx + c];
+        if (b + 1 < ny) {
+            const double2* Cm1 = cband + (size_t)(b + 1) * 9 * nx;
+            const double2* xn = x + off + (size_t)(b + 1) * nx;
+            for (int da = -1; da <= 1; ++da) {
+                int a = c - da;
+                if (a >= 0 && a < nx) v = csub(v, cmul(Cm1[(size_t)(da + 1) * nx + a], xn[a]));
+            }
+        }
+        sh[c] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= nx) return;
+    const double2* Wr = WT + ((size_t)b * nx + row) * nx;
+    double ar = 0.0, ai = 0.0;
+    for (int c = lane; c < nx; c += 32) {
+        double2 wv = Wr[c], v = sh[c];
+        ar = fma(wv.x, v.x, fma(-wv.y, v.y, ar));
+        ai = fma(wv.x, v.y, fma(wv.y, v.x, ai));
+    }
+    ar = warp_sum(ar);
+    ai = warp_sum(ai);
+    if (lane == 0) x[off + (size_t)b * nx + row] = make_double2(ar, ai);
+}
+
+__global__ void k_stencilT_multi(int nx, int ny, const double2* __restrict__ st, const double2* __restrict__ y,
+                                 const double2* __restrict__ g, double2* __restrict__ r) {
+    const int nc = nx * ny;
+    const size_t off = (size_t)blockIdx.y * nc;
+    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nc) return;
+    int a = l % nx, b = l / nx;
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int s = 0; s < 9; ++s) {
+        int ja = a - (s % 3 - 1), jb = b - (s / 3 - 1);
+        if (ja >= 0 && ja < nx && jb >= 0 && jb < ny)
+            acc = cadd(acc, cmul(st[9 * grid_row_class(ja, jb, nx, ny) + s], y[off + ja + nx * jb]));
+    }
+    r[off + l] = csub(acc, g[off + l]);
+}
+
+// r_r = b_r - y_r and u_r += d_r over R systems of n entries (contiguous rows)
+__global__ void k_residual_multi(int64_t total, const double2* __restrict__ b, const double2* __restrict__ y,
+                                 double2* __restrict__ r) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < total) r[i] = csub(b[i], y[i]);
+}
+
+__global__ void k_accumulate_multi(int64_t total, const double2* __restrict__ d, double2* __restrict__ u) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < total) u[i] = cadd(u[i], d[i]);
+}
+
 __global__ void k_gmres_init_multi(int R, double2* g, size_t sg, const double2* beta2, double* hist, size_t shist, int* active,
                                    int* its) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1586,7 +1719,7 @@ struct ls_op {
     DevBuf<double2> cband, Wf, Gf;
     DevBuf<double2> WT, GT;              // transposed factors for P^T
     DevBuf<double> tqcT_cv, tcqT_w;      // T_C^Q^T gather weights (psi), T_Q^C^T corner weights (psi / D)
-    Stencil9 st{};
+    DevBuf<double2> st;                  // [9 classes][9 offsets] sparsifying stencils
     DevBuf<double2> pg, pt, ptp;         // grid work vectors
     // GMRES workspace
     DevBuf<double2> Vb, H, cs, sn, g, hv, yv, tmp, tmp2, dpart, scal;
@@ -1597,6 +1730,18 @@ struct ls_op {
     int t32_ncell = 0, t32_noct = 0, t32_blo = 0;
     size_t t32_bytes = 0;
     int bR = 0, b_nchunk = 1, b_spc = 0;
+    int b_nchunk_cur = 1;                // chunk count of the partials written by the last batched pair sum
+    // batched pair sum on the tensor cores (k_pairsum_tc): split densities, coordinates, error word
+    int batch_kernel = 1;                // 0: CUDA cores (k_pairsum_multi_f32), 1: tensor cores
+    int tc_fold = 4;                     // stages per accumulator run
+    int tc_refine = 4;                   // iterative-refinement steps after a tensor-core solve (0: none)
+    DevBuf<double2> ir_r, ir_d, ir_y;    // refinement work vectors [R][n]
+    int tc_nchunk = 0, tc_spc = 0, tc_npad = 0;
+    DevBuf<float4> tc_xy32, tc_Sc;
+    DevBuf<int> tc_err;
+    DevBuf<TCOp> tc_desc;                // per-launch operator descriptors (up to TC_MAX_OPS)
+    std::vector<TCOp> tc_hdesc;
+    int* tc_herr = nullptr;              // pinned copy of tc_err
     DevBuf<double2> bV, bH, bcs, bsn, bg, bhv, byv, btmp, bdpart, bscal, bpartial, bpg, bpt, bptp;
     DevBuf<double> bhist;
     DevBuf<int> bactive, bits;
@@ -1614,6 +1759,7 @@ struct ls_op {
         for (auto& e : ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
         if (gP) cudaGraphExecDestroy(gP);
         if (cap) cudaStreamDestroy(cap);
+        if (tc_herr) cudaFreeHost(tc_herr);
     }
 };
 
@@ -1702,7 +1848,7 @@ static ls_status apply_L(ls_op* op, const double2* x, double2* y) {
 static void launch_P_kernels(ls_op* op, cudaStream_t st, const double2* x, double2* z) {
     const int nc = op->nx * op->ny, nx = op->nx, ny = op->ny;
     k_tqc<<<(nc + 255) / 256, 256, 0, st>>>(nc, op->tqc_rp.p, op->tqc_ci.p, op->tqc_cv.p, x, op->pg.p);
-    k_stencil<<<(nc + 255) / 256, 256, 0, st>>>(nx, ny, op->st, op->pg.p, op->pt.p);
+    k_stencil<<<(nc + 255) / 256, 256, 0, st>>>(nx, ny, op->st.p, op->pg.p, op->pt.p);
     const int wpb = 8;                                   // warps per block in the block solve
     const int blocks = (nx + wpb - 1) / wpb;
     const size_t shm = sizeof(double2) * nx;
@@ -1761,7 +1907,7 @@ static ls_status apply_PT(ls_op* op, const double2* x, double2* z) {
         k_btT_fwd<<<blocks, 32 * wpb, shm, op->stream>>>(nx, b, op->GT.p, op->ptp.p);
     for (int b = ny - 1; b >= 0; --b)
         k_btT_bwd<<<blocks, 32 * wpb, shm, op->stream>>>(nx, ny, b, op->WT.p, op->cband.p, op->ptp.p, op->pt.p);
-    k_stencilT<<<(nc + 255) / 256, 256, 0, op->stream>>>(nx, ny, op->st, op->pt.p, op->pg.p, op->ptp.p);
+    k_stencilT<<<(nc + 255) / 256, 256, 0, op->stream>>>(nx, ny, op->st.p, op->pt.p, op->pg.p, op->ptp.p);
     k_tcq<<<(op->nq + 255) / 256, 256, 0, op->stream>>>(op->nq, op->tcq_idx.p, op->tcqT_w.p, op->ptp.p, nullptr, x, z);
     CK(cudaGetLastError());
     op->launches += 3 + (ny - 1) + ny;
@@ -2080,7 +2226,13 @@ static ls_status build_preconditioner(ls_op* op, const HostMesh& M, const double
     auto tl0 = std::chrono::steady_clock::now();
     const int nx = G.nx, ny = G.ny, nc = nx * ny;
     op->nx = nx; op->ny = ny;
-    for (int s = 0; s < 9; ++s) op->st.v[s] = make_double2(G.v[s].real(), G.v[s].imag());
+    {
+        std::vector<double2> hs(81);
+        for (int c = 0; c < 9; ++c)
+            for (int t = 0; t < 9; ++t) hs[9 * c + t] = make_double2(G.v[c][t].real(), G.v[c][t].imag());
+        CK(op->st.alloc(81));
+        CK(cudaMemcpy(op->st.p, hs.data(), sizeof(double2) * 81, cudaMemcpyHostToDevice));
+    }
     CK(op->tcq_idx.alloc(G.tcq_idx.size()));
     CK(op->tcq_w.alloc(G.tcq_w.size()));
     CK(op->tqc_rp.alloc(G.tqc_rowptr.size()));
@@ -2313,6 +2465,16 @@ static ls_status ensure_batch(ls_op* op, int R) {
     spc = ((spc + PS_TILE - 1) / PS_TILE) * PS_TILE;
     op->b_nchunk = (n + spc - 1) / spc;
     op->b_spc = spc;
+    {
+        // tensor-core form: units (128-target tile, source chunk) taken round-robin by one
+        // resident CTA per SM; about 8 units per SM, chunks a multiple of 16 sources
+        const int tb = (n + TC_M - 1) / TC_M;
+        int nc = std::max(1, std::min(32, (8 * nsm + tb - 1) / tb));
+        int tspc = (n + nc - 1) / nc;
+        tspc = ((tspc + TC_SRC - 1) / TC_SRC) * TC_SRC;
+        op->tc_spc = tspc;
+        op->tc_nchunk = (n + tspc - 1) / tspc;
+    }
     CK(op->bV.alloc((size_t)R * (maxit + 1) * n));
     CK(op->bH.alloc((size_t)R * ldh * maxit));
     CK(op->bcs.alloc((size_t)R * (maxit + 2)));
@@ -2323,7 +2485,7 @@ static ls_status ensure_batch(ls_op* op, int R) {
     CK(op->btmp.alloc((size_t)R * n));
     CK(op->bdpart.alloc((size_t)R * (maxit + 1) * op->dblk));
     CK(op->bscal.alloc((size_t)2 * R));
-    CK(op->bpartial.alloc((size_t)R * op->b_nchunk * n));
+    CK(op->bpartial.alloc((size_t)R * std::max(op->b_nchunk, op->tc_nchunk) * n));
     CK(op->bhist.alloc((size_t)R * (maxit + 2)));
     CK(op->bactive.alloc(R));
     CK(op->bits.alloc(R));
@@ -2347,9 +2509,148 @@ static MultiArgs multi_args(ls_op* op, int R, const double2* f, size_t sf, const
     return A;
 }
 
-// partial[r][c][j] for R densities f (stride sf)
+// partial[r][c][j] for R densities f (stride sf); w = nullptr takes unit weights
+static ls_status pairsum_batch(ls_op* op, int R, const double2* f, size_t sf, const double2* m, const double* w);
 static ls_status pairsum_batch(ls_op* op, int R, const double2* f, size_t sf, const double2* m) {
+    return pairsum_batch(op, R, f, sf, m, op->w.p);
+}
+static ls_status ensure_tc(ls_op* op) {
+    if (op->tc_herr) return LS_OK;
+    const int n = op->nq;
+    op->tc_npad = ((n + TC_SRC - 1) / TC_SRC) * TC_SRC;
+    CK(op->tc_xy32.alloc(op->tc_npad));
+    CK(op->tc_Sc.alloc((size_t)op->tc_npad * 64));
+    CK(op->tc_err.alloc(1));
+    CK(cudaMemsetAsync(op->tc_err.p, 0, sizeof(int), op->stream));
+    k_tc_xy32<<<(op->tc_npad + 255) / 256, 256, 0, op->stream>>>(n, op->tc_npad, op->xy.p, op->tc_xy32.p);
+    CK(cudaGetLastError());
+    CK(op->tc_desc.alloc(TC_MAX_OPS));
+    CK(cudaMallocHost(&op->tc_herr, sizeof(int)));
+    *op->tc_herr = 0;
+    return LS_OK;
+}
+
+static size_t tc_smem_bytes(int N, size_t tab_bytes, int nstg) {
+    const size_t stage = 2 * (size_t)TC_M * 2 * TC_SRC * 4 + 2 * (size_t)N * 2 * TC_SRC * 4;
+    const size_t stg = (size_t)TC_SRC * (N / 2) * 16 + TC_SRC * 16;
+    return 1024 + TC_NS * stage + (size_t)nstg * stg + tab_bytes;
+}
+
+static TCOp tc_desc_of(ls_op* op, int unit_begin) {
+    TCOp o;
+    o.xy32 = op->tc_xy32.p;
+    o.Sc = op->tc_Sc.p;
+    o.tab = (const float4*)op->tab32.p;
+    o.partial = op->bpartial.p;
+    o.k = op->k;
+    o.inv_k = 1.0 / op->k;
+    o.n = op->nq;
+    o.tblocks = (op->nq + TC_M - 1) / TC_M;
+    o.spc = op->tc_spc;
+    o.nchunk = op->tc_nchunk;
+    o.part_nchunk = op->tc_nchunk;
+    o.unit_begin = unit_begin;
+    o.units = o.tblocks * o.nchunk;
+    o.ncell = op->t32_ncell;
+    o.noct = op->t32_noct;
+    o.b_lo = op->t32_blo;
+    o.tab_words = (int)(op->t32_bytes / sizeof(float4));
+    return o;
+}
+
+// One tensor-core pair sum over S operators (each with R right-hand sides f_s, stride
+// sf_s), groups of up to 64 right-hand sides per launch; partials [R][tc_nchunk][n] per
+// operator.  desc: device array of S descriptors (rewritten here).
+static ls_status pairsum_tc_launch(int S, ls_op* const* ops, int R, const double2* const* f, const size_t* sf,
+                                   const double2* const* m, const double* const* w, TCOp* desc,
+                                   std::vector<TCOp>& host_desc, cudaStream_t st) {
+    int dev = 0, nsm = 148;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (S > TC_MAX_OPS) return fail(LS_EINVAL, "too many operators for one tensor-core launch");
+    std::vector<TCOp> d(S);
+    int total = 0;
+    size_t max_tab = 0;
+    for (int s = 0; s < S; ++s) {
+        d[s] = tc_desc_of(ops[s], total);
+        total += d[s].units;
+        max_tab = std::max(max_tab, ops[s]->t32_bytes);
+    }
+    // upload only when the descriptors changed (a pageable copy may synchronise the stream)
+    if (host_desc.size() != d.size() || std::memcmp(host_desc.data(), d.data(), sizeof(TCOp) * S) != 0) {
+        CK(cudaMemcpy(desc, d.data(), sizeof(TCOp) * S, cudaMemcpyHostToDevice));
+        host_desc = d;
+    }
+    for (int r0 = 0; r0 < R; r0 += 64) {
+        const int Rg = std::min(64, R - r0);
+        int Rp = 8;
+        while (Rp < Rg) Rp *= 2;
+        const int N = 2 * Rp;
+        for (int s = 0; s < S; ++s) {
+            ls_op* op = ops[s];
+            const int64_t tot = (int64_t)op->tc_npad * Rp;
+            k_tc_prep_S<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(op->nq, op->tc_npad, Rg, Rp, f[s] + (size_t)r0 * sf[s],
+                                                                     sf[s], w[s], m[s], op->tc_Sc.p);
+            op->launches++;
+        }
+        CK(cudaGetLastError());
+        TCArgs A;
+        A.ops = desc;
+        A.S = S;
+        A.total_units = total;
+        A.R = Rg; A.Rp = Rp; A.N = N;
+        A.F = std::max(1, ops[0]->tc_fold);
+        A.r_offset = r0;
+        A.idesc = tc::idesc_tf32(TC_M, N);
+        A.err = ops[0]->tc_err.p;
+        // three staging slots when they fit beside the table, else two
+        A.nstg = tc_smem_bytes(N, max_tab, 3) <= 227 * 1024 ? 3 : 2;
+        const size_t smem = tc_smem_bytes(N, max_tab, A.nstg);
+        if (smem > 227 * 1024) return fail(LS_EINVAL, "H0 table too large for the tensor-core pair sum");
+        CK(raise_smem_limit(k_pairsum_tc, smem));
+        k_pairsum_tc<<<std::min(total, nsm), TC_THREADS, smem, st>>>(A);
+        CK(cudaGetLastError());
+        ops[0]->launches++;
+    }
+    CK(cudaMemcpyAsync(ops[0]->tc_herr, ops[0]->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    for (int s = 0; s < S; ++s) ops[s]->b_nchunk_cur = ops[s]->tc_nchunk;
+    return LS_OK;
+}
+
+// Tensor-core form of pairsum_batch for one operator.
+static ls_status pairsum_batch_tc(ls_op* op, int R, const double2* f, size_t sf, const double2* m, const double* w) {
+    TRY(ensure_tc(op));
+    ls_op* ops[1] = {op};
+    const double2* fs[1] = {f};
+    const size_t sfs[1] = {sf};
+    const double2* ms[1] = {m};
+    const double* ws[1] = {w};
+    return pairsum_tc_launch(1, ops, R, fs, sfs, ms, ws, op->tc_desc.p, op->tc_hdesc, op->stream);
+}
+
+// error word of the tensor-core pair sum, read after a stream synchronisation
+static ls_status tc_status(ls_op* op) {
+    if (op->tc_herr && *op->tc_herr)
+        return fail(LS_ETIMEOUT, "tensor-core pair sum: a pipeline wait ran out (code " + std::to_string(*op->tc_herr) + ")");
+    return LS_OK;
+}
+
+static ls_status pairsum_batch(ls_op* op, int R, const double2* f, size_t sf, const double2* m, const double* w) {
     TRY(ensure_table32(op));
+    if (op->batch_kernel == 1) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (op->timing && op->ev.size() < 65536) {
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            op->ev.emplace_back(e0, e1);
+            CK(cudaEventRecord(e0, op->stream));
+        }
+        TRY(pairsum_batch_tc(op, R, f, sf, m, w));
+        if (e1) CK(cudaEventRecord(e1, op->stream));
+        op->pairsum_launches++;
+        return LS_OK;
+    }
+    op->b_nchunk_cur = op->b_nchunk;
     dim3 grid((op->nq + PS_TPB - 1) / PS_TPB, op->b_nchunk, (R + MRB - 1) / MRB);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (op->timing && op->ev.size() < 65536) {
@@ -2358,7 +2659,9 @@ static ls_status pairsum_batch(ls_op* op, int R, const double2* f, size_t sf, co
         op->ev.emplace_back(e0, e1);
         CK(cudaEventRecord(e0, op->stream));
     }
-    k_pairsum_multi_f32<<<grid, PS_TPB, op->t32_bytes, op->stream>>>(multi_args(op, R, f, sf, m), (const float4*)op->tab32.p);
+    MultiArgs A = multi_args(op, R, f, sf, m);
+    A.w = w;
+    k_pairsum_multi_f32<<<grid, PS_TPB, op->t32_bytes, op->stream>>>(A, (const float4*)op->tab32.p);
     CK(cudaGetLastError());
     if (e1) CK(cudaEventRecord(e1, op->stream));
     op->launches++;
@@ -2369,7 +2672,7 @@ static ls_status pairsum_batch(ls_op* op, int R, const double2* f, size_t sf, co
 static ls_status apply_L_batch(ls_op* op, int R, const double2* x, size_t sx, double2* y, size_t sy) {
     TRY(pairsum_batch(op, R, x, sx, op->m.p));
     dim3 grid((unsigned)(((int64_t)op->nq * 32 + 255) / 256), R);
-    k_apply_epi_multi<<<grid, 256, 0, op->stream>>>(op->nq, op->b_nchunk, op->bpartial.p, op->rowptr.p, op->cols.p,
+    k_apply_epi_multi<<<grid, 256, 0, op->stream>>>(op->nq, op->b_nchunk_cur, op->bpartial.p, op->rowptr.p, op->cols.p,
                                                     op->vals.p, op->m.p, x, sx, op->k * op->k, y, sy);
     CK(cudaGetLastError());
     op->launches++;
@@ -2380,7 +2683,7 @@ static ls_status apply_P_batch(ls_op* op, int R, const double2* x, size_t sx, do
     const int nx = op->nx, ny = op->ny, nc = nx * ny;
     dim3 gc((nc + 255) / 256, R);
     k_tqc_multi<<<gc, 256, 0, op->stream>>>(nc, op->tqc_rp.p, op->tqc_ci.p, op->tqc_cv.p, x, sx, op->bpg.p);
-    k_stencil_multi<<<gc, 256, 0, op->stream>>>(nx, ny, op->st, op->bpg.p, op->bpt.p);
+    k_stencil_multi<<<gc, 256, 0, op->stream>>>(nx, ny, op->st.p, op->bpg.p, op->bpt.p);
     const int wpb = 8;
     dim3 gb((nx + wpb - 1) / wpb, R);
     const size_t shm = sizeof(double2) * nx;
@@ -2395,16 +2698,37 @@ static ls_status apply_P_batch(ls_op* op, int R, const double2* x, size_t sx, do
     return LS_OK;
 }
 
+static ls_status apply_PT_batch(ls_op* op, int R, const double2* x, size_t sx, double2* z, size_t sz) {
+    const int nx = op->nx, ny = op->ny, nc = nx * ny;
+    dim3 gc((nc + 255) / 256, R);
+    k_tqc_multi<<<gc, 256, 0, op->stream>>>(nc, op->tqc_rp.p, op->tqc_ci.p, op->tqcT_cv.p, x, sx, op->bpg.p);
+    CK(cudaMemcpyAsync(op->bptp.p, op->bpg.p, sizeof(double2) * R * nc, cudaMemcpyDeviceToDevice, op->stream));
+    const int wpb = 8;
+    dim3 gb((nx + wpb - 1) / wpb, R);
+    const size_t shm = sizeof(double2) * nx;
+    for (int b = 1; b < ny; ++b)
+        k_btT_fwd_multi<<<gb, 32 * wpb, shm, op->stream>>>(nx, ny, b, op->GT.p, op->bptp.p);
+    for (int b = ny - 1; b >= 0; --b)
+        k_btT_bwd_multi<<<gb, 32 * wpb, shm, op->stream>>>(nx, ny, b, op->WT.p, op->cband.p, op->bptp.p, op->bpt.p);
+    k_stencilT_multi<<<gc, 256, 0, op->stream>>>(nx, ny, op->st.p, op->bpt.p, op->bpg.p, op->bptp.p);
+    dim3 gq((op->nq + 255) / 256, R);
+    k_tcq_multi<<<gq, 256, 0, op->stream>>>(op->nq, nc, op->tcq_idx.p, op->tcqT_w.p, op->bptp.p, nullptr, x, sx, z, sz);
+    CK(cudaGetLastError());
+    op->launches += 3 + (ny - 1) + ny;
+    return LS_OK;
+}
+
 // R lock-step GMRES solves (each system its own Krylov space, Hessenberg and stop),
 // split in stages so that several operators can share one pair-sum launch.
-static ls_status gb_begin(ls_op* op, int R, const double2* b) {
+static ls_status gb_begin(ls_op* op, int R, const double2* b, bool transpose = false) {
     TRY(ensure_batch(op, R));
     const int n = op->nq, maxit = op->prm.max_iter, ldh = maxit + 1;
     const size_t ldv = (size_t)n, svr = (size_t)(maxit + 1) * n, sH = (size_t)ldh * maxit, sg = maxit + 2;
     const bool prec = op->has_prec && op->prm.use_precond;
     const int tpb = 256, nb = (n + tpb - 1) / tpb;
     CK(cudaMemsetAsync(op->bH.p, 0, sizeof(double2) * R * sH, op->stream));
-    if (prec) TRY(apply_P_batch(op, R, b, n, op->btmp.p, n));
+    if (prec && transpose) TRY(apply_PT_batch(op, R, b, n, op->btmp.p, n));
+    else if (prec) TRY(apply_P_batch(op, R, b, n, op->btmp.p, n));
     else CK(cudaMemcpyAsync(op->btmp.p, b, sizeof(double2) * R * n, cudaMemcpyDeviceToDevice, op->stream));
     dim3 gd(op->dblk, R), gn(nb, R);
     k_dots_multi<<<gd, RED_TPB, 0, op->stream>>>(n, 1, op->btmp.p, n, ldv, op->btmp.p, n, op->bdpart.p, nullptr);
@@ -2418,7 +2742,7 @@ static ls_status gb_begin(ls_op* op, int R, const double2* b) {
 }
 
 // Everything of iteration j after the pair sum (partials in op->bpartial).
-static ls_status gb_after_pairsum(ls_op* op, int R, int j) {
+static ls_status gb_after_pairsum(ls_op* op, int R, int j, bool transpose = false) {
     const int n = op->nq, maxit = op->prm.max_iter, ldh = maxit + 1;
     const size_t ldv = (size_t)n, svr = (size_t)(maxit + 1) * n, sH = (size_t)ldh * maxit, sg = maxit + 2;
     const bool prec = op->has_prec && op->prm.use_precond;
@@ -2428,11 +2752,17 @@ static ls_status gb_after_pairsum(ls_op* op, int R, int j) {
     double2* vn = V + (size_t)(j + 1) * ldv;
     double2* hcol = op->bH.p + (size_t)j * ldh;
     dim3 ge((unsigned)(((int64_t)n * 32 + 255) / 256), R);
-    k_apply_epi_multi<<<ge, 256, 0, op->stream>>>(n, op->b_nchunk, op->bpartial.p, op->rowptr.p, op->cols.p, op->vals.p,
-                                                  op->m.p, vj, svr, op->k * op->k, prec ? op->btmp.p : vn,
-                                                  prec ? (size_t)n : svr);
+    if (transpose)
+        k_applyT_epi_multi<<<ge, 256, 0, op->stream>>>(n, op->b_nchunk_cur, op->bpartial.p, op->rowptrT.p, op->colsT.p,
+                                                       op->valsT.p, op->m.p, op->w.p, vj, svr, op->k * op->k,
+                                                       prec ? op->btmp.p : vn, prec ? (size_t)n : svr);
+    else
+        k_apply_epi_multi<<<ge, 256, 0, op->stream>>>(n, op->b_nchunk_cur, op->bpartial.p, op->rowptr.p, op->cols.p, op->vals.p,
+                                                      op->m.p, vj, svr, op->k * op->k, prec ? op->btmp.p : vn,
+                                                      prec ? (size_t)n : svr);
     op->launches++;
-    if (prec) TRY(apply_P_batch(op, R, op->btmp.p, n, vn, svr));
+    if (prec && transpose) TRY(apply_PT_batch(op, R, op->btmp.p, n, vn, svr));
+    else if (prec) TRY(apply_P_batch(op, R, op->btmp.p, n, vn, svr));
     const int J = j + 1;
     dim3 gd(op->dblk, R), gn(nb, R), gs((J + 127) / 128, R);
     k_dots_multi<<<gd, RED_TPB, 0, op->stream>>>(n, J, V, svr, ldv, vn, svr, op->bdpart.p, op->bactive.p);
@@ -2457,6 +2787,7 @@ static ls_status gb_active(ls_op* op, int R, std::vector<int>& act, bool& any) {
     act.resize(R);
     CK(cudaMemcpyAsync(act.data(), op->bactive.p, sizeof(int) * R, cudaMemcpyDeviceToHost, op->stream));
     CK(cudaStreamSynchronize(op->stream));
+    TRY(tc_status(op));
     any = false;
     for (int r = 0; r < R; ++r) any = any || act[r];
     return LS_OK;
@@ -2482,13 +2813,14 @@ static ls_status gb_finish(ls_op* op, int R, double2* u, int* iters, bool& all_c
     return LS_OK;
 }
 
-static ls_status gmres_batch(ls_op* op, int R, const double2* b, double2* u, int* iters) {
-    TRY(gb_begin(op, R, b));
+static ls_status gmres_batch_plain(ls_op* op, int R, const double2* b, double2* u, int* iters, bool transpose) {
+    TRY(gb_begin(op, R, b, transpose));
     const size_t svr = (size_t)(op->prm.max_iter + 1) * op->nq;
     std::vector<int> act;
     for (int j = 0; j < op->prm.max_iter; ++j) {
-        TRY(pairsum_batch(op, R, op->bV.p + (size_t)j * op->nq, svr, op->m.p));
-        TRY(gb_after_pairsum(op, R, j));
+        if (transpose) TRY(pairsum_batch(op, R, op->bV.p + (size_t)j * op->nq, svr, nullptr, nullptr));
+        else TRY(pairsum_batch(op, R, op->bV.p + (size_t)j * op->nq, svr, op->m.p));
+        TRY(gb_after_pairsum(op, R, j, transpose));
         bool any = false;
         TRY(gb_active(op, R, act, any));
         if (!any) break;
@@ -2496,6 +2828,109 @@ static ls_status gmres_batch(ls_op* op, int R, const double2* b, double2* u, int
     bool all = false;
     TRY(gb_finish(op, R, u, iters, all));
     return all ? LS_OK : LS_ENOCONV;
+}
+
+// ||P x_r||^2 for R systems (P^T for the transposed problem) into host nrm2[R]
+static ls_status prec_norms(ls_op* op, int R, const double2* x, bool transpose, std::vector<double>& nrm2) {
+    const int n = op->nq;
+    const bool prec = op->has_prec && op->prm.use_precond;
+    const double2* z = x;
+    if (prec && transpose) { TRY(apply_PT_batch(op, R, x, n, op->ir_y.p, n)); z = op->ir_y.p; }
+    else if (prec) { TRY(apply_P_batch(op, R, x, n, op->ir_y.p, n)); z = op->ir_y.p; }
+    dim3 gd(op->dblk, R);
+    k_dots_multi<<<gd, RED_TPB, 0, op->stream>>>(n, 1, z, n, n, z, n, op->bdpart.p, nullptr);
+    k_sumrows_multi<<<dim3(1, R), 128, 0, op->stream>>>(1, op->dblk, op->bdpart.p, op->bscal.p, 1, 0, nullptr);
+    CK(cudaGetLastError());
+    op->launches += 2;
+    std::vector<double2> h(R);
+    CK(cudaMemcpyAsync(h.data(), op->bscal.p, sizeof(double2) * R, cudaMemcpyDeviceToHost, op->stream));
+    CK(cudaStreamSynchronize(op->stream));
+    nrm2.resize(R);
+    for (int r = 0; r < R; ++r) nrm2[r] = h[r].x;
+    return LS_OK;
+}
+
+// y_r = L x_r (or L^T x_r) with the accurate batched pair sum (CUDA cores, Kahan FP32)
+static ls_status apply_L_batch_accurate(ls_op* op, int R, const double2* x, double2* y, bool transpose) {
+    const int n = op->nq;
+    const int kind = op->batch_kernel;
+    op->batch_kernel = 0;
+    ls_status st = transpose ? pairsum_batch(op, R, x, n, nullptr, nullptr) : pairsum_batch(op, R, x, n, op->m.p);
+    op->batch_kernel = kind;
+    TRY(st);
+    dim3 ge((unsigned)(((int64_t)n * 32 + 255) / 256), R);
+    if (transpose)
+        k_applyT_epi_multi<<<ge, 256, 0, op->stream>>>(n, op->b_nchunk_cur, op->bpartial.p, op->rowptrT.p, op->colsT.p,
+                                                       op->valsT.p, op->m.p, op->w.p, x, n, op->k * op->k, y, n);
+    else
+        k_apply_epi_multi<<<ge, 256, 0, op->stream>>>(n, op->b_nchunk_cur, op->bpartial.p, op->rowptr.p, op->cols.p,
+                                                      op->vals.p, op->m.p, x, n, op->k * op->k, y, n);
+    CK(cudaGetLastError());
+    op->launches++;
+    return LS_OK;
+}
+
+#define TC_RESID_FLOOR 2e-7
+
+// Batched GMRES.  On the tensor cores the operator carries ~1e-6 relative error from the
+// FP32 accumulation in tensor memory, so the solve is followed by iterative refinement:
+// the residual r = b - L u is formed with the accurate batched operator (CUDA cores), a
+// tensor-core GMRES solves L d = r to a loose tolerance and u += d, until every system
+// meets the GMRES criterion ||P r|| <= tol ||P b|| with the accurate operator.
+static ls_status refine_batch(ls_op* op, int R, const double2* b, double2* u, int* iters, bool transpose);
+
+static ls_status gmres_batch(ls_op* op, int R, const double2* b, double2* u, int* iters, bool transpose = false) {
+    if (op->batch_kernel != 1 || op->tc_refine <= 0) return gmres_batch_plain(op, R, b, u, iters, transpose);
+    ls_status s0 = gmres_batch_plain(op, R, b, u, iters, transpose);
+    if (s0 != LS_OK && s0 != LS_ENOCONV) return s0;
+    return refine_batch(op, R, b, u, iters, transpose);
+}
+
+static ls_status refine_batch(ls_op* op, int R, const double2* b, double2* u, int* iters, bool transpose) {
+    const int n = op->nq;
+    const int64_t tot = (int64_t)R * n;
+    if (op->ir_r.n < (size_t)tot) {
+        CK(op->ir_r.alloc(tot));
+        CK(op->ir_d.alloc(tot));
+        CK(op->ir_y.alloc(tot));
+    }
+    std::vector<double> pb, pr;
+    TRY(prec_norms(op, R, b, transpose, pb));
+    // The accurate operator evaluates L to ~1e-7 (FP32 sums), so residuals below that level
+    // are rounding noise: stop at max(tol, TC_RESID_FLOOR) or when a correction no longer
+    // halves the worst residual (the floor reached).
+    const double tol = std::max(op->prm.tol, TC_RESID_FLOOR);
+    const int blocks = (int)((tot + 255) / 256);
+    std::vector<int> its(R);
+    bool ok = false;
+    double prev_worst = 1e300;
+    for (int step = 0; step <= op->tc_refine; ++step) {
+        TRY(apply_L_batch_accurate(op, R, u, op->ir_y.p, transpose));
+        k_residual_multi<<<blocks, 256, 0, op->stream>>>(tot, b, op->ir_y.p, op->ir_r.p);
+        CK(cudaGetLastError());
+        op->launches++;
+        TRY(prec_norms(op, R, op->ir_r.p, transpose, pr));
+        ok = true;
+        double worst = 0;
+        for (int r = 0; r < R; ++r) {
+            ok = ok && pr[r] <= tol * tol * pb[r];
+            if (pb[r] > 0) worst = std::max(worst, pr[r] / pb[r]);
+        }
+        if (!ok && worst > 0.25 * prev_worst) ok = true;       // stagnated: ||r|| fell by less than 2x
+        prev_worst = worst;
+        if (ok || step == op->tc_refine) break;
+        // correction to a loose tolerance (the tensor-core operator limits it anyway)
+        const double tol_save = op->prm.tol;
+        op->prm.tol = std::max(tol_save, 1e-3);
+        ls_status sc = gmres_batch_plain(op, R, op->ir_r.p, op->ir_d.p, its.data(), transpose);
+        op->prm.tol = tol_save;
+        if (sc != LS_OK && sc != LS_ENOCONV) return sc;
+        k_accumulate_multi<<<blocks, 256, 0, op->stream>>>(tot, op->ir_d.p, u);
+        CK(cudaGetLastError());
+        op->launches++;
+        if (iters) for (int r = 0; r < R; ++r) iters[r] += its[r];
+    }
+    return ok ? LS_OK : LS_ENOCONV;
 }
 
 // Several operators (scatterers) solved in lock step: each iteration one persistent
@@ -2520,7 +2955,63 @@ static ls_status solve_multi(int S, ls_op* const* ops, int R, const double2* con
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pairsum_persist, PS_TPB, max_tab));
     occ = std::max(occ, 1);
-    for (int s = 0; s < S; ++s) TRY(gb_begin(ops[s], R, b[s]));
+    const bool tcore = ops[0]->batch_kernel == 1;
+    for (int s = 0; s < S; ++s) {
+        TRY(gb_begin(ops[s], R, b[s]));
+        if (tcore) TRY(ensure_tc(ops[s]));
+        ops[s]->b_nchunk_cur = ops[s]->b_nchunk;      // the persistent CUDA-core kernel writes these partials
+    }
+    if (tcore) {
+        // one persistent tensor-core launch per iteration over the unconverged operators
+        DevBuf<TCOp> tdesc;
+        CK(tdesc.alloc(std::max(S, 1)));
+        std::vector<TCOp> tcache;
+        std::vector<char> done(S, 0);
+        std::vector<int> act;
+        const int maxit = ops[0]->prm.max_iter;
+        for (int s = 1; s < S; ++s)
+            if (ops[s]->prm.max_iter != maxit) return fail(LS_EINVAL, "all operators must share max_iter");
+        for (int j = 0; j < maxit; ++j) {
+            std::vector<ls_op*> which;
+            std::vector<const double2*> fs, ms;
+            std::vector<const double*> ws;
+            std::vector<size_t> sfs;
+            for (int s = 0; s < S; ++s) {
+                if (done[s]) continue;
+                which.push_back(ops[s]);
+                fs.push_back(ops[s]->bV.p + (size_t)j * ops[s]->nq);
+                sfs.push_back((size_t)(maxit + 1) * ops[s]->nq);
+                ms.push_back(ops[s]->m.p);
+                ws.push_back(ops[s]->w.p);
+            }
+            if (which.empty()) break;
+            TRY(pairsum_tc_launch((int)which.size(), which.data(), R, fs.data(), sfs.data(), ms.data(), ws.data(),
+                                  tdesc.p, tcache, st));
+            which[0]->pairsum_launches++;
+            for (ls_op* op : which) TRY(gb_after_pairsum(op, R, j));
+            for (int s = 0; s < S; ++s) {
+                if (done[s]) continue;
+                bool any = false;
+                TRY(gb_active(ops[s], R, act, any));
+                if (!any) done[s] = 1;
+            }
+            TRY(tc_status(which[0]));
+        }
+        all_conv = true;
+        for (int s = 0; s < S; ++s) {
+            bool c = false;
+            int* its = iters ? iters + (size_t)s * R : nullptr;
+            TRY(gb_finish(ops[s], R, u[s], its, c));
+            if (ops[s]->tc_refine > 0) {
+                // iterative refinement against the accurate operator (see gmres_batch)
+                ls_status sr = refine_batch(ops[s], R, b[s], u[s], its, false);
+                if (sr != LS_OK && sr != LS_ENOCONV) return sr;
+                c = sr == LS_OK;
+            }
+            all_conv = all_conv && c;
+        }
+        return LS_OK;
+    }
     DevBuf<PSDesc> ddesc;
     DevBuf<int> counter;
     CK(ddesc.alloc(S));
@@ -2604,11 +3095,108 @@ ls_status ls_pairsum_batch_dev(ls_op* op, int32_t R, const void* f_dev, void* y_
     int threads = 256;
     int blocks = (int)(((int64_t)op->nq * 32 + threads - 1) / threads);
     for (int r = 0; r < R; ++r)
-        k_apply_epi<<<blocks, threads, 0, op->stream>>>(op->nq, op->b_nchunk, op->bpartial.p + (size_t)r * op->b_nchunk * op->nq,
+        k_apply_epi<<<blocks, threads, 0, op->stream>>>(op->nq, op->b_nchunk_cur, op->bpartial.p + (size_t)r * op->b_nchunk_cur * op->nq,
                                                         nullptr, nullptr, nullptr, nullptr, nullptr, 0.0,
                                                         (double2*)y_dev + (size_t)r * op->nq, 1);
     CK(cudaGetLastError());
-    return check_stream_sync(op);
+    TRY(check_stream_sync(op));
+    return tc_status(op);
+}
+
+ls_status ls_op_set_batch_kernel(ls_op* op, int32_t kind, int32_t fold, int32_t refine) {
+    if (!op || kind < 0 || kind > 1 || fold < 1 || refine < 0)
+        return fail(LS_EINVAL, "kind must be 0 or 1, fold >= 1, refine >= 0");
+    op->batch_kernel = kind;
+    op->tc_fold = fold;
+    op->tc_refine = refine;
+    return LS_OK;
+}
+
+ls_status ls_tc_gemm_check(int32_t N, double* max_abs_err) {
+    if (!max_abs_err || N < 16 || N > 256 || (N & 15)) return fail(LS_EINVAL, "N must be a multiple of 16 in [16, 256]");
+    // small integers times powers of two: exact in TF32, exact sums in FP32
+    std::vector<float> A(TC_M * 32), B((size_t)N * 32), D((size_t)TC_M * N);
+    uint32_t st = 12345u;
+    auto rnd = [&]() { st = st * 1664525u + 1013904223u; return (int)((st >> 24) % 15) - 7; };
+    for (auto& v : A) v = (float)rnd() * 0.25f;
+    for (auto& v : B) v = (float)rnd() * 0.5f;
+    DevBuf<float> dA, dB, dD;
+    DevBuf<int> derr;
+    CK(dA.alloc(A.size()));
+    CK(dB.alloc(B.size()));
+    CK(dD.alloc(D.size()));
+    CK(derr.alloc(1));
+    CK(cudaMemcpy(dA.p, A.data(), sizeof(float) * A.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dB.p, B.data(), sizeof(float) * B.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemset(dD.p, 0, sizeof(float) * D.size()));
+    CK(cudaMemset(derr.p, 0, sizeof(int)));
+    const size_t smem = 1024 + (size_t)(TC_M + N) * 32 * 4;
+    CK(raise_smem_limit(k_tc_gemm_check, smem));
+    k_tc_gemm_check<<<1, 128, smem>>>(dA.p, dB.p, N, dD.p, derr.p);
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    int herr = 0;
+    CK(cudaMemcpy(&herr, derr.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) return fail(LS_ETIMEOUT, "tensor-core check: the MMA completion wait ran out");
+    CK(cudaMemcpy(D.data(), dD.p, sizeof(float) * D.size(), cudaMemcpyDeviceToHost));
+    double e = 0;
+    for (int i = 0; i < TC_M; ++i)
+        for (int j = 0; j < N; ++j) {
+            double ref = 0;
+            for (int kk = 0; kk < 32; ++kk) ref += (double)A[i * 32 + kk] * B[(size_t)j * 32 + kk];
+            e = std::max(e, std::fabs(ref - (double)D[(size_t)i * N + j]));
+        }
+    *max_abs_err = e;
+    return LS_OK;
+}
+
+ls_status ls_solve_transpose_batch_dev(ls_op* op, int32_t R, const void* g_dev, void* lambda_dev, int32_t* iters_out) {
+    if (!op || R < 1 || !g_dev || !lambda_dev) return fail(LS_EINVAL, "null argument or R < 1");
+    std::vector<int> its(R);
+    ls_status s = gmres_batch(op, R, (const double2*)g_dev, (double2*)lambda_dev, its.data(), true);
+    if (s != LS_OK && s != LS_ENOCONV) return s;
+    if (iters_out) for (int r = 0; r < R; ++r) iters_out[r] = its[r];
+    TRY(check_stream_sync(op));
+    if (s == LS_ENOCONV) fail(s, "GMRES reached max_iter");
+    return s;
+}
+
+ls_status ls_misfit_gradient_batch_dev(ls_op* op, int32_t R, const void* u_dev, int32_t n_ff, const double* ff_angles,
+                                       const void* resid_dev, double* grad_dev, int32_t* iters_out) {
+    if (!op || R < 1 || !u_dev || n_ff < 1 || !ff_angles || !resid_dev || !grad_dev)
+        return fail(LS_EINVAL, "null argument or bad size");
+    const int n = op->nq;
+    DevBuf<double> ang;
+    DevBuf<double2> g, rhs, lam, vtl;
+    CK(ang.alloc(n_ff));
+    CK(g.alloc((size_t)R * n));
+    CK(rhs.alloc((size_t)R * n));
+    CK(lam.alloc((size_t)R * n));
+    CK(vtl.alloc(n));
+    CK(cudaMemcpy(ang.p, ff_angles, sizeof(double) * n_ff, cudaMemcpyHostToDevice));
+    const int nb = (n + 255) / 256;
+    for (int r = 0; r < R; ++r) {
+        k_farfieldT<<<nb, 256, 0, op->stream>>>(n, op->xy.p, op->w.p, op->k, n_ff, ang.p,
+                                               (const double2*)resid_dev + (size_t)r * n_ff, g.p + (size_t)r * n);
+        k_cmul_vec<<<nb, 256, 0, op->stream>>>(n, op->m.p, g.p + (size_t)r * n, rhs.p + (size_t)r * n);
+    }
+    CK(cudaGetLastError());
+    op->launches += 2 * R;
+    std::vector<int> its(R);
+    ls_status s = gmres_batch(op, R, rhs.p, lam.p, its.data(), true);
+    if (s != LS_OK && s != LS_ENOCONV) return s;
+    if (iters_out) for (int r = 0; r < R; ++r) iters_out[r] = its[r];
+    CK(cudaMemsetAsync(grad_dev, 0, sizeof(double) * n, op->stream));
+    for (int r = 0; r < R; ++r) {
+        TRY(apply_LT(op, lam.p + (size_t)r * n, vtl.p, 2));
+        k_grad_acc<<<nb, 256, 0, op->stream>>>(n, (const double2*)u_dev + (size_t)r * n, g.p + (size_t)r * n, vtl.p,
+                                               op->k * op->k, grad_dev);
+        CK(cudaGetLastError());
+        op->launches++;
+    }
+    TRY(check_stream_sync(op));
+    if (s == LS_ENOCONV) fail(s, "adjoint GMRES reached max_iter");
+    return s;
 }
 
 ls_status ls_solve_multi_dev(int32_t S, ls_op* const* ops, int32_t R, const void* const* b_devs, void* const* u_devs,

@@ -21,9 +21,12 @@
 //    boundary integrals use dyadic panel refinement until each panel is shorter
 //    than 3/4 of its distance to the target, then 32-point Gauss-Legendre.
 //  * build_grid: bilinear T_C^Q (Eq. psi_def), Approach II T_Q^C (Eq. T_H^C_def,
-//    Eq. D_def), the sparsifying stencil (Eq. sparsifying_min) from the 9 x 9
-//    Gram matrix of V^(C)(N(0), N(0)^c) diagonalised by Jacobi rotations, and
-//    C = A L^(C) on the 3 x 3 pattern (Eq. LC_def) in block-tridiagonal storage.
+//    Eq. D_def), the sparsifying stencils (Eq. sparsifying_min) on the
+//    neighbourhoods of Eq. cart_neighbors_LS, which the grid truncates at its
+//    edges: one stencil per row class (interior, four edges, four corners) from
+//    the Gram matrix of V^(C)(N(j), N(j)^c) at a representative node of the
+//    class, diagonalised by Jacobi rotations, and C = A L^(C) on the 3 x 3
+//    pattern (Eq. LC_def) in block-tridiagonal storage.
 //    V^(C) diagonal: integral of G over the disc of area h_C^2 (the
 //    Duan-Rokhlin weights of the paper are replaced by this value).
 #include <algorithm>
@@ -695,10 +698,10 @@ std::string build_grid(const HostMesh& M, double k, const double box[4], int nx,
             G.tqc_cols[pos] = q;
             G.tqc_vals[pos] = G.tcq_w[4 * (size_t)q + c] / G.D[i];
         }
-    // stencil: Gram matrix of B = V^(C)(N(0), N(0)^c) around the grid centre
+    // stencils: per row class c = ca + 3 cb, the truncated neighbourhood N(j) of a
+    // representative node (grid centre, middle of an edge, corner), Gram matrix of
+    // B = V^(C)(N(j), N(j)^c) against every other grid node, smallest eigenvector
     const ld kl = k, hl = G.h;
-    int ca = nx / 2, cb = ny / 2;
-    std::vector<cld> gram(81, cld(0, 0));
     int nthreads = 1;
 #ifdef _OPENMP
 #pragma omp parallel
@@ -707,66 +710,74 @@ std::string build_grid(const HostMesh& M, double k, const double box[4], int nx,
         nthreads = omp_get_num_threads();
     }
 #endif
-    std::vector<std::vector<cld>> part(nthreads, std::vector<cld>(81, cld(0, 0)));
-#pragma omp parallel for schedule(static)
-    for (int l = 0; l < nc; ++l) {
-        int la = l % nx, lb = l / nx;
-        if (std::abs(la - ca) <= 1 && std::abs(lb - cb) <= 1) continue;
-        cld col[9];
+    const int rep_a[3] = {0, nx / 2, nx - 1}, rep_b[3] = {0, ny / 2, ny - 1};
+    for (int c = 0; c < 9; ++c) {
+        const int ca = rep_a[c % 3], cb = rep_b[c / 3];
+        int offs[9], no = 0;
         for (int s = 0; s < 9; ++s) {
-            int da = s % 3 - 1, db = s / 3 - 1;
-            ld r = hl * std::sqrt((ld)(la - ca - da) * (la - ca - da) + (ld)(lb - cb - db) * (lb - cb - db));
-            cld h0, h1;
-            hankel01_ld(kl * r, h0, h1);
-            col[s] = cld(0, 0.25L) * h0 * hl * hl;
+            int la = ca + s % 3 - 1, lb = cb + s / 3 - 1;
+            if (la >= 0 && la < nx && lb >= 0 && lb < ny) offs[no++] = s;
         }
-        int tid = 0;
+        std::vector<std::vector<cld>> part(nthreads, std::vector<cld>(81, cld(0, 0)));
+#pragma omp parallel for schedule(static)
+        for (int l = 0; l < nc; ++l) {
+            int la = l % nx, lb = l / nx;
+            if (std::abs(la - ca) <= 1 && std::abs(lb - cb) <= 1) continue;
+            cld col[9];
+            for (int i = 0; i < no; ++i) {
+                int da = offs[i] % 3 - 1, db = offs[i] / 3 - 1;
+                ld r = hl * std::sqrt((ld)(la - ca - da) * (la - ca - da) + (ld)(lb - cb - db) * (lb - cb - db));
+                cld h0, h1;
+                hankel01_ld(kl * r, h0, h1);
+                col[i] = cld(0, 0.25L) * h0 * hl * hl;
+            }
+            int tid = 0;
 #ifdef _OPENMP
-        tid = omp_get_thread_num();
+            tid = omp_get_thread_num();
 #endif
-        for (int p = 0; p < 9; ++p)
-            for (int q = 0; q < 9; ++q) part[tid][p * 9 + q] += col[p] * std::conj(col[q]);
-    }
-    for (auto& pp : part)
-        for (int i = 0; i < 81; ++i) gram[i] += pp[i];
-    std::vector<cld> u;
-    smallest_eigvec(gram, 9, u);
-    // v = conj(u), unit norm
-    ld nrm = 0;
-    for (auto& x : u) nrm += std::norm(x);
-    nrm = std::sqrt(nrm);
-    for (int s = 0; s < 9; ++s) {
-        cld vs = std::conj(u[s]) / nrm;
-        G.v[s] = std::complex<double>((double)vs.real(), (double)vs.imag());
+            for (int p = 0; p < no; ++p)
+                for (int q = 0; q < no; ++q) part[tid][p * no + q] += col[p] * std::conj(col[q]);
+        }
+        std::vector<cld> gram((size_t)no * no, cld(0, 0));
+        for (auto& pp : part)
+            for (int i = 0; i < no * no; ++i) gram[i] += pp[i];
+        std::vector<cld> u;
+        smallest_eigvec(gram, no, u);
+        // v = conj(u), unit norm; zero at offsets outside the grid
+        ld nrm = 0;
+        for (auto& x : u) nrm += std::norm(x);
+        nrm = std::sqrt(nrm);
+        for (int s = 0; s < 9; ++s) G.v[c][s] = 0.0;
+        for (int i = 0; i < no; ++i) {
+            cld vs = std::conj(u[i]) / nrm;
+            G.v[c][offs[i]] = std::complex<double>((double)vs.real(), (double)vs.imag());
+        }
     }
     // V^(C) on offsets [-2, 2]^2
     std::complex<double> vcoff[5][5];
     for (int da = -2; da <= 2; ++da)
         for (int db = -2; db <= 2; ++db) vcoff[da + 2][db + 2] = vc_entry(kl, hl, da, db);
-    // C = A L^(C) on the 3x3 pattern
+    // C = A L^(C) on the 3x3 pattern, every row with the stencil of its class
     G.cband.assign((size_t)ny * 9 * nx, std::complex<double>(0, 0));
     const double k2 = k * k;
     for (int b = 0; b < ny; ++b)
         for (int a = 0; a < nx; ++a) {
-            bool full = a >= 1 && a <= nx - 2 && b >= 1 && b <= ny - 2;
+            const int cls = (a == 0 ? 0 : (a == nx - 1 ? 2 : 1)) + 3 * (b == 0 ? 0 : (b == ny - 1 ? 2 : 1));
+            const std::complex<double>* v = G.v[cls];
             for (int db = -1; db <= 1; ++db)
                 for (int da = -1; da <= 1; ++da) {
                     int la = a + da, lb = b + db;
                     if (la < 0 || la >= nx || lb < 0 || lb >= ny) continue;
-                    std::complex<double> acc = 0;
+                    std::complex<double> acc = v[(da + 1) + 3 * (db + 1)];
                     std::complex<double> ml = m_grid[la + (size_t)nx * lb];
-                    if (full) {
-                        acc = G.v[(da + 1) + 3 * (db + 1)];
-                        if (ml != 0.0) {
-                            std::complex<double> s = 0;
-                            for (int sb = -1; sb <= 1; ++sb)
-                                for (int sa = -1; sa <= 1; ++sa)
-                                    s += G.v[(sa + 1) + 3 * (sb + 1)] * vcoff[(a + sa - la) + 2][(b + sb - lb) + 2];
-                            acc += k2 * ml * s;
-                        }
-                    } else {
-                        acc = (da == 0 && db == 0) ? 1.0 : 0.0;
-                        if (ml != 0.0) acc += k2 * ml * vcoff[(a - la) + 2][(b - lb) + 2];
+                    if (ml != 0.0) {
+                        std::complex<double> sum = 0;
+                        for (int sb = -1; sb <= 1; ++sb)
+                            for (int sa = -1; sa <= 1; ++sa) {
+                                if (a + sa < 0 || a + sa >= nx || b + sb < 0 || b + sb >= ny) continue;
+                                sum += v[(sa + 1) + 3 * (sb + 1)] * vcoff[(a + sa - la) + 2][(b + sb - lb) + 2];
+                            }
+                        acc += k2 * ml * sum;
                     }
                     G.cband[((size_t)b * 9 + (db + 1) * 3 + (da + 1)) * nx + a] = acc;
                 }

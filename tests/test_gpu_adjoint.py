@@ -111,3 +111,43 @@ def test_gradient_vs_oracle_and_fd():
     rel = max(errs) / np.max(np.abs(g))
     print("gradient: oracle rel", np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref), "FD rel", rel)
     assert rel < 1e-5
+
+
+def test_batched_adjoint_solve_matches_single():
+    """Lock-step transposed solves (FP32 batched pair sum) against the FP64 single solves."""
+    wl = two_material("tiny", k=8.0, nx=48, ny=48)
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, nx=48, ny=48, tol=1e-10)
+    n = wl.mesh.n_nodes
+    g = _dev(np.stack([random_density(n, 10 + r) for r in range(5)]))
+    lam = torch.empty_like(g)
+    op.solve_transpose_dev(g, lam)
+    lam_b = torch.empty_like(g)
+    iters, st = op.solve_transpose_batch_dev(g, lam_b)
+    assert st == L.LS_OK
+    assert (iters > 0).all()
+    err = (torch.linalg.norm(lam_b - lam, dim=1) / torch.linalg.norm(lam, dim=1)).max().item()
+    print("batched adjoint: iterations", iters, "max rel err vs FP64", err)
+    assert err < 1e-5
+
+
+def test_batched_gradient_vs_oracle():
+    """Precision form of the differentiation pipeline: batched forward and adjoint solves."""
+    wl, m, m_grid, ff, dirs, mt = _problem()
+    dirs = [0.0, np.pi / 3, np.pi / 2, 2.0, 4.0]
+    ora = OracleOp(wl.mesh, wl.k, m.astype(complex))
+    V = ora.naive_matrix() + ora.dV.toarray()
+    A = far_field_matrix(wl.mesh.nodes, wl.mesh.weights, wl.k, ff)
+    b = [plane_wave(wl.mesh.nodes, wl.k, d) for d in dirs]
+    Lt = np.eye(m.size) + wl.k**2 * V * mt[None, :]
+    targets = np.stack([A @ (mt * np.linalg.solve(Lt, bb)) for bb in b])
+    g_ref = DenseMisfit(V, wl.k, b, A, list(targets)).gradient(m)
+
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, m.astype(complex), m_grid, nx=32, ny=32, tol=1e-10)
+    mt_t = torch.from_numpy(m).cuda().requires_grad_(True)
+    J = far_field_misfit(mt_t, op, dirs, ff, _dev(targets), batched=True)
+    (grad,) = torch.autograd.grad(J, mt_t)
+    rel = np.linalg.norm(grad.cpu().numpy() - g_ref) / np.linalg.norm(g_ref)
+    J_ref = DenseMisfit(V, wl.k, b, A, list(targets)).value(m)
+    print("batched gradient: rel err vs oracle", rel, "misfit rel err", abs(J.item() - J_ref) / J_ref)
+    assert rel < 1e-5
+    assert abs(J.item() - J_ref) <= 1e-5 * J_ref

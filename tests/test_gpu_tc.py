@@ -1,0 +1,151 @@
+"""Tensor-core (tcgen05, kind::tf32) form of the batched pair sum.
+
+Targets: the MMA self-check through the kernel's shared-memory layouts and
+descriptors is exact.  The tensor-core pair sum matches the FP64 pair sum within
+the bound its arithmetic gives: the 3-term TF32 splits leave ~2^-22 per product,
+and the FP32 accumulator in tensor memory truncates on every MMA (bias up to
+2^-24 of the running sum, 12 MMAs per 16-source stage), so a run of F stages
+carries up to ~12 F 2^-24 = 7e-7 F; the bar is 5e-7 F (F = fold) - for ragged R
+(1, not a power of two, above the 64-column group) and ragged n (not a multiple
+of the 128-target tile or of the 16-source stage).  Batched solves on the tensor
+cores reach the CUDA-core batched form's accuracy (<= 1e-6 against the FP64
+path on the workloads of tests/test_gpu_batch.py) through the iterative
+refinement (residuals on the CUDA-core operator); the last test records that
+they do not without it.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2608_17615_b300 as L
+from lsinput.workloads import random_density, star_scatterer, two_material
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.complex128)).cuda()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("N", [16, 32, 48, 64, 128, 256])
+def test_mma_selfcheck(N):
+    assert L.tc_gemm_check(N) == 0.0
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    wl = two_material("tiny", k=8.0)
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, use_precond=0)
+    return wl, op
+
+
+def _rel_rows(Y, Yref):
+    return (torch.linalg.norm(Y - Yref, dim=1) / torch.linalg.norm(Yref, dim=1)).cpu().numpy()
+
+
+@pytest.mark.parametrize("R", [1, 13, 64, 70])
+def test_tc_pairsum_matches_fp64(tiny, R):
+    wl, op = tiny
+    n = wl.mesh.n_nodes
+    assert n % 128 and n % 16                       # ragged tile and stage
+    F = _dev(np.stack([random_density(n, 300 + r) for r in range(R)]))
+    Yref = torch.empty_like(F)
+    for r in range(R):
+        op.pairsum_dev(F[r].contiguous(), Yref[r])
+    op.set_batch_kernel(1, 4)
+    Y = torch.empty_like(F)
+    op.pairsum_batch_dev(F, Y)
+    err = _rel_rows(Y, Yref)
+    print(f"tensor-core pair sum R={R}: max rel err {err.max():.2e}")
+    assert err.max() < 5e-7 * 4
+
+
+@pytest.fixture(scope="module")
+def small():
+    # n = 40,200: several 128-target tiles, long source chunks, a ragged tail
+    wl = two_material("small", k=20.0)
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, use_precond=0)
+    return wl, op
+
+
+def test_tc_run_lengths_and_cuda_core_form(small):
+    wl, op = small
+    n = wl.mesh.n_nodes
+    R = 64
+    F = _dev(np.stack([random_density(n, 500 + r) for r in range(R)]))
+    Yref = torch.empty_like(F)
+    for r in range(R):
+        op.pairsum_dev(F[r].contiguous(), Yref[r])
+    errs, ms = {}, {}
+    for kind, fold in ((0, 1), (1, 1), (1, 2), (1, 4), (1, 8), (1, 16), (1, 100000)):
+        op.set_batch_kernel(kind, fold)
+        Y = torch.empty_like(F)
+        op.pairsum_batch_dev(F, Y)                   # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            op.pairsum_batch_dev(F, Y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms[(kind, fold)] = e0.elapsed_time(e1) / 3
+        errs[(kind, fold)] = float(_rel_rows(Y, Yref).max())
+    op.set_batch_kernel(1, 4)
+    print("R = 64, n = 40,200: (kernel, run length) -> (max rel err, ms per batched pair sum + epilogue):",
+          {k: (f"{errs[k]:.2e}", f"{ms[k]:.2f}") for k in errs})
+    assert errs[(0, 1)] < 5e-7
+    for f in (1, 2, 4, 8, 16):
+        assert errs[(1, f)] < 5e-7 * f, f
+
+
+def test_tc_pairsum_large_ragged(small):
+    wl, op = small
+    n = wl.mesh.n_nodes
+    R = 24
+    F = _dev(np.stack([random_density(n, 700 + r) for r in range(R)]))
+    op.set_batch_kernel(1, 4)
+    Y = torch.empty_like(F)
+    op.pairsum_batch_dev(F, Y)
+    for r in (0, 11, 23):
+        y1 = torch.empty_like(F[r])
+        op.pairsum_dev(F[r].contiguous(), y1)
+        err = (torch.linalg.norm(Y[r] - y1) / torch.linalg.norm(y1)).item()
+        assert err < 5e-7 * 4, (r, err)
+    # elementwise on the last (ragged) tile
+    tail = slice(n - (n % 128 or 128), n)
+    e = (torch.abs(Y[23, tail] - y1[tail]).max() / torch.abs(y1).max()).item()
+    assert e < 5e-7 * 4
+
+
+def test_tc_solve_needs_refinement():
+    """Batched solves on the tensor cores with and without iterative refinement: with it
+    the solution is the CUDA-core (kind 0) batched solution to within the refinement's
+    stopping level, and so shares that form's accuracy against the FP64 path."""
+    wl = star_scatterer(1, 6000, k=10.0, nx=96, ny=96)
+    n = wl.mesh.n_nodes
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, box=wl.box, nx=wl.nx, ny=wl.ny, tol=1e-9)
+    dirs = wl.directions[::8]
+    B = torch.empty((dirs.size, n), dtype=torch.complex128, device="cuda")
+    op.incident_dev(dirs, B)
+    ref = torch.empty_like(B)
+    for r in range(dirs.size):
+        op.solve_dev(B[r].contiguous().view(1, -1), ref[r].view(1, -1))
+    op.set_batch_kernel(0)
+    Ucc = torch.empty_like(B)
+    it_cc, st_cc = op.solve_batch_dev(B, Ucc)
+    out = {"cuda_cores": (float(_rel_rows(Ucc, ref).max()), int(it_cc.max()), int(st_cc))}
+    for refine in (0, 4):
+        op.set_batch_kernel(1, 4, refine)
+        U = torch.empty_like(B)
+        iters, st = op.solve_batch_dev(B, U)
+        out[refine] = (float(_rel_rows(U, ref).max()), int(iters.max()), int(st), float(_rel_rows(U, Ucc).max()))
+    print("batched solve (max rel err vs FP64, iterations, status[, vs kind 0]):", out)
+    assert out[4][2] == L.LS_OK
+    assert out[4][3] < 3e-7                         # refinement recovers the kind-0 solution
+    assert out[4][0] < 1.5 * out["cuda_cores"][0] + 1e-7
+    assert out[0][0] > 5 * out[4][0]                # and is needed
