@@ -2870,7 +2870,7 @@ static ls_status apply_L_batch_accurate(ls_op* op, int R, const double2* x, doub
     return LS_OK;
 }
 
-#define TC_RESID_FLOOR 2e-7
+#define TC_RESID_FLOOR 2e-8
 
 // Batched GMRES.  On the tensor cores the operator carries ~1e-6 relative error from the
 // FP32 accumulation in tensor memory, so the solve is followed by iterative refinement:

@@ -45,7 +45,6 @@
 #define TC_FOLD_WARP0 17
 #define TC_THREADS (21 * 32)
 #define TC_WAIT_NS 1000000000ull
-#define TC_SUSPEND_NS 100000u      // hint: a waiting thread may sleep up to 0.1 ms per try
 #define TC_MAX_OPS 64
 
 // One operator (scatterer) of a launch.  Units of all operators are numbered
@@ -96,10 +95,10 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(TC_SUSPEND_NS)
+        : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     return ok != 0;
 }
@@ -270,7 +269,6 @@ struct TCCursor {
 __global__ void __launch_bounds__(TC_THREADS, 1) k_pairsum_tc(TCArgs a) {
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     __shared__ TCShared sh;
-    __shared__ float4 s_coord[TC_PROD_WARPS][4];
     // dynamic shared memory: ring of TC_NS stages {A_hi, A_lo, B_hi, B_lo}, nstg staging slots
     // {Sc tile, coordinates}, then the H0 table of the current operator (the largest fits)
     unsigned char* base = (unsigned char*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
@@ -393,11 +391,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairsum_tc(TCArgs a) {
                 Blo[c2 * N + r] = make_float4(v0.y, -v0.w, v1.y, -v1.w);
                 Blo[c2 * N + Rp + r] = make_float4(v0.w, v0.y, v1.w, v1.y);
             }
-            // the warp's 4 source coordinates into its own shared slot; then the staging slot is
-            // free for the next copy
-            if (lane < 4) s_coord[warp][lane] = sxy[4 * q + lane];
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&sh.stempty[stgi]);
             // A: sources 4q .. 4q + 3 of the stage for target j; element (row, kk) at float4 (kk / 4) * 128 + row
             float hr[4], hi[4];
 #pragma unroll
@@ -407,7 +400,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairsum_tc(TCArgs a) {
                 hr[e] = 0.f;
                 hi[e] = 0.f;
                 if (src >= c.s_end) continue;
-                const float4 sc4 = s_coord[warp][e];
+                const float4 sc4 = sxy[sl];
                 float dxh, dxl, dyh, dyl;
                 df_diff(txh, txl, sc4.x, sc4.y, dxh, dxl);
                 df_diff(tyh, tyl, sc4.z, sc4.w, dyh, dyl);
@@ -446,6 +439,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairsum_tc(TCArgs a) {
                 }
                 // th == 0: the self pair, excluded from the naive sum
             }
+            // the staging slot has been read (densities and coordinates): free for the next copy
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&sh.stempty[stgi]);
 #pragma unroll
             for (int h2 = 0; h2 < 2; ++h2) {
                 const float x0 = hr[2 * h2], y0 = hi[2 * h2], x1 = hr[2 * h2 + 1], y1 = hi[2 * h2 + 1];

