@@ -530,6 +530,27 @@ def main():
                            "rel_err_vs_fp64_solution": reld,
                            "pairs_per_s": itd[0] * n * (n - 1) * args.steps / (sum(msd) * 1e-3)}
     op.set_pairsum(0)
+    # batching form on the same operator: 64 incident directions (the bench direction among
+    # them) in one lock-step solve, on the tensor cores (with refinement) and on the CUDA cores
+    R64 = 64
+    dirs64 = rank_direction(rank, world) + 2 * np.pi * np.arange(R64) / R64
+    B64 = torch.empty((R64, n), dtype=torch.complex128, device=u.device)
+    op.incident_dev(dirs64, B64)
+    U64 = torch.empty_like(B64)
+    for kind, name in ((1, "batched_tensor_cores_64rhs"), (0, "batched_cuda_cores_64rhs")):
+        op.set_batch_kernel(kind)
+        op.solve_batch_dev(B64, U64)                          # warm-up (workspace)
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it64, st64 = op.solve_batch_dev(B64, U64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        forms[name] = {"value": R64 / (ms64 * 1e-3), "unit": "solves/s", "rhs": R64, "status": int(st64),
+                       "iterations_max": int(np.max(it64)),
+                       "rel_err_vs_fp64_solution": (torch.linalg.norm(U64[0] - u) / torch.linalg.norm(u)).item()}
+    op.set_batch_kernel(1)
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
