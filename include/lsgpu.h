@@ -285,6 +285,25 @@ ls_status ls_op_correction(const ls_op* op, int64_t* nnz, int64_t* rowptr, int32
 ls_status ls_correction_host(const ls_mesh* mesh, double k, double kappa, int64_t* nnz,
                              int64_t* rowptr, int32_t* cols, double* vals);
 
+/*
+ * Host-only build of the Cartesian preconditioner's sparsifying stencils and of
+ * the banded C = A L^(C) (Section 4: Eq. sparsifying_min on the neighbourhoods of
+ * Eq. cart_neighbors_LS, Eq. LC_def), the same setup ls_operator_create runs,
+ * for checking on machines without a GPU.
+ *   box [4] = (x0, x1, y0, y1), nx x ny grid nodes including the box edges
+ *   m_grid [nx*ny][2]   contrast at the grid nodes (complex, index a + nx b)
+ *   stencils [9][9][2]  out: stencil of row class c = ca + 3 cb (ca = 0 / 1 / 2 for
+ *                       the first / an inner / the last column; cb likewise for
+ *                       rows) at offset (da+1) + 3 (db+1); zero outside the grid
+ *   cband [ny][9][nx][2] out (or null): C((a, b), (a+da, b+db)) at
+ *                       [b][(db+1) 3 + (da+1)][a]
+ * Stencils are unit vectors fixed up to a complex phase per class (C rows carry
+ * the same phase).  Errors: LS_EINVAL (null arguments, k <= 0, a grid smaller
+ * than 4 x 4, unequal steps, quadrature nodes outside the box).
+ */
+ls_status ls_grid_host(const ls_mesh* mesh, double k, const double* box, int32_t nx, int32_t ny, const double* m_grid,
+                       double* stencils, double* cband);
+
 /* Diagnostic: h_dev[i] = H0^(1)(z_dev[i]) (complex) by the device routine of the pair sum. */
 ls_status ls_hankel0_dev(int64_t n, const double* z_dev, void* h_dev, void* stream);
 

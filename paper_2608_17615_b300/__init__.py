@@ -18,7 +18,7 @@ _STATUS = {0: "LS_OK", 1: "LS_EINVAL", 2: "LS_ENOMEM", 3: "LS_ECUDA", 4: "LS_ESI
 
 EXPORTED = ["ls_params_default", "ls_mesh_create", "ls_mesh_destroy", "ls_mesh_num_nodes", "ls_operator_create",
             "ls_op_destroy", "ls_op_num_nodes", "ls_apply_dev", "ls_apply", "ls_apply_precond_dev", "ls_pairsum_dev",
-            "ls_solve", "ls_solve_dev", "ls_op_correction", "ls_correction_host", "ls_hankel0_dev",
+            "ls_solve", "ls_solve_dev", "ls_op_correction", "ls_correction_host", "ls_grid_host", "ls_hankel0_dev",
             "ls_pairsum_batch_dev", "ls_solve_batch_dev", "ls_solve_multi_dev", "ls_apply_transpose_dev", "ls_potential_transpose_dev", "ls_apply_precond_transpose_dev",
             "ls_solve_transpose_dev", "ls_op_set_contrast", "ls_incident_dev", "ls_misfit_gradient_dev",
             "ls_solve_transpose_batch_dev", "ls_misfit_gradient_batch_dev",
@@ -59,6 +59,7 @@ def _load():
         "ls_solve_dev": (I32, [P, I32, P, P, I32, P, P, P]),
         "ls_op_correction": (I32, [P, P, P, P, P]),
         "ls_correction_host": (I32, [P, D, D, P, P, P, P]),
+        "ls_grid_host": (I32, [P, D, P, I32, I32, P, P, P]),
         "ls_hankel0_dev": (I32, [I64, P, P, P]),
         "ls_pairsum_batch_dev": (I32, [P, I32, P, P]),
         "ls_solve_batch_dev": (I32, [P, I32, P, P, I32, P, P, P]),
@@ -331,6 +332,17 @@ def correction_host(mesh, k, kappa=3.0):
     _check(_lib.ls_correction_host(mesh.handle, float(k), float(kappa), ctypes.byref(nnz), _ptr(rp), _ptr(ci),
                                    _ptr(va.view(np.float64))))
     return rp, ci, va
+
+
+def grid_host(mesh, k, box, nx, ny, m_grid):
+    """Host-only preconditioner setup: (stencils [9 classes, 9 offsets], cband [ny, 3, 3, nx]) complex."""
+    bx = np.ascontiguousarray(box, np.float64)
+    mg = np.ascontiguousarray(np.asarray(m_grid, np.complex128).ravel())
+    st = np.zeros((9, 9), np.complex128)
+    cb = np.zeros((ny, 3, 3, nx), np.complex128)
+    _check(_lib.ls_grid_host(mesh.handle, float(k), _ptr(bx), int(nx), int(ny), _ptr(mg.view(np.float64)),
+                             _ptr(st.view(np.float64)), _ptr(cb.view(np.float64))))
+    return st, cb
 
 
 def solve_multi_dev(ops, B, U):

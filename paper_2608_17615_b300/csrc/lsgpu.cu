@@ -3324,6 +3324,30 @@ ls_status ls_correction_host(const ls_mesh* mesh, double k, double kappa, int64_
     return LS_OK;
 }
 
+ls_status ls_grid_host(const ls_mesh* mesh, double k, const double* box, int32_t nx, int32_t ny, const double* m_grid,
+                       double* stencils, double* cband) {
+    if (!mesh || !box || !m_grid || !stencils) return fail(LS_EINVAL, "null argument");
+    if (!(k > 0)) return fail(LS_EINVAL, "k must be positive");
+    if (nx < 4 || ny < 4) return fail(LS_EINVAL, "grid needs at least 4 x 4 nodes");
+    const size_t nc = (size_t)nx * ny;
+    std::vector<std::complex<double>> mg(nc);
+    for (size_t i = 0; i < nc; ++i) mg[i] = std::complex<double>(m_grid[2 * i], m_grid[2 * i + 1]);
+    lsgpu::GridSetup G;
+    std::string err = lsgpu::build_grid(mesh->h, k, box, nx, ny, mg.data(), G);
+    if (!err.empty()) return fail(LS_EINVAL, err);
+    for (int c = 0; c < 9; ++c)
+        for (int t = 0; t < 9; ++t) {
+            stencils[2 * (9 * c + t)] = G.v[c][t].real();
+            stencils[2 * (9 * c + t) + 1] = G.v[c][t].imag();
+        }
+    if (cband)
+        for (size_t i = 0; i < G.cband.size(); ++i) {
+            cband[2 * i] = G.cband[i].real();
+            cband[2 * i + 1] = G.cband[i].imag();
+        }
+    return LS_OK;
+}
+
 ls_status ls_apply_transpose_dev(ls_op* op, const void* x_dev, void* y_dev) {
     if (!op || !x_dev || !y_dev) return fail(LS_EINVAL, "null argument");
     if (x_dev == y_dev) return fail(LS_EINVAL, "x and y may not alias");

@@ -1,6 +1,7 @@
 """CPU-side checks of the C-ABI library: it loads, exports every declared
 symbol, validates inputs, and its host setup of the VDIM correction agrees with
-the oracle's (both in extended precision, independently written)."""
+the oracle's (both in extended precision, independently written), as does its
+host setup of the preconditioner's stencils and banded C."""
 import ctypes
 import os
 import re
@@ -85,3 +86,47 @@ def test_correction_matches_oracle_two_materials():
     assert np.array_equal(Ar.indptr, B.indptr)
     assert np.max(np.diff(B.indptr)) == 30          # some rows carry a foreign block
     assert abs(Ar - B).max() < 1e-13 * abs(B).max()
+
+
+def _phase_align(a, b):
+    """b rotated by the unit complex factor that best matches it to a."""
+    z = np.vdot(b, a)
+    return b * (z / abs(z)) if abs(z) > 0 else b
+
+
+@pytest.mark.parametrize("k, nx", [(5.0, 24), (10.0, 36)])
+def test_grid_host_matches_oracle(k, nx):
+    """The library's host setup of the sparsifying stencils (one per row class, on the
+    truncated neighbourhoods) and of C = A L^(C) on the 3x3 pattern against the oracle's
+    (independent SVD-based construction).  Stencils are unit vectors fixed up to a phase,
+    which C's rows share."""
+    from lsinput.workloads import constant_disk
+    from oracle.precond import Grid, Preconditioner, STENCIL, row_class
+
+    wl = constant_disk(k=k, n_rings=2, nx=nx, ny=nx)
+    g = Grid(wl.box, wl.nx, wl.ny)
+    P = Preconditioner(g, wl.mesh.nodes, wl.k, wl.m_grid)
+    st, cb = L.grid_host(L.Mesh(wl.mesh), wl.k, wl.box, wl.nx, wl.ny, wl.m_grid)
+    phase = np.ones(9, complex)
+    for c in range(9):
+        ca = (0, nx // 2, nx - 1)[c % 3]
+        cb_ = (0, nx // 2, nx - 1)[c // 3]
+        outside = [s for s, (da, db) in enumerate(STENCIL) if not (0 <= ca + da < nx and 0 <= cb_ + db < nx)]
+        assert np.all(st[c, outside] == 0)
+        assert abs(np.linalg.norm(st[c]) - 1) < 1e-13
+        v = _phase_align(st[c], P.v[c])
+        assert np.linalg.norm(st[c] - v) < 1e-8, c
+        z = np.vdot(P.v[c], st[c])
+        phase[c] = z / abs(z)
+    C = P.C.tocsr()
+    worst, scale = 0.0, abs(C).max()
+    for b in range(nx):
+        for a in range(nx):
+            j = a + nx * b
+            ph = phase[row_class(g, a, b)]
+            for da, db in STENCIL:
+                la, lb = a + da, b + db
+                if not (0 <= la < nx and 0 <= lb < nx):
+                    continue
+                worst = max(worst, abs(cb[b, db + 1, da + 1, a] - ph * C[j, la + nx * lb]))
+    assert worst < 1e-8 * scale, worst / scale
