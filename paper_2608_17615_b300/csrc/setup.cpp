@@ -139,6 +139,72 @@ static void asym01(ld z, ld& j0, ld& j1, ld& y0, ld& y1) {
     j0 = out[0]; y0 = out[1]; j1 = out[2]; y1 = out[3];
 }
 
+// H0 alone, bit-identical to the h0 of hankel01_ld (same sums in the same order, same
+// loop exits): the patch sums of the correction need no H1.
+static void series0(ld z, ld& j0, ld& y0) {
+    const SeriesTables& T = series_tables();
+    ld q = z * z / 4;
+    ld t0 = 1, t1 = 1;
+    ld s0 = 1, a0 = 0;
+    for (int k = 1; k <= 40; ++k) {
+        t0 *= -q * T.rk2[k];
+        t1 *= -q * T.rkk1[k];        // only for the stopping test shared with series01
+        s0 += t0;
+        a0 += T.hk[k] * t0;
+        if (std::fabs(t0) < 1e-24L && std::fabs(t1) < 1e-24L) break;
+    }
+    ld L = std::log(z / 2) + EG_L;
+    j0 = s0;
+    y0 = (2 / PI_L) * (L * j0 - a0);
+}
+
+static void miller0(ld z, ld& j0, ld& y0) {
+    int nstart = 2 * ((int)(z + 56) / 2);
+    ld J[96];
+    for (int i = 0; i < nstart + 2; ++i) J[i] = 0.0L;
+    J[nstart] = 1e-300L;
+    for (int n = nstart; n >= 1; --n) {
+        J[n - 1] = (2.0L * n / z) * J[n] - J[n + 1];
+        if (std::fabs(J[n - 1]) > 1e300L)
+            for (int i = n - 1; i <= nstart; ++i) J[i] *= 1e-300L;
+    }
+    ld norm = J[0];
+    for (int k = 2; k <= nstart; k += 2) norm += 2 * J[k];
+    for (int i = 0; i < nstart + 2; ++i) J[i] /= norm;
+    ld s0 = 0;
+    for (int k = 1; 2 * k + 1 <= nstart + 1; ++k) {
+        ld sg = (k % 2) ? -1.0L : 1.0L;
+        s0 += sg * J[2 * k] / k;
+    }
+    ld L = std::log(z / 2) + EG_L;
+    j0 = J[0];
+    y0 = (2 / PI_L) * (L * j0 - 2 * s0);
+}
+
+static void asym0(ld z, ld& j0, ld& y0) {
+    ld c = std::cos(z), s = std::sin(z);
+    ld r2 = std::sqrt(0.5L);
+    ld amp = std::sqrt(2 / (PI_L * z));
+    ld P = 1, Q = 0, term = 1;
+    for (int k = 1; k < 100; ++k) {
+        term *= (0.0L - (ld)(2 * k - 1) * (2 * k - 1)) / (k * 8 * z);
+        if (k % 2) Q += (((k - 1) / 2) % 2 ? -term : term);
+        else       P += ((k / 2) % 2 ? -term : term);
+        if (std::fabs(term) < 1e-22L) break;
+    }
+    ld cc = r2 * (c + s), ss = r2 * (s - c);
+    j0 = amp * (P * cc - Q * ss);
+    y0 = amp * (P * ss + Q * cc);
+}
+
+static cld hankel0_ld(ld z) {
+    ld j0, y0;
+    if (z <= 6) series0(z, j0, y0);
+    else if (z < 30) miller0(z, j0, y0);
+    else asym0(z, j0, y0);
+    return cld(j0, y0);
+}
+
 void hankel01_ld(ld z, cld& h0, cld& h1) {
     ld j0, j1, y0, y1;
     if (z <= 6) series01(z, j0, j1, y0, y1);
@@ -394,8 +460,7 @@ static bool correction_block(const HostMesh& M, int j, ld k, const std::vector<i
             if (n == j) continue;
             ld yx = M.nodes[2 * n], yy = M.nodes[2 * n + 1];
             ld r = std::sqrt((yx - xj) * (yx - xj) + (yy - yj) * (yy - yj));
-            cld h0, h1;
-            hankel01_ld(k * r, h0, h1);
+            cld h0 = hankel0_ld(k * r);
             cld Gw = cld(0, 0.25L) * h0 * (ld)M.w[n];
             mono_eval((yx - P.cx) * P.invh, (yy - P.cy) * P.invh, m, nullptr, nullptr, P.invh);
             for (int a = 0; a < 15; ++a) Mn[a] += Gw * m[a];
