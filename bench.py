@@ -241,6 +241,7 @@ def precision_report(args):
         sols[name] = u
         out[name] = {"solve_ms": ms, "solves_per_s": 1e3 / ms, "iterations": int(it[0]), "status": int(st),
                      "pairs_per_s": int(it[0]) * n * (n - 1) / (ms * 1e-3)}
+        print(f"[precision] setup {setup_s:.1f} s; {name}: {json.dumps(out[name])}", file=sys.stderr, flush=True)
     out["fp32"]["rel_err_vs_double_float_solution"] = (
         torch.linalg.norm(sols["fp32"] - sols["double_float"]) / torch.linalg.norm(sols["double_float"])).item()
     # FP32 matvec against the oracle on sampled rows
@@ -372,6 +373,7 @@ def batching_report(args):
         out[name] = {"ms": ms, "solves_per_s": len(ops) * R / (ms * 1e-3), "status": int(st),
                      "iterations_max_per_scatterer": [int(x.max()) for x in it],
                      "pair_interactions_per_s": pairs / (ms * 1e-3)}
+        print(f"[batching] setup {setup:.1f} s; {name}: {json.dumps(out[name])}", file=sys.stderr, flush=True)
         sols[name] = [u[0].clone() for u in U]
     errs = []
     for s, op in enumerate(ops):
