@@ -161,12 +161,16 @@ ls_status ls_solve_dev(ls_op* op, int32_t R, const void* b_dev, void* u_dev,
  *   ls_solve_batch_dev    R independent GMRES solves in lock step (each system
  *                         keeps its own Krylov space, Hessenberg matrix and stop),
  *                         b_dev, u_dev [R][N]; far field as ls_solve_dev
- * The pair sum of all R systems is one launch per iteration: each H(j, n) comes
- * from an FP32 table (degree 6, validated to 2e-8) with double-float t and is
- * applied to blocks of 8 right-hand sides; sums are Kahan-compensated FP32 over
- * runs of 64 sources and FP64 across runs (the precision of the batching form: <= 1e-6
- * relative solution error).  The preconditioner sweeps and the Arnoldi kernels
- * are batched over r as well.  Workspace grows on first use with a larger R.
+ * The pair sum of all R systems is one launch per iteration on the kernel chosen
+ * by ls_op_set_batch_kernel.  Each H(j, n) comes from an FP32 table (degree 6,
+ * validated to 2e-8) with double-float t.  On the CUDA cores (kind 0) it is applied
+ * to blocks of 8 right-hand sides with Kahan-compensated FP32 sums over runs of 64
+ * sources and FP64 across runs; on the tensor cores (kind 1, the default) the sum
+ * over sources is a tcgen05 GEMM over up to 64 right-hand sides, and the solve is
+ * followed by iterative refinement against the kind 0 operator, so both reach the
+ * kind 0 accuracy (the batching form's target: <= 1e-6 relative solution error).
+ * The preconditioner sweeps and the Arnoldi kernels are batched over r as well.
+ * Workspace grows on first use with a larger R.
  */
 ls_status ls_pairsum_batch_dev(ls_op* op, int32_t R, const void* f_dev, void* y_dev);
 ls_status ls_solve_batch_dev(ls_op* op, int32_t R, const void* b_dev, void* u_dev, int32_t n_ff,
@@ -175,10 +179,12 @@ ls_status ls_solve_batch_dev(ls_op* op, int32_t R, const void* b_dev, void* u_de
 /*
  * Several scatterers (operators of uneven size, own k and mesh) with R right-hand
  * sides each, advanced in lock step; every iteration runs ONE persistent pair-sum
- * launch over all (scatterer, target block, source chunk, RHS block) work units,
- * fetched dynamically from an atomic counter (load balance across uneven sizes),
+ * launch over all (scatterer, target block, source chunk[, RHS block]) work units,
  * followed by each operator's batched epilogue, preconditioner and Arnoldi kernels.
- * The persistent grid size is autotuned on the first iteration.
+ * Kernel as set on ops[0] by ls_op_set_batch_kernel: tensor cores (one CTA per SM
+ * taking units round-robin, then each operator's iterative refinement) or CUDA
+ * cores (units fetched from an atomic counter, grid size autotuned on the first
+ * iteration).
  *   ops [S]; b_devs[s], u_devs[s]: [R][N_s] complex; iters_out [S][R] (may be NULL)
  * All operators must share one stream and max_iter.  LS_ENOCONV if any system
  * hit max_iter.
