@@ -553,6 +553,28 @@ def main():
                        "iterations_max": int(np.max(it64)),
                        "rel_err_vs_fp64_solution": (torch.linalg.norm(U64[0] - u) / torch.linalg.norm(u)).item()}
     op.set_batch_kernel(1)
+    # differentiation form on the same operator: gradient of the far-field misfit with respect
+    # to the nodal contrast for 16 directions and 32 receivers (batched forward and adjoint
+    # solves on the tensor cores, then V^T lambda per direction in FP64), once after a warm-up
+    try:
+        from paper_2608_17615_b300.misfit import far_field_misfit
+        dirs16 = rank_direction(rank, world) + 2 * np.pi * np.arange(16) / 16
+        ff32 = 2 * np.pi * np.arange(32) / 32
+        m_t = torch.from_numpy(np.ascontiguousarray(np.real(wl.m), np.float64)).to(u.device).requires_grad_(True)
+        tg = torch.zeros((16, 32), dtype=torch.complex128, device=u.device)
+        (gr,) = torch.autograd.grad(far_field_misfit(m_t, op, dirs16, ff32, tg, batched=True), m_t)   # warm-up
+        torch.cuda.synchronize()
+        t_g = time.perf_counter()
+        Jg = far_field_misfit(m_t, op, dirs16, ff32, tg, batched=True)
+        (gr,) = torch.autograd.grad(Jg, m_t)
+        torch.cuda.synchronize()
+        dt_g = time.perf_counter() - t_g
+        forms["gradient_16dirs_32receivers"] = {"value": 1.0 / dt_g, "unit": "gradients/s", "seconds": dt_g,
+                                                "misfit": float(Jg.item()),
+                                                "grad_norm": float(torch.linalg.norm(gr).item()),
+                                                "timing": "host wall clock around forward + backward, synchronised"}
+    except Exception as exc:                        # a form's failure must not cost the bench line
+        forms["gradient_16dirs_32receivers"] = {"error": f"{type(exc).__name__}: {str(exc)[:200]}"}
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
