@@ -34,7 +34,7 @@ WORKLOAD = "two-material disk, k=20, 40,200 nodes (2,680 curved P4 triangles), 2
 METRIC = "LS GMRES solves/s (FP64, preconditioned)"
 # Preconditioned GMRES iterations of this workload as measured by the GPU arm;
 # the reference arm scales its sampled matvec cost by it.
-REFERENCE_ITERS = 55
+REFERENCE_ITERS = 8
 
 
 def _env_rank():
@@ -160,43 +160,6 @@ def reference_arm(args):
             times.append(((t1 - t0) / rows.size + (t2 - t1) / 8) * n * REFERENCE_ITERS)
     t_solve = statistics.mean(times)
     value = 1.0 / t_solve
-    # precision form on the same operator (FP32 pair sum), timed the same way
-    forms = {}
-    op.set_pairsum(2)
-    u32 = torch.empty_like(u)
-    op.solve_dev(b.view(1, -1), u32.view(1, -1))
-    ms32, it32 = [], []
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        it, st = op.solve_dev(b.view(1, -1), u32.view(1, -1), wl.ff_angles, uinf.view(1, -1))
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms32.append(e0.elapsed_time(e1))
-        it32.append(int(it[0]))
-    rel32 = (torch.linalg.norm(u32 - u) / torch.linalg.norm(u)).item()
-    forms["fp32_pairsum"] = {"value": args.steps / (sum(ms32) * 1e-3), "unit": "solves/s", "iterations": it32[0],
-                             "rel_err_vs_fp64_solution": rel32,
-                             "pairs_per_s": it32[0] * n * (n - 1) * args.steps / (sum(ms32) * 1e-3)}
-    # FP64-accurate double-float pair sum on the same operator
-    op.set_pairsum(3)
-    op.solve_dev(b.view(1, -1), u32.view(1, -1))
-    msd, itd = [], []
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        it, st = op.solve_dev(b.view(1, -1), u32.view(1, -1), wl.ff_angles, uinf.view(1, -1))
-        e1.record(stream)
-        torch.cuda.synchronize()
-        msd.append(e0.elapsed_time(e1))
-        itd.append(int(it[0]))
-    reld = (torch.linalg.norm(u32 - u) / torch.linalg.norm(u)).item()
-    forms["df_pairsum"] = {"value": args.steps / (sum(msd) * 1e-3), "unit": "solves/s", "iterations": itd[0],
-                           "rel_err_vs_fp64_solution": reld,
-                           "pairs_per_s": itd[0] * n * (n - 1) * args.steps / (sum(msd) * 1e-3)}
-    op.set_pairsum(0)
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
