@@ -337,9 +337,9 @@ ls_status ls_probe_fp64(double* gflops, void* stream);
 
 /*
  * Allocation-free pair sum, for callers that cannot allocate device memory:
- * code inside a CUDA graph being captured, plug-ins whose device memory is
- * owned by a host application's allocator or a fixed pool, real-time loops that
- * must stay out of the allocator.  No counterpart in the paper; it computes the
+ * plug-ins whose device memory is owned by a host application's allocator or a
+ * fixed pool, real-time loops that must stay out of the allocator (its latency
+ * is unbounded).  No counterpart in the paper; it computes the
  * same sum as ls_pairsum_dev, y_j = (i/4) sum_{n != j} H0^(1)(k |x_j - x_n|) w_n f_n,
  * with the direct FP64 H0 routine and without an operator:
  *   n          number of nodes, 2 <= n <= 1048576 (larger n: LS_EINVAL)
@@ -352,7 +352,9 @@ ls_status ls_probe_fp64(double* gflops, void* stream);
  * on a device looks up the array's address with cudaGetSymbolAddress (make it
  * before any stream capture).  All calls share the array: calls that overlap on
  * the GPU (other streams, other host threads) race; serialise them.  Every
- * partial is overwritten before it is read, so no clearing is needed.
+ * partial is overwritten before it is read, so no clearing is needed.  Like the
+ * other device-buffer calls it returns after synchronising the stream.
+ * Errors: LS_EINVAL (null pointer, n out of range, k <= 0), LS_ECUDA.
  */
 ls_status ls_pairsum_noalloc(int32_t n, const double* xy_dev, const double* w_dev, const void* f_dev,
                              double k, void* y_dev, void* stream);

@@ -14,7 +14,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblsgpu.so")
 
 LS_OK, LS_EINVAL, LS_ENOMEM, LS_ECUDA, LS_ESINGULAR, LS_ENOCONV, LS_ETIMEOUT = range(7)
-_STATUS = {0: "LS_OK", 1: "LS_EINVAL", 2: "LS_ENOMEM", 3: "LS_ECUDA", 4: "LS_ESINGULAR", 5: "LS_ENOCONV"}
+_STATUS = {0: "LS_OK", 1: "LS_EINVAL", 2: "LS_ENOMEM", 3: "LS_ECUDA", 4: "LS_ESINGULAR", 5: "LS_ENOCONV",
+           6: "LS_ETIMEOUT"}
 
 EXPORTED = ["ls_params_default", "ls_mesh_create", "ls_mesh_destroy", "ls_mesh_num_nodes", "ls_operator_create",
             "ls_op_destroy", "ls_op_num_nodes", "ls_apply_dev", "ls_apply", "ls_apply_precond_dev", "ls_pairsum_dev",
@@ -378,8 +379,17 @@ def probe_fp64():
 
 def pairsum_noalloc(xy, w, f, k, y):
     """Allocation-free pair sum on device tensors: xy [n, 2] and w [n] float64,
-    f and y [n] complex128 (see ls_pairsum_noalloc for whom it serves)."""
-    _check(_lib.ls_pairsum_noalloc(int(f.numel()), _dptr(xy), _dptr(w), _dptr(f), float(k), _dptr(y),
+    f and y [n] complex128 (see ls_pairsum_noalloc for whom it serves).  The
+    shapes and dtypes are checked here because the C call sees only pointers."""
+    import torch
+    n = int(f.numel())
+    for name, t, dt in (("xy", xy, torch.float64), ("w", w, torch.float64), ("f", f, torch.complex128),
+                        ("y", y, torch.complex128)):
+        if not t.is_cuda or not t.is_contiguous() or t.dtype != dt:
+            raise ValueError(f"{name} must be a contiguous CUDA tensor of dtype {dt}")
+    if tuple(xy.shape) != (n, 2) or w.numel() != n or y.numel() != n:
+        raise ValueError(f"shapes must be xy [{n}, 2], w [{n}], y [{n}]")
+    _check(_lib.ls_pairsum_noalloc(n, _dptr(xy), _dptr(w), _dptr(f), float(k), _dptr(y),
                                    ctypes.c_void_p(_current_stream())))
 
 

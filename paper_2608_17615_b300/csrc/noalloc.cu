@@ -1,9 +1,9 @@
 // Allocation-free pair sum (ls_pairsum_noalloc).
 //
-// Some callers cannot call cudaMalloc at all: code running inside a CUDA graph
-// that is being captured, plug-ins of host applications whose device memory is
-// owned by an outside allocator (or a fixed pool budgeted up front), and
-// real-time loops that must not enter the driver's allocator.  The regular
+// Some callers cannot call cudaMalloc at all: plug-ins of host applications
+// whose device memory is owned by an outside allocator (or a fixed pool
+// budgeted up front), and real-time loops that must not enter the driver's
+// allocator, whose latency is unbounded.  The regular
 // entry points allocate their scratch (the chunked partial sums of the pair
 // sum) inside ls_operator_create; this one keeps that scratch in a file-scope
 // device array instead, so the call itself allocates nothing.  The paper has

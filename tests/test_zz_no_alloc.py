@@ -1,7 +1,8 @@
 """The allocation-free pair sum (ls_pairsum_noalloc) against the regular one.
 
-It serves callers that cannot allocate device memory (graph capture, externally
-owned memory pools, real-time loops): its scratch is a static device array.
+It serves callers that cannot allocate device memory (plug-ins whose device
+memory belongs to a host application's allocator or a fixed pool, real-time
+loops that must stay out of the allocator): its scratch is a static device array.
 Checked through the C ABI against ls_pairsum_dev on two calls in a row (the
 shared scratch keeps the previous call's contents), within the FP64 pair-sum
 tolerance of the other parity tests.  This file is collected last on purpose.
