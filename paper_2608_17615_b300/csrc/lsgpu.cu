@@ -11,8 +11,9 @@
 //   k_tqc            T_Q^C gather (Approach II, Eq. T_H^C_def) over the transposed CSR
 //   k_stencil        t = A g with the 3 x 3 sparsifying stencils (Eq. sparsifying_min), one per
 //                    grid-row class (interior, edges, corners; Eq. cart_neighbors_LS)
-//   k_bt_fwd/bwd     block-tridiagonal solve C t' = t with precomputed dense
-//                    S_b^{-1} and S_b^{-1} C_{b,b+1} (block LU of C, Eq. LC_def)
+//   k_cr_mv/k_cr_tri block-cyclic-reduction solve C t' = t (Eq. LC_def): batched dense
+//                    block products per level (cr_solve.cuh); the batched forms use the
+//                    block LU sweeps k_bt_fwd_multi / k_bt_bwd_multi
 //   k_tcq            z_q = w_q + sum_4 psi (t' - g) (Eq. preconditioner_factored)
 //   k_dots/k_sumrows/k_update/k_norm...  classical Gram-Schmidt (twice) for GMRES
 //   k_givens         Hessenberg column update and Givens rotation, residual history
@@ -23,6 +24,7 @@
 // 9.1.13); for z > 6 the modulus/phase form sqrt(2/(pi z)) (P + i Q) e^{i(z - pi/4)}
 // with P, zQ fitted polynomials in 36/z^2 (constants in hankel_fit.h).
 #include <cuda_runtime.h>
+#include <cublas_v2.h>
 #include <cusolverDn.h>
 
 #include <algorithm>
@@ -61,6 +63,12 @@ static ls_status fail(ls_status s, const std::string& msg) {
         cusolverStatus_t s_ = (call);                                                             \
         if (s_ != CUSOLVER_STATUS_SUCCESS)                                                        \
             return fail(LS_ECUDA, std::string(#call) + ": cusolver status " + std::to_string(s_)); \
+    } while (0)
+
+#define TRY(x)                         \
+    do {                               \
+        ls_status s__ = (x);           \
+        if (s__ != LS_OK) return s__;  \
     } while (0)
 
 // The dynamic shared-memory limit is a per-kernel attribute shared by all operators:
@@ -693,6 +701,7 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum_persist(const PSDesc* __rest
 }
 
 #include "tc_pairsum.cuh"
+#include "cr_solve.cuh"
 
 // mode 0: y = x + k2 * ((i/4) sum_c partial + dV (m x));  mode 1: y = (i/4) sum_c partial
 __global__ void k_apply_epi(int n, int nchunk, const double2* __restrict__ partial, const int64_t* __restrict__ rowptr,
@@ -790,61 +799,6 @@ __global__ void k_stencilT(int nx, int ny, const double2* __restrict__ st, const
     r[l] = csub(acc, g[l]);                  // (S^T - I) g = A^T C^{-T} g - g
 }
 
-// transposed forward sweep, in place: z_b -= GT_{b-1} z_{b-1}   (GT_b = G_b^T, row-major)
-__global__ void k_btT_fwd(int nx, int b, const double2* __restrict__ GT, double2* __restrict__ z) {
-    extern __shared__ double2 sh[];
-    for (int c = threadIdx.x; c < nx; c += blockDim.x) sh[c] = z[(size_t)(b - 1) * nx + c];
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (row >= nx) return;
-    const double2* Gr = GT + ((size_t)(b - 1) * nx + row) * nx;
-    double ar = 0.0, ai = 0.0;
-    for (int c = lane; c < nx; c += 32) {
-        double2 gv = Gr[c], v = sh[c];
-        ar = fma(gv.x, v.x, fma(-gv.y, v.y, ar));
-        ai = fma(gv.x, v.y, fma(gv.y, v.x, ai));
-    }
-    ar = warp_sum(ar);
-    ai = warp_sum(ai);
-    if (lane == 0) {
-        double2 v = z[(size_t)b * nx + row];
-        z[(size_t)b * nx + row] = make_double2(v.x - ar, v.y - ai);
-    }
-}
-
-// transposed backward sweep: x_b = WT_b (z_b - C_{b+1,b}^T x_{b+1})  (x and z distinct buffers)
-__global__ void k_btT_bwd(int nx, int ny, int b, const double2* __restrict__ WT, const double2* __restrict__ cband,
-                          const double2* __restrict__ z, double2* __restrict__ x) {
-    extern __shared__ double2 sh[];
-    for (int c = threadIdx.x; c < nx; c += blockDim.x) {
-        double2 v = z[(size_t)b * nx + c];
-        if (b + 1 < ny) {
-            const double2* Cm1 = cband + (size_t)(b + 1) * 9 * nx;   // db = -1 diagonals of block row b+1
-            const double2* xn = x + (size_t)(b + 1) * nx;
-            for (int da = -1; da <= 1; ++da) {
-                int a = c - da;                    // C_{b+1,b}(a, c) with c = a + da
-                if (a >= 0 && a < nx) v = csub(v, cmul(Cm1[(size_t)(da + 1) * nx + a], xn[a]));
-            }
-        }
-        sh[c] = v;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (row >= nx) return;
-    const double2* Wr = WT + ((size_t)b * nx + row) * nx;
-    double ar = 0.0, ai = 0.0;
-    for (int c = lane; c < nx; c += 32) {
-        double2 wv = Wr[c], v = sh[c];
-        ar = fma(wv.x, v.x, fma(-wv.y, v.y, ar));
-        ai = fma(wv.x, v.y, fma(wv.y, v.x, ai));
-    }
-    ar = warp_sum(ar);
-    ai = warp_sum(ai);
-    if (lane == 0) x[(size_t)b * nx + row] = make_double2(ar, ai);
-}
-
 // block transpose for the factors: out_b = in_b^T (row-major nx x nx blocks)
 __global__ void k_transpose_blocks(int nx, int nblk, const double2* __restrict__ in, double2* __restrict__ out) {
     __shared__ double2 t[32][33];
@@ -934,61 +888,6 @@ __global__ void k_stencil(int nx, int ny, const double2* __restrict__ st, const 
         if (la >= 0 && la < nx && lb >= 0 && lb < ny) acc = cadd(acc, cmul(v[s], g[la + nx * lb]));
     }
     t[idx] = acc;
-}
-
-// forward step of the block solve: y_b = W_b (t_b - Cm_b y_{b-1}); warp per row, W row-major
-__global__ void k_bt_fwd(int nx, int b, const double2* __restrict__ W, const double2* __restrict__ cband,
-                         const double2* __restrict__ t, double2* __restrict__ y) {
-    extern __shared__ double2 sh[];
-    const double2* Cm = cband + (size_t)b * 9 * nx;           // db = -1 diagonals at [0..2][nx]
-    for (int c = threadIdx.x; c < nx; c += blockDim.x) {
-        double2 v = t[(size_t)b * nx + c];
-        if (b > 0) {
-            const double2* yp = y + (size_t)(b - 1) * nx;
-            for (int da = -1; da <= 1; ++da) {
-                int cc = c + da;
-                if (cc >= 0 && cc < nx) v = csub(v, cmul(Cm[(size_t)(da + 1) * nx + c], yp[cc]));
-            }
-        }
-        sh[c] = v;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (row >= nx) return;
-    const double2* Wr = W + ((size_t)b * nx + row) * nx;
-    double ar = 0.0, ai = 0.0;
-    for (int c = lane; c < nx; c += 32) {
-        double2 wv = Wr[c], s = sh[c];
-        ar = fma(wv.x, s.x, fma(-wv.y, s.y, ar));
-        ai = fma(wv.x, s.y, fma(wv.y, s.x, ai));
-    }
-    ar = warp_sum(ar);
-    ai = warp_sum(ai);
-    if (lane == 0) y[(size_t)b * nx + row] = make_double2(ar, ai);
-}
-
-// backward step: x_b = y_b - G_b x_{b+1} (in place in y)
-__global__ void k_bt_bwd(int nx, int b, const double2* __restrict__ Gm, double2* __restrict__ y) {
-    extern __shared__ double2 sh[];
-    for (int c = threadIdx.x; c < nx; c += blockDim.x) sh[c] = y[(size_t)(b + 1) * nx + c];
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (row >= nx) return;
-    const double2* Gr = Gm + ((size_t)b * nx + row) * nx;
-    double ar = 0.0, ai = 0.0;
-    for (int c = lane; c < nx; c += 32) {
-        double2 gv = Gr[c], s = sh[c];
-        ar = fma(gv.x, s.x, fma(-gv.y, s.y, ar));
-        ai = fma(gv.x, s.y, fma(gv.y, s.x, ai));
-    }
-    ar = warp_sum(ar);
-    ai = warp_sum(ai);
-    if (lane == 0) {
-        double2 v = y[(size_t)b * nx + row];
-        y[(size_t)b * nx + row] = make_double2(v.x - ar, v.y - ai);
-    }
 }
 
 // z_q = w_q + sum_c psi_c (tp[i_c] - g[i_c])
@@ -1682,6 +1581,20 @@ struct DevBuf {
     }
 };
 
+// Cyclic-reduction solve of C (cr_solve.cuh): persistent factor blocks, the vector
+// arena [t | x | scratch] and the launch steps of C x = t and C^T x = t.
+struct CRPlan {
+    struct Step { int kind; int first; int count; };   // kind 0: dense products, 1: band, 2: band transposed
+    int nx = 0, ny = 0;
+    size_t svec = 0;                                    // arena stride per right-hand side
+    DevBuf<double2> store, arena;
+    DevBuf<CRJob> jobs;
+    DevBuf<CRTriJob> tjobs;
+    std::vector<Step> fwd, trn;
+    double2* t() const { return arena.p; }
+    double2* x() const { return arena.p + (size_t)nx * ny; }
+};
+
 struct ls_op {
     int nq = 0;
     double k = 0;
@@ -1751,6 +1664,9 @@ struct ls_op {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t gP = nullptr;
     DevBuf<double2> pin, pout;
+    cudaGraphExec_t gPT = nullptr;         // graph of the P^T apply
+    int nlaunch_P = 0, nlaunch_PT = 0;     // kernels in each graph
+    CRPlan cr;                           // cyclic reduction of C for the single-RHS P and P^T
     // instrumentation: kernel launches on this operator, CUDA-event timing of the pair sum
     int64_t launches = 0, pairsum_launches = 0;
     bool timing = false;
@@ -1758,6 +1674,7 @@ struct ls_op {
     ~ls_op() {
         for (auto& e : ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
         if (gP) cudaGraphExecDestroy(gP);
+        if (gPT) cudaGraphExecDestroy(gPT);
         if (cap) cudaStreamDestroy(cap);
         if (tc_herr) cudaFreeHost(tc_herr);
     }
@@ -1844,43 +1761,372 @@ static ls_status apply_L(ls_op* op, const double2* x, double2* y) {
     return LS_OK;
 }
 
-// The kernel sequence of P x (3 + 2 ny - 1 launches) on stream st.
-static void launch_P_kernels(ls_op* op, cudaStream_t st, const double2* x, double2* z) {
-    const int nc = op->nx * op->ny, nx = op->nx, ny = op->ny;
-    k_tqc<<<(nc + 255) / 256, 256, 0, st>>>(nc, op->tqc_rp.p, op->tqc_ci.p, op->tqc_cv.p, x, op->pg.p);
-    k_stencil<<<(nc + 255) / 256, 256, 0, st>>>(nx, ny, op->st.p, op->pg.p, op->pt.p);
-    const int wpb = 8;                                   // warps per block in the block solve
-    const int blocks = (nx + wpb - 1) / wpb;
-    const size_t shm = sizeof(double2) * nx;
-    for (int b = 0; b < ny; ++b)
-        k_bt_fwd<<<blocks, 32 * wpb, shm, st>>>(nx, b, op->Wf.p, op->cband.p, op->pt.p, op->ptp.p);
-    for (int b = ny - 2; b >= 0; --b)
-        k_bt_bwd<<<blocks, 32 * wpb, shm, st>>>(nx, b, op->Gf.p, op->ptp.p);
-    k_tcq<<<(op->nq + 255) / 256, 256, 0, st>>>(op->nq, op->tcq_idx.p, op->tcq_w.p, op->ptp.p, op->pg.p, x, z);
+// ------------------------------------------------------------------ cyclic reduction (host)
+#define CKB(call)                                                                                 \
+    do {                                                                                          \
+        cublasStatus_t s_ = (call);                                                               \
+        if (s_ != CUBLAS_STATUS_SUCCESS)                                                          \
+            return fail(LS_ECUDA, std::string(#call) + ": cublas status " + std::to_string(s_));  \
+    } while (0)
+
+// Batched row-major products C_b = alpha A_b B_b + beta C_b (cuBLAS is column-major:
+// a row-major matrix is its transpose there, so the operands are passed swapped).
+static ls_status cr_gemm(cublasHandle_t h, cudaStream_t st, int nx, double alpha, double beta,
+                         const std::vector<const double2*>& A, const std::vector<const double2*>& B,
+                         const std::vector<double2*>& C, DevBuf<const double2*>& scratch) {
+    const int cnt = (int)C.size();
+    if (cnt == 0) return LS_OK;
+    std::vector<const double2*> ptrs(3 * (size_t)cnt);
+    for (int i = 0; i < cnt; ++i) { ptrs[i] = B[i]; ptrs[cnt + i] = A[i]; ptrs[2 * cnt + i] = C[i]; }
+    CK(scratch.alloc(ptrs.size()));
+    CK(cudaMemcpyAsync(scratch.p, ptrs.data(), sizeof(void*) * ptrs.size(), cudaMemcpyHostToDevice, st));
+    const cuDoubleComplex a = make_cuDoubleComplex(alpha, 0.0), b = make_cuDoubleComplex(beta, 0.0);
+    CKB(cublasZgemmBatched(h, CUBLAS_OP_N, CUBLAS_OP_N, nx, nx, nx, &a, (const cuDoubleComplex* const*)scratch.p, nx,
+                           (const cuDoubleComplex* const*)(scratch.p + cnt), nx, &b,
+                           (cuDoubleComplex* const*)(scratch.p + 2 * cnt), nx, cnt));
+    CK(cudaStreamSynchronize(st));            // the pointer scratch is reused by the next call
+    return LS_OK;
 }
 
-// P x.  The sequence is captured once into a CUDA graph (on a private stream, with
-// fixed input/output buffers) and replayed; x and z are copied in and out.
-static ls_status apply_P(ls_op* op, const double2* x, double2* z) {
-    const int ny = op->ny;
-    if (!op->gP) {
+// Factor blocks of the cyclic reduction of C (cr_solve.cuh) and the job tables of
+// both solves.  Needs op->cband, op->nx, op->ny.
+static ls_status build_cr(ls_op* op) {
+    CRPlan& P = op->cr;
+    const int nx = op->nx, ny = op->ny;
+    const size_t bs = (size_t)nx * nx, nc = (size_t)nx * ny;
+    cudaStream_t st = op->stream;
+    P.nx = nx;
+    P.ny = ny;
+    std::vector<int> nl{ny};
+    while (nl.back() > 1) nl.push_back((nl.back() + 1) / 2);
+    const int NL = (int)nl.size() - 1;                 // levels with an elimination
+    const size_t NONE = SIZE_MAX;
+    // persistent slots (in blocks): per level the odd rows' Dinv, gamma, delta and, from
+    // level 1 on, every row's L and U; the transposed copy of slot s is slot s + nN
+    std::vector<std::vector<size_t>> sDinv(NL), sGam(NL), sDlt(NL), sL(NL + 1), sU(NL + 1);
+    size_t nN = 0;
+    for (int l = 0; l < NL; ++l) {
+        const int n = nl[l];
+        for (int i = 1; i < n; i += 2) {
+            sDinv[l].push_back(nN++);
+            sGam[l].push_back(nN++);
+            sDlt[l].push_back(i + 1 < n ? nN++ : NONE);
+        }
+        const int n1 = nl[l + 1];
+        sL[l + 1].assign(n1, NONE);
+        sU[l + 1].assign(n1, NONE);
+        if (n1 > 1)
+            for (int p = 0; p < n1; ++p) {
+                if (p >= 1) sL[l + 1][p] = nN++;
+                if (2 * p + 2 < n) sU[l + 1][p] = nN++;
+            }
+    }
+    const size_t sTop = nN++;
+    CK(P.store.alloc(2 * nN * bs));
+    auto blk = [&](size_t s) { return P.store.p + s * bs; };
+    // working blocks: D of every row (updated in place level by level), dense level-0 L and U
+    DevBuf<double2> work;
+    CK(work.alloc(3 * (size_t)ny * bs));
+    double2* Dw = work.p;
+    double2* L0 = work.p + (size_t)ny * bs;
+    double2* U0 = work.p + 2 * (size_t)ny * bs;
+    {
+        std::vector<int> ids(ny);
+        std::vector<double2*> outD(ny), outL(ny), outU(ny);
+        for (int b = 0; b < ny; ++b) {
+            ids[b] = b;
+            outD[b] = Dw + b * bs;
+            outL[b] = L0 + b * bs;
+            outU[b] = U0 + b * bs;
+        }
+        DevBuf<int> dids;
+        DevBuf<double2*> dout;
+        CK(dids.alloc(ny));
+        CK(dout.alloc(3 * (size_t)ny));
+        CK(cudaMemcpy(dids.p, ids.data(), sizeof(int) * ny, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(dout.p, outL.data(), sizeof(void*) * ny, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(dout.p + ny, outD.data(), sizeof(void*) * ny, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(dout.p + 2 * ny, outU.data(), sizeof(void*) * ny, cudaMemcpyHostToDevice));
+        for (int which = 0; which < 3; ++which) {
+            dim3 g((nx + 127) / 128, nx, ny);
+            k_cr_expand<<<g, 128, 0, st>>>(nx, op->cband.p, dids.p, which, dout.p + (size_t)which * ny);
+        }
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(st));
+    }
+    // current level's blocks (null: no such coupling)
+    std::vector<double2*> Dp(ny), Lp(ny), Up(ny);
+    for (int b = 0; b < ny; ++b) {
+        Dp[b] = Dw + b * bs;
+        Lp[b] = b > 0 ? L0 + b * bs : nullptr;
+        Up[b] = b + 1 < ny ? U0 + b * bs : nullptr;
+    }
+    cusolverDnHandle_t hs = nullptr;
+    CKS(cusolverDnCreate(&hs));
+    struct HS { cusolverDnHandle_t h; ~HS() { cusolverDnDestroy(h); } } gs{hs};
+    CKS(cusolverDnSetStream(hs, st));
+    cublasHandle_t hb = nullptr;
+    CKB(cublasCreate(&hb));
+    struct HB { cublasHandle_t h; ~HB() { cublasDestroy(h); } } gb{hb};
+    CKB(cublasSetStream(hb, st));
+    int lwork = 0;
+    CKS(cusolverDnZgetrf_bufferSize(hs, nx, nx, (cuDoubleComplex*)Dw, nx, &lwork));
+    DevBuf<double2> wsp;
+    DevBuf<int> piv, info;
+    CK(wsp.alloc(std::max(lwork, 1)));
+    CK(piv.alloc(nx));
+    CK(info.alloc((size_t)ny + 1));
+    CK(cudaMemsetAsync(info.p, 0, sizeof(int) * (ny + 1), st));
+    DevBuf<const double2*> pscr;
+    DevBuf<double2*> tptr;
+    CK(tptr.alloc(1));
+    int ninv = 0;
+    // X = D^{-1} (row-major) by LU of the column-major view D^T: X^T = (D^T)^{-1}
+    auto invert = [&](double2* D, double2* X) -> ls_status {
+        CK(cudaMemcpyAsync(tptr.p, &X, sizeof(void*), cudaMemcpyHostToDevice, st));
+        k_cr_identity<<<dim3((nx + 127) / 128, nx, 1), 128, 0, st>>>(nx, tptr.p);
+        CK(cudaGetLastError());
+        CKS(cusolverDnZgetrf(hs, nx, nx, (cuDoubleComplex*)D, nx, (cuDoubleComplex*)wsp.p, piv.p, info.p + ninv));
+        CKS(cusolverDnZgetrs(hs, CUBLAS_OP_N, nx, nx, (const cuDoubleComplex*)D, nx, piv.p, (cuDoubleComplex*)X, nx,
+                             info.p + ny));
+        CK(cudaStreamSynchronize(st));        // tptr is reused
+        ++ninv;
+        return LS_OK;
+    };
+    for (int l = 0; l < NL; ++l) {
+        const int n = nl[l];
+        std::vector<const double2*> A, B;
+        std::vector<double2*> C;
+        for (int i = 1, o = 0; i < n; i += 2, ++o) TRY(invert(Dp[i], blk(sDinv[l][o])));
+        for (int i = 1, o = 0; i < n; i += 2, ++o) {            // gamma_i = Dinv_i L_i, delta_i = Dinv_i U_i
+            A.push_back(blk(sDinv[l][o])); B.push_back(Lp[i]); C.push_back(blk(sGam[l][o]));
+            if (sDlt[l][o] != NONE) { A.push_back(blk(sDinv[l][o])); B.push_back(Up[i]); C.push_back(blk(sDlt[l][o])); }
+        }
+        TRY(cr_gemm(hb, st, nx, 1.0, 0.0, A, B, C, pscr));
+        A.clear(); B.clear(); C.clear();
+        for (int j = 2; j < n; j += 2) {                           // D_j -= L_j delta_{j-1}
+            A.push_back(Lp[j]); B.push_back(blk(sDlt[l][(j - 1) / 2])); C.push_back(Dp[j]);
+        }
+        TRY(cr_gemm(hb, st, nx, -1.0, 1.0, A, B, C, pscr));
+        A.clear(); B.clear(); C.clear();
+        for (int j = 0; j + 1 < n; j += 2) {                       // D_j -= U_j gamma_{j+1}
+            A.push_back(Up[j]); B.push_back(blk(sGam[l][j / 2])); C.push_back(Dp[j]);
+        }
+        TRY(cr_gemm(hb, st, nx, -1.0, 1.0, A, B, C, pscr));
+        A.clear(); B.clear(); C.clear();
+        const int n1 = nl[l + 1];
+        if (n1 > 1) {
+            for (int p = 0; p < n1; ++p) {
+                const int j = 2 * p;
+                if (sL[l + 1][p] != NONE) { A.push_back(Lp[j]); B.push_back(blk(sGam[l][(j - 1) / 2])); C.push_back(blk(sL[l + 1][p])); }
+                if (sU[l + 1][p] != NONE) { A.push_back(Up[j]); B.push_back(blk(sDlt[l][(j + 1) / 2])); C.push_back(blk(sU[l + 1][p])); }
+            }
+            TRY(cr_gemm(hb, st, nx, -1.0, 0.0, A, B, C, pscr));
+        }
+        std::vector<double2*> D2(n1), L2(n1), U2(n1);
+        for (int p = 0; p < n1; ++p) {
+            D2[p] = Dp[2 * p];
+            L2[p] = sL[l + 1][p] != NONE ? blk(sL[l + 1][p]) : nullptr;
+            U2[p] = sU[l + 1][p] != NONE ? blk(sU[l + 1][p]) : nullptr;
+        }
+        Dp.swap(D2); Lp.swap(L2); Up.swap(U2);
+    }
+    TRY(invert(Dp[0], blk(sTop)));
+    {
+        std::vector<int> hinfo(ny + 1);
+        CK(cudaMemcpy(hinfo.data(), info.p, sizeof(int) * (ny + 1), cudaMemcpyDeviceToHost));
+        for (int i = 0; i <= ny; ++i)
+            if (hinfo[i] != 0) return fail(LS_ESINGULAR, "cyclic reduction: a diagonal block of C is singular");
+    }
+    {   // transposed copies
+        std::vector<const double2*> in(nN);
+        std::vector<double2*> out(nN);
+        for (size_t s = 0; s < nN; ++s) { in[s] = blk(s); out[s] = blk(s + nN); }
+        DevBuf<const double2*> din;
+        DevBuf<double2*> dout;
+        CK(din.alloc(nN));
+        CK(dout.alloc(nN));
+        CK(cudaMemcpy(din.p, in.data(), sizeof(void*) * nN, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(dout.p, out.data(), sizeof(void*) * nN, cudaMemcpyHostToDevice));
+        for (size_t s0 = 0; s0 < nN; s0 += 65535) {
+            const unsigned cnt = (unsigned)std::min<size_t>(65535, nN - s0);
+            dim3 tb(32, 8), tg((nx + 31) / 32, (nx + 31) / 32, cnt);
+            k_cr_transpose<<<tg, tb, 0, st>>>(nx, din.p + s0, dout.p + s0);
+        }
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(st));
+    }
+    // vector arena [t | x | scratch] and the job tables
+    CK(P.arena.alloc(4 * nc));
+    P.svec = 4 * nc;
+    double2* scr = P.arena.p + 2 * nc;
+    size_t soff = 0;
+    auto take = [&]() { double2* p = scr + soff; soff += nx; return p; };
+    std::vector<std::vector<double2*>> T(NL + 1), Z(NL);
+    T[0].resize(ny);
+    for (int b = 0; b < ny; ++b) T[0][b] = P.t() + (size_t)b * nx;
+    for (int l = 0; l < NL; ++l) {
+        for (int i = 1; i < nl[l]; i += 2) Z[l].push_back(take());
+        for (int p = 0; p < nl[l + 1]; ++p) T[l + 1].push_back(take());
+    }
+    if (soff > 2 * nc) return fail(LS_ECUDA, "cyclic reduction: scratch overflow");
+    auto X = [&](int l, int p) { return P.x() + ((size_t)p << l) * nx; };
+    auto N_ = [&](size_t s) -> const double2* { return s == NONE ? nullptr : blk(s); };
+    auto T_ = [&](size_t s) -> const double2* { return s == NONE ? nullptr : blk(s + nN); };
+    std::vector<CRJob> J;
+    std::vector<CRTriJob> TJ;
+    auto dense = [&](double2* y, const double2* base, const double2* M1, const double2* v1, const double2* M2,
+                     const double2* v2) {
+        if (!M1) { M1 = M2; v1 = v2; M2 = nullptr; v2 = nullptr; }
+        J.push_back(CRJob{y, base, M1, v1, M2, M2 ? v2 : nullptr});
+    };
+    auto step = [&](std::vector<CRPlan::Step>& list, int kind, size_t first) {
+        const size_t cnt = (kind == 0 ? J.size() : TJ.size()) - first;
+        if (cnt) list.push_back({kind, (int)first, (int)cnt});
+    };
+    // C x = t
+    for (int l = 0; l < NL; ++l) {
+        const int n = nl[l];
+        size_t f0 = J.size();
+        for (int i = 1, o = 0; i < n; i += 2, ++o) dense(Z[l][o], nullptr, N_(sDinv[l][o]), T[l][i], nullptr, nullptr);
+        step(P.fwd, 0, f0);
+        if (l == 0) {
+            size_t t0 = TJ.size();
+            for (int j = 0; j < n; j += 2)
+                TJ.push_back(CRTriJob{T[1][j / 2], T[0][j], j >= 1 ? Z[0][(j - 1) / 2] : nullptr,
+                                      j + 1 < n ? Z[0][(j + 1) / 2] : nullptr, j >= 1 ? j : -1, j + 1 < n ? j : -1});
+            step(P.fwd, 1, t0);
+        } else {
+            f0 = J.size();
+            for (int j = 0; j < n; j += 2)
+                dense(T[l + 1][j / 2], T[l][j], j >= 1 ? N_(sL[l][j]) : nullptr, j >= 1 ? Z[l][(j - 1) / 2] : nullptr,
+                      j + 1 < n ? N_(sU[l][j]) : nullptr, j + 1 < n ? Z[l][(j + 1) / 2] : nullptr);
+            step(P.fwd, 0, f0);
+        }
+    }
+    {
+        size_t f0 = J.size();
+        dense(X(NL, 0), nullptr, N_(sTop), T[NL][0], nullptr, nullptr);
+        step(P.fwd, 0, f0);
+    }
+    for (int l = NL - 1; l >= 0; --l) {
+        const int n = nl[l];
+        size_t f0 = J.size();
+        for (int i = 1, o = 0; i < n; i += 2, ++o)
+            dense(X(l, i), Z[l][o], N_(sGam[l][o]), X(l, i - 1), N_(sDlt[l][o]), i + 1 < n ? X(l, i + 1) : nullptr);
+        step(P.fwd, 0, f0);
+    }
+    // C^T x = t
+    for (int l = 0; l < NL; ++l) {
+        const int n = nl[l];
+        size_t f0 = J.size();
+        for (int j = 0; j < n; j += 2)
+            dense(T[l + 1][j / 2], T[l][j], j + 1 < n ? T_(sGam[l][j / 2]) : nullptr, j + 1 < n ? T[l][j + 1] : nullptr,
+                  j >= 1 ? T_(sDlt[l][(j - 1) / 2]) : nullptr, j >= 1 ? T[l][j - 1] : nullptr);
+        step(P.trn, 0, f0);
+    }
+    {
+        size_t f0 = J.size();
+        dense(X(NL, 0), nullptr, T_(sTop), T[NL][0], nullptr, nullptr);
+        step(P.trn, 0, f0);
+    }
+    for (int l = NL - 1; l >= 0; --l) {
+        const int n = nl[l];
+        if (l == 0) {
+            size_t t0 = TJ.size();
+            for (int i = 1, o = 0; i < n; i += 2, ++o)
+                TJ.push_back(CRTriJob{Z[0][o], T[0][i], i + 1 < n ? X(0, i + 1) : nullptr, X(0, i - 1),
+                                      i + 1 < n ? i + 1 : -1, i - 1});
+            step(P.trn, 2, t0);
+        } else {
+            size_t f0 = J.size();
+            for (int i = 1, o = 0; i < n; i += 2, ++o)
+                dense(Z[l][o], T[l][i], i + 1 < n ? T_(sL[l][i + 1]) : nullptr, i + 1 < n ? X(l, i + 1) : nullptr,
+                      T_(sU[l][i - 1]), X(l, i - 1));
+            step(P.trn, 0, f0);
+        }
+        size_t f0 = J.size();
+        for (int i = 1, o = 0; i < n; i += 2, ++o) dense(X(l, i), nullptr, T_(sDinv[l][o]), Z[l][o], nullptr, nullptr);
+        step(P.trn, 0, f0);
+    }
+    for (const auto& j : J)
+        if (!j.M1 || !j.v1 || !j.y) return fail(LS_ECUDA, "cyclic reduction: incomplete job table");
+    CK(P.jobs.alloc(J.size()));
+    CK(cudaMemcpy(P.jobs.p, J.data(), sizeof(CRJob) * J.size(), cudaMemcpyHostToDevice));
+    if (!TJ.empty()) {
+        CK(P.tjobs.alloc(TJ.size()));
+        CK(cudaMemcpy(P.tjobs.p, TJ.data(), sizeof(CRTriJob) * TJ.size(), cudaMemcpyHostToDevice));
+    }
+    return LS_OK;
+}
+
+// The steps of C x = t (transposed: C^T x = t) on P.t() -> P.x(), single right-hand side.
+static int launch_cr(ls_op* op, cudaStream_t st, bool transposed) {
+    const CRPlan& P = op->cr;
+    const int nx = P.nx;
+    const size_t shm = sizeof(double2) * 2 * nx;
+    const int rows = CR_WARPS * CR_ROWS_PER_WARP;
+    int nl = 0;
+    for (const auto& s : transposed ? P.trn : P.fwd) {
+        if (s.kind == 0)
+            k_cr_mv<1><<<dim3((nx + rows - 1) / rows, s.count, 1), 32 * CR_WARPS, shm, st>>>(nx, 1, P.svec,
+                                                                                         P.jobs.p + s.first);
+        else
+            k_cr_tri<<<dim3((nx + 127) / 128, s.count), 128, 0, st>>>(nx, 1, P.svec, op->cband.p, P.tjobs.p + s.first,
+                                                                       s.kind == 2);
+        ++nl;
+    }
+    return nl;
+}
+
+// The kernel sequence of P x on stream st (T_Q^C, the stencil A, the cyclic-reduction
+// solve of C, then T_C^Q fused with the identity term); returns the number of launches.
+static int launch_P_kernels(ls_op* op, cudaStream_t st, const double2* x, double2* z) {
+    const int nc = op->nx * op->ny, nx = op->nx, ny = op->ny;
+    k_tqc<<<(nc + 255) / 256, 256, 0, st>>>(nc, op->tqc_rp.p, op->tqc_ci.p, op->tqc_cv.p, x, op->pg.p);
+    k_stencil<<<(nc + 255) / 256, 256, 0, st>>>(nx, ny, op->st.p, op->pg.p, op->cr.t());
+    const int ncr = launch_cr(op, st, false);
+    k_tcq<<<(op->nq + 255) / 256, 256, 0, st>>>(op->nq, op->tcq_idx.p, op->tcq_w.p, op->cr.x(), op->pg.p, x, z);
+    return 3 + ncr;
+}
+
+// P^T x = x + T_Q^C^T (A^T C^{-T} - I) T_C^Q^T x on stream st; returns the number of launches.
+static int launch_PT_kernels(ls_op* op, cudaStream_t st, const double2* x, double2* z) {
+    const int nc = op->nx * op->ny, nx = op->nx, ny = op->ny;
+    k_tqc<<<(nc + 255) / 256, 256, 0, st>>>(nc, op->tqc_rp.p, op->tqc_ci.p, op->tqcT_cv.p, x, op->cr.t());
+    const int ncr = launch_cr(op, st, true);
+    k_stencilT<<<(nc + 255) / 256, 256, 0, st>>>(nx, ny, op->st.p, op->cr.x(), op->cr.t(), op->ptp.p);
+    k_tcq<<<(op->nq + 255) / 256, 256, 0, st>>>(op->nq, op->tcq_idx.p, op->tcqT_w.p, op->ptp.p, nullptr, x, z);
+    return 3 + ncr;
+}
+
+// P x (transpose: P^T x).  Each sequence is captured once into a CUDA graph (on a
+// private stream, with fixed input/output buffers) and replayed; x and z are copied
+// in and out.
+static ls_status apply_P_graph(ls_op* op, const double2* x, double2* z, bool transpose) {
+    cudaGraphExec_t& ge = transpose ? op->gPT : op->gP;
+    int& nlaunch = transpose ? op->nlaunch_PT : op->nlaunch_P;
+    if (!ge) {
         if (!op->cap) CK(cudaStreamCreateWithFlags(&op->cap, cudaStreamNonBlocking));
-        CK(op->pin.alloc(op->nq));
-        CK(op->pout.alloc(op->nq));
+        if (!op->pin.p) CK(op->pin.alloc(op->nq));
+        if (!op->pout.p) CK(op->pout.alloc(op->nq));
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(op->cap, cudaStreamCaptureModeThreadLocal));
-        launch_P_kernels(op, op->cap, op->pin.p, op->pout.p);
+        nlaunch = transpose ? launch_PT_kernels(op, op->cap, op->pin.p, op->pout.p)
+                            : launch_P_kernels(op, op->cap, op->pin.p, op->pout.p);
         CK(cudaStreamEndCapture(op->cap, &g));
-        cudaError_t e = cudaGraphInstantiate(&op->gP, g, 0);
+        cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
         cudaGraphDestroy(g);
         CK(e);
     }
     CK(cudaMemcpyAsync(op->pin.p, x, sizeof(double2) * op->nq, cudaMemcpyDeviceToDevice, op->stream));
-    CK(cudaGraphLaunch(op->gP, op->stream));
+    CK(cudaGraphLaunch(ge, op->stream));
     CK(cudaMemcpyAsync(z, op->pout.p, sizeof(double2) * op->nq, cudaMemcpyDeviceToDevice, op->stream));
-    op->launches += 3 + ny + (ny - 1);
+    op->launches += nlaunch;
     return LS_OK;
 }
+
+static ls_status apply_P(ls_op* op, const double2* x, double2* z) { return apply_P_graph(op, x, z, false); }
 
 // y = L^T x (mode 0) or y = V^T x (mode 2)
 static ls_status apply_LT(ls_op* op, const double2* x, double2* y, int mode = 0) {
@@ -1896,23 +2142,7 @@ static ls_status apply_LT(ls_op* op, const double2* x, double2* y, int mode = 0)
 }
 
 // z = P^T x = x + T_Q^C^T (A^T C^{-T} - I) T_C^Q^T x
-static ls_status apply_PT(ls_op* op, const double2* x, double2* z) {
-    const int nc = op->nx * op->ny, nx = op->nx, ny = op->ny;
-    k_tqc<<<(nc + 255) / 256, 256, 0, op->stream>>>(nc, op->tqc_rp.p, op->tqc_ci.p, op->tqcT_cv.p, x, op->pg.p);
-    CK(cudaMemcpyAsync(op->ptp.p, op->pg.p, sizeof(double2) * nc, cudaMemcpyDeviceToDevice, op->stream));
-    const int wpb = 8;
-    const int blocks = (nx + wpb - 1) / wpb;
-    const size_t shm = sizeof(double2) * nx;
-    for (int b = 1; b < ny; ++b)
-        k_btT_fwd<<<blocks, 32 * wpb, shm, op->stream>>>(nx, b, op->GT.p, op->ptp.p);
-    for (int b = ny - 1; b >= 0; --b)
-        k_btT_bwd<<<blocks, 32 * wpb, shm, op->stream>>>(nx, ny, b, op->WT.p, op->cband.p, op->ptp.p, op->pt.p);
-    k_stencilT<<<(nc + 255) / 256, 256, 0, op->stream>>>(nx, ny, op->st.p, op->pt.p, op->pg.p, op->ptp.p);
-    k_tcq<<<(op->nq + 255) / 256, 256, 0, op->stream>>>(op->nq, op->tcq_idx.p, op->tcqT_w.p, op->ptp.p, nullptr, x, z);
-    CK(cudaGetLastError());
-    op->launches += 3 + (ny - 1) + ny;
-    return LS_OK;
-}
+static ls_status apply_PT(ls_op* op, const double2* x, double2* z) { return apply_P_graph(op, x, z, true); }
 
 // h[0:J] = V[0:J]^H z (into dst, accumulate or overwrite)
 static ls_status dots(ls_op* op, int J, const double2* V, const double2* z, double2* dst, int accumulate) {
@@ -1923,11 +2153,6 @@ static ls_status dots(ls_op* op, int J, const double2* V, const double2* z, doub
     return LS_OK;
 }
 
-#define TRY(x)                         \
-    do {                               \
-        ls_status s__ = (x);           \
-        if (s__ != LS_OK) return s__;  \
-    } while (0)
 
 // One GMRES solve for device rhs b -> u. Writes hist (host, may be null) and iterations.
 static ls_status gmres_one(ls_op* op, const double2* b, double2* u, double* hist_host, int* iters, bool transpose = false) {
@@ -2297,6 +2522,7 @@ static ls_status build_preconditioner(ls_op* op, const HostMesh& M, const double
         CK(cudaGetLastError());
     }
     CK(cudaStreamSynchronize(op->stream));
+    TRY(build_cr(op));
     op->t_setup[2] = std::chrono::duration<double>(std::chrono::steady_clock::now() - tl0).count();
     op->has_prec = true;
     return LS_OK;
