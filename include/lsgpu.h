@@ -47,6 +47,18 @@ typedef enum {
 typedef struct ls_mesh ls_mesh;
 typedef struct ls_op ls_op;
 
+/* Pair-sum arithmetic of an operator (ls_params.prec). */
+enum {
+    LS_PREC_FP64_TABLE = 0,   /* FP64, H0 from a per-operator table of polynomials in t = r^2 on
+                                 octave-graded cells (each table validated to 2e-15 against the
+                                 long-double routine at setup; degree chosen by timing at setup) */
+    LS_PREC_FP64_DIRECT = 1,  /* FP64 direct evaluation of H0 (series / fitted asymptotic form)  */
+    LS_PREC_FP32 = 2,         /* precision form: FP32 table (degree 6, validated to 2e-8),
+                                 double-float coordinate differences, Kahan-compensated FP32 sums */
+    LS_PREC_FP64_DF = 3       /* FP64-accurate: the FP64 table evaluated in double-float (pairs of
+                                 FP32) arithmetic and accumulated on the FP32 pipe                */
+};
+
 /* Build parameters of an operator. */
 typedef struct {
     double  tol;          /* GMRES stop: ||P(b - L u_k)|| / ||P b|| <= tol          */
@@ -56,18 +68,18 @@ typedef struct {
     double  box[4];       /* Cartesian grid box xmin, xmax, ymin, ymax (Section 4)    */
     int32_t nx, ny;       /* grid nodes per direction, endpoints included; the step
                              (xmax - xmin)/(nx - 1) must equal (ymax - ymin)/(ny - 1) */
-    int32_t pairsum;      /* 0: FP64, H0 from a per-operator table of polynomials in
-                             t = r^2 on octave-graded cells (each table validated to
-                             2e-15 against the long-double routine at setup; degree 11,
-                             9 or 8 chosen by timing at setup); 1: FP64 direct
-                             evaluation; 2: precision form -- FP32 table (degree 6,
-                             validated to 2e-8), double-float coordinate differences,
-                             Kahan-compensated FP32 accumulation; 3: FP64-accurate
-                             double-float (FP32 pairs) evaluation of the mode-0 table
-                             and accumulation on the FP32 pipe                   */
+    int32_t prec;         /* LS_PREC_* above                                          */
+    int32_t approach;     /* transfer T_Q^C of the preconditioner: 2 = Approach II, the
+                             renormalised transpose D^{-1} (T_C^Q)^T (Eq. T_H^C_def);
+                             1 = Approach I, the element-wise L^2 projection
+                             E_C (M^tri)^{-1} E_Q^T W (Eq. T_HC_proj_def)             */
+    int32_t setup_on_device; /* 1: the correction dV is built on the GPU in double-double
+                             arithmetic (blocks out of its series range on the host);
+                             0: entirely on the host in long double                  */
 } ls_params;
 
-/* Defaults: tol 1e-8, max_iter 600, use_precond 1, kappa 3, box [-1.2,1.2]^2, 256 x 256, pairsum 0. */
+/* Defaults: tol 1e-8, max_iter 600, use_precond 1, kappa 3, box [-1.2,1.2]^2, 256 x 256,
+   prec LS_PREC_FP64_TABLE, approach 2, setup_on_device 1. */
 void ls_params_default(ls_params* p);
 
 /*
@@ -106,9 +118,10 @@ int32_t ls_mesh_num_nodes(const ls_mesh* mesh);
  *   m_grid   [nx * ny] complex contrast at the grid nodes (x fastest), zero
  *            outside the scatterer; required when use_precond, else may be NULL
  *   stream   cudaStream_t (NULL = default stream) for all device work
- * Setup builds the VDIM correction dV in extended precision on the host
- * (OpenMP) and the preconditioner factors on the device; it is not part of
- * the timed solve.  The mesh may be destroyed afterwards.
+ * Setup builds the VDIM correction dV in extended precision (on the GPU in
+ * double-double arithmetic, or on the host in long double, see setup_on_device)
+ * and the preconditioner factors on the device; it is not part of the timed
+ * solve.  The mesh may be destroyed afterwards.
  * Errors: LS_EINVAL (k <= 0, NaN contrast, bad grid), LS_ENOMEM, LS_ECUDA,
  * LS_ESINGULAR (a Schur block of C is singular).
  */
@@ -265,6 +278,19 @@ ls_status ls_solve_transpose_batch_dev(ls_op* op, int32_t R, const void* g_dev, 
 ls_status ls_op_set_batch_kernel(ls_op* op, int32_t kind, int32_t fold, int32_t refine);
 
 /*
+ * Failure-detection test hook of the tensor-core pair sum (no counterpart in the
+ * paper).  With stall_ms > 0 the MMA issuer of every following tensor-core launch
+ * on this operator first waits stall_ms on a barrier that nothing completes; the
+ * wait is bounded like every other wait of the pipeline, so it runs out, the CTA
+ * raises its abort flag, the other roles leave their (abort-aware, bounded) waits,
+ * issued bulk copies are drained, tensor memory is freed, and the call returns
+ * LS_ETIMEOUT.  The error word is cleared when reported, so after
+ * ls_op_set_stall_test(op, 0) the next call succeeds on the same context.
+ * Errors: LS_EINVAL for stall_ms outside [0, 1000].
+ */
+ls_status ls_op_set_stall_test(ls_op* op, double stall_ms);
+
+/*
  * Self-check of the tensor-core MMA path (no counterpart in the paper): one
  * 128 x N x 32 product of exactly representable values through the shared-memory
  * layouts, descriptors and tcgen05.mma / tcgen05.ld sequence of the batched pair
@@ -310,10 +336,23 @@ ls_status ls_correction_host(const ls_mesh* mesh, double k, double kappa, int64_
 ls_status ls_grid_host(const ls_mesh* mesh, double k, const double* box, int32_t nx, int32_t ny, const double* m_grid,
                        double* stencils, double* cband);
 
+/*
+ * Device build of the correction dV for a mesh (the setup ls_operator_create runs when
+ * params->setup_on_device): per (target, subdomain patch) block the Green's-identity
+ * boundary moments and the plain-quadrature patch moments in double-double arithmetic
+ * on the GPU, combined with the host's long-double coefficient matrices.  Same CSR
+ * layout and two-call size query as ls_correction_host; values recomputed on every
+ * call.  *host_blocks (may be NULL) receives the number of blocks rebuilt on the host
+ * (those whose patch reaches k r > 32, beyond the device series).
+ * Errors: LS_EINVAL (null arguments, k <= 0), LS_ECUDA, LS_ESINGULAR.
+ */
+ls_status ls_correction_dev(const ls_mesh* mesh, double k, double kappa, void* stream, int64_t* nnz,
+                            int64_t* rowptr, int32_t* cols, double* vals, int64_t* host_blocks);
+
 /* Diagnostic: h_dev[i] = H0^(1)(z_dev[i]) (complex) by the device routine of the pair sum. */
 ls_status ls_hankel0_dev(int64_t n, const double* z_dev, void* h_dev, void* stream);
 
-/* Switch the pair-sum kernel of an operator (0, 1 or 2 as ls_params.pairsum); rebuilds the H0 table. */
+/* Switch the pair-sum kernel of an operator (LS_PREC_* as ls_params.prec); rebuilds the H0 table. */
 ls_status ls_op_set_pairsum(ls_op* op, int32_t mode);
 
 /*

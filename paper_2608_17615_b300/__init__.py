@@ -19,11 +19,12 @@ _STATUS = {0: "LS_OK", 1: "LS_EINVAL", 2: "LS_ENOMEM", 3: "LS_ECUDA", 4: "LS_ESI
 
 EXPORTED = ["ls_params_default", "ls_mesh_create", "ls_mesh_destroy", "ls_mesh_num_nodes", "ls_operator_create",
             "ls_op_destroy", "ls_op_num_nodes", "ls_apply_dev", "ls_apply", "ls_apply_precond_dev", "ls_pairsum_dev",
-            "ls_solve", "ls_solve_dev", "ls_op_correction", "ls_correction_host", "ls_grid_host", "ls_hankel0_dev",
+            "ls_solve", "ls_solve_dev", "ls_op_correction", "ls_correction_host", "ls_correction_dev", "ls_grid_host",
+            "ls_hankel0_dev",
             "ls_pairsum_batch_dev", "ls_solve_batch_dev", "ls_solve_multi_dev", "ls_apply_transpose_dev", "ls_potential_transpose_dev", "ls_apply_precond_transpose_dev",
             "ls_solve_transpose_dev", "ls_op_set_contrast", "ls_incident_dev", "ls_misfit_gradient_dev",
             "ls_solve_transpose_batch_dev", "ls_misfit_gradient_batch_dev",
-            "ls_op_set_batch_kernel", "ls_tc_gemm_check",
+            "ls_op_set_batch_kernel", "ls_op_set_stall_test", "ls_tc_gemm_check",
             "ls_op_set_pairsum", "ls_op_set_timing", "ls_op_setup_times", "ls_op_tuning", "ls_op_stats", "ls_probe_fp64", "ls_pairsum_noalloc", "ls_last_error"]
 
 
@@ -33,10 +34,23 @@ class LsError(RuntimeError):
         self.status = status
 
 
+LS_PREC_FP64_TABLE, LS_PREC_FP64_DIRECT, LS_PREC_FP32, LS_PREC_FP64_DF = range(4)
+
+
 class Params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("use_precond", ctypes.c_int32),
                 ("kappa", ctypes.c_double), ("box", ctypes.c_double * 4), ("nx", ctypes.c_int32),
-                ("ny", ctypes.c_int32), ("pairsum", ctypes.c_int32)]
+                ("ny", ctypes.c_int32), ("prec", ctypes.c_int32), ("approach", ctypes.c_int32),
+                ("setup_on_device", ctypes.c_int32)]
+
+    @property
+    def pairsum(self):
+        """The pair-sum arithmetic (alias of prec)."""
+        return self.prec
+
+    @pairsum.setter
+    def pairsum(self, v):
+        self.prec = v
 
 
 def _load():
@@ -60,6 +74,7 @@ def _load():
         "ls_solve_dev": (I32, [P, I32, P, P, I32, P, P, P]),
         "ls_op_correction": (I32, [P, P, P, P, P]),
         "ls_correction_host": (I32, [P, D, D, P, P, P, P]),
+        "ls_correction_dev": (I32, [P, D, D, P, P, P, P, P, P]),
         "ls_grid_host": (I32, [P, D, P, I32, I32, P, P, P]),
         "ls_hankel0_dev": (I32, [I64, P, P, P]),
         "ls_pairsum_batch_dev": (I32, [P, I32, P, P]),
@@ -74,6 +89,7 @@ def _load():
         "ls_misfit_gradient_dev": (I32, [P, I32, P, I32, P, P, P, P]),
         "ls_solve_transpose_batch_dev": (I32, [P, I32, P, P, P]),
         "ls_op_set_batch_kernel": (I32, [P, I32, I32, I32]),
+        "ls_op_set_stall_test": (I32, [P, D]),
         "ls_tc_gemm_check": (I32, [I32, P]),
         "ls_misfit_gradient_batch_dev": (I32, [P, I32, P, I32, P, P, P, P]),
         "ls_op_set_pairsum": (I32, [P, I32]),
@@ -158,7 +174,11 @@ class Operator:
             if key == "box":
                 for i in range(4):
                     p.box[i] = val[i]
+            elif key == "pairsum":
+                p.prec = val
             else:
+                if key not in dict(Params._fields_):
+                    raise TypeError(f"unknown operator parameter {key!r}")
                 setattr(p, key, val)
         self.params = p
         m_arr, m_f = _c128(m)
@@ -281,12 +301,17 @@ class Operator:
     def set_pairsum(self, mode):
         """0: FP64 table, 1: FP64 direct, 2: FP32 precision form."""
         _check(_lib.ls_op_set_pairsum(self.handle, int(mode)))
-        self.params.pairsum = int(mode)
+        self.params.prec = int(mode)
 
     def set_batch_kernel(self, kind, fold=4, refine=4):
         """Batched pair sum on 0: CUDA cores, 1: tensor cores (accumulator restarted every fold
         stages; batched solves refined up to `refine` times against the kind-0 operator)."""
         _check(_lib.ls_op_set_batch_kernel(self.handle, int(kind), int(fold), int(refine)))
+
+    def set_stall_test(self, stall_ms):
+        """Failure-detection test: the next tensor-core launches stall stall_ms on a
+        barrier nothing completes and return LS_ETIMEOUT (0 turns it off)."""
+        _check(_lib.ls_op_set_stall_test(self.handle, float(stall_ms)))
 
     def set_timing(self, on=True):
         _check(_lib.ls_op_set_timing(self.handle, 1 if on else 0))
@@ -333,6 +358,20 @@ def correction_host(mesh, k, kappa=3.0):
     _check(_lib.ls_correction_host(mesh.handle, float(k), float(kappa), ctypes.byref(nnz), _ptr(rp), _ptr(ci),
                                    _ptr(va.view(np.float64))))
     return rp, ci, va
+
+
+def correction_dev(mesh, k, kappa=3.0):
+    """Device build of dV for a Mesh handle: (rowptr, cols, vals, blocks rebuilt on the host)."""
+    nnz = ctypes.c_int64()
+    nh = ctypes.c_int64()
+    st = ctypes.c_void_p(_current_stream())
+    _check(_lib.ls_correction_dev(mesh.handle, float(k), float(kappa), st, ctypes.byref(nnz), None, None, None, None))
+    rp = np.empty(mesh.n + 1, np.int64)
+    ci = np.empty(nnz.value, np.int32)
+    va = np.empty(nnz.value, np.complex128)
+    _check(_lib.ls_correction_dev(mesh.handle, float(k), float(kappa), st, ctypes.byref(nnz), _ptr(rp), _ptr(ci),
+                                  _ptr(va.view(np.float64)), ctypes.byref(nh)))
+    return rp, ci, va, nh.value
 
 
 def grid_host(mesh, k, box, nx, ny, m_grid):

@@ -32,6 +32,32 @@ struct CsrC {                     // complex CSR, int64 row pointers
 // Returns "" on success, else an error message.
 std::string build_correction(const HostMesh& mesh, double k, double kappa, CsrC& out);
 
+// Work list of the device build of dV: one block per (target, subdomain with a patch),
+// the blocks of a target consecutive and in the order of the host build's columns.
+struct CorrPlan {
+    std::vector<int64_t> row_blocks;           // [nq + 1] first block of each target
+    std::vector<int32_t> target, tau;          // [nb] target node, interpolation element
+    std::vector<int8_t> own;                   // [nb] target's own subdomain (chi = 1)
+    std::vector<int64_t> elem_off;             // [nb + 1] into elems
+    std::vector<int32_t> elems;                // patch elements
+    std::vector<int64_t> pan_off;              // [nb + 1] into the panel arrays
+    std::vector<int32_t> pan_edge;             // 3 element + local edge
+    std::vector<long double> pan_a, pan_b;     // parameter interval of the panel on its edge
+};
+std::string plan_correction(const HostMesh& mesh, double kappa, CorrPlan& plan);
+// Monomial centre/scale (cx, cy, 1/h) and coefficient matrices C, Phi [15 monomials][15 nodes]
+// of the Lagrange basis of element tau and of its Helmholtz particular solutions.
+bool poly_context(const HostMesh& mesh, int tau, double k, long double* c3, long double* C, long double* Phi);
+// One block of dV by the host routine (extended precision): 15 values.
+bool correction_block_host(const HostMesh& mesh, int j, double k, const std::vector<int>& patch, int tau, bool own,
+                           std::complex<double>* out15);
+// 32-point Gauss-Legendre rule on [0, 1] (long double).
+void gl32_unit(long double* x, long double* w);
+// The same dV built on the GPU (double-double moments, vdim_dev.cu); blocks whose patch
+// leaves the series range are rebuilt on the host (their count in *host_blocks).
+std::string build_correction_device(const HostMesh& mesh, double k, double kappa, void* stream, CsrC& out,
+                                    int64_t* host_blocks);
+
 struct GridSetup {
     int nx = 0, ny = 0;
     double x0 = 0, y0 = 0, h = 0;

@@ -1648,6 +1648,8 @@ struct ls_op {
     int batch_kernel = 1;                // 0: CUDA cores (k_pairsum_multi_f32), 1: tensor cores
     int tc_fold = 4;                     // stages per accumulator run
     int tc_refine = 4;                   // iterative-refinement steps after a tensor-core solve (0: none)
+    uint64_t tc_stall_ns = 0;            // failure-detection test: forced stall of the MMA issuer (ns)
+    int64_t corr_host_blocks = 0;        // correction blocks the device setup left to the host
     DevBuf<double2> ir_r, ir_d, ir_y;    // refinement work vectors [R][n]
     int tc_nchunk = 0, tc_spc = 0, tc_npad = 0;
     DevBuf<float4> tc_xy32, tc_Sc;
@@ -2228,7 +2230,9 @@ void ls_params_default(ls_params* p) {
     p->box[0] = -1.2; p->box[1] = 1.2; p->box[2] = -1.2; p->box[3] = 1.2;
     p->nx = 256;
     p->ny = 256;
-    p->pairsum = 0;
+    p->prec = LS_PREC_FP64_TABLE;
+    p->approach = 2;
+    p->setup_on_device = 1;
 }
 
 ls_status ls_mesh_create(int32_t n_vert, const double* vert_xy, int32_t n_elem, const int32_t* elem_vert,
@@ -2538,8 +2542,9 @@ ls_status ls_operator_create(const ls_mesh* mesh, double k, const double* m, con
     ls_params_default(&prm);
     if (params) prm = *params;
     if (prm.max_iter < 1 || !(prm.tol > 0) || !(prm.kappa > 0)) return fail(LS_EINVAL, "bad tol / max_iter / kappa");
-    if (prm.pairsum < 0 || prm.pairsum > 3)
-        return fail(LS_EINVAL, "pairsum must be 0 (FP64 table), 1 (FP64 direct), 2 (FP32) or 3 (double-float)");
+    if (prm.prec < 0 || prm.prec > 3)
+        return fail(LS_EINVAL, "prec must be 0 (FP64 table), 1 (FP64 direct), 2 (FP32) or 3 (double-float)");
+    if (prm.approach != 1 && prm.approach != 2) return fail(LS_EINVAL, "approach must be 1 or 2");
     if (prm.use_precond && !m_grid) return fail(LS_EINVAL, "m_grid is required with use_precond");
     const HostMesh& M = mesh->h;
     for (int q = 0; q < M.nq; ++q)
@@ -2554,9 +2559,11 @@ ls_status ls_operator_create(const ls_mesh* mesh, double k, const double* m, con
     const int n = M.nq;
     // correction (host, extended precision)
     auto tc0 = std::chrono::steady_clock::now();
-    std::string err = lsgpu::build_correction(M, k, prm.kappa, op->host_csr);
+    std::string err = prm.setup_on_device
+                          ? lsgpu::build_correction_device(M, k, prm.kappa, stream, op->host_csr, &op->corr_host_blocks)
+                          : lsgpu::build_correction(M, k, prm.kappa, op->host_csr);
     op->t_setup[0] = std::chrono::duration<double>(std::chrono::steady_clock::now() - tc0).count();
-    if (!err.empty()) return fail(LS_ESINGULAR, err);
+    if (!err.empty()) return fail(err.find("singular") != std::string::npos ? LS_ESINGULAR : LS_ECUDA, err);
     op->host_nodes = M.nodes;
     op->host_w = M.w;
     op->host_m.resize(n);
@@ -2607,10 +2614,10 @@ ls_status ls_operator_create(const ls_mesh* mesh, double k, const double* m, con
     op->nchunk = nchunk;
     op->src_per_chunk = spc;
     CK(op->partial.alloc((size_t)nchunk * n));
-    op->mode = prm.pairsum;
+    op->mode = prm.prec;
     table_range(op, M);
     auto tt0 = std::chrono::steady_clock::now();
-    if (prm.pairsum != 1) TRY(build_table_range(op, op->tab_tlo, op->tab_thi, prm.pairsum));
+    if (prm.prec != 1) TRY(build_table_range(op, op->tab_tlo, op->tab_thi, prm.prec));
     op->t_setup[3] = std::chrono::duration<double>(std::chrono::steady_clock::now() - tt0).count();
     // GMRES workspace
     const int maxit = prm.max_iter;
@@ -2829,6 +2836,7 @@ static ls_status pairsum_tc_launch(int S, ls_op* const* ops, int R, const double
         A.r_offset = r0;
         A.idesc = tc::idesc_tf32(TC_M, N);
         A.err = ops[0]->tc_err.p;
+        A.stall_ns = ops[0]->tc_stall_ns;
         // three staging slots when they fit beside the table, else two
         A.nstg = tc_smem_bytes(N, max_tab, 3) <= 227 * 1024 ? 3 : 2;
         const size_t smem = tc_smem_bytes(N, max_tab, A.nstg);
@@ -2855,9 +2863,15 @@ static ls_status pairsum_batch_tc(ls_op* op, int R, const double2* f, size_t sf,
 }
 
 // error word of the tensor-core pair sum, read after a stream synchronisation
+// (the word is cleared on report, so the operator stays usable for the next call)
 static ls_status tc_status(ls_op* op) {
-    if (op->tc_herr && *op->tc_herr)
-        return fail(LS_ETIMEOUT, "tensor-core pair sum: a pipeline wait ran out (code " + std::to_string(*op->tc_herr) + ")");
+    if (op->tc_herr && *op->tc_herr) {
+        const int code = *op->tc_herr;
+        *op->tc_herr = 0;
+        CK(cudaMemsetAsync(op->tc_err.p, 0, sizeof(int), op->stream));
+        CK(cudaStreamSynchronize(op->stream));
+        return fail(LS_ETIMEOUT, "tensor-core pair sum: a pipeline wait ran out (code " + std::to_string(code) + ")");
+    }
     return LS_OK;
 }
 
@@ -3329,6 +3343,12 @@ ls_status ls_pairsum_batch_dev(ls_op* op, int32_t R, const void* f_dev, void* y_
     return tc_status(op);
 }
 
+ls_status ls_op_set_stall_test(ls_op* op, double stall_ms) {
+    if (!op || !(stall_ms >= 0) || stall_ms > 1000.0) return fail(LS_EINVAL, "stall_ms must be in [0, 1000]");
+    op->tc_stall_ns = (uint64_t)(stall_ms * 1e6);
+    return LS_OK;
+}
+
 ls_status ls_op_set_batch_kernel(ls_op* op, int32_t kind, int32_t fold, int32_t refine) {
     if (!op || kind < 0 || kind > 1 || fold < 1 || refine < 0)
         return fail(LS_EINVAL, "kind must be 0 or 1, fold >= 1, refine >= 0");
@@ -3547,6 +3567,21 @@ ls_status ls_correction_host(const ls_mesh* mesh, double k, double kappa, int64_
     if (rowptr) std::memcpy(rowptr, csr.rowptr.data(), sizeof(int64_t) * csr.rowptr.size());
     if (cols) std::memcpy(cols, csr.cols.data(), sizeof(int32_t) * csr.cols.size());
     if (vals) std::memcpy(vals, csr.vals.data(), sizeof(double) * 2 * csr.vals.size());
+    return LS_OK;
+}
+
+ls_status ls_correction_dev(const ls_mesh* mesh, double k, double kappa, void* stream, int64_t* nnz,
+                            int64_t* rowptr, int32_t* cols, double* vals, int64_t* host_blocks) {
+    if (!mesh || !nnz) return fail(LS_EINVAL, "null argument");
+    if (!(k > 0) || !(kappa > 0)) return fail(LS_EINVAL, "k and kappa must be positive");
+    CsrC A;
+    std::string err = lsgpu::build_correction_device(mesh->h, k, kappa, stream, A, host_blocks);
+    if (!err.empty()) return fail(err.find("singular") != std::string::npos ? LS_ESINGULAR : LS_ECUDA, err);
+    *nnz = (int64_t)A.cols.size();
+    if (rowptr) std::copy(A.rowptr.begin(), A.rowptr.end(), rowptr);
+    if (cols) std::copy(A.cols.begin(), A.cols.end(), cols);
+    if (vals)
+        for (size_t e = 0; e < A.vals.size(); ++e) { vals[2 * e] = A.vals[e].real(); vals[2 * e + 1] = A.vals[e].imag(); }
     return LS_OK;
 }
 

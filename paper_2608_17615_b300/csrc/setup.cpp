@@ -398,7 +398,9 @@ static void panel_integral(const Edge& e, ld ta, ld tb, ld xj, ld yj, ld k, cons
     }
 }
 
-static void edge_integral(const Edge& e, ld xj, ld yj, ld k, const PolyCtx& P, cld* Mo) {
+// Dyadic refinement of the parameter interval [0, 1] of an edge until every panel is
+// shorter than 3/4 of its distance to the target (the panels of the boundary rule).
+static void edge_panels(const Edge& e, ld xj, ld yj, std::vector<std::pair<ld, ld>>& out) {
     struct Pan { ld a, b; int depth; };
     std::vector<Pan> stack{{0, 1, 0}};
     while (!stack.empty()) {
@@ -415,8 +417,32 @@ static void edge_integral(const Edge& e, ld xj, ld yj, ld k, const PolyCtx& P, c
             stack.push_back({p.a, mid, p.depth + 1});
             stack.push_back({mid, p.b, p.depth + 1});
         } else {
-            panel_integral(e, p.a, p.b, xj, yj, k, P, Mo);
+            out.push_back({p.a, p.b});
         }
+    }
+}
+
+static void edge_integral(const Edge& e, ld xj, ld yj, ld k, const PolyCtx& P, cld* Mo) {
+    std::vector<std::pair<ld, ld>> pans;
+    edge_panels(e, xj, yj, pans);
+    for (const auto& p : pans) panel_integral(e, p.first, p.second, xj, yj, k, P, Mo);
+}
+
+// Edges met once among the patch elements, as (element, local edge), in a fixed order.
+static void patch_boundary(const HostMesh& M, const std::vector<int>& patch, std::vector<std::array<int, 2>>& edges) {
+    std::vector<std::array<int, 4>> keys;   // (min v, max v, element, edge)
+    keys.reserve(patch.size() * 3);
+    for (int t : patch)
+        for (int e = 0; e < 3; ++e) {
+            int a = M.tri[3 * t + e], b = M.tri[3 * t + (e + 1) % 3];
+            keys.push_back({std::min(a, b), std::max(a, b), t, e});
+        }
+    std::sort(keys.begin(), keys.end());
+    for (size_t i = 0; i < keys.size();) {
+        size_t r = i + 1;
+        while (r < keys.size() && keys[r][0] == keys[i][0] && keys[r][1] == keys[i][1]) ++r;
+        if (r - i == 1) edges.push_back({keys[i][2], keys[i][3]});
+        i = r;
     }
 }
 
@@ -429,20 +455,9 @@ static bool correction_block(const HostMesh& M, int j, ld k, const std::vector<i
     cld E[15], N[15], Mo[15], Mn[15];
     for (int q = 0; q < 15; ++q) { E[q] = 0; N[q] = 0; Mo[q] = 0; Mn[q] = 0; }
     // boundary edges of the patch: edges met once among the patch elements
-    std::vector<std::array<int, 4>> keys;   // (min v, max v, element, edge)
-    keys.reserve(patch.size() * 3);
-    for (int t : patch)
-        for (int e = 0; e < 3; ++e) {
-            int a = M.tri[3 * t + e], b = M.tri[3 * t + (e + 1) % 3];
-            keys.push_back({std::min(a, b), std::max(a, b), t, e});
-        }
-    std::sort(keys.begin(), keys.end());
-    for (size_t i = 0; i < keys.size();) {
-        size_t r = i + 1;
-        while (r < keys.size() && keys[r][0] == keys[i][0] && keys[r][1] == keys[i][1]) ++r;
-        if (r - i == 1) edge_integral(make_edge(M, keys[i][2], keys[i][3]), xj, yj, k, P, Mo);
-        i = r;
-    }
+    std::vector<std::array<int, 2>> bedges;
+    patch_boundary(M, patch, bedges);
+    for (const auto& be : bedges) edge_integral(make_edge(M, be[0], be[1]), xj, yj, k, P, Mo);
     for (int q = 0; q < 15; ++q)
         for (int a = 0; a < 15; ++a) E[q] += P.Phi[a * 15 + q] * Mo[a];
     ld m[15];
@@ -501,46 +516,52 @@ static inline double dist2(double ax, double ay, double bx, double by) {
 }
 #pragma GCC pop_options
 
-std::string build_correction(const HostMesh& M, double k, double kappa, CsrC& out) {
-    std::vector<double> cen, h2;
-    element_geometry(M, cen, h2);
-    int ndom = 0;
-    for (int d : M.dom) ndom = std::max(ndom, d + 1);
-    // bucket grid of element centroids
-    double rmax = 0, xmin = 1e300, ymin = 1e300, xmax = -1e300, ymax = -1e300;
-    for (int t = 0; t < M.nt; ++t) {
-        rmax = std::max(rmax, kappa * std::sqrt(h2[t]));
-        xmin = std::min(xmin, cen[2 * t]); xmax = std::max(xmax, cen[2 * t]);
-        ymin = std::min(ymin, cen[2 * t + 1]); ymax = std::max(ymax, cen[2 * t + 1]);
+// Patches of every target: element centroids bucketed on a grid of cells no smaller
+// than the largest patch radius, so a patch lies in the 3 x 3 cells around its target.
+struct PatchBlock {
+    std::vector<int> elems;       // sorted element ids of the patch in one subdomain
+    int tau;                      // interpolation element (own element, or the nearest one)
+    bool own;                     // the target's own subdomain
+};
+
+class PatchFinder {
+  public:
+    PatchFinder(const HostMesh& M, double kappa) : M_(M), kappa_(kappa) {
+        element_geometry(M, cen_, h2_);
+        for (int d : M.dom) ndom_ = std::max(ndom_, d + 1);
+        double rmax = 0;
+        xmin_ = ymin_ = 1e300;
+        double xmax = -1e300, ymax = -1e300;
+        for (int t = 0; t < M.nt; ++t) {
+            rmax = std::max(rmax, kappa * std::sqrt(h2_[t]));
+            xmin_ = std::min(xmin_, cen_[2 * t]); xmax = std::max(xmax, cen_[2 * t]);
+            ymin_ = std::min(ymin_, cen_[2 * t + 1]); ymax = std::max(ymax, cen_[2 * t + 1]);
+        }
+        cell_ = std::max(rmax, 1e-12) * 1.0000001;
+        gx_ = std::max(1, (int)std::ceil((xmax - xmin_) / cell_) + 1);
+        gy_ = std::max(1, (int)std::ceil((ymax - ymin_) / cell_) + 1);
+        bucket_.resize((size_t)gx_ * gy_);
+        for (int t = 0; t < M.nt; ++t) {
+            int bx = std::min(gx_ - 1, (int)((cen_[2 * t] - xmin_) / cell_));
+            int by = std::min(gy_ - 1, (int)((cen_[2 * t + 1] - ymin_) / cell_));
+            bucket_[(size_t)by * gx_ + bx].push_back(t);
+        }
     }
-    double cell = std::max(rmax, 1e-12) * 1.0000001;
-    int gx = std::max(1, (int)std::ceil((xmax - xmin) / cell) + 1);
-    int gy = std::max(1, (int)std::ceil((ymax - ymin) / cell) + 1);
-    std::vector<std::vector<int>> bucket((size_t)gx * gy);
-    for (int t = 0; t < M.nt; ++t) {
-        int bx = std::min(gx - 1, (int)((cen[2 * t] - xmin) / cell));
-        int by = std::min(gy - 1, (int)((cen[2 * t + 1] - ymin) / cell));
-        bucket[(size_t)by * gx + bx].push_back(t);
-    }
-    const int nq = M.nq;
-    std::vector<std::vector<int32_t>> rcols(nq);
-    std::vector<std::vector<std::complex<double>>> rvals(nq);
-    int failed = -1;
-    const ld kl = k;
-#pragma omp parallel for schedule(dynamic, 16)
-    for (int j = 0; j < nq; ++j) {
-        int tau = j / NQ_ELEM;
-        int l = M.dom[tau];
-        double xj = M.nodes[2 * j], yj = M.nodes[2 * j + 1];
-        double thr = kappa * kappa * h2[tau];
-        int bx = std::min(gx - 1, std::max(0, (int)((xj - xmin) / cell)));
-        int by = std::min(gy - 1, std::max(0, (int)((yj - ymin) / cell)));
-        std::vector<std::vector<int>> patch(ndom);
-        for (int cy = std::max(0, by - 1); cy <= std::min(gy - 1, by + 1); ++cy)
-            for (int cx = std::max(0, bx - 1); cx <= std::min(gx - 1, bx + 1); ++cx)
-                for (int t : bucket[(size_t)cy * gx + cx])
-                    if (dist2(cen[2 * t], cen[2 * t + 1], xj, yj) < thr) patch[M.dom[t]].push_back(t);
-        for (int d = 0; d < ndom; ++d) {
+
+    // Blocks of target j in subdomain order (patch rule as documented at the top).
+    void blocks(int j, std::vector<PatchBlock>& out) const {
+        out.clear();
+        const int tau = j / NQ_ELEM, l = M_.dom[tau];
+        const double xj = M_.nodes[2 * j], yj = M_.nodes[2 * j + 1];
+        const double thr = kappa_ * kappa_ * h2_[tau];
+        const int bx = std::min(gx_ - 1, std::max(0, (int)((xj - xmin_) / cell_)));
+        const int by = std::min(gy_ - 1, std::max(0, (int)((yj - ymin_) / cell_)));
+        std::vector<std::vector<int>> patch(ndom_);
+        for (int cy = std::max(0, by - 1); cy <= std::min(gy_ - 1, by + 1); ++cy)
+            for (int cx = std::max(0, bx - 1); cx <= std::min(gx_ - 1, bx + 1); ++cx)
+                for (int t : bucket_[(size_t)cy * gx_ + cx])
+                    if (dist2(cen_[2 * t], cen_[2 * t + 1], xj, yj) < thr) patch[M_.dom[t]].push_back(t);
+        for (int d = 0; d < ndom_; ++d) {
             auto& P = patch[d];
             std::sort(P.begin(), P.end());
             int interp;
@@ -550,17 +571,41 @@ std::string build_correction(const HostMesh& M, double k, double kappa, CsrC& ou
             } else {
                 if (P.empty()) continue;
                 interp = P[0];
-                double best = dist2(cen[2 * P[0]], cen[2 * P[0] + 1], xj, yj);
+                double best = dist2(cen_[2 * P[0]], cen_[2 * P[0] + 1], xj, yj);
                 for (int t : P) {
-                    double d2 = dist2(cen[2 * t], cen[2 * t + 1], xj, yj);
+                    double d2 = dist2(cen_[2 * t], cen_[2 * t + 1], xj, yj);
                     if (d2 < best) { best = d2; interp = t; }
                 }
             }
-            if (!correction_block(M, j, kl, P, interp, d == l, rcols[j], rvals[j])) {
+            out.push_back(PatchBlock{std::move(P), interp, d == l});
+        }
+    }
+
+  private:
+    const HostMesh& M_;
+    double kappa_;
+    std::vector<double> cen_, h2_;
+    int ndom_ = 0, gx_ = 1, gy_ = 1;
+    double xmin_ = 0, ymin_ = 0, cell_ = 1;
+    std::vector<std::vector<int>> bucket_;
+};
+
+std::string build_correction(const HostMesh& M, double k, double kappa, CsrC& out) {
+    PatchFinder finder(M, kappa);
+    const int nq = M.nq;
+    std::vector<std::vector<int32_t>> rcols(nq);
+    std::vector<std::vector<std::complex<double>>> rvals(nq);
+    int failed = -1;
+    const ld kl = k;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int j = 0; j < nq; ++j) {
+        std::vector<PatchBlock> blk;
+        finder.blocks(j, blk);
+        for (const auto& B : blk)
+            if (!correction_block(M, j, kl, B.elems, B.tau, B.own, rcols[j], rvals[j])) {
 #pragma omp critical
                 failed = j;
             }
-        }
     }
     if (failed >= 0) return "singular interpolation matrix for target " + std::to_string(failed);
     out.rowptr.assign(nq + 1, 0);
@@ -572,6 +617,103 @@ std::string build_correction(const HostMesh& M, double k, double kappa, CsrC& ou
         std::copy(rvals[j].begin(), rvals[j].end(), out.vals.begin() + out.rowptr[j]);
     }
     return "";
+}
+
+// ---------------------------------------------------------------- plan of the device build
+std::string plan_correction(const HostMesh& M, double kappa, CorrPlan& P) {
+    PatchFinder finder(M, kappa);
+    const int nq = M.nq;
+    struct Local {
+        std::vector<int32_t> tau, nelem, npan, elems, pedge;
+        std::vector<int8_t> own;
+        std::vector<long double> pa, pb;
+    };
+    std::vector<Local> per(nq);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int j = 0; j < nq; ++j) {
+        std::vector<PatchBlock> blk;
+        finder.blocks(j, blk);
+        Local& L = per[j];
+        const ld xj = M.nodes[2 * j], yj = M.nodes[2 * j + 1];
+        for (const auto& B : blk) {
+            L.tau.push_back(B.tau);
+            L.own.push_back(B.own ? 1 : 0);
+            L.nelem.push_back((int32_t)B.elems.size());
+            L.elems.insert(L.elems.end(), B.elems.begin(), B.elems.end());
+            std::vector<std::array<int, 2>> bedges;
+            patch_boundary(M, B.elems, bedges);
+            int np = 0;
+            for (const auto& be : bedges) {
+                std::vector<std::pair<ld, ld>> pans;
+                edge_panels(make_edge(M, be[0], be[1]), xj, yj, pans);
+                for (const auto& p : pans) {
+                    L.pedge.push_back(3 * be[0] + be[1]);
+                    L.pa.push_back(p.first);
+                    L.pb.push_back(p.second);
+                    ++np;
+                }
+            }
+            L.npan.push_back(np);
+        }
+    }
+    P = CorrPlan{};
+    P.row_blocks.assign(nq + 1, 0);
+    for (int j = 0; j < nq; ++j) P.row_blocks[j + 1] = P.row_blocks[j] + (int64_t)per[j].tau.size();
+    const int64_t nb = P.row_blocks[nq];
+    P.target.resize(nb); P.tau.resize(nb); P.own.resize(nb);
+    P.elem_off.assign(nb + 1, 0);
+    P.pan_off.assign(nb + 1, 0);
+    for (int j = 0; j < nq; ++j) {
+        const Local& L = per[j];
+        int64_t b0 = P.row_blocks[j];
+        for (size_t i = 0; i < L.tau.size(); ++i) {
+            P.target[b0 + i] = j;
+            P.tau[b0 + i] = L.tau[i];
+            P.own[b0 + i] = L.own[i];
+            P.elem_off[b0 + i + 1] = L.nelem[i];
+            P.pan_off[b0 + i + 1] = L.npan[i];
+        }
+    }
+    for (int64_t b = 0; b < nb; ++b) {
+        P.elem_off[b + 1] += P.elem_off[b];
+        P.pan_off[b + 1] += P.pan_off[b];
+    }
+    P.elems.reserve(P.elem_off[nb]);
+    P.pan_edge.reserve(P.pan_off[nb]);
+    P.pan_a.reserve(P.pan_off[nb]);
+    P.pan_b.reserve(P.pan_off[nb]);
+    for (int j = 0; j < nq; ++j) {
+        const Local& L = per[j];
+        P.elems.insert(P.elems.end(), L.elems.begin(), L.elems.end());
+        P.pan_edge.insert(P.pan_edge.end(), L.pedge.begin(), L.pedge.end());
+        P.pan_a.insert(P.pan_a.end(), L.pa.begin(), L.pa.end());
+        P.pan_b.insert(P.pan_b.end(), L.pb.begin(), L.pb.end());
+    }
+    return "";
+}
+
+bool poly_context(const HostMesh& M, int tau, double k, long double* c3, long double* C, long double* Phi) {
+    PolyCtx P;
+    if (!make_poly(M, tau, k, P)) return false;
+    c3[0] = P.cx; c3[1] = P.cy; c3[2] = P.invh;
+    std::copy(P.C, P.C + 225, C);
+    std::copy(P.Phi, P.Phi + 225, Phi);
+    return true;
+}
+
+bool correction_block_host(const HostMesh& M, int j, double k, const std::vector<int>& patch, int tau, bool own,
+                           std::complex<double>* out15) {
+    std::vector<int32_t> cols;
+    std::vector<std::complex<double>> vals;
+    if (!correction_block(M, j, (ld)k, patch, tau, own, cols, vals)) return false;
+    std::copy(vals.begin(), vals.end(), out15);
+    return true;
+}
+
+void gl32_unit(long double* x, long double* w) {
+    const GL32& g = gl32();
+    std::copy(g.x, g.x + 32, x);
+    std::copy(g.w, g.w + 32, w);
 }
 
 // ---------------------------------------------------------------- H0 table

@@ -67,6 +67,8 @@ struct TCArgs {
     int r_offset;         // first right-hand side of this launch in the partial layout
     uint32_t idesc;
     int* err;             // device error word (0 = ok)
+    uint64_t stall_ns;    // failure-detection test: > 0 makes the MMA issuer wait this long on a
+                          // barrier that nothing completes, then abort like a stalled pipeline
 };
 
 namespace tc {
@@ -103,12 +105,24 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity; false after TC_WAIT_NS.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the phase with the given parity; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = TC_WAIT_NS) {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = now_ns();
     for (;;) {
         if (mbar_try(bar, parity)) return true;
+        if (now_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// As mbar_wait, but also gives up (false) as soon as another role of the CTA has
+// raised the abort flag, so that one stalled wait ends the whole pipeline quickly.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, const int* abort_flag) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = now_ns();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (*(const volatile int*)abort_flag) return false;
         if (now_ns() - t0 > TC_WAIT_NS) return false;
     }
 }
@@ -231,6 +245,7 @@ __global__ void k_tc_xy32(int n, int npad, const double2* __restrict__ xy, float
 
 struct TCShared {
     uint64_t full[TC_NS], empty[TC_NS], stfull[TC_NSTG_MAX], stempty[TC_NSTG_MAX], accfull[2], accempty[2], done, tabbar;
+    uint64_t never;       // initialised, never arrived on (failure-detection test only)
     uint32_t tmem;
     int abort_flag;
 };
@@ -300,6 +315,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairsum_tc(TCArgs a) {
         }
         tc::mbar_init(&sh.done, 1);
         tc::mbar_init(&sh.tabbar, TC_PROD_WARPS);
+        tc::mbar_init(&sh.never, 1);
         sh.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -367,8 +383,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairsum_tc(TCArgs a) {
             }
             const uint32_t slot = gs % TC_NS, stgi = gs % nstg;
             bool ok = true;
-            if (gs >= TC_NS) ok = tc::mbar_wait(&sh.empty[slot], ((gs / TC_NS) - 1) & 1);
-            if (ok) ok = tc::mbar_wait(&sh.stfull[stgi], (gs / nstg) & 1);
+            if (gs >= TC_NS) ok = tc::mbar_wait_or_abort(&sh.empty[slot], ((gs / TC_NS) - 1) & 1, &sh.abort_flag);
+            if (ok) ok = tc::mbar_wait_or_abort(&sh.stfull[stgi], (gs / nstg) & 1, &sh.abort_flag);
             ok = __all_sync(0xffffffffu, ok);                 // one decision per warp
             if (!ok) {
                 if (lane == 0) { atomicOr(a.err, 1); sh.abort_flag = 1; }
@@ -475,21 +491,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairsum_tc(TCArgs a) {
             const uint32_t ring_addr = tc::smem_u32(ring);
             uint32_t rr = 0;              // runs started
             bool ok = true;
-            for (uint32_t gs = 0; c.valid(a); ++gs, c.next(a)) {
+            if (a.stall_ns && !tc::mbar_wait(&sh.never, 0, a.stall_ns)) {
+                atomicOr(a.err, 64);
+                sh.abort_flag = 1;
+                ok = false;
+            }
+            for (uint32_t gs = 0; ok && c.valid(a); ++gs, c.next(a)) {
                 const uint32_t slot = gs % TC_NS;
                 const bool first = (c.g % a.F) == 0;
                 const bool last = ((c.g % a.F) == a.F - 1) || (c.g == c.G - 1);
                 const uint32_t ab = rr & 1;
                 // once the producers have read staging slot gs % nstg, refill it with stage gs + nstg
                 if (issued == gs + nstg && cs.valid(a)) {
-                    ok = tc::mbar_wait(&sh.stempty[gs % nstg], (gs / nstg) & 1);
+                    ok = tc::mbar_wait_or_abort(&sh.stempty[gs % nstg], (gs / nstg) & 1, &sh.abort_flag);
                     if (ok) {
                         issue_stage(issued);
                         ++issued;
                     }
                 }
-                if (ok && first && rr >= 2) ok = tc::mbar_wait(&sh.accempty[ab], ((rr >> 1) - 1) & 1);
-                if (ok) ok = tc::mbar_wait(&sh.full[slot], (gs / TC_NS) & 1);
+                if (ok && first && rr >= 2) ok = tc::mbar_wait_or_abort(&sh.accempty[ab], ((rr >> 1) - 1) & 1, &sh.abort_flag);
+                if (ok) ok = tc::mbar_wait_or_abort(&sh.full[slot], (gs / TC_NS) & 1, &sh.abort_flag);
                 if (!ok || *(volatile int*)&sh.abort_flag) {
                     if (!ok) { atomicOr(a.err, 2); sh.abort_flag = 1; }
                     break;
@@ -536,7 +557,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairsum_tc(TCArgs a) {
             bool ok = true;
             for (int kr = 0; kr < nruns; ++kr, ++rr) {
                 const uint32_t ab = rr & 1;
-                ok = __all_sync(0xffffffffu, tc::mbar_wait(&sh.accfull[ab], (rr >> 1) & 1));
+                ok = __all_sync(0xffffffffu, tc::mbar_wait_or_abort(&sh.accfull[ab], (rr >> 1) & 1, &sh.abort_flag));
                 if (!ok) {
                     if (lane == 0) { atomicOr(a.err, 8); sh.abort_flag = 1; }
                     break;

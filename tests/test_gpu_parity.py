@@ -174,6 +174,10 @@ def test_precond_parity_small():
 
 
 def test_precond_parity_full_size(cfg2):
+    # The library and the oracle build C = A L^(C) independently (entries agree to 4.7e-14
+    # of max |C|) and cond_1(C) ~ 2.6e5 on this 256^2 grid (scipy onenormest), so the
+    # worst case for C^{-1} t is ~1e-8; measured 4.0e-13 with the cyclic-reduction solve,
+    # and the bar is the FP64 matvec bar 1e-11.
     wl, op = cfg2
     n = wl.mesh.n_nodes
     x = random_density(n, 13)
@@ -182,7 +186,7 @@ def test_precond_parity_full_size(cfg2):
     P = Preconditioner(Grid(wl.box, wl.nx, wl.ny), wl.mesh.nodes, wl.k, wl.m_grid)
     err = _rel(y.cpu().numpy(), P.apply(x))
     print("precond full-size rel err", err)
-    assert err < 1e-9
+    assert err < 1e-11
 
 
 def test_solve_matches_oracle_small_disk():
@@ -245,6 +249,16 @@ def test_two_material_full_size_solve(cfg2):
     op.apply_precond_dev(b - Lu, r)
     op.apply_precond_dev(b, pb)
     assert (torch.linalg.norm(r) / torch.linalg.norm(pb)).item() < 2e-8
+    # the same solution through the oracle's operator on 48 sampled rows: the residual
+    # b - L u the oracle computes matches the library's to the matvec bar (1e-11 of L u)
+    # and is itself small (GMRES tolerance 1e-8 on the preconditioned residual)
+    rows = np.sort(np.random.default_rng(5).choice(n, 48, replace=False))
+    Lu_rows = OracleOp(wl.mesh, wl.k, wl.m, rows_only=True).apply_rows(u[0], rows)
+    bh = b.cpu().numpy()
+    r_oracle = bh[rows] - Lu_rows
+    r_lib = (b - Lu).cpu().numpy()[rows]
+    assert np.linalg.norm(r_oracle - r_lib) <= 1e-11 * np.linalg.norm(Lu_rows)
+    assert np.linalg.norm(r_oracle) <= 1e-6 * np.linalg.norm(bh[rows])
 
 
 def test_solve_dev_and_enoconv():
