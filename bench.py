@@ -353,6 +353,58 @@ def batching_report(args):
     print(json.dumps(line), flush=True)
 
 
+def gradient_report(args):
+    """--workload gradient: the differentiation form's configuration (two-material disk,
+    k = 40, 32,830 curved triangles = 492,450 nodes, 512^2 preconditioner): gradient of
+    the far-field misfit 1/2 sum |u_inf - t|^2 over 16 incident directions and 32
+    receivers with respect to every nodal contrast, the target t made by a forward solve
+    with a Gaussian blob added to the index; forward and adjoint solves batched over the
+    16 directions.  One gradient after a warm-up, timed with the host clock around the
+    synchronised forward + backward.  One JSON line; the finite-difference check of the
+    gradient runs in the GPU tests on smaller meshes."""
+    import torch
+    import paper_2608_17615_b300 as L
+    from lsinput.workloads import perturbed_contrast, two_material
+    from paper_2608_17615_b300.misfit import far_field_misfit
+
+    torch.cuda.set_device(0)
+    wl = two_material("large", k=40.0, nx=512, ny=512)
+    n = wl.mesh.n_nodes
+    t0 = time.perf_counter()
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, nx=512, ny=512, tol=1e-8)
+    setup_s = time.perf_counter() - t0
+    print(f"[gradient] setup {setup_s:.1f} s {op.setup_times()}", file=sys.stderr, flush=True)
+    dirs = 2 * np.pi * np.arange(16) / 16
+    ff = 2 * np.pi * np.arange(32) / 32
+    B = torch.empty((16, n), dtype=torch.complex128, device="cuda")
+    U = torch.empty_like(B)
+    uinf_t = torch.empty((16, 32), dtype=torch.complex128, device="cuda")
+    op.set_contrast(perturbed_contrast(wl))
+    op.incident_dev(dirs, B)
+    t1 = time.perf_counter()
+    it_t, st_t = op.solve_batch_dev(B, U, ff, uinf_t)
+    torch.cuda.synchronize()
+    t_target = time.perf_counter() - t1
+    op.set_contrast(wl.m)
+    m_t = torch.from_numpy(np.ascontiguousarray(np.real(wl.m), np.float64)).cuda().requires_grad_(True)
+    (g,) = torch.autograd.grad(far_field_misfit(m_t, op, dirs, ff, uinf_t, batched=True), m_t)   # warm-up
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    J = far_field_misfit(m_t, op, dirs, ff, uinf_t, batched=True)
+    (g,) = torch.autograd.grad(J, m_t)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t2
+    line = {"report": "differentiation form", "config": {"workload": "two-material disk, k=40, 492,450 nodes "
+            "(32,830 curved P4 triangles), 512^2 Cartesian preconditioner, 16 directions x 32 receivers, "
+            "target: +0.05 Gaussian blob at (-0.3, -0.2)", "nodes": n},
+            "setup_s": setup_s, "setup_parts_s": dict(zip(["correction", "grid", "block_lu", "table"],
+                                                         [round(float(t), 3) for t in op.setup_times()])),
+            "target_solve_s": t_target, "target_iterations_max": int(np.max(it_t)),
+            "value": 1.0 / dt, "unit": "gradients/s", "seconds": dt, "misfit": float(J.item()),
+            "grad_norm": float(torch.linalg.norm(g).item())}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -360,7 +412,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="default", choices=["default", "precision", "batching", "batched"])
+    ap.add_argument("--workload", default="default", choices=["default", "precision", "batching", "batched",
+                                                                 "gradient"])
     args = ap.parse_args()
     rank, world, local = _env_rank()
     if args.workload == "precision":
@@ -374,6 +427,10 @@ def main():
     if args.workload == "batched":
         if rank == 0:
             batched_pairsum_report(args)
+        return
+    if args.workload == "gradient":
+        if rank == 0:
+            gradient_report(args)
         return
     if args.impl == "reference":
         if rank == 0:

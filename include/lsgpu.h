@@ -144,21 +144,39 @@ ls_status ls_apply_precond_dev(ls_op* op, const void* x_dev, void* y_dev);
 ls_status ls_pairsum_dev(ls_op* op, const void* f_dev, void* y_dev);
 
 /*
- * Full solve for R plane waves u_inc = exp(i k d . y), d = (cos a, sin a)
- * (b_j = u_inc(y_j), Eq. nystrom_linear_system), with host outputs:
- *   dir_angles [R];  ff_angles [n_ff]
+ * Full solve for R right-hand sides with host buffers (Eq. nystrom_linear_system):
+ *   b          [R][N_Q] complex right-hand sides, or NULL for the plane waves
+ *              b_j = u_inc(y_j) = exp(i k d . y_j), d = (cos a, sin a), a = dir_angles[r]
+ *   dir_angles [R] (unused when b is given, may then be NULL);  ff_angles [n_ff]
  *   u_out    [R][N_Q] complex total field at the nodes (may be NULL)
  *   uinf_out [R][n_ff] complex far-field pattern
  *            u_inf(t) = -k^2 e^{i pi/4} / sqrt(8 pi k) sum_j w_j m_j u_j e^{-i k (cos t, sin t) . y_j}
  *            (may be NULL)
  *   hist_out [R][max_iter + 1] relative residual estimates (may be NULL)
  *   iters_out [R] iterations taken (may be NULL)
- * Returns LS_ENOCONV when any right-hand side hit max_iter (outputs are still
- * written).
+ * Every GMRES solve ends with an explicit residual check: ||P b - sum_i y_i P L v_i|| /
+ * ||P b|| from the stored operator products (independent of the orthogonality of the
+ * Krylov basis that the Givens estimate assumes); ls_op_last_residual returns the largest
+ * of the last call.  Returns LS_ENOCONV when any right-hand side hit max_iter or its
+ * explicit residual exceeds 10 tol (outputs are still written).
  */
-ls_status ls_solve(ls_op* op, int32_t R, const double* dir_angles,
-                   int32_t n_ff, const double* ff_angles,
-                   double* u_out, double* uinf_out, double* hist_out, int32_t* iters_out);
+ls_status ls_solve(ls_op* op, int32_t R, const double* dir_angles, const double* b, int32_t n_ff,
+                   const double* ff_angles, double* u_out, double* uinf_out, double* hist_out, int32_t* iters_out);
+
+/* y = P x (Eq. preconditioner_factored) and y = L^T x with host buffers of N_Q complex
+   (the copies included); LS_EINVAL without a preconditioner for ls_apply_precond. */
+ls_status ls_apply_precond(ls_op* op, const double* x, double* y);
+ls_status ls_apply_transpose(ls_op* op, const double* x, double* y);
+
+/* Adjoint solves L^T lambda_r = g_r (GMRES left-preconditioned by P^T when built) with host
+   buffers g, lambda_out [R][N_Q] complex; iters_out [R] (may be NULL).  LS_ENOCONV as ls_solve. */
+ls_status ls_solve_adjoint(ls_op* op, int32_t R, const double* g, double* lambda_out, int32_t* iters_out);
+
+/* ||P (b - L u)|| / ||P b|| (without P: ||b - L u|| / ||b||) by full applies of L and P, for
+   device buffers b_dev, u_dev of N_Q complex. */
+ls_status ls_residual_dev(ls_op* op, const void* b_dev, const void* u_dev, double* rel);
+/* Largest explicit residual (see ls_solve) of the last single-system solve call. */
+ls_status ls_op_last_residual(const ls_op* op, double* rel);
 
 /*
  * Device-buffer solve for R right-hand sides b_dev [R][N_Q] complex; writes
@@ -227,6 +245,15 @@ ls_status ls_solve_transpose_dev(ls_op* op, int32_t R, const void* g_dev, void* 
  * was built with (it stays a valid preconditioner, only its quality changes).
  */
 ls_status ls_op_set_contrast(ls_op* op, const double* m);
+
+/* Replace the nodal contrast from a device buffer: m_dev [N] complex, or [N] double
+   (the real part, imaginary part zero) when real_only; same semantics as ls_op_set_contrast. */
+ls_status ls_op_set_contrast_dev(ls_op* op, const void* m_dev, int32_t real_only);
+
+/* Far-field misfit on device buffers of `total` complex entries (e.g. R x n_ff):
+   resid_dev = uinf_dev - target_dev and *J = 1/2 sum |resid|^2 (reduced in a fixed order). */
+ls_status ls_misfit_dev(ls_op* op, int32_t total, const void* uinf_dev, const void* target_dev, void* resid_dev,
+                        double* J);
 
 /* b_dev [R][N] = exp(i k d . y_j), d = (cos a, sin a) for the R angles (host). */
 ls_status ls_incident_dev(ls_op* op, int32_t R, const double* dir_angles, void* b_dev);

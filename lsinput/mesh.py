@@ -235,6 +235,24 @@ def _finish(b, curves):
     return map_nodes(mesh)
 
 
+def square_mesh(n, half=0.75):
+    """Straight-edged mesh of the square [-half, half]^2: n x n cells, each split into
+    two triangles (2 n^2 elements, one subdomain, no curved edges)."""
+    g = np.linspace(-half, half, n + 1)
+    X, Y = np.meshgrid(g, g)
+    verts = np.stack([X.ravel(), Y.ravel()], axis=1)
+    tris = []
+    for b in range(n):
+        for a in range(n):
+            v0, v1, v2, v3 = b * (n + 1) + a, b * (n + 1) + a + 1, (b + 1) * (n + 1) + a + 1, (b + 1) * (n + 1) + a
+            tris += [[v0, v1, v2], [v0, v2, v3]]
+    nt = len(tris)
+    mesh = Mesh(vertices=verts, tris=np.array(tris, dtype=np.int32), domain=np.zeros(nt, dtype=np.int32),
+                edge_curve=np.full((nt, 3), -1, dtype=np.int32), edge_theta=np.zeros((nt, 3, 2)),
+                curves=np.zeros((0, 6)))
+    return map_nodes(mesh)
+
+
 def disk_mesh(n_rings, radius=1.0, center=(0.0, 0.0)):
     """Single-subdomain disk: 6 n_rings^2 curved triangles (domain 0)."""
     curves = [(center[0], center[1], radius, 0.0, 0.0, 0.0)]

@@ -88,6 +88,15 @@ def two_material(level="small", k=20.0, nx=256, ny=256, box=(-1.2, 1.2, -1.2, 1.
                     np.asarray(directions, float), 2 * np.pi * np.arange(n_ff) / n_ff, tol)
 
 
+def perturbed_contrast(wl, amp=0.05, center=(-0.3, -0.2), width=0.02):
+    """Contrast of the differentiation form's target medium: the two-material index
+    plus a Gaussian blob amp exp(-|x - center|^2 / width) (m = 1 - n_opt^2)."""
+    x, y = wl.mesh.nodes[:, 0], wl.mesh.nodes[:, 1]
+    n_opt = np.sqrt(1.0 - wl.m.real)
+    n_opt = n_opt + amp * np.exp(-((x - center[0]) ** 2 + (y - center[1]) ** 2) / width)
+    return (1.0 - n_opt**2).astype(np.complex128)
+
+
 def star_scatterer(s, n_nodes_target, k=None, nx=128, ny=128, n_dirs=64, n_ff=64, tol=1e-8):
     """Scatterer s of the batched workload: star r = 1 + 0.2 cos(5 theta + phi_s)
     with phi_s ~ U[0, 2 pi) from default_rng(20261202 + s), an inner interface at

@@ -5,7 +5,9 @@
 * T_C^Q (Eq. psi_def): bilinear interpolation from the four corners of the
   cell containing each quadrature node; rows sum to one.
 * T_Q^C, Approach II (Eq. T_H^C_def, Eq. D_def): D^{-1} (T_C^Q)^T with D the
-  column sums at pixelation nodes and 1 elsewhere.
+  column sums at pixelation nodes and 1 elsewhere.  Approach I (Eq. T_HC_proj_def):
+  the element-wise L^2 projection onto P1, evaluated at the interior grid nodes
+  (transfer_QC_I below).
 * V^(C) (Eq. LS_eq_on_cartesian_points): G(z_i - z_l) h_C^2 off the diagonal.
   Reading: the Duan-Rokhlin corrected weights are not available, the diagonal
   is the integral of G over the disc of area h_C^2,
@@ -80,6 +82,95 @@ def transfer_QC_II(T):
     return sps.diags(1.0 / D) @ T.T.tocsr(), D
 
 
+def _element_map_and_jacobian(mesh, t, xi, eta):
+    """Physical point of reference point (xi, eta) in element t and the Jacobian of the
+    element map (complex-step derivatives of the geometry map)."""
+    from lsinput.mesh import _element_map
+    V = mesh.vertices[mesh.tris[t]]
+    curve, t0, t1, e = None, 0.0, 0.0, -1
+    for ee in range(3):
+        if mesh.edge_curve[t, ee] >= 0:
+            curve = mesh.curves[mesh.edge_curve[t, ee]]
+            t0, t1 = mesh.edge_theta[t, ee]
+            e = ee
+    hs = 1e-30
+    x, y = _element_map(V, curve, t0, t1, e, xi, eta)
+    xa, ya = _element_map(V, curve, t0, t1, e, xi + 1j * hs, eta + 0j)
+    xb, yb = _element_map(V, curve, t0, t1, e, xi + 0j, eta + 1j * hs)
+    J = np.array([[np.imag(xa) / hs, np.imag(xb) / hs], [np.imag(ya) / hs, np.imag(yb) / hs]])
+    return np.real(x), np.real(y), J
+
+
+def locate_points(mesh, pts, tol=1e-12):
+    """Element containing each point (-1 if none): the point is in element t when the
+    inverse of t's (curved) map, found by Newton's method from the affine guess, lies in
+    the closed reference triangle; of several such elements the lowest index is taken."""
+    owner = np.full(len(pts), -1, dtype=np.int64)
+    for t in range(mesh.n_elem):
+        V = mesh.vertices[mesh.tris[t]]
+        # bounding box of the element, the curved edge's bulge included (edge points
+        # strictly between the vertices, where the blending map is defined, plus the vertices)
+        s_ = (np.arange(32) + 0.5) / 32
+        with np.errstate(invalid="ignore", divide="ignore"):
+            xs, ys = _element_map_and_jacobian(mesh, t, s_, np.zeros(32))[:2]
+            xs2, ys2 = _element_map_and_jacobian(mesh, t, np.zeros(32), s_)[:2]
+            xs3, ys3 = _element_map_and_jacobian(mesh, t, 1 - s_, s_)[:2]
+        X = np.concatenate([xs, xs2, xs3, V[:, 0]]); Y = np.concatenate([ys, ys2, ys3, V[:, 1]])
+        pad = 1e-9 * (1 + np.ptp(X) + np.ptp(Y))
+        cand = np.nonzero((owner < 0) & (pts[:, 0] >= X.min() - pad) & (pts[:, 0] <= X.max() + pad)
+                          & (pts[:, 1] >= Y.min() - pad) & (pts[:, 1] <= Y.max() + pad))[0]
+        for j in cand:
+            A = np.array([[V[1, 0] - V[0, 0], V[2, 0] - V[0, 0]], [V[1, 1] - V[0, 1], V[2, 1] - V[0, 1]]])
+            ref = np.linalg.solve(A, pts[j] - V[0])
+            with np.errstate(invalid="ignore", divide="ignore"):
+                for _ in range(40):
+                    x, y, J = _element_map_and_jacobian(mesh, t, np.array([ref[0]]), np.array([ref[1]]))
+                    r = np.array([x[0] - pts[j, 0], y[0] - pts[j, 1]])
+                    if not (np.all(np.isfinite(r)) and np.all(np.isfinite(J))):
+                        break          # at a vertex of a curved element the blending is affine
+                    step = np.linalg.solve(J[:, :, 0], r)
+                    ref = ref - step
+                    if np.max(np.abs(step)) < 1e-15:
+                        break
+            if np.all(np.isfinite(ref)) and ref[0] >= -tol and ref[1] >= -tol and ref[0] + ref[1] <= 1 + tol:
+                owner[j] = t
+    return owner
+
+
+def barycentric(V, p):
+    """Barycentric coordinates of points p [n, 2] in the straight triangle V [3, 2]."""
+    A = np.array([[V[1, 0] - V[0, 0], V[2, 0] - V[0, 0]], [V[1, 1] - V[0, 1], V[2, 1] - V[0, 1]]])
+    lam12 = np.linalg.solve(A, (p - V[0]).T).T
+    return np.stack([1 - lam12[:, 0] - lam12[:, 1], lam12[:, 0], lam12[:, 1]], axis=1)
+
+
+def transfer_QC_I(grid, mesh):
+    """Approach I (Eq. T_HC_proj_def, Eq. T_HC_I_block): row j of an interior grid node
+    z_j in element tau is E_C (M^tri)^{-1} E_Q^T W restricted to tau,
+        T[j, q] = w_q sum_{i, i'} phi_i(z_j) (M^tau)^{-1}_{i i'} phi_i'(y_q),  y_q in tau,
+    with phi_i the P1 Lagrange basis of tau's vertices (barycentric coordinates of the
+    straight triangle through them, evaluated at the physical points) and the
+    straight-triangle mass inverse of Eq. mass_closed_form,
+    (M^tau)^{-1} = (3/|tau|) [[3, -1, -1], [-1, 3, -1], [-1, -1, 3]]; exterior rows zero.
+    Returns the sparse matrix and the element of every grid node (-1 exterior)."""
+    pts = grid.points()
+    owner = locate_points(mesh, pts)
+    Minv_unit = np.array([[3.0, -1.0, -1.0], [-1.0, 3.0, -1.0], [-1.0, -1.0, 3.0]])
+    rows, cols, vals = [], [], []
+    for j in np.nonzero(owner >= 0)[0]:
+        t = owner[j]
+        V = mesh.vertices[mesh.tris[t]]
+        area = 0.5 * abs((V[1, 0] - V[0, 0]) * (V[2, 1] - V[0, 1]) - (V[2, 0] - V[0, 0]) * (V[1, 1] - V[0, 1]))
+        q = np.arange(t * 15, (t + 1) * 15)
+        phz = barycentric(V, pts[j:j + 1])[0]
+        phq = barycentric(V, mesh.nodes[q])
+        row = mesh.weights[q] * (phq @ ((3.0 / area) * Minv_unit) @ phz)
+        rows.append(np.full(15, j)); cols.append(q); vals.append(row)
+    T = sps.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                       shape=(grid.n, mesh.n_nodes))
+    return T, owner
+
+
 def cartesian_kernel(k, h, da, db):
     """V^(C) entry for grid offset (da, db) (arrays)."""
     r = h * np.sqrt(np.asarray(da, float) ** 2 + np.asarray(db, float) ** 2)
@@ -122,10 +213,12 @@ def stencil_vectors(grid, k):
 
 
 class Preconditioner:
-    def __init__(self, grid, nodes, k, m_grid):
+    def __init__(self, grid, nodes, k, m_grid, approach=2, mesh=None):
         self.grid, self.k = grid, float(k)
         self.T = transfer_CQ(grid, nodes)
         self.TQC, self.D = transfer_QC_II(self.T)
+        if approach == 1:
+            self.TQC, self.owner = transfer_QC_I(grid, mesh)
         self.v, self.sv = stencil_vectors(grid, k)
         self.m_grid = np.asarray(m_grid, np.complex128)
         self.A, self.C = self._assemble()

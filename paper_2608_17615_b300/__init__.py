@@ -25,6 +25,8 @@ EXPORTED = ["ls_params_default", "ls_mesh_create", "ls_mesh_destroy", "ls_mesh_n
             "ls_solve_transpose_dev", "ls_op_set_contrast", "ls_incident_dev", "ls_misfit_gradient_dev",
             "ls_solve_transpose_batch_dev", "ls_misfit_gradient_batch_dev",
             "ls_op_set_batch_kernel", "ls_op_set_stall_test", "ls_tc_gemm_check",
+            "ls_apply_precond", "ls_apply_transpose", "ls_solve_adjoint", "ls_residual_dev", "ls_op_last_residual",
+            "ls_op_set_contrast_dev", "ls_misfit_dev",
             "ls_op_set_pairsum", "ls_op_set_timing", "ls_op_setup_times", "ls_op_tuning", "ls_op_stats", "ls_probe_fp64", "ls_pairsum_noalloc", "ls_last_error"]
 
 
@@ -70,7 +72,14 @@ def _load():
         "ls_apply": (I32, [P, P, P]),
         "ls_apply_precond_dev": (I32, [P, P, P]),
         "ls_pairsum_dev": (I32, [P, P, P]),
-        "ls_solve": (I32, [P, I32, P, I32, P, P, P, P, P]),
+        "ls_solve": (I32, [P, I32, P, P, I32, P, P, P, P, P]),
+        "ls_apply_precond": (I32, [P, P, P]),
+        "ls_apply_transpose": (I32, [P, P, P]),
+        "ls_solve_adjoint": (I32, [P, I32, P, P, P]),
+        "ls_residual_dev": (I32, [P, P, P, P]),
+        "ls_op_last_residual": (I32, [P, P]),
+        "ls_op_set_contrast_dev": (I32, [P, P, I32]),
+        "ls_misfit_dev": (I32, [P, I32, P, P, P, P]),
         "ls_solve_dev": (I32, [P, I32, P, P, I32, P, P, P]),
         "ls_op_correction": (I32, [P, P, P, P, P]),
         "ls_correction_host": (I32, [P, D, D, P, P, P, P]),
@@ -208,22 +217,81 @@ class Operator:
         _check(_lib.ls_apply(self.handle, _ptr(xf), _ptr(y.view(np.float64))))
         return y
 
+    def apply_precond(self, x):
+        """y = P x with host buffers."""
+        x, xf = _c128(x)
+        y = np.empty_like(x)
+        _check(_lib.ls_apply_precond(self.handle, _ptr(xf), _ptr(y.view(np.float64))))
+        return y
+
+    def apply_transpose(self, x):
+        """y = L^T x with host buffers."""
+        x, xf = _c128(x)
+        y = np.empty_like(x)
+        _check(_lib.ls_apply_transpose(self.handle, _ptr(xf), _ptr(y.view(np.float64))))
+        return y
+
+    def solve_adjoint(self, g):
+        """L^T lambda = g for host g [R, N]; returns (lambda [R, N], iters [R], status)."""
+        g, gf = _c128(np.atleast_2d(g))
+        lam = np.empty_like(g)
+        iters = np.zeros(g.shape[0], np.int32)
+        st = _check(_lib.ls_solve_adjoint(self.handle, g.shape[0], _ptr(gf), _ptr(lam.view(np.float64)), _ptr(iters)),
+                    allow=(LS_ENOCONV,))
+        return lam, iters, st
+
+    def residual_dev(self, b, u):
+        """||P (b - L u)|| / ||P b|| by full applies (device tensors of N complex)."""
+        r = ctypes.c_double()
+        _check(_lib.ls_residual_dev(self.handle, _dptr(b), _dptr(u), ctypes.byref(r)))
+        return r.value
+
+    def last_residual(self):
+        """Largest explicit GMRES exit residual of the last single-system solve call."""
+        r = ctypes.c_double()
+        _check(_lib.ls_op_last_residual(self.handle, ctypes.byref(r)))
+        return r.value
+
+    def set_contrast_dev(self, m):
+        """Contrast from a device tensor: [N] complex128, or [N] float64 (real part)."""
+        import torch
+        if m.dtype == torch.float64:
+            _check(_lib.ls_op_set_contrast_dev(self.handle, _dptr(m), 1))
+        elif m.dtype == torch.complex128:
+            _check(_lib.ls_op_set_contrast_dev(self.handle, _dptr(m), 0))
+        else:
+            raise ValueError("contrast must be float64 or complex128")
+
+    def misfit_dev(self, uinf, target, resid):
+        """resid = uinf - target and J = 1/2 sum |resid|^2 on device tensors; returns J."""
+        J = ctypes.c_double()
+        _check(_lib.ls_misfit_dev(self.handle, int(uinf.numel()), _dptr(uinf), _dptr(target), _dptr(resid),
+                                  ctypes.byref(J)))
+        return J.value
+
     def apply_precond_dev(self, x, y):
         _check(_lib.ls_apply_precond_dev(self.handle, _dptr(x), _dptr(y)))
 
     def pairsum_dev(self, f, y):
         _check(_lib.ls_pairsum_dev(self.handle, _dptr(f), _dptr(y)))
 
-    def solve(self, dir_angles, ff_angles=None, want_u=True, want_hist=True):
-        """Host-buffer solve; returns (u [R, N], uinf [R, n_ff], hist [R, max_iter+1], iters [R], status)."""
-        dirs = np.ascontiguousarray(dir_angles, np.float64).ravel()
-        R = dirs.size
+    def solve(self, dir_angles=None, ff_angles=None, want_u=True, want_hist=True, b=None):
+        """Host-buffer solve for plane waves (dir_angles) or explicit right-hand sides b [R, N];
+        returns (u [R, N], uinf [R, n_ff], hist [R, max_iter+1], iters [R], status)."""
+        bf = None
+        if b is not None:
+            b, bf = _c128(np.atleast_2d(b))
+            R = b.shape[0]
+            dirs = None
+        else:
+            dirs = np.ascontiguousarray(dir_angles, np.float64).ravel()
+            R = dirs.size
         ff = np.ascontiguousarray(ff_angles if ff_angles is not None else [], np.float64).ravel()
         u = np.empty((R, self.n), np.complex128) if want_u else None
         uinf = np.empty((R, ff.size), np.complex128) if ff.size else None
         hist = np.zeros((R, self.params.max_iter + 1)) if want_hist else None
         iters = np.zeros(R, np.int32)
-        st = _check(_lib.ls_solve(self.handle, R, _ptr(dirs), ff.size, _ptr(ff) if ff.size else None,
+        st = _check(_lib.ls_solve(self.handle, R, _ptr(dirs), _ptr(bf), ff.size, _ptr(ff) if ff.size else None,
                                   _ptr(u.view(np.float64)) if u is not None else None,
                                   _ptr(uinf.view(np.float64)) if uinf is not None else None,
                                   _ptr(hist), _ptr(iters)), allow=(LS_ENOCONV,))

@@ -1026,6 +1026,47 @@ __global__ void k_combine(int n, int J, const double2* __restrict__ V, size_t ld
     u[r] = acc;
 }
 
+// res = sqrt(nrm2_b) v0 - pu: the preconditioned residual P b - P L u from the first basis
+// vector (P b / ||P b||) and the recombined operator products pu = sum_i y_i P L v_i
+__global__ void k_resid_check(int n, const double2* __restrict__ v0, const double2* __restrict__ nrm2_b,
+                              const double2* __restrict__ pu, double2* __restrict__ res) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const double beta = sqrt(nrm2_b->x);
+    res[r] = make_double2(beta * v0[r].x - pu[r].x, beta * v0[r].y - pu[r].y);
+}
+
+// y = a - b
+__global__ void k_sub_vec(int n, const double2* __restrict__ a, const double2* __restrict__ b, double2* __restrict__ y) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) y[r] = csub(a[r], b[r]);
+}
+
+// J = 1/2 sum |uinf - t|^2 over total entries (one block, fixed order); resid = uinf - t
+__global__ void k_misfit(int total, const double2* __restrict__ uinf, const double2* __restrict__ t,
+                         double2* __restrict__ resid, double* __restrict__ J) {
+    __shared__ double part[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const double2 d = csub(uinf[i], t[i]);
+        resid[i] = d;
+        acc = fma(d.x, d.x, fma(d.y, d.y, acc));
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *J = 0.5 * part[0];
+}
+
+// m = Re(m_real) + 0 i from a real device vector
+__global__ void k_real_to_complex(int n, const double* __restrict__ a, double2* __restrict__ out) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) out[r] = make_double2(a[r], 0.0);
+}
+
 // dst = src / nrm (nrm = sqrt(*nrm2)); writes nrm to *hout if given
 __global__ void k_scale(int n, const double2* __restrict__ src, const double2* __restrict__ nrm2, double2* __restrict__ dst,
                         double2* hout) {
@@ -1608,7 +1649,6 @@ struct ls_op {
     DevBuf<double2> vals, valsT;         // dV and its transpose
     CsrC host_csr;
     std::vector<double> host_nodes, host_w;
-    std::vector<std::complex<double>> host_m;
     // pair-sum decomposition and scratch
     int nchunk = 1, src_per_chunk = 0;
     DevBuf<double2> partial;
@@ -1636,6 +1676,8 @@ struct ls_op {
     DevBuf<double2> pg, pt, ptp;         // grid work vectors
     // GMRES workspace
     DevBuf<double2> Vb, H, cs, sn, g, hv, yv, tmp, tmp2, dpart, scal;
+    DevBuf<double2> Wb;                  // raw operator products P L v_j of the last solve (exit check)
+    double last_res = -1.0;              // explicit relative residual of the last single-RHS solve(s) (max)
     DevBuf<double> hist;
     int dblk = 0;
     // batched form: FP32 table and lock-step GMRES workspace for R systems
@@ -2187,6 +2229,7 @@ static ls_status gmres_one(ls_op* op, const double2* b, double2* u, double* hist
         } else {
             TRY(opL(vj, vn));
         }
+        CK(cudaMemcpyAsync(op->Wb.p + (size_t)j * ldv, vn, sizeof(double2) * n, cudaMemcpyDeviceToDevice, op->stream));
         // classical Gram-Schmidt, twice
         TRY(dots(op, j + 1, V, vn, hcol, 0));
         k_update<<<nb, tpb, sizeof(double2) * (j + 1), op->stream>>>(n, j + 1, V, ldv, hcol, vn);
@@ -2205,12 +2248,52 @@ static ls_status gmres_one(ls_op* op, const double2* b, double2* u, double* hist
     }
     k_backsolve<<<1, 1, 0, op->stream>>>(it, op->H.p, ldh, op->g.p, op->yv.p);
     k_combine<<<nb, tpb, sizeof(double2) * it, op->stream>>>(n, it, V, ldv, op->yv.p, u);
+    // explicit residual at exit: P b - sum_i y_i (P L v_i) from the stored operator products
+    // (it does not rely on the orthogonality of the basis the Givens estimate assumes)
+    k_combine<<<nb, tpb, sizeof(double2) * it, op->stream>>>(n, it, op->Wb.p, ldv, op->yv.p, op->tmp2.p);
+    k_resid_check<<<nb, tpb, 0, op->stream>>>(n, V, op->scal.p, op->tmp2.p, op->tmp.p);
     CK(cudaGetLastError());
-    op->launches += 2;
+    op->launches += 4;
+    TRY(dots(op, 1, op->tmp.p, op->tmp.p, op->scal.p + 2, 0));
+    double2 sc[3];
+    CK(cudaMemcpyAsync(sc, op->scal.p, sizeof(double2) * 3, cudaMemcpyDeviceToHost, op->stream));
     if (hist_host) CK(cudaMemcpyAsync(hist_host, op->hist.p, sizeof(double) * (it + 1), cudaMemcpyDeviceToHost, op->stream));
     CK(cudaStreamSynchronize(op->stream));
+    const double rel = sc[0].x > 0 ? std::sqrt(sc[2].x / sc[0].x) : 0.0;
+    op->last_res = std::max(op->last_res, rel);
     if (iters) *iters = it;
+    if (conv && !(rel <= 10.0 * op->prm.tol)) {
+        fail(LS_ENOCONV, "GMRES: explicit residual " + std::to_string(rel) + " exceeds 10 x tol");
+        return LS_ENOCONV;
+    }
     return conv ? LS_OK : LS_ENOCONV;
+}
+
+// ||P (b - L u)|| / ||P b|| by full applies of L and P (||b - L u|| / ||b|| without P).
+static ls_status residual_full(ls_op* op, const double2* b, const double2* u, double* rel) {
+    const int n = op->nq, nb = (n + 255) / 256;
+    DevBuf<double2> r, pr, pb;
+    CK(r.alloc(n));
+    CK(pr.alloc(n));
+    CK(pb.alloc(n));
+    TRY(apply_L(op, u, op->tmp2.p));
+    k_sub_vec<<<nb, 256, 0, op->stream>>>(n, b, op->tmp2.p, r.p);
+    CK(cudaGetLastError());
+    const bool prec = op->has_prec && op->prm.use_precond;
+    if (prec) {
+        TRY(apply_P(op, r.p, pr.p));
+        TRY(apply_P(op, b, pb.p));
+    } else {
+        CK(cudaMemcpyAsync(pr.p, r.p, sizeof(double2) * n, cudaMemcpyDeviceToDevice, op->stream));
+        CK(cudaMemcpyAsync(pb.p, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, op->stream));
+    }
+    TRY(dots(op, 1, pr.p, pr.p, op->scal.p + 2, 0));
+    TRY(dots(op, 1, pb.p, pb.p, op->scal.p + 3, 0));
+    double2 sc[2];
+    CK(cudaMemcpyAsync(sc, op->scal.p + 2, sizeof(double2) * 2, cudaMemcpyDeviceToHost, op->stream));
+    CK(cudaStreamSynchronize(op->stream));
+    *rel = sc[1].x > 0 ? std::sqrt(sc[0].x / sc[1].x) : 0.0;
+    return LS_OK;
 }
 
 // Error reporting for other translation units of the library.
@@ -2566,8 +2649,6 @@ ls_status ls_operator_create(const ls_mesh* mesh, double k, const double* m, con
     if (!err.empty()) return fail(err.find("singular") != std::string::npos ? LS_ESINGULAR : LS_ECUDA, err);
     op->host_nodes = M.nodes;
     op->host_w = M.w;
-    op->host_m.resize(n);
-    for (int q = 0; q < n; ++q) op->host_m[q] = std::complex<double>(m[2 * q], m[2 * q + 1]);
     CK(op->xy.alloc(n));
     CK(op->w.alloc(n));
     CK(op->m.alloc(n));
@@ -2622,6 +2703,7 @@ ls_status ls_operator_create(const ls_mesh* mesh, double k, const double* m, con
     // GMRES workspace
     const int maxit = prm.max_iter;
     CK(op->Vb.alloc((size_t)(maxit + 1) * n));
+    CK(op->Wb.alloc((size_t)maxit * n));
     CK(op->H.alloc((size_t)(maxit + 1) * maxit));
     CK(op->cs.alloc(maxit + 1));
     CK(op->sn.alloc(maxit + 1));
@@ -3490,6 +3572,7 @@ ls_status ls_solve_dev(ls_op* op, int32_t R, const void* b_dev, void* u_dev, int
         CK(cudaMemcpy(ang.p, ff_angles, sizeof(double) * n_ff, cudaMemcpyHostToDevice));
     }
     ls_status worst = LS_OK;
+    op->last_res = 0.0;
     for (int r = 0; r < R; ++r) {
         const double2* b = (const double2*)b_dev + (size_t)r * op->nq;
         double2* u = (double2*)u_dev + (size_t)r * op->nq;
@@ -3505,9 +3588,9 @@ ls_status ls_solve_dev(ls_op* op, int32_t R, const void* b_dev, void* u_dev, int
     return worst;
 }
 
-ls_status ls_solve(ls_op* op, int32_t R, const double* dir_angles, int32_t n_ff, const double* ff_angles,
-                   double* u_out, double* uinf_out, double* hist_out, int32_t* iters_out) {
-    if (!op || R < 1 || !dir_angles) return fail(LS_EINVAL, "null argument or R < 1");
+ls_status ls_solve(ls_op* op, int32_t R, const double* dir_angles, const double* b_in, int32_t n_ff,
+                   const double* ff_angles, double* u_out, double* uinf_out, double* hist_out, int32_t* iters_out) {
+    if (!op || R < 1 || (!dir_angles && !b_in)) return fail(LS_EINVAL, "null argument or R < 1");
     if (n_ff > 0 && !ff_angles) return fail(LS_EINVAL, "ff_angles missing");
     const int n = op->nq;
     DevBuf<double2> b, u, uinf;
@@ -3521,11 +3604,16 @@ ls_status ls_solve(ls_op* op, int32_t R, const double* dir_angles, int32_t n_ff,
     }
     std::vector<double> hist(op->prm.max_iter + 2);
     ls_status worst = LS_OK;
+    op->last_res = 0.0;
     for (int r = 0; r < R; ++r) {
-        k_incident<<<(n + 255) / 256, 256, 0, op->stream>>>(n, op->xy.p, op->k, std::cos(dir_angles[r]),
-                                                             std::sin(dir_angles[r]), b.p);
-        CK(cudaGetLastError());
-        op->launches++;
+        if (b_in) {
+            CK(cudaMemcpyAsync(b.p, b_in + 2 * (size_t)r * n, sizeof(double2) * n, cudaMemcpyHostToDevice, op->stream));
+        } else {
+            k_incident<<<(n + 255) / 256, 256, 0, op->stream>>>(n, op->xy.p, op->k, std::cos(dir_angles[r]),
+                                                                 std::sin(dir_angles[r]), b.p);
+            CK(cudaGetLastError());
+            op->launches++;
+        }
         int it = 0;
         ls_status s = gmres_one(op, b.p, u.p, hist.data(), &it);
         if (s != LS_OK && s != LS_ENOCONV) return s;
@@ -3545,6 +3633,83 @@ ls_status ls_solve(ls_op* op, int32_t R, const double* dir_angles, int32_t n_ff,
     }
     if (worst != LS_OK) fail(worst, "GMRES reached max_iter");
     return worst;
+}
+
+// Host-buffer forms of the apply calls: x, y [N] complex on the host.
+static ls_status apply_host(ls_op* op, const double* x, double* y, int which) {
+    if (!op || !x || !y) return fail(LS_EINVAL, "null argument");
+    if (which == 1 && !op->has_prec) return fail(LS_EINVAL, "operator was built without a preconditioner");
+    DevBuf<double2> xd, yd;
+    CK(xd.alloc(op->nq));
+    CK(yd.alloc(op->nq));
+    CK(cudaMemcpyAsync(xd.p, x, sizeof(double2) * op->nq, cudaMemcpyHostToDevice, op->stream));
+    if (which == 1) TRY(apply_P(op, xd.p, yd.p));
+    else if (which == 2) TRY(apply_LT(op, xd.p, yd.p));
+    else TRY(apply_PT(op, xd.p, yd.p));
+    CK(cudaMemcpyAsync(y, yd.p, sizeof(double2) * op->nq, cudaMemcpyDeviceToHost, op->stream));
+    return check_stream_sync(op);
+}
+
+ls_status ls_apply_precond(ls_op* op, const double* x, double* y) { return apply_host(op, x, y, 1); }
+ls_status ls_apply_transpose(ls_op* op, const double* x, double* y) { return apply_host(op, x, y, 2); }
+
+ls_status ls_solve_adjoint(ls_op* op, int32_t R, const double* g, double* lambda_out, int32_t* iters_out) {
+    if (!op || R < 1 || !g || !lambda_out) return fail(LS_EINVAL, "null argument or R < 1");
+    const int n = op->nq;
+    DevBuf<double2> gd, ld;
+    CK(gd.alloc(n));
+    CK(ld.alloc(n));
+    ls_status worst = LS_OK;
+    op->last_res = 0.0;
+    for (int r = 0; r < R; ++r) {
+        CK(cudaMemcpyAsync(gd.p, g + 2 * (size_t)r * n, sizeof(double2) * n, cudaMemcpyHostToDevice, op->stream));
+        int it = 0;
+        ls_status s = gmres_one(op, gd.p, ld.p, nullptr, &it, true);
+        if (s != LS_OK && s != LS_ENOCONV) return s;
+        if (s == LS_ENOCONV) worst = s;
+        if (iters_out) iters_out[r] = it;
+        CK(cudaMemcpyAsync(lambda_out + 2 * (size_t)r * n, ld.p, sizeof(double2) * n, cudaMemcpyDeviceToHost, op->stream));
+        TRY(check_stream_sync(op));
+    }
+    if (worst != LS_OK) fail(worst, "adjoint GMRES reached max_iter");
+    return worst;
+}
+
+ls_status ls_residual_dev(ls_op* op, const void* b_dev, const void* u_dev, double* rel) {
+    if (!op || !b_dev || !u_dev || !rel) return fail(LS_EINVAL, "null argument");
+    return residual_full(op, (const double2*)b_dev, (const double2*)u_dev, rel);
+}
+
+ls_status ls_op_last_residual(const ls_op* op, double* rel) {
+    if (!op || !rel) return fail(LS_EINVAL, "null argument");
+    *rel = op->last_res;
+    return LS_OK;
+}
+
+ls_status ls_op_set_contrast_dev(ls_op* op, const void* m_dev, int32_t real_only) {
+    if (!op || !m_dev) return fail(LS_EINVAL, "null argument");
+    const int n = op->nq;
+    if (real_only) {
+        k_real_to_complex<<<(n + 255) / 256, 256, 0, op->stream>>>(n, (const double*)m_dev, op->m.p);
+        CK(cudaGetLastError());
+        op->launches++;
+    } else {
+        CK(cudaMemcpyAsync(op->m.p, m_dev, sizeof(double2) * n, cudaMemcpyDeviceToDevice, op->stream));
+    }
+    return check_stream_sync(op);
+}
+
+ls_status ls_misfit_dev(ls_op* op, int32_t total, const void* uinf_dev, const void* target_dev, void* resid_dev,
+                        double* J) {
+    if (!op || total < 1 || !uinf_dev || !target_dev || !resid_dev || !J) return fail(LS_EINVAL, "null argument");
+    DevBuf<double> jd;
+    CK(jd.alloc(1));
+    k_misfit<<<1, 256, 0, op->stream>>>(total, (const double2*)uinf_dev, (const double2*)target_dev,
+                                        (double2*)resid_dev, jd.p);
+    CK(cudaGetLastError());
+    op->launches++;
+    CK(cudaMemcpyAsync(J, jd.p, sizeof(double), cudaMemcpyDeviceToHost, op->stream));
+    return check_stream_sync(op);
 }
 
 ls_status ls_op_correction(const ls_op* op, int64_t* nnz, int64_t* rowptr, int32_t* cols, double* vals) {
@@ -3634,6 +3799,7 @@ ls_status ls_apply_precond_transpose_dev(ls_op* op, const void* x_dev, void* y_d
 ls_status ls_solve_transpose_dev(ls_op* op, int32_t R, const void* g_dev, void* lambda_dev, int32_t* iters_out) {
     if (!op || R < 1 || !g_dev || !lambda_dev) return fail(LS_EINVAL, "null argument or R < 1");
     ls_status worst = LS_OK;
+    op->last_res = 0.0;
     for (int r = 0; r < R; ++r) {
         int it = 0;
         ls_status s = gmres_one(op, (const double2*)g_dev + (size_t)r * op->nq, (double2*)lambda_dev + (size_t)r * op->nq,
@@ -3652,7 +3818,6 @@ ls_status ls_op_set_contrast(ls_op* op, const double* m) {
     for (int q = 0; q < op->nq; ++q)
         if (!std::isfinite(m[2 * q]) || !std::isfinite(m[2 * q + 1])) return fail(LS_EINVAL, "non-finite contrast");
     CK(cudaMemcpyAsync(op->m.p, m, sizeof(double2) * op->nq, cudaMemcpyHostToDevice, op->stream));
-    for (int q = 0; q < op->nq; ++q) op->host_m[q] = std::complex<double>(m[2 * q], m[2 * q + 1]);
     return check_stream_sync(op);
 }
 
