@@ -376,6 +376,22 @@ ls_status ls_grid_host(const ls_mesh* mesh, double k, const double* box, int32_t
 ls_status ls_correction_dev(const ls_mesh* mesh, double k, double kappa, void* stream, int64_t* nnz,
                             int64_t* rowptr, int32_t* cols, double* vals, int64_t* host_blocks);
 
+/*
+ * Host-only build of the transfer T_Q^C from the quadrature nodes to the grid (no device
+ * work), as a CSR over the nx * ny grid rows (x fastest), two-call size query as
+ * ls_correction_host:
+ *   approach 2  Approach II, D^{-1} (T_C^Q)^T (Eq. T_H^C_def, Eq. D_def), T_C^Q bilinear
+ *   approach 1  Approach I, E_C (M^tri)^{-1} E_Q^T W (Eq. T_HC_proj_def): a grid node inside
+ *               element t (Newton inverse of t's curved map in the closed reference triangle,
+ *               lowest element index on shared edges) takes w_q sum phi_i(z) (M^t)^{-1}_{ii'}
+ *               phi_i'(y_q) over t's 15 nodes, phi the P1 basis of t's vertices and M^t the
+ *               straight-triangle mass matrix (Eq. mass_closed_form); other rows are empty.
+ * *n_interior (may be NULL): grid nodes inside the mesh (approach 1) or with a nonzero
+ * T_C^Q column (approach 2).  Errors: LS_EINVAL (null arguments, bad grid, approach).
+ */
+ls_status ls_transfer_host(const ls_mesh* mesh, const double* box, int32_t nx, int32_t ny, int32_t approach,
+                           int64_t* nnz, int64_t* rowptr, int32_t* cols, double* vals, int32_t* n_interior);
+
 /* Diagnostic: h_dev[i] = H0^(1)(z_dev[i]) (complex) by the device routine of the pair sum. */
 ls_status ls_hankel0_dev(int64_t n, const double* z_dev, void* h_dev, void* stream);
 

@@ -19,7 +19,7 @@ _STATUS = {0: "LS_OK", 1: "LS_EINVAL", 2: "LS_ENOMEM", 3: "LS_ECUDA", 4: "LS_ESI
 
 EXPORTED = ["ls_params_default", "ls_mesh_create", "ls_mesh_destroy", "ls_mesh_num_nodes", "ls_operator_create",
             "ls_op_destroy", "ls_op_num_nodes", "ls_apply_dev", "ls_apply", "ls_apply_precond_dev", "ls_pairsum_dev",
-            "ls_solve", "ls_solve_dev", "ls_op_correction", "ls_correction_host", "ls_correction_dev", "ls_grid_host",
+            "ls_solve", "ls_solve_dev", "ls_op_correction", "ls_correction_host", "ls_correction_dev", "ls_grid_host", "ls_transfer_host",
             "ls_hankel0_dev",
             "ls_pairsum_batch_dev", "ls_solve_batch_dev", "ls_solve_multi_dev", "ls_apply_transpose_dev", "ls_potential_transpose_dev", "ls_apply_precond_transpose_dev",
             "ls_solve_transpose_dev", "ls_op_set_contrast", "ls_incident_dev", "ls_misfit_gradient_dev",
@@ -84,6 +84,7 @@ def _load():
         "ls_op_correction": (I32, [P, P, P, P, P]),
         "ls_correction_host": (I32, [P, D, D, P, P, P, P]),
         "ls_correction_dev": (I32, [P, D, D, P, P, P, P, P, P]),
+        "ls_transfer_host": (I32, [P, P, I32, I32, I32, P, P, P, P, P]),
         "ls_grid_host": (I32, [P, D, P, I32, I32, P, P, P]),
         "ls_hankel0_dev": (I32, [I64, P, P, P]),
         "ls_pairsum_batch_dev": (I32, [P, I32, P, P]),
@@ -440,6 +441,21 @@ def correction_dev(mesh, k, kappa=3.0):
     _check(_lib.ls_correction_dev(mesh.handle, float(k), float(kappa), st, ctypes.byref(nnz), _ptr(rp), _ptr(ci),
                                   _ptr(va.view(np.float64)), ctypes.byref(nh)))
     return rp, ci, va, nh.value
+
+
+def transfer_host(mesh, box, nx, ny, approach=2):
+    """Host-only T_Q^C as (rowptr [nx*ny+1], cols, vals, interior count)."""
+    bx = np.ascontiguousarray(box, np.float64)
+    nnz = ctypes.c_int64()
+    ni = ctypes.c_int32()
+    _check(_lib.ls_transfer_host(mesh.handle, _ptr(bx), int(nx), int(ny), int(approach), ctypes.byref(nnz), None,
+                                 None, None, None))
+    rp = np.empty(nx * ny + 1, np.int64)
+    ci = np.empty(nnz.value, np.int32)
+    va = np.empty(nnz.value, np.float64)
+    _check(_lib.ls_transfer_host(mesh.handle, _ptr(bx), int(nx), int(ny), int(approach), ctypes.byref(nnz), _ptr(rp),
+                                 _ptr(ci), _ptr(va), ctypes.byref(ni)))
+    return rp, ci, va, ni.value
 
 
 def grid_host(mesh, k, box, nx, ny, m_grid):

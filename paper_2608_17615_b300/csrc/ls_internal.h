@@ -64,11 +64,21 @@ struct GridSetup {
     // T_C^Q: per quadrature node the 4 corner grid indices and bilinear weights
     std::vector<int32_t> tcq_idx;     // [nq][4]
     std::vector<double> tcq_w;        // [nq][4]
-    // T_Q^C (Approach II) as a gather CSR over grid rows: weight psi_i(y_q) / D_i
+    // T_Q^C as a gather CSR over grid rows: Approach II weight psi_i(y_q) / D_i, or
+    // Approach I the local L^2 projection (rows of interior grid nodes only)
     std::vector<int64_t> tqc_rowptr;  // [nx*ny + 1]
     std::vector<int32_t> tqc_cols;
     std::vector<double> tqc_vals;
     std::vector<double> D;            // [nx*ny]
+    // (T_C^Q)^T as a gather CSR over grid rows (weights psi_i(y_q)), for P^T
+    std::vector<int64_t> tcqT_rowptr;
+    std::vector<int32_t> tcqT_cols;
+    std::vector<double> tcqT_vals;
+    // (T_Q^C)^T as a gather CSR over quadrature rows, for P^T
+    std::vector<int64_t> tqcT_rowptr;  // [nq + 1]
+    std::vector<int32_t> tqcT_cols;
+    std::vector<double> tqcT_vals;
+    int n_interior = 0;               // grid nodes inside an element (Approach I rows)
     // sparsifying stencils v[c][(da+1) + 3 (db+1)] per grid-row class c = ca + 3 cb
     // (0 / 1 / 2 = first / inner / last column or row); zero at offsets outside the grid
     std::complex<double> v[9][9];
@@ -78,7 +88,9 @@ struct GridSetup {
 
 // Grid transfers, stencil and the banded C (Section 4).  "" on success.
 std::string build_grid(const HostMesh& mesh, double k, const double box[4], int nx, int ny,
-                       const std::complex<double>* m_grid, GridSetup& out);
+                       const std::complex<double>* m_grid, GridSetup& out, int approach = 2);
+// The transfer operators alone (T_C^Q, D, T_Q^C of the approach and the transposed CSRs).
+std::string build_transfers(const HostMesh& mesh, const double box[4], int nx, int ny, int approach, GridSetup& out);
 
 // Per-operator table of H0^(1)(k sqrt(t)) over t = r^2 for the pair sum.
 // Octave [2^(B-1023), 2^(B-1022)) (B = biased exponent of t) is split into

@@ -906,6 +906,24 @@ __global__ void k_tcq(int nq, const int* __restrict__ idx, const double* __restr
     z[q] = acc;
 }
 
+// z_r[q] = x_r[q] + sum_e cv[e] t_r[ci[e]] over quadrature rows (the last step of P^T:
+// x + (T_Q^C)^T r, any sparsity); grid.y = right-hand side r
+__global__ void k_tqcT(int nq, const int64_t* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ cv,
+                       const double2* __restrict__ t, size_t st, const double2* __restrict__ x, size_t sx,
+                       double2* __restrict__ z, size_t sz) {
+    const int r = blockIdx.y;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    const double2* tr = t + (size_t)r * st;
+    double2 acc = x[(size_t)r * sx + q];
+    for (int64_t e = rp[q]; e < rp[q + 1]; ++e) {
+        const double2 v = tr[ci[e]];
+        acc.x = fma(cv[e], v.x, acc.x);
+        acc.y = fma(cv[e], v.y, acc.y);
+    }
+    z[(size_t)r * sz + q] = acc;
+}
+
 // ------------------------------------------------------------------ block LU setup helpers
 // S (column-major, nx x nx) = tri(Cd_b) - Cm_b * Gprev (Gprev row-major, may be null)
 __global__ void k_build_S(int nx, int b, const double2* __restrict__ cband, const double2* __restrict__ Gprev,
@@ -1671,7 +1689,10 @@ struct ls_op {
     DevBuf<double> tqc_cv;
     DevBuf<double2> cband, Wf, Gf;
     DevBuf<double2> WT, GT;              // transposed factors for P^T
-    DevBuf<double> tqcT_cv, tcqT_w;      // T_C^Q^T gather weights (psi), T_Q^C^T corner weights (psi / D)
+    DevBuf<int64_t> tcqT_rp, tqcT_rp;    // (T_C^Q)^T over grid rows, (T_Q^C)^T over quadrature rows (for P^T)
+    DevBuf<int> tcqT_ci, tqcT_ci;
+    DevBuf<double> tcqT_cv, tqcT_cv;
+    int n_interior = 0;                  // grid nodes inside the mesh (Approach I) or pixelation nodes (II)
     DevBuf<double2> st;                  // [9 classes][9 offsets] sparsifying stencils
     DevBuf<double2> pg, pt, ptp;         // grid work vectors
     // GMRES workspace
@@ -2137,10 +2158,11 @@ static int launch_P_kernels(ls_op* op, cudaStream_t st, const double2* x, double
 // P^T x = x + T_Q^C^T (A^T C^{-T} - I) T_C^Q^T x on stream st; returns the number of launches.
 static int launch_PT_kernels(ls_op* op, cudaStream_t st, const double2* x, double2* z) {
     const int nc = op->nx * op->ny, nx = op->nx, ny = op->ny;
-    k_tqc<<<(nc + 255) / 256, 256, 0, st>>>(nc, op->tqc_rp.p, op->tqc_ci.p, op->tqcT_cv.p, x, op->cr.t());
+    k_tqc<<<(nc + 255) / 256, 256, 0, st>>>(nc, op->tcqT_rp.p, op->tcqT_ci.p, op->tcqT_cv.p, x, op->cr.t());
     const int ncr = launch_cr(op, st, true);
     k_stencilT<<<(nc + 255) / 256, 256, 0, st>>>(nx, ny, op->st.p, op->cr.x(), op->cr.t(), op->ptp.p);
-    k_tcq<<<(op->nq + 255) / 256, 256, 0, st>>>(op->nq, op->tcq_idx.p, op->tcqT_w.p, op->ptp.p, nullptr, x, z);
+    k_tqcT<<<(op->nq + 255) / 256, 256, 0, st>>>(op->nq, op->tqcT_rp.p, op->tqcT_ci.p, op->tqcT_cv.p, op->ptp.p, nc, x,
+                                                 op->nq, z, op->nq);
     return 3 + ncr;
 }
 
@@ -2532,7 +2554,7 @@ static ls_status build_preconditioner(ls_op* op, const HostMesh& M, const double
         if (!std::isfinite(mg[i].real()) || !std::isfinite(mg[i].imag())) return fail(LS_EINVAL, "non-finite m_grid");
     }
     auto tg0 = std::chrono::steady_clock::now();
-    std::string err = lsgpu::build_grid(M, op->k, op->prm.box, op->prm.nx, op->prm.ny, mg.data(), G);
+    std::string err = lsgpu::build_grid(M, op->k, op->prm.box, op->prm.nx, op->prm.ny, mg.data(), G, op->prm.approach);
     if (!err.empty()) return fail(LS_EINVAL, err);
     op->t_setup[1] = std::chrono::duration<double>(std::chrono::steady_clock::now() - tg0).count();
     auto tl0 = std::chrono::steady_clock::now();
@@ -2557,16 +2579,21 @@ static ls_status build_preconditioner(ls_op* op, const HostMesh& M, const double
     CK(cudaMemcpy(op->tqc_ci.p, G.tqc_cols.data(), sizeof(int) * G.tqc_cols.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(op->tqc_cv.p, G.tqc_vals.data(), sizeof(double) * G.tqc_vals.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(op->cband.p, G.cband.data(), sizeof(double2) * G.cband.size(), cudaMemcpyHostToDevice));
-    {
-        std::vector<double> tT(G.tqc_vals.size()), cT(G.tcq_w.size());
-        for (int i = 0; i < nc; ++i)
-            for (int64_t e = G.tqc_rowptr[i]; e < G.tqc_rowptr[i + 1]; ++e) tT[e] = G.tqc_vals[e] * G.D[i];
-        for (size_t e = 0; e < cT.size(); ++e) cT[e] = G.tcq_w[e] / G.D[G.tcq_idx[e]];
-        CK(op->tqcT_cv.alloc(tT.size()));
-        CK(op->tcqT_w.alloc(cT.size()));
-        CK(cudaMemcpy(op->tqcT_cv.p, tT.data(), sizeof(double) * tT.size(), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(op->tcqT_w.p, cT.data(), sizeof(double) * cT.size(), cudaMemcpyHostToDevice));
+    CK(op->tcqT_rp.alloc(G.tcqT_rowptr.size()));
+    CK(op->tcqT_ci.alloc(G.tcqT_cols.size()));
+    CK(op->tcqT_cv.alloc(G.tcqT_vals.size()));
+    CK(op->tqcT_rp.alloc(G.tqcT_rowptr.size()));
+    CK(op->tqcT_ci.alloc(std::max<size_t>(1, G.tqcT_cols.size())));
+    CK(op->tqcT_cv.alloc(std::max<size_t>(1, G.tqcT_vals.size())));
+    CK(cudaMemcpy(op->tcqT_rp.p, G.tcqT_rowptr.data(), sizeof(int64_t) * G.tcqT_rowptr.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(op->tcqT_ci.p, G.tcqT_cols.data(), sizeof(int) * G.tcqT_cols.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(op->tcqT_cv.p, G.tcqT_vals.data(), sizeof(double) * G.tcqT_vals.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(op->tqcT_rp.p, G.tqcT_rowptr.data(), sizeof(int64_t) * G.tqcT_rowptr.size(), cudaMemcpyHostToDevice));
+    if (!G.tqcT_cols.empty()) {
+        CK(cudaMemcpy(op->tqcT_ci.p, G.tqcT_cols.data(), sizeof(int) * G.tqcT_cols.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(op->tqcT_cv.p, G.tqcT_vals.data(), sizeof(double) * G.tqcT_vals.size(), cudaMemcpyHostToDevice));
     }
+    op->n_interior = G.n_interior;
     CK(op->pg.alloc(nc));
     CK(op->pt.alloc(nc));
     CK(op->ptp.alloc(nc));
@@ -3023,7 +3050,7 @@ static ls_status apply_P_batch(ls_op* op, int R, const double2* x, size_t sx, do
 static ls_status apply_PT_batch(ls_op* op, int R, const double2* x, size_t sx, double2* z, size_t sz) {
     const int nx = op->nx, ny = op->ny, nc = nx * ny;
     dim3 gc((nc + 255) / 256, R);
-    k_tqc_multi<<<gc, 256, 0, op->stream>>>(nc, op->tqc_rp.p, op->tqc_ci.p, op->tqcT_cv.p, x, sx, op->bpg.p);
+    k_tqc_multi<<<gc, 256, 0, op->stream>>>(nc, op->tcqT_rp.p, op->tcqT_ci.p, op->tcqT_cv.p, x, sx, op->bpg.p);
     CK(cudaMemcpyAsync(op->bptp.p, op->bpg.p, sizeof(double2) * R * nc, cudaMemcpyDeviceToDevice, op->stream));
     const int wpb = 8;
     dim3 gb((nx + wpb - 1) / wpb, R);
@@ -3034,7 +3061,7 @@ static ls_status apply_PT_batch(ls_op* op, int R, const double2* x, size_t sx, d
         k_btT_bwd_multi<<<gb, 32 * wpb, shm, op->stream>>>(nx, ny, b, op->WT.p, op->cband.p, op->bptp.p, op->bpt.p);
     k_stencilT_multi<<<gc, 256, 0, op->stream>>>(nx, ny, op->st.p, op->bpt.p, op->bpg.p, op->bptp.p);
     dim3 gq((op->nq + 255) / 256, R);
-    k_tcq_multi<<<gq, 256, 0, op->stream>>>(op->nq, nc, op->tcq_idx.p, op->tcqT_w.p, op->bptp.p, nullptr, x, sx, z, sz);
+    k_tqcT<<<gq, 256, 0, op->stream>>>(op->nq, op->tqcT_rp.p, op->tqcT_ci.p, op->tqcT_cv.p, op->bptp.p, nc, x, sx, z, sz);
     CK(cudaGetLastError());
     op->launches += 3 + (ny - 1) + ny;
     return LS_OK;
@@ -3747,6 +3774,21 @@ ls_status ls_correction_dev(const ls_mesh* mesh, double k, double kappa, void* s
     if (cols) std::copy(A.cols.begin(), A.cols.end(), cols);
     if (vals)
         for (size_t e = 0; e < A.vals.size(); ++e) { vals[2 * e] = A.vals[e].real(); vals[2 * e + 1] = A.vals[e].imag(); }
+    return LS_OK;
+}
+
+ls_status ls_transfer_host(const ls_mesh* mesh, const double* box, int32_t nx, int32_t ny, int32_t approach,
+                           int64_t* nnz, int64_t* rowptr, int32_t* cols, double* vals, int32_t* n_interior) {
+    if (!mesh || !box || !nnz) return fail(LS_EINVAL, "null argument");
+    if (approach != 1 && approach != 2) return fail(LS_EINVAL, "approach must be 1 or 2");
+    GridSetup G;
+    std::string err = lsgpu::build_transfers(mesh->h, box, nx, ny, approach, G);
+    if (!err.empty()) return fail(LS_EINVAL, err);
+    *nnz = (int64_t)G.tqc_cols.size();
+    if (rowptr) std::copy(G.tqc_rowptr.begin(), G.tqc_rowptr.end(), rowptr);
+    if (cols) std::copy(G.tqc_cols.begin(), G.tqc_cols.end(), cols);
+    if (vals) std::copy(G.tqc_vals.begin(), G.tqc_vals.end(), vals);
+    if (n_interior) *n_interior = G.n_interior;
     return LS_OK;
 }
 

@@ -861,8 +861,126 @@ static void smallest_eigvec(std::vector<cld>& A, int n, std::vector<cld>& vec) {
     for (int r = 0; r < n; ++r) vec[r] = Vm[r * n + best];
 }
 
-std::string build_grid(const HostMesh& M, double k, const double box[4], int nx, int ny,
-                       const std::complex<double>* m_grid, GridSetup& G) {
+// ---------------------------------------------------------------- Approach I transfer
+// Element map of the mesh: the affine map of the vertex triangle plus, for an element
+// with a curved edge e (vertices i = e, j = e + 1), the edge bubble 4 l_i l_j d(t),
+// t = (1 + l_j - l_i) / 2, d(t) = (gamma(theta(t)) - chord(t)) / (4 t (1 - t)), which puts
+// that edge on its polar curve and keeps the other two straight.
+static void element_point(const HostMesh& M, int t, double xi, double eta, double& x, double& y) {
+    const int* v = &M.tri[3 * t];
+    const double l[3] = {1.0 - xi - eta, xi, eta};
+    x = 0; y = 0;
+    for (int a = 0; a < 3; ++a) { x += l[a] * M.vxy[2 * v[a]]; y += l[a] * M.vxy[2 * v[a] + 1]; }
+    for (int e = 0; e < 3; ++e) {
+        const int c = M.ecurve[3 * t + e];
+        if (c < 0) continue;
+        const int i = e, j = (e + 1) % 3;
+        const double li = l[i], lj = l[j];
+        if (li * lj == 0.0) return;
+        const double tt = 0.5 * (1.0 + lj - li);
+        const double* C = &M.curves[6 * c];
+        const double th = M.etheta[6 * t + 2 * e] + tt * (M.etheta[6 * t + 2 * e + 1] - M.etheta[6 * t + 2 * e]);
+        const double r = C[2] * (1.0 + C[3] * std::cos(C[4] * th + C[5]));
+        const double gx = C[0] + r * std::cos(th), gy = C[1] + r * std::sin(th);
+        const double den = 4.0 * tt * (1.0 - tt);
+        const double dx = (gx - ((1 - tt) * M.vxy[2 * v[i]] + tt * M.vxy[2 * v[j]])) / den;
+        const double dy = (gy - ((1 - tt) * M.vxy[2 * v[i] + 1] + tt * M.vxy[2 * v[j] + 1])) / den;
+        x += 4.0 * li * lj * dx;
+        y += 4.0 * li * lj * dy;
+        return;
+    }
+}
+
+// Element owning each grid node (-1: none).  A node is in element t when Newton's method
+// on t's map (central-difference Jacobian, started from the affine inverse) lands in the
+// closed reference triangle (tolerance 1e-12); the lowest such element index wins.
+static void locate_grid_nodes(const HostMesh& M, const GridSetup& G, std::vector<int>& owner) {
+    owner.assign((size_t)G.nx * G.ny, -1);
+    for (int t = 0; t < M.nt; ++t) {
+        const int* v = &M.tri[3 * t];
+        double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+        auto grow = [&](double x, double y) {
+            xmin = std::min(xmin, x); xmax = std::max(xmax, x); ymin = std::min(ymin, y); ymax = std::max(ymax, y);
+        };
+        for (int a = 0; a < 3; ++a) grow(M.vxy[2 * v[a]], M.vxy[2 * v[a] + 1]);
+        for (int i = 0; i < 32; ++i) {
+            const double s_ = (i + 0.5) / 32;
+            double x, y;
+            element_point(M, t, s_, 0.0, x, y); grow(x, y);
+            element_point(M, t, 0.0, s_, x, y); grow(x, y);
+            element_point(M, t, 1.0 - s_, s_, x, y); grow(x, y);
+        }
+        const double pad = 1e-9 * (1.0 + (xmax - xmin) + (ymax - ymin));
+        const int a0 = std::max(0, (int)std::ceil((xmin - pad - G.x0) / G.h));
+        const int a1 = std::min(G.nx - 1, (int)std::floor((xmax + pad - G.x0) / G.h));
+        const int b0 = std::max(0, (int)std::ceil((ymin - pad - G.y0) / G.h));
+        const int b1 = std::min(G.ny - 1, (int)std::floor((ymax + pad - G.y0) / G.h));
+        const double x0 = M.vxy[2 * v[0]], y0 = M.vxy[2 * v[0] + 1];
+        const double A00 = M.vxy[2 * v[1]] - x0, A01 = M.vxy[2 * v[2]] - x0;
+        const double A10 = M.vxy[2 * v[1] + 1] - y0, A11 = M.vxy[2 * v[2] + 1] - y0;
+        const double det = A00 * A11 - A01 * A10;
+        for (int b = b0; b <= b1; ++b)
+            for (int a = a0; a <= a1; ++a) {
+                const size_t j = a + (size_t)G.nx * b;
+                if (owner[j] >= 0) continue;
+                const double zx = G.x0 + a * G.h, zy = G.y0 + b * G.h;
+                double xi = (A11 * (zx - x0) - A01 * (zy - y0)) / det;
+                double eta = (-A10 * (zx - x0) + A00 * (zy - y0)) / det;
+                bool ok = true;
+                for (int it = 0; it < 40; ++it) {
+                    double fx, fy, px, py, mx, my, qx, qy, nx_, ny_;
+                    element_point(M, t, xi, eta, fx, fy);
+                    const double hd = 1e-7;
+                    element_point(M, t, xi + hd, eta, px, py);
+                    element_point(M, t, xi - hd, eta, mx, my);
+                    element_point(M, t, xi, eta + hd, qx, qy);
+                    element_point(M, t, xi, eta - hd, nx_, ny_);
+                    const double j00 = (px - mx) / (2 * hd), j10 = (py - my) / (2 * hd);
+                    const double j01 = (qx - nx_) / (2 * hd), j11 = (qy - ny_) / (2 * hd);
+                    const double dj = j00 * j11 - j01 * j10;
+                    const double rx = fx - zx, ry = fy - zy;
+                    if (!(std::isfinite(dj) && std::isfinite(rx) && std::isfinite(ry)) || dj == 0.0) { ok = false; break; }
+                    const double sx = (j11 * rx - j01 * ry) / dj, sy = (-j10 * rx + j00 * ry) / dj;
+                    xi -= sx;
+                    eta -= sy;
+                    if (std::max(std::fabs(sx), std::fabs(sy)) < 1e-15) break;
+                }
+                if (ok && xi >= -1e-12 && eta >= -1e-12 && xi + eta <= 1 + 1e-12) owner[j] = t;
+            }
+    }
+}
+
+// Barycentric coordinates of (x, y) in the straight triangle of element t's vertices.
+static void bary(const HostMesh& M, int t, double x, double y, double* lam) {
+    const int* v = &M.tri[3 * t];
+    const double x0 = M.vxy[2 * v[0]], y0 = M.vxy[2 * v[0] + 1];
+    const double A00 = M.vxy[2 * v[1]] - x0, A01 = M.vxy[2 * v[2]] - x0;
+    const double A10 = M.vxy[2 * v[1] + 1] - y0, A11 = M.vxy[2 * v[2] + 1] - y0;
+    const double det = A00 * A11 - A01 * A10;
+    lam[1] = (A11 * (x - x0) - A01 * (y - y0)) / det;
+    lam[2] = (-A10 * (x - x0) + A00 * (y - y0)) / det;
+    lam[0] = 1.0 - lam[1] - lam[2];
+}
+
+// Transpose of a gather CSR (rows x ncols) into a gather CSR over the columns.
+static void csr_transpose(int nrows, int ncols, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                          const std::vector<double>& cv, std::vector<int64_t>& rpT, std::vector<int32_t>& ciT,
+                          std::vector<double>& cvT) {
+    rpT.assign(ncols + 1, 0);
+    for (int32_t c : ci) rpT[c + 1]++;
+    for (int c = 0; c < ncols; ++c) rpT[c + 1] += rpT[c];
+    ciT.resize(ci.size());
+    cvT.resize(cv.size());
+    std::vector<int64_t> fill(rpT.begin(), rpT.end() - 1);
+    for (int r = 0; r < nrows; ++r)
+        for (int64_t e = rp[r]; e < rp[r + 1]; ++e) {
+            const int64_t pos = fill[ci[e]]++;
+            ciT[pos] = r;
+            cvT[pos] = cv[e];
+        }
+}
+
+std::string build_transfers(const HostMesh& M, const double box[4], int nx, int ny, int approach, GridSetup& G) {
     if (nx < 4 || ny < 4) return "grid needs at least 4 x 4 nodes";
     double hx = (box[1] - box[0]) / (nx - 1), hy = (box[3] - box[2]) / (ny - 1);
     if (!(hx > 0) || std::fabs(hx - hy) > 1e-12 * hx) return "grid step must be equal in x and y";
@@ -891,20 +1009,73 @@ std::string build_grid(const HostMesh& M, double k, const double box[4], int nx,
     }
     G.D.resize(nc);
     for (int i = 0; i < nc; ++i) G.D[i] = colsum[i] > 0 ? colsum[i] : 1.0;
-    // gather CSR of T_Q^C = D^{-1} (T_C^Q)^T
-    G.tqc_rowptr.assign(nc + 1, 0);
-    for (size_t e = 0; e < 4 * (size_t)nq; ++e) G.tqc_rowptr[G.tcq_idx[e] + 1]++;
-    for (int i = 0; i < nc; ++i) G.tqc_rowptr[i + 1] += G.tqc_rowptr[i];
-    G.tqc_cols.resize(4 * (size_t)nq);
-    G.tqc_vals.resize(4 * (size_t)nq);
-    std::vector<int64_t> fill(G.tqc_rowptr.begin(), G.tqc_rowptr.end() - 1);
+    // gather CSR of (T_C^Q)^T over grid rows; Approach II: T_Q^C = D^{-1} (T_C^Q)^T
+    G.tcqT_rowptr.assign(nc + 1, 0);
+    for (size_t e = 0; e < 4 * (size_t)nq; ++e) G.tcqT_rowptr[G.tcq_idx[e] + 1]++;
+    for (int i = 0; i < nc; ++i) G.tcqT_rowptr[i + 1] += G.tcqT_rowptr[i];
+    G.tcqT_cols.resize(4 * (size_t)nq);
+    G.tcqT_vals.resize(4 * (size_t)nq);
+    std::vector<int64_t> fill(G.tcqT_rowptr.begin(), G.tcqT_rowptr.end() - 1);
     for (int q = 0; q < nq; ++q)
         for (int c = 0; c < 4; ++c) {
             int i = G.tcq_idx[4 * (size_t)q + c];
             int64_t pos = fill[i]++;
-            G.tqc_cols[pos] = q;
-            G.tqc_vals[pos] = G.tcq_w[4 * (size_t)q + c] / G.D[i];
+            G.tcqT_cols[pos] = q;
+            G.tcqT_vals[pos] = G.tcq_w[4 * (size_t)q + c];
         }
+    if (approach == 2) {
+        G.tqc_rowptr = G.tcqT_rowptr;
+        G.tqc_cols = G.tcqT_cols;
+        G.tqc_vals.resize(G.tcqT_vals.size());
+        for (int i = 0; i < nc; ++i)
+            for (int64_t e = G.tqc_rowptr[i]; e < G.tqc_rowptr[i + 1]; ++e) G.tqc_vals[e] = G.tcqT_vals[e] / G.D[i];
+        G.n_interior = 0;
+        for (int i = 0; i < nc; ++i) G.n_interior += colsum[i] > 0;
+    } else {
+        // Approach I (Eq. T_HC_proj_def): z_j in element t gets
+        // T[j, q] = w_q sum_{i, i'} phi_i(z_j) (3 / |t|) [3 delta_ii' - (1 - delta_ii')] phi_i'(y_q)
+        std::vector<int> owner;
+        locate_grid_nodes(M, G, owner);
+        G.tqc_rowptr.assign(nc + 1, 0);
+        G.tqc_cols.clear();
+        G.tqc_vals.clear();
+        G.n_interior = 0;
+        for (int j = 0; j < nc; ++j) {
+            const int t = owner[j];
+            if (t >= 0) {
+                ++G.n_interior;
+                const int* v = &M.tri[3 * t];
+                const double area = 0.5 * std::fabs((M.vxy[2 * v[1]] - M.vxy[2 * v[0]]) * (M.vxy[2 * v[2] + 1] - M.vxy[2 * v[0] + 1]) -
+                                                    (M.vxy[2 * v[2]] - M.vxy[2 * v[0]]) * (M.vxy[2 * v[1] + 1] - M.vxy[2 * v[0] + 1]));
+                double pz[3];
+                bary(M, t, G.x0 + (j % nx) * G.h, G.y0 + (j / nx) * G.h, pz);
+                // c_i' = sum_i phi_i(z) Minv_{i i'}
+                double cz[3];
+                for (int i2 = 0; i2 < 3; ++i2) {
+                    double acc = 0;
+                    for (int i = 0; i < 3; ++i) acc += pz[i] * (i == i2 ? 3.0 : -1.0);
+                    cz[i2] = acc * 3.0 / area;
+                }
+                for (int q = 0; q < NQ_ELEM; ++q) {
+                    const int n = t * NQ_ELEM + q;
+                    double pq[3];
+                    bary(M, t, M.nodes[2 * n], M.nodes[2 * n + 1], pq);
+                    G.tqc_cols.push_back(n);
+                    G.tqc_vals.push_back(M.w[n] * (cz[0] * pq[0] + cz[1] * pq[1] + cz[2] * pq[2]));
+                }
+            }
+            G.tqc_rowptr[j + 1] = (int64_t)G.tqc_cols.size();
+        }
+    }
+    csr_transpose(nc, nq, G.tqc_rowptr, G.tqc_cols, G.tqc_vals, G.tqcT_rowptr, G.tqcT_cols, G.tqcT_vals);
+    return "";
+}
+
+std::string build_grid(const HostMesh& M, double k, const double box[4], int nx, int ny,
+                       const std::complex<double>* m_grid, GridSetup& G, int approach) {
+    std::string err = build_transfers(M, box, nx, ny, approach, G);
+    if (!err.empty()) return err;
+    const int nc = nx * ny;
     // stencils: per row class c = ca + 3 cb, the truncated neighbourhood N(j) of a
     // representative node (grid centre, middle of an edge, corner), Gram matrix of
     // B = V^(C)(N(j), N(j)^c) against every other grid node, smallest eigenvector

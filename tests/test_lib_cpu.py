@@ -131,3 +131,22 @@ def test_grid_host_matches_oracle(k, nx):
                     continue
                 worst = max(worst, abs(cb[b, db + 1, da + 1, a] - ph * C[j, la + nx * lb]))
     assert worst < 1e-8 * scale, worst / scale
+
+
+@pytest.mark.parametrize("approach", [1, 2])
+def test_transfer_host_matches_oracle(approach):
+    """The library's host T_Q^C (both approaches) against the oracle's, on the curved
+    two-material mesh (curved elements on both sides of the interface)."""
+    from oracle.precond import Grid, transfer_CQ, transfer_QC_I, transfer_QC_II
+    wl = two_material("tiny", k=8.0)
+    box, nx = (-1.2, 1.2, -1.2, 1.2), 41
+    rp, ci, va, nint = L.transfer_host(L.Mesh(wl.mesh), box, nx, nx, approach)
+    A = sps.csr_matrix((va, ci, rp), shape=(nx * nx, wl.mesh.n_nodes))
+    g = Grid(box, nx, nx)
+    if approach == 1:
+        B, owner = transfer_QC_I(g, wl.mesh)
+        assert nint == int((owner >= 0).sum())
+    else:
+        B, _ = transfer_QC_II(transfer_CQ(g, wl.mesh.nodes))
+    assert (A != 0).nnz == (B != 0).nnz
+    assert abs(A - B).max() < 1e-13 * abs(B).max()
