@@ -127,6 +127,22 @@ int32_t ls_mesh_num_nodes(const ls_mesh* mesh);
  */
 ls_status ls_operator_create(const ls_mesh* mesh, double k, const double* m, const double* m_grid,
                              const ls_params* params, void* stream, ls_op** out);
+/*
+ * Purely Cartesian operator (Section 6, comparison with a purely Cartesian discretization;
+ * Eq. LS_eq_on_cartesian_points): the unknowns are the nx x ny grid nodes of params->box
+ * (x fastest), L^(C) = I + k^2 V^(C) M^(C) with V^(C)_il = G(z_i - z_l) h^2 off the diagonal
+ * and the integral of G over the disc of area h^2 on it, applied by zero-padded FFT
+ * convolution (cuFFT, 2 nx x 2 ny); preconditioner (params->use_precond) the sparsifying
+ * S^(C) = C^{-1} A of the same grid (Eq. sparsifying_min, Eq. LC_def).  The returned ls_op
+ * works with ls_apply[_dev], ls_apply_precond[_dev], ls_apply_transpose[_dev],
+ * ls_solve[_dev] (plane waves and far field use the grid nodes with weights h^2),
+ * ls_solve_adjoint and ls_residual_dev; the quadrature-node calls (pair sums, batched
+ * forms, correction) return LS_EINVAL.
+ *   m_grid [nx * ny] complex contrast at the grid nodes
+ * Errors: LS_EINVAL (k <= 0, bad grid, non-finite contrast), LS_ENOMEM, LS_ECUDA, LS_ESINGULAR.
+ */
+ls_status ls_cartesian_create(double k, const double* m_grid, const ls_params* params, void* stream, ls_op** out);
+
 void ls_op_destroy(ls_op* op);
 int32_t ls_op_num_nodes(const ls_op* op);
 

@@ -18,6 +18,7 @@ _STATUS = {0: "LS_OK", 1: "LS_EINVAL", 2: "LS_ENOMEM", 3: "LS_ECUDA", 4: "LS_ESI
            6: "LS_ETIMEOUT"}
 
 EXPORTED = ["ls_params_default", "ls_mesh_create", "ls_mesh_destroy", "ls_mesh_num_nodes", "ls_operator_create",
+            "ls_cartesian_create",
             "ls_op_destroy", "ls_op_num_nodes", "ls_apply_dev", "ls_apply", "ls_apply_precond_dev", "ls_pairsum_dev",
             "ls_solve", "ls_solve_dev", "ls_op_correction", "ls_correction_host", "ls_correction_dev", "ls_grid_host", "ls_transfer_host",
             "ls_hankel0_dev",
@@ -66,6 +67,7 @@ def _load():
         "ls_mesh_destroy": (None, [P]),
         "ls_mesh_num_nodes": (I32, [P]),
         "ls_operator_create": (I32, [P, D, P, P, P, P, P]),
+        "ls_cartesian_create": (I32, [D, P, P, P, P]),
         "ls_op_destroy": (None, [P]),
         "ls_op_num_nodes": (I32, [P]),
         "ls_apply_dev": (I32, [P, P, P]),
@@ -415,6 +417,31 @@ class Operator:
         va = np.empty(nnz.value, np.complex128)
         _check(_lib.ls_op_correction(self.handle, ctypes.byref(nnz), _ptr(rp), _ptr(ci), _ptr(va.view(np.float64))))
         return rp, ci, va
+
+
+class CartesianOperator(Operator):
+    """Purely Cartesian L^(C) on the grid of box / nx / ny (ls_cartesian_create): unknowns
+    at the grid nodes, preconditioner S^(C) when use_precond."""
+
+    def __init__(self, k, m_grid, params=None, stream=None, **overrides):
+        p = params if params is not None else params_default()
+        for key, val in overrides.items():
+            if key == "box":
+                for i in range(4):
+                    p.box[i] = val[i]
+            else:
+                if key not in dict(Params._fields_):
+                    raise TypeError(f"unknown operator parameter {key!r}")
+                setattr(p, key, val)
+        self.params = p
+        _, mg = _c128(m_grid)
+        h = ctypes.c_void_p()
+        if stream is None:
+            stream = _current_stream()
+        _check(_lib.ls_cartesian_create(float(k), _ptr(mg), ctypes.byref(p), ctypes.c_void_p(stream), ctypes.byref(h)))
+        self.handle = h
+        self.n = _lib.ls_op_num_nodes(h)
+        self.k = float(k)
 
 
 def correction_host(mesh, k, kappa=3.0):

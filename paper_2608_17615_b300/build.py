@@ -36,7 +36,7 @@ def build(verbose_ptxas=False):
         else:
             continue
         objs.append(obj)
-    _run([NVCC, "-shared", *ARCH, "-o", LIB, *objs, "-lcusolver", "-lcublas", "-Xcompiler", "-fopenmp"])
+    _run([NVCC, "-shared", *ARCH, "-o", LIB, *objs, "-lcusolver", "-lcublas", "-lcufft", "-Xcompiler", "-fopenmp"])
     return LIB
 
 

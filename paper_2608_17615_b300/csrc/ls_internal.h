@@ -89,6 +89,11 @@ struct GridSetup {
 // Grid transfers, stencil and the banded C (Section 4).  "" on success.
 std::string build_grid(const HostMesh& mesh, double k, const double box[4], int nx, int ny,
                        const std::complex<double>* m_grid, GridSetup& out, int approach = 2);
+// The sparsifying stencils and the banded C on a grid with the given contrast (no mesh).
+std::string build_stencil_C(double k, const double box[4], int nx, int ny, const std::complex<double>* m_grid,
+                            GridSetup& out);
+// V^(C) entries for offsets (a, b), 0 <= a < nx, 0 <= b < ny: K[b nx + a] (long double Hankel).
+void cartesian_kernel_table(double k, double h, int nx, int ny, std::vector<std::complex<double>>& K);
 // The transfer operators alone (T_C^Q, D, T_Q^C of the approach and the transposed CSRs).
 std::string build_transfers(const HostMesh& mesh, const double box[4], int nx, int ny, int approach, GridSetup& out);
 

@@ -25,6 +25,7 @@
 // with P, zQ fitted polynomials in 36/z^2 (constants in hankel_fit.h).
 #include <cuda_runtime.h>
 #include <cublas_v2.h>
+#include <cufft.h>
 #include <cusolverDn.h>
 
 #include <algorithm>
@@ -1732,6 +1733,12 @@ struct ls_op {
     cudaGraphExec_t gPT = nullptr;         // graph of the P^T apply
     int nlaunch_P = 0, nlaunch_PT = 0;     // kernels in each graph
     CRPlan cr;                           // cyclic reduction of C for the single-RHS P and P^T
+    // purely Cartesian operator (ls_cartesian_create): the unknowns are the grid nodes,
+    // L^(C) = I + k^2 V^(C) M^(C) with V^(C) applied by FFT convolution, P = S^(C) = C^{-1} A
+    bool cartesian = false;
+    int cNX = 0, cNY = 0;                // zero-padded FFT grid (2 nx x 2 ny)
+    cufftHandle fft = 0;
+    DevBuf<double2> khat, fpad, czero;   // kernel spectrum / (NX NY), padded work array, zeros
     // instrumentation: kernel launches on this operator, CUDA-event timing of the pair sum
     int64_t launches = 0, pairsum_launches = 0;
     bool timing = false;
@@ -1742,6 +1749,7 @@ struct ls_op {
         if (gPT) cudaGraphExecDestroy(gPT);
         if (cap) cudaStreamDestroy(cap);
         if (tc_herr) cudaFreeHost(tc_herr);
+        if (fft) cufftDestroy(fft);
     }
 };
 
@@ -1786,6 +1794,7 @@ static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m, c
 static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m) { return launch_pairsum(op, f, m, op->w.p); }
 
 static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m, const double* w) {
+    if (op->cartesian) return fail(LS_EINVAL, "a purely Cartesian operator has no quadrature-node pair sum");
     dim3 grid((op->nq + PS_TPB - 1) / PS_TPB, op->nchunk);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (op->timing && op->ev.size() < 65536) {
@@ -1814,7 +1823,67 @@ static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m, c
     return LS_OK;
 }
 
+// ------------------------------------------------------------------ purely Cartesian operator
+// padded input: f[b][a] = (m x)_(a, b) (or x when m is null) inside the nx x ny block, 0 elsewhere
+__global__ void k_cart_pad(int nx, int ny, int NX, int NY, const double2* __restrict__ m, const double2* __restrict__ x,
+                           double2* __restrict__ f) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (a >= NX || b >= NY) return;
+    double2 v = make_double2(0.0, 0.0);
+    if (a < nx && b < ny) {
+        const int j = a + nx * b;
+        v = m ? cmul(m[j], x[j]) : x[j];
+    }
+    f[(size_t)b * NX + a] = v;
+}
+
+__global__ void k_cart_mul(int64_t n, const double2* __restrict__ khat, double2* __restrict__ f) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) f[i] = cmul(khat[i], f[i]);
+}
+
+// mode 0: y = x + k2 V(m x);  mode 1: y = x + k2 m V(x);  mode 2: y = V(x)
+__global__ void k_cart_epi(int nx, int ny, int NX, const double2* __restrict__ x, const double2* __restrict__ m,
+                           const double2* __restrict__ f, double k2, double2* __restrict__ y, int mode) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (a >= nx || b >= ny) return;
+    const int j = a + nx * b;
+    const double2 v = f[(size_t)b * NX + a];
+    if (mode == 2) { y[j] = v; return; }
+    const double2 w = mode == 1 ? cmul(m[j], v) : v;
+    y[j] = make_double2(x[j].x + k2 * w.x, x[j].y + k2 * w.y);
+}
+
+// padded kernel K(da, db) from the table of offsets (|da|, |db|) (V^(C) is even in both)
+__global__ void k_cart_kernel(int nx, int ny, int NX, int NY, const double2* __restrict__ tab, double2* __restrict__ K) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (a >= NX || b >= NY) return;
+    const int da = a < nx ? a : NX - a, db = b < ny ? b : NY - b;   // offsets 0..nx-1 and -(nx-1)..-1
+    double2 v = make_double2(0.0, 0.0);
+    if (da < nx && db < ny && a != nx && b != ny) v = tab[(size_t)db * nx + da];
+    K[(size_t)b * NX + a] = v;
+}
+
+static ls_status cart_apply(ls_op* op, const double2* x, double2* y, int mode) {
+    const int nx = op->nx, ny = op->ny, NX = op->cNX, NY = op->cNY;
+    dim3 gp((NX + 127) / 128, NY), ge((nx + 127) / 128, ny);
+    k_cart_pad<<<gp, 128, 0, op->stream>>>(nx, ny, NX, NY, mode == 0 ? op->m.p : nullptr, x, op->fpad.p);
+    if (cufftExecZ2Z(op->fft, (cufftDoubleComplex*)op->fpad.p, (cufftDoubleComplex*)op->fpad.p, CUFFT_FORWARD) !=
+        CUFFT_SUCCESS)
+        return fail(LS_ECUDA, "cufftExecZ2Z (forward) failed");
+    const int64_t tot = (int64_t)NX * NY;
+    k_cart_mul<<<(unsigned)((tot + 255) / 256), 256, 0, op->stream>>>(tot, op->khat.p, op->fpad.p);
+    if (cufftExecZ2Z(op->fft, (cufftDoubleComplex*)op->fpad.p, (cufftDoubleComplex*)op->fpad.p, CUFFT_INVERSE) !=
+        CUFFT_SUCCESS)
+        return fail(LS_ECUDA, "cufftExecZ2Z (inverse) failed");
+    k_cart_epi<<<ge, 128, 0, op->stream>>>(nx, ny, NX, x, op->m.p, op->fpad.p, op->k * op->k, y, mode);
+    CK(cudaGetLastError());
+    op->launches += 3;
+    return LS_OK;
+}
+
 static ls_status apply_L(ls_op* op, const double2* x, double2* y) {
+    if (op->cartesian) return cart_apply(op, x, y, 0);
     ls_status s = launch_pairsum(op, x, op->m.p);
     if (s != LS_OK) return s;
     int threads = 256;
@@ -2155,6 +2224,21 @@ static int launch_P_kernels(ls_op* op, cudaStream_t st, const double2* x, double
     return 3 + ncr;
 }
 
+// Cartesian operator: S^(C) x = C^{-1} A x; S^(C)^T x = A^T C^{-T} x.
+static int launch_S_kernels(ls_op* op, cudaStream_t st, const double2* x, double2* z, bool transpose) {
+    const int nc = op->nx * op->ny, nx = op->nx, ny = op->ny;
+    if (!transpose) {
+        k_stencil<<<(nc + 255) / 256, 256, 0, st>>>(nx, ny, op->st.p, x, op->cr.t());
+        const int ncr = launch_cr(op, st, false);
+        k_sub_vec<<<(nc + 255) / 256, 256, 0, st>>>(nc, op->cr.x(), op->czero.p, z);
+        return 2 + ncr;
+    }
+    k_sub_vec<<<(nc + 255) / 256, 256, 0, st>>>(nc, x, op->czero.p, op->cr.t());
+    const int ncr = launch_cr(op, st, true);
+    k_stencilT<<<(nc + 255) / 256, 256, 0, st>>>(nx, ny, op->st.p, op->cr.x(), op->czero.p, z);
+    return 2 + ncr;
+}
+
 // P^T x = x + T_Q^C^T (A^T C^{-T} - I) T_C^Q^T x on stream st; returns the number of launches.
 static int launch_PT_kernels(ls_op* op, cudaStream_t st, const double2* x, double2* z) {
     const int nc = op->nx * op->ny, nx = op->nx, ny = op->ny;
@@ -2178,8 +2262,9 @@ static ls_status apply_P_graph(ls_op* op, const double2* x, double2* z, bool tra
         if (!op->pout.p) CK(op->pout.alloc(op->nq));
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(op->cap, cudaStreamCaptureModeThreadLocal));
-        nlaunch = transpose ? launch_PT_kernels(op, op->cap, op->pin.p, op->pout.p)
-                            : launch_P_kernels(op, op->cap, op->pin.p, op->pout.p);
+        nlaunch = op->cartesian ? launch_S_kernels(op, op->cap, op->pin.p, op->pout.p, transpose)
+                  : transpose   ? launch_PT_kernels(op, op->cap, op->pin.p, op->pout.p)
+                                : launch_P_kernels(op, op->cap, op->pin.p, op->pout.p);
         CK(cudaStreamEndCapture(op->cap, &g));
         cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
         cudaGraphDestroy(g);
@@ -2196,6 +2281,7 @@ static ls_status apply_P(ls_op* op, const double2* x, double2* z) { return apply
 
 // y = L^T x (mode 0) or y = V^T x (mode 2)
 static ls_status apply_LT(ls_op* op, const double2* x, double2* y, int mode = 0) {
+    if (op->cartesian) return cart_apply(op, x, y, mode == 2 ? 2 : 1);   // V^(C) is symmetric
     ls_status s = launch_pairsum(op, x, nullptr, nullptr);
     if (s != LS_OK) return s;
     int threads = 256;
@@ -2642,6 +2728,26 @@ static ls_status build_preconditioner(ls_op* op, const HostMesh& M, const double
     return LS_OK;
 }
 
+// GMRES workspace of an operator with op->nq unknowns and op->prm.max_iter
+static ls_status alloc_gmres(ls_op* op, int nsm) {
+    const int n = op->nq, maxit = op->prm.max_iter;
+    CK(op->Vb.alloc((size_t)(maxit + 1) * n));
+    CK(op->Wb.alloc((size_t)maxit * n));
+    CK(op->H.alloc((size_t)(maxit + 1) * maxit));
+    CK(op->cs.alloc(maxit + 1));
+    CK(op->sn.alloc(maxit + 1));
+    CK(op->g.alloc(maxit + 2));
+    CK(op->hv.alloc(maxit + 1));
+    CK(op->yv.alloc(maxit + 1));
+    CK(op->tmp.alloc(n));
+    CK(op->tmp2.alloc(n));
+    CK(op->scal.alloc(4));
+    CK(op->hist.alloc(maxit + 2));
+    op->dblk = std::max(1, std::min(nsm * 2, (n + RED_TPB - 1) / RED_TPB));
+    CK(op->dpart.alloc((size_t)op->dblk * (maxit + 1)));
+    return LS_OK;
+}
+
 ls_status ls_operator_create(const ls_mesh* mesh, double k, const double* m, const double* m_grid,
                              const ls_params* params, void* stream, ls_op** out) {
     if (!out) return fail(LS_EINVAL, "out is null");
@@ -2727,23 +2833,103 @@ ls_status ls_operator_create(const ls_mesh* mesh, double k, const double* m, con
     auto tt0 = std::chrono::steady_clock::now();
     if (prm.prec != 1) TRY(build_table_range(op, op->tab_tlo, op->tab_thi, prm.prec));
     op->t_setup[3] = std::chrono::duration<double>(std::chrono::steady_clock::now() - tt0).count();
-    // GMRES workspace
-    const int maxit = prm.max_iter;
-    CK(op->Vb.alloc((size_t)(maxit + 1) * n));
-    CK(op->Wb.alloc((size_t)maxit * n));
-    CK(op->H.alloc((size_t)(maxit + 1) * maxit));
-    CK(op->cs.alloc(maxit + 1));
-    CK(op->sn.alloc(maxit + 1));
-    CK(op->g.alloc(maxit + 2));
-    CK(op->hv.alloc(maxit + 1));
-    CK(op->yv.alloc(maxit + 1));
-    CK(op->tmp.alloc(n));
-    CK(op->tmp2.alloc(n));
-    CK(op->scal.alloc(4));
-    CK(op->hist.alloc(maxit + 2));
-    op->dblk = std::max(1, std::min(nsm * 2, (n + RED_TPB - 1) / RED_TPB));
-    CK(op->dpart.alloc((size_t)op->dblk * (maxit + 1)));
+    TRY(alloc_gmres(op, nsm));
     if (prm.use_precond) TRY(build_preconditioner(op, M, m_grid));
+    guard.keep = true;
+    *out = op;
+    return LS_OK;
+}
+
+ls_status ls_cartesian_create(double k, const double* m_grid, const ls_params* params, void* stream, ls_op** out) {
+    if (!out) return fail(LS_EINVAL, "out is null");
+    *out = nullptr;
+    if (!m_grid) return fail(LS_EINVAL, "null contrast");
+    if (!(k > 0) || !std::isfinite(k)) return fail(LS_EINVAL, "k must be positive");
+    ls_params prm;
+    ls_params_default(&prm);
+    if (params) prm = *params;
+    if (prm.max_iter < 1 || !(prm.tol > 0)) return fail(LS_EINVAL, "bad tol / max_iter");
+    const int nx = prm.nx, ny = prm.ny;
+    if (nx < 4 || ny < 4) return fail(LS_EINVAL, "grid needs at least 4 x 4 nodes");
+    const double h = (prm.box[1] - prm.box[0]) / (nx - 1);
+    if (!(h > 0) || std::fabs((prm.box[3] - prm.box[2]) / (ny - 1) - h) > 1e-12 * h)
+        return fail(LS_EINVAL, "grid step must be equal in x and y");
+    const int n = nx * ny;
+    for (int q = 0; q < n; ++q)
+        if (!std::isfinite(m_grid[2 * q]) || !std::isfinite(m_grid[2 * q + 1])) return fail(LS_EINVAL, "non-finite contrast");
+    ls_op* op = new (std::nothrow) ls_op;
+    if (!op) return fail(LS_ENOMEM, "host allocation");
+    struct Guard { ls_op*& p; bool keep = false; ~Guard() { if (!keep) delete p; } } guard{op};
+    op->cartesian = true;
+    op->nq = n;
+    op->k = k;
+    op->prm = prm;
+    op->stream = (cudaStream_t)stream;
+    op->nx = nx;
+    op->ny = ny;
+    int dev = 0, nsm = 148;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    {   // unknowns at the grid nodes (x fastest), weights h^2 for the far field
+        std::vector<double2> xy(n);
+        std::vector<double> w(n, h * h);
+        for (int b = 0; b < ny; ++b)
+            for (int a = 0; a < nx; ++a) xy[a + (size_t)nx * b] = make_double2(prm.box[0] + a * h, prm.box[2] + b * h);
+        CK(op->xy.alloc(n));
+        CK(op->w.alloc(n));
+        CK(op->m.alloc(n));
+        CK(cudaMemcpy(op->xy.p, xy.data(), sizeof(double2) * n, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(op->w.p, w.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(op->m.p, m_grid, sizeof(double2) * n, cudaMemcpyHostToDevice));
+    }
+    auto tt0 = std::chrono::steady_clock::now();
+    {   // spectrum of the zero-padded kernel, scaled by 1 / (NX NY) for the inverse transform
+        op->cNX = 2 * nx;
+        op->cNY = 2 * ny;
+        const int NX = op->cNX, NY = op->cNY;
+        std::vector<std::complex<double>> tab;
+        lsgpu::cartesian_kernel_table(k, h, nx, ny, tab);
+        const double sc = 1.0 / ((double)NX * NY);
+        for (auto& v : tab) v *= sc;
+        DevBuf<double2> dtab;
+        CK(dtab.alloc(tab.size()));
+        CK(cudaMemcpy(dtab.p, tab.data(), sizeof(double2) * tab.size(), cudaMemcpyHostToDevice));
+        CK(op->khat.alloc((size_t)NX * NY));
+        CK(op->fpad.alloc((size_t)NX * NY));
+        CK(op->czero.alloc(n));
+        CK(cudaMemsetAsync(op->czero.p, 0, sizeof(double2) * n, op->stream));
+        k_cart_kernel<<<dim3((NX + 127) / 128, NY), 128, 0, op->stream>>>(nx, ny, NX, NY, dtab.p, op->khat.p);
+        CK(cudaGetLastError());
+        if (cufftPlan2d(&op->fft, NY, NX, CUFFT_Z2Z) != CUFFT_SUCCESS) return fail(LS_ECUDA, "cufftPlan2d failed");
+        if (cufftSetStream(op->fft, op->stream) != CUFFT_SUCCESS) return fail(LS_ECUDA, "cufftSetStream failed");
+        if (cufftExecZ2Z(op->fft, (cufftDoubleComplex*)op->khat.p, (cufftDoubleComplex*)op->khat.p, CUFFT_FORWARD) !=
+            CUFFT_SUCCESS)
+            return fail(LS_ECUDA, "cufftExecZ2Z failed");
+        CK(cudaStreamSynchronize(op->stream));
+    }
+    op->t_setup[3] = std::chrono::duration<double>(std::chrono::steady_clock::now() - tt0).count();
+    TRY(alloc_gmres(op, nsm));
+    if (prm.use_precond) {
+        auto tg0 = std::chrono::steady_clock::now();
+        GridSetup G;
+        std::vector<std::complex<double>> mg(n);
+        for (int i = 0; i < n; ++i) mg[i] = std::complex<double>(m_grid[2 * i], m_grid[2 * i + 1]);
+        std::string err = lsgpu::build_stencil_C(k, prm.box, nx, ny, mg.data(), G);
+        if (!err.empty()) return fail(LS_EINVAL, err);
+        op->t_setup[1] = std::chrono::duration<double>(std::chrono::steady_clock::now() - tg0).count();
+        auto tl0 = std::chrono::steady_clock::now();
+        std::vector<double2> hs(81);
+        for (int c = 0; c < 9; ++c)
+            for (int t = 0; t < 9; ++t) hs[9 * c + t] = make_double2(G.v[c][t].real(), G.v[c][t].imag());
+        CK(op->st.alloc(81));
+        CK(cudaMemcpy(op->st.p, hs.data(), sizeof(double2) * 81, cudaMemcpyHostToDevice));
+        CK(op->cband.alloc(G.cband.size()));
+        CK(cudaMemcpy(op->cband.p, G.cband.data(), sizeof(double2) * G.cband.size(), cudaMemcpyHostToDevice));
+        CK(op->ptp.alloc(n));
+        TRY(build_cr(op));
+        op->t_setup[2] = std::chrono::duration<double>(std::chrono::steady_clock::now() - tl0).count();
+        op->has_prec = true;
+    }
     guard.keep = true;
     *out = op;
     return LS_OK;
@@ -2796,6 +2982,7 @@ static ls_status farfield(ls_op* op, const double2* u, int n_ff, const double* a
 
 // ------------------------------------------------------------------ batched form (host side)
 static ls_status ensure_batch(ls_op* op, int R) {
+    if (op->cartesian) return fail(LS_EINVAL, "the batched forms need a quadrature-node operator");
     if (op->bR >= R) return LS_OK;
     const int n = op->nq, maxit = op->prm.max_iter, ldh = maxit + 1;
     int dev = 0, nsm = 148;
@@ -3914,6 +4101,7 @@ ls_status ls_misfit_gradient_dev(ls_op* op, int32_t R, const void* u_dev, int32_
 
 ls_status ls_op_set_pairsum(ls_op* op, int32_t mode) {
     if (!op) return fail(LS_EINVAL, "null op");
+    if (op->cartesian) return fail(LS_EINVAL, "a purely Cartesian operator has no pair-sum kernel");
     if (mode < 0 || mode > 3) return fail(LS_EINVAL, "pairsum must be 0, 1, 2 or 3");
     CK(cudaStreamSynchronize(op->stream));
     if (mode != 1 && !(op->tab_thi > 0)) return fail(LS_EINVAL, "operator has no table range (built with pairsum = 1)");

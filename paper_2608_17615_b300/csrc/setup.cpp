@@ -1075,6 +1075,22 @@ std::string build_grid(const HostMesh& M, double k, const double box[4], int nx,
                        const std::complex<double>* m_grid, GridSetup& G, int approach) {
     std::string err = build_transfers(M, box, nx, ny, approach, G);
     if (!err.empty()) return err;
+    return build_stencil_C(k, box, nx, ny, m_grid, G);
+}
+
+void cartesian_kernel_table(double k, double h, int nx, int ny, std::vector<std::complex<double>>& K) {
+    K.assign((size_t)nx * ny, 0.0);
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int b = 0; b < ny; ++b)
+        for (int a = 0; a < nx; ++a) K[(size_t)b * nx + a] = vc_entry((ld)k, (ld)h, a, b);
+}
+
+std::string build_stencil_C(double k, const double box[4], int nx, int ny, const std::complex<double>* m_grid,
+                            GridSetup& G) {
+    if (nx < 4 || ny < 4) return "grid needs at least 4 x 4 nodes";
+    const double hx = (box[1] - box[0]) / (nx - 1), hy = (box[3] - box[2]) / (ny - 1);
+    if (!(hx > 0) || std::fabs(hx - hy) > 1e-12 * hx) return "grid step must be equal in x and y";
+    G.nx = nx; G.ny = ny; G.x0 = box[0]; G.y0 = box[2]; G.h = hx;
     const int nc = nx * ny;
     // stencils: per row class c = ca + 3 cb, the truncated neighbourhood N(j) of a
     // representative node (grid centre, middle of an edge, corner), Gram matrix of
