@@ -191,6 +191,29 @@ ls_status ls_solve_adjoint(ls_op* op, int32_t R, const double* g, double* lambda
 /* ||P (b - L u)|| / ||P b|| (without P: ||b - L u|| / ||b||) by full applies of L and P, for
    device buffers b_dev, u_dev of N_Q complex. */
 ls_status ls_residual_dev(ls_op* op, const void* b_dev, const void* u_dev, double* rel);
+/*
+ * Ritz values of the last single-system GMRES solve on this operator (Section 6: the
+ * eigenvalues of the square Hessenberg matrix H_k of k Arnoldi steps on P L, the matrix
+ * whose spectrum the preconditioner clusters around 1; Figure ritz_spectrum uses 80 steps,
+ * e.g. tol tiny and max_iter 80).  *count = k; with ritz [cap >= k][2] non-null the k
+ * values are written (order unspecified).  Errors: LS_EINVAL (cap < k), LS_ENOCONV (the
+ * QR iteration did not converge).
+ */
+ls_status ls_op_ritz(ls_op* op, int32_t cap, int32_t* count, double* ritz);
+/* Eigenvalues of an upper Hessenberg matrix H [n][n] complex, column-major (host utility of
+   ls_op_ritz: shifted QR iteration with Wilkinson shifts); eig [n] complex out. */
+ls_status ls_hessenberg_eigenvalues(int32_t n, const double* H, double* eig);
+
+/*
+ * Invertibility diagnostic of the Approach II preconditioner (appendix on invertibility in
+ * practice, Eq. rho_def): for R grid vectors x_dev [R][nx * ny] complex (the caller draws them,
+ * e.g. standard complex normal), w = R_II x = D^{-1} (T_C^Q)^T T_C^Q x and
+ *   rho = <S^(C) w, w>_D / <w, w>_D,   <x, y>_D = x^* D y (Eq. D_inner_product),
+ * S^(C) w = C^{-1} A w; rho [R][2] (re, im) on the host.  Errors: LS_EINVAL without a
+ * preconditioner (or on a purely Cartesian operator).
+ */
+ls_status ls_precond_rho_dev(ls_op* op, int32_t R, const void* x_dev, double* rho);
+
 /* Largest explicit residual (see ls_solve) of the last single-system solve call. */
 ls_status ls_op_last_residual(const ls_op* op, double* rel);
 

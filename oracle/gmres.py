@@ -50,3 +50,29 @@ def gmres(apply_L, b, tol=1e-10, max_iter=600, apply_P=None):
     y = np.linalg.solve(np.triu(H[:it, :it]), g[:it])
     x = Vb[:it].T @ y
     return x, np.array(hist), it
+
+
+def ritz_values(apply_L, b, n_steps, apply_P=None):
+    """Ritz values of P L: the eigenvalues of the square Hessenberg matrix of n_steps
+    Arnoldi steps started from P b, with reorthogonalization (modified Gram-Schmidt, two
+    passes; Section 6, Figure ritz_spectrum); fewer when the Krylov space is exhausted."""
+    P = apply_P if apply_P is not None else (lambda v: v)
+    r0 = P(b)
+    n = b.size
+    V = np.zeros((n_steps + 1, n), dtype=np.complex128)
+    H = np.zeros((n_steps + 1, n_steps), dtype=np.complex128)
+    V[0] = r0 / np.linalg.norm(r0)
+    k = n_steps
+    for j in range(n_steps):
+        w = P(apply_L(V[j]))
+        for _ in range(2):
+            for i in range(j + 1):
+                c = np.vdot(V[i], w)
+                H[i, j] += c
+                w = w - c * V[i]
+        H[j + 1, j] = np.linalg.norm(w)
+        if H[j + 1, j] < 1e-14 * np.abs(H[:j + 1, j]).max():
+            k = j + 1
+            break
+        V[j + 1] = w / H[j + 1, j]
+    return np.linalg.eigvals(H[:k, :k])

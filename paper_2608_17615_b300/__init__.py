@@ -27,7 +27,8 @@ EXPORTED = ["ls_params_default", "ls_mesh_create", "ls_mesh_destroy", "ls_mesh_n
             "ls_solve_transpose_batch_dev", "ls_misfit_gradient_batch_dev",
             "ls_op_set_batch_kernel", "ls_op_set_stall_test", "ls_tc_gemm_check",
             "ls_apply_precond", "ls_apply_transpose", "ls_solve_adjoint", "ls_residual_dev", "ls_op_last_residual",
-            "ls_op_set_contrast_dev", "ls_misfit_dev",
+            "ls_op_set_contrast_dev", "ls_misfit_dev", "ls_op_ritz", "ls_hessenberg_eigenvalues",
+            "ls_precond_rho_dev",
             "ls_op_set_pairsum", "ls_op_set_timing", "ls_op_setup_times", "ls_op_tuning", "ls_op_stats", "ls_probe_fp64", "ls_pairsum_noalloc", "ls_last_error"]
 
 
@@ -82,6 +83,9 @@ def _load():
         "ls_op_last_residual": (I32, [P, P]),
         "ls_op_set_contrast_dev": (I32, [P, P, I32]),
         "ls_misfit_dev": (I32, [P, I32, P, P, P, P]),
+        "ls_op_ritz": (I32, [P, I32, P, P]),
+        "ls_precond_rho_dev": (I32, [P, I32, P, P]),
+        "ls_hessenberg_eigenvalues": (I32, [I32, P, P]),
         "ls_solve_dev": (I32, [P, I32, P, P, I32, P, P, P]),
         "ls_op_correction": (I32, [P, P, P, P, P]),
         "ls_correction_host": (I32, [P, D, D, P, P, P, P]),
@@ -248,6 +252,22 @@ class Operator:
         r = ctypes.c_double()
         _check(_lib.ls_residual_dev(self.handle, _dptr(b), _dptr(u), ctypes.byref(r)))
         return r.value
+
+    def ritz(self):
+        """Ritz values (eigenvalues of the square Hessenberg matrix) of the last single-system solve."""
+        cnt = ctypes.c_int32()
+        _check(_lib.ls_op_ritz(self.handle, 0, ctypes.byref(cnt), None))
+        out = np.empty(cnt.value, np.complex128)
+        if cnt.value:
+            _check(_lib.ls_op_ritz(self.handle, cnt.value, ctypes.byref(cnt), _ptr(out.view(np.float64))))
+        return out
+
+    def precond_rho_dev(self, X):
+        """rho(R_II x) (Eq. rho_def) for grid vectors X torch [R, nx * ny] complex128; numpy [R] complex."""
+        R = X.shape[0]
+        out = np.empty(R, np.complex128)
+        _check(_lib.ls_precond_rho_dev(self.handle, R, _dptr(X), _ptr(out.view(np.float64))))
+        return out
 
     def last_residual(self):
         """Largest explicit GMRES exit residual of the last single-system solve call."""
@@ -442,6 +462,15 @@ class CartesianOperator(Operator):
         self.handle = h
         self.n = _lib.ls_op_num_nodes(h)
         self.k = float(k)
+
+
+def hessenberg_eigenvalues(H):
+    """Eigenvalues of an upper Hessenberg matrix (host routine of the Ritz values)."""
+    H = np.asfortranarray(np.asarray(H, np.complex128))
+    n = H.shape[0]
+    e = np.empty(n, np.complex128)
+    _check(_lib.ls_hessenberg_eigenvalues(n, _ptr(H.ravel(order="F").view(np.float64)), _ptr(e.view(np.float64))))
+    return e
 
 
 def correction_host(mesh, k, kappa=3.0):

@@ -1080,6 +1080,36 @@ __global__ void k_misfit(int total, const double2* __restrict__ uinf, const doub
     if (threadIdx.x == 0) *J = 0.5 * part[0];
 }
 
+// w = w' / D
+__global__ void k_div_real(int n, const double* __restrict__ D, double2* __restrict__ w) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) w[r] = make_double2(w[r].x / D[r], w[r].y / D[r]);
+}
+
+// rho = sum_j D_j conj(Sw_j) w_j / sum_j D_j |w_j|^2 (one block, fixed order)
+__global__ void k_rho(int n, const double* __restrict__ D, const double2* __restrict__ w, const double2* __restrict__ Sw,
+                      double* __restrict__ out) {
+    __shared__ double pr[256], pi[256], pd[256];
+    double ar = 0.0, ai = 0.0, ad = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double2 t = conjmul(Sw[j], w[j]);
+        ar = fma(D[j], t.x, ar);
+        ai = fma(D[j], t.y, ai);
+        ad = fma(D[j], w[j].x * w[j].x + w[j].y * w[j].y, ad);
+    }
+    pr[threadIdx.x] = ar; pi[threadIdx.x] = ai; pd[threadIdx.x] = ad;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            pr[threadIdx.x] += pr[threadIdx.x + o];
+            pi[threadIdx.x] += pi[threadIdx.x + o];
+            pd[threadIdx.x] += pd[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { out[0] = pr[0] / pd[0]; out[1] = pi[0] / pd[0]; }
+}
+
 // m = Re(m_real) + 0 i from a real device vector
 __global__ void k_real_to_complex(int n, const double* __restrict__ a, double2* __restrict__ out) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1694,11 +1724,14 @@ struct ls_op {
     DevBuf<int> tcqT_ci, tqcT_ci;
     DevBuf<double> tcqT_cv, tqcT_cv;
     int n_interior = 0;                  // grid nodes inside the mesh (Approach I) or pixelation nodes (II)
+    DevBuf<double> Dg;                   // Approach II column sums D (1 off the pixelation), Eq. D_def
     DevBuf<double2> st;                  // [9 classes][9 offsets] sparsifying stencils
     DevBuf<double2> pg, pt, ptp;         // grid work vectors
     // GMRES workspace
     DevBuf<double2> Vb, H, cs, sn, g, hv, yv, tmp, tmp2, dpart, scal;
     DevBuf<double2> Wb;                  // raw operator products P L v_j of the last solve (exit check)
+    DevBuf<double2> Hraw;                // Hessenberg matrix of the last solve before the Givens rotations
+    int last_it = 0;                     // iterations of the last single-RHS GMRES solve
     double last_res = -1.0;              // explicit relative residual of the last single-RHS solve(s) (max)
     DevBuf<double> hist;
     int dblk = 0;
@@ -2346,6 +2379,8 @@ static ls_status gmres_one(ls_op* op, const double2* b, double2* u, double* hist
         k_sumrows<<<(j + 1 + 127) / 128, 128, 0, op->stream>>>(j + 1, 1, op->hv.p, hcol, 1);
         TRY(dots(op, 1, vn, vn, op->scal.p + 1, 0));
         k_scale<<<nb, tpb, 0, op->stream>>>(n, vn, op->scal.p + 1, vn, hcol + j + 1);
+        CK(cudaMemcpyAsync(op->Hraw.p + (size_t)j * ldh, hcol, sizeof(double2) * (j + 2), cudaMemcpyDeviceToDevice,
+                           op->stream));
         k_givens<<<1, 1, 0, op->stream>>>(j, op->H.p, ldh, op->cs.p, op->sn.p, op->g.p, op->hist.p, op->scal.p);
         CK(cudaGetLastError());
         op->launches += 5;
@@ -2369,6 +2404,7 @@ static ls_status gmres_one(ls_op* op, const double2* b, double2* u, double* hist
     CK(cudaStreamSynchronize(op->stream));
     const double rel = sc[0].x > 0 ? std::sqrt(sc[2].x / sc[0].x) : 0.0;
     op->last_res = std::max(op->last_res, rel);
+    op->last_it = it;
     if (iters) *iters = it;
     if (conv && !(rel <= 10.0 * op->prm.tol)) {
         fail(LS_ENOCONV, "GMRES: explicit residual " + std::to_string(rel) + " exceeds 10 x tol");
@@ -2680,6 +2716,8 @@ static ls_status build_preconditioner(ls_op* op, const HostMesh& M, const double
         CK(cudaMemcpy(op->tqcT_cv.p, G.tqcT_vals.data(), sizeof(double) * G.tqcT_vals.size(), cudaMemcpyHostToDevice));
     }
     op->n_interior = G.n_interior;
+    CK(op->Dg.alloc(nc));
+    CK(cudaMemcpy(op->Dg.p, G.D.data(), sizeof(double) * nc, cudaMemcpyHostToDevice));
     CK(op->pg.alloc(nc));
     CK(op->pt.alloc(nc));
     CK(op->ptp.alloc(nc));
@@ -2734,6 +2772,7 @@ static ls_status alloc_gmres(ls_op* op, int nsm) {
     CK(op->Vb.alloc((size_t)(maxit + 1) * n));
     CK(op->Wb.alloc((size_t)maxit * n));
     CK(op->H.alloc((size_t)(maxit + 1) * maxit));
+    CK(op->Hraw.alloc((size_t)(maxit + 1) * maxit));
     CK(op->cs.alloc(maxit + 1));
     CK(op->sn.alloc(maxit + 1));
     CK(op->g.alloc(maxit + 2));
@@ -3892,6 +3931,115 @@ ls_status ls_solve_adjoint(ls_op* op, int32_t R, const double* g, double* lambda
 ls_status ls_residual_dev(ls_op* op, const void* b_dev, const void* u_dev, double* rel) {
     if (!op || !b_dev || !u_dev || !rel) return fail(LS_EINVAL, "null argument");
     return residual_full(op, (const double2*)b_dev, (const double2*)u_dev, rel);
+}
+
+// Eigenvalues of an upper Hessenberg matrix (n x n, column-major) by the shifted QR
+// iteration: deflation at negligible subdiagonals, Wilkinson shift from the trailing 2 x 2
+// block of the active window, an exceptional shift every 10 iterations without
+// deflation; each step H - mu I = Q R, H <- R Q + mu I with complex Givens rotations.
+static bool hessenberg_eig(int n, std::vector<std::complex<double>>& H, std::vector<std::complex<double>>& eig) {
+    using cd = std::complex<double>;
+    auto A = [&](int r, int c) -> cd& { return H[(size_t)c * n + r]; };
+    eig.clear();
+    int hi = n - 1, iter = 0, total = 0;
+    std::vector<cd> cs(n), sn(n);
+    while (hi >= 0) {
+        if (hi == 0) { eig.push_back(A(0, 0)); --hi; continue; }
+        int l = hi;
+        while (l > 0 && std::abs(A(l, l - 1)) > 1e-15 * (std::abs(A(l - 1, l - 1)) + std::abs(A(l, l)))) --l;
+        if (l == hi) { eig.push_back(A(hi, hi)); --hi; iter = 0; continue; }
+        if (++total > 100 * n) return false;
+        cd mu;
+        if (iter % 10 == 9) {
+            mu = A(hi, hi) + cd(std::abs(A(hi, hi - 1)), 0.0);
+        } else {
+            const cd a = A(hi - 1, hi - 1), b = A(hi - 1, hi), c = A(hi, hi - 1), d = A(hi, hi);
+            const cd half = 0.5 * (a - d);
+            const cd disc = std::sqrt(half * half + b * c);
+            const cd m1 = 0.5 * (a + d) + disc, m2 = 0.5 * (a + d) - disc;
+            mu = std::abs(m1 - d) < std::abs(m2 - d) ? m1 : m2;
+        }
+        ++iter;
+        for (int k = l; k <= hi; ++k) A(k, k) -= mu;
+        for (int k = l; k < hi; ++k) {
+            const cd a = A(k, k), b = A(k + 1, k);
+            const double r = std::sqrt(std::norm(a) + std::norm(b));
+            const cd c = r > 0 ? a / r : cd(1, 0), s = r > 0 ? b / r : cd(0, 0);
+            cs[k] = c;
+            sn[k] = s;
+            for (int j = k; j <= hi; ++j) {
+                const cd x = A(k, j), y = A(k + 1, j);
+                A(k, j) = std::conj(c) * x + std::conj(s) * y;
+                A(k + 1, j) = -s * x + c * y;
+            }
+        }
+        for (int k = l; k < hi; ++k) {
+            const cd c = cs[k], s = sn[k];
+            for (int i = l; i <= std::min(k + 2, hi); ++i) {
+                const cd x = A(i, k), y = A(i, k + 1);
+                A(i, k) = x * c + y * s;
+                A(i, k + 1) = -x * std::conj(s) + y * std::conj(c);
+            }
+        }
+        for (int k = l; k <= hi; ++k) A(k, k) += mu;
+    }
+    return true;
+}
+
+ls_status ls_hessenberg_eigenvalues(int32_t n, const double* H, double* eig) {
+    if (n < 1 || !H || !eig) return fail(LS_EINVAL, "null argument or n < 1");
+    std::vector<std::complex<double>> A((size_t)n * n), e;
+    for (size_t i = 0; i < A.size(); ++i) A[i] = std::complex<double>(H[2 * i], H[2 * i + 1]);
+    if (!hessenberg_eig(n, A, e)) return fail(LS_ENOCONV, "Hessenberg QR iteration did not converge");
+    for (int i = 0; i < n; ++i) { eig[2 * i] = e[i].real(); eig[2 * i + 1] = e[i].imag(); }
+    return LS_OK;
+}
+
+ls_status ls_op_ritz(ls_op* op, int32_t cap, int32_t* count, double* ritz) {
+    if (!op || !count) return fail(LS_EINVAL, "null argument");
+    const int it = op->last_it, ldh = op->prm.max_iter + 1;
+    *count = it;
+    if (!ritz || it == 0) return LS_OK;
+    if (cap < it) return fail(LS_EINVAL, "ritz buffer smaller than the iteration count");
+    std::vector<double2> raw((size_t)ldh * it);
+    CK(cudaMemcpyAsync(raw.data(), op->Hraw.p, sizeof(double2) * raw.size(), cudaMemcpyDeviceToHost, op->stream));
+    CK(cudaStreamSynchronize(op->stream));
+    std::vector<std::complex<double>> A((size_t)it * it), e;
+    for (int c = 0; c < it; ++c)
+        for (int r = 0; r < it; ++r)
+            A[(size_t)c * it + r] = r <= c + 1 ? std::complex<double>(raw[(size_t)c * ldh + r].x, raw[(size_t)c * ldh + r].y)
+                                               : std::complex<double>(0, 0);
+    if (!hessenberg_eig(it, A, e)) return fail(LS_ENOCONV, "Hessenberg QR iteration did not converge");
+    for (int i = 0; i < it; ++i) { ritz[2 * i] = e[i].real(); ritz[2 * i + 1] = e[i].imag(); }
+    return LS_OK;
+}
+
+ls_status ls_precond_rho_dev(ls_op* op, int32_t R, const void* x_dev, double* rho) {
+    if (!op || R < 1 || !x_dev || !rho) return fail(LS_EINVAL, "null argument or R < 1");
+    if (!op->has_prec || op->cartesian) return fail(LS_EINVAL, "needs an operator with the Cartesian preconditioner");
+    const int nc = op->nx * op->ny, nq = op->nq;
+    DevBuf<double2> zq, q, w;
+    DevBuf<double> out;
+    CK(zq.alloc(nq));
+    CK(q.alloc(nq));
+    CK(w.alloc(nc));
+    CK(out.alloc(2 * (size_t)R));
+    CK(cudaMemsetAsync(zq.p, 0, sizeof(double2) * nq, op->stream));
+    for (int r = 0; r < R; ++r) {
+        const double2* x = (const double2*)x_dev + (size_t)r * nc;
+        // w = R_II x = D^{-1} (T_C^Q)^T T_C^Q x
+        k_tcq<<<(nq + 255) / 256, 256, 0, op->stream>>>(nq, op->tcq_idx.p, op->tcq_w.p, x, nullptr, zq.p, q.p);
+        k_tqc<<<(nc + 255) / 256, 256, 0, op->stream>>>(nc, op->tcqT_rp.p, op->tcqT_ci.p, op->tcqT_cv.p, q.p, w.p);
+        k_div_real<<<(nc + 255) / 256, 256, 0, op->stream>>>(nc, op->Dg.p, w.p);
+        // S^(C) w = C^{-1} A w
+        k_stencil<<<(nc + 255) / 256, 256, 0, op->stream>>>(op->nx, op->ny, op->st.p, w.p, op->cr.t());
+        const int ncr = launch_cr(op, op->stream, false);
+        k_rho<<<1, 256, 0, op->stream>>>(nc, op->Dg.p, w.p, op->cr.x(), out.p + 2 * r);
+        CK(cudaGetLastError());
+        op->launches += 5 + ncr;
+    }
+    CK(cudaMemcpyAsync(rho, out.p, sizeof(double) * 2 * R, cudaMemcpyDeviceToHost, op->stream));
+    return check_stream_sync(op);
 }
 
 ls_status ls_op_last_residual(const ls_op* op, double* rel) {

@@ -150,3 +150,24 @@ def test_transfer_host_matches_oracle(approach):
         B, _ = transfer_QC_II(transfer_CQ(g, wl.mesh.nodes))
     assert (A != 0).nnz == (B != 0).nnz
     assert abs(A - B).max() < 1e-13 * abs(B).max()
+
+
+def test_hessenberg_eigenvalues_match_numpy():
+    """The library's host QR iteration (Ritz values) against LAPACK through numpy, on random
+    complex upper Hessenberg matrices and on one with a nearly repeated cluster at 1 (the
+    preconditioned spectrum's shape)."""
+    rng = np.random.default_rng(11)
+    for n in (1, 2, 7, 40, 120):
+        H = np.triu(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)), -1)
+        e = np.sort_complex(L.hessenberg_eigenvalues(H))
+        ref = np.sort_complex(np.linalg.eigvals(H))
+        assert np.max(np.abs(e - ref)) < 1e-9 * max(1.0, np.max(np.abs(ref)))
+    n = 60
+    Q = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))[0]
+    A = Q @ np.diag(1 + 0.05 * (rng.standard_normal(n) + 1j * rng.standard_normal(n))) @ Q.conj().T
+    import scipy.linalg as sl
+    Hh = sl.hessenberg(A)
+    e = L.hessenberg_eigenvalues(Hh)
+    ref = np.linalg.eigvals(A)
+    d = np.abs(e[:, None] - ref[None, :]).min(axis=1)
+    assert np.max(d) < 1e-10
