@@ -235,6 +235,36 @@ def _finish(b, curves):
     return map_nodes(mesh)
 
 
+def open_resonator_mesh(n_s, n_theta, r_in=0.8, r_out=1.0, theta0=np.pi / 9):
+    """Truncated annulus {r_in < |x| < r_out, |theta| > theta0} (an open cavity whose
+    aperture faces +x): the (s, theta) grid of the blend between the two circles over
+    theta in [theta0, 2 pi - theta0], each cell split into two triangles; arcs exact,
+    the two radial end edges straight."""
+    inner = (0.0, 0.0, r_in, 0.0, 0.0, 0.0)
+    outer = (0.0, 0.0, r_out, 0.0, 0.0, 0.0)
+    b = _Builder()
+    th = theta0 + (2 * np.pi - 2 * theta0) * np.arange(n_theta + 1) / n_theta
+    idx = np.zeros((n_s + 1, n_theta + 1), dtype=np.int64)
+    for i in range(n_s + 1):
+        s_ = i / n_s
+        for j in range(n_theta + 1):
+            xi, yi = curve_point(inner, th[j])
+            xo, yo = curve_point(outer, th[j])
+            if i == 0:
+                idx[i, j] = b.add_vertex(xi, yi)
+            elif i == n_s:
+                idx[i, j] = b.add_vertex(xo, yo)
+            else:
+                idx[i, j] = b.add_vertex((1 - s_) * xi + s_ * xo, (1 - s_) * yi + s_ * yo)
+    for i in range(n_s):
+        for j in range(n_theta):
+            curved = (1, 1, th[j], th[j + 1]) if i + 1 == n_s else None
+            b.add_tri((idx[i, j], idx[i + 1, j], idx[i + 1, j + 1]), 0, curved)
+            curved = (2, 0, th[j + 1], th[j]) if i == 0 else None
+            b.add_tri((idx[i, j], idx[i + 1, j + 1], idx[i, j + 1]), 0, curved)
+    return _finish(b, [inner, outer])
+
+
 def square_mesh(n, half=0.75):
     """Straight-edged mesh of the square [-half, half]^2: n x n cells, each split into
     two triangles (2 n^2 elements, one subdomain, no curved edges)."""

@@ -13,7 +13,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .mesh import disk_mesh, inclusion_disk_mesh, star_mesh
+from .mesh import disk_mesh, inclusion_disk_mesh, open_resonator_mesh, star_mesh
 
 
 @dataclass
@@ -126,6 +126,24 @@ def star_scatterer(s, n_nodes_target, k=None, nx=128, ny=128, n_dirs=64, n_ff=64
     m_grid = np.where(r < rb, 1.0 - ng**2, 0.0).astype(np.complex128)
     dirs = 2 * np.pi * np.arange(n_dirs) / n_dirs
     return Workload(f"star{s}", mesh, float(k), m, box, nx, ny, m_grid, dirs,
+                    2 * np.pi * np.arange(n_ff) / n_ff, tol)
+
+
+def open_resonator(k=10.0, n_s=3, n_theta=60, nx=96, ny=96, box=(-1.2, 1.2, -1.2, 1.2), n_ff=64, tol=1e-10):
+    """The paper's open-cavity resonator (Section 6, more general examples): the truncated
+    annulus 0.8 < |x| < 1, |theta| > 20 degrees, with the radial contrast
+    m(x) = exp(-((|x| - 0.9) / 0.1201)^2) inside (m given directly), a plane wave along
+    d = (-1, 0) entering the cavity through its aperture; k kept small here (the paper
+    runs k = 200)."""
+    th0 = np.pi / 9
+    mesh = open_resonator_mesh(n_s, n_theta, theta0=th0)
+    r = np.hypot(mesh.nodes[:, 0], mesh.nodes[:, 1])
+    m = np.exp(-(((r - 0.9) / 0.1201) ** 2)).astype(np.complex128)
+    X, Y = _grid(box, nx, ny)
+    R = np.hypot(X, Y)
+    inside = (R > 0.8) & (R < 1.0) & (np.abs(np.arctan2(Y, X)) > th0)
+    m_grid = np.where(inside, np.exp(-(((R - 0.9) / 0.1201) ** 2)), 0.0).astype(np.complex128)
+    return Workload("open_resonator", mesh, float(k), m, box, nx, ny, m_grid, np.array([np.pi]),
                     2 * np.pi * np.arange(n_ff) / n_ff, tol)
 
 

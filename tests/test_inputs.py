@@ -78,3 +78,14 @@ def test_curved_edges_on_curve():
             for v in (m.tris[t, e], m.tris[t, (e + 1) % 3]):
                 p = m.vertices[v]
                 assert abs(np.hypot(p[0] - cx, p[1] - cy) - R) < 1e-15
+
+
+def test_open_resonator_mesh_area_and_contrast():
+    from lsinput.workloads import open_resonator
+    wl = open_resonator(n_s=2, n_theta=30)
+    exact = 0.5 * (1.0 - 0.8**2) * (2 * np.pi - 2 * np.pi / 9)      # truncated annulus
+    assert abs(wl.mesh.weights.sum() - exact) < 1e-13
+    r = np.hypot(wl.mesh.nodes[:, 0], wl.mesh.nodes[:, 1])
+    th = np.arctan2(wl.mesh.nodes[:, 1], wl.mesh.nodes[:, 0])
+    assert np.all((r > 0.8) & (r < 1.0) & (np.abs(th) > np.pi / 9))
+    assert np.allclose(wl.m.real, np.exp(-(((r - 0.9) / 0.1201) ** 2)))
