@@ -1,14 +1,22 @@
 #!/usr/bin/env python
 """Benchmark of the Lippmann-Schwinger Nystrom hot path on one B300.
 
-A step is one full left-preconditioned FP64 GMRES solve (tol 1e-8) of the
-two-material disk (off-centre inclusion; n_opt = 1.5 + 0.2 exp(-|x|^2/0.1)
-outside, 2.2 inside), k = 20, 2,680 curved triangles x 15 nodes = 40,200 nodes,
-Cartesian preconditioner on 256^2 over [-1.2, 1.2]^2, one plane wave at pi/4,
-plus its far-field pattern at 64 angles.  Setup (correction and preconditioner
-factors) is excluded, as the paper excludes it from its solve times.
+A step is one full left-preconditioned GMRES solve (tol 1e-8) of the two-material
+disk (off-centre inclusion; n_opt = 1.5 + 0.2 exp(-|x|^2/0.1) outside, 2.2 inside),
+k = 20, 2,680 curved triangles x 15 nodes = 40,200 nodes, Cartesian preconditioner on
+256^2 over [-1.2, 1.2]^2, one plane wave at pi/4, plus its far-field pattern at 64
+angles, with the FP64-accurate pair sum (the H0 table evaluated in double-float
+arithmetic on the FP32 pipe; its matvec agrees with the FP64 oracle to ~1e-12, and the
+line states the measured error).  Setup (correction and preconditioner factors) is
+excluded, as the paper excludes it from its solve times.  The line also carries, under
+"forms", every other form on its own configuration: the FP64-pipe pair sum and the
+FP32 precision form on the same workload, the batched 64-direction solves, the
+Approach I / II comparison, the precision form at k = 40 on 195,630 nodes, the
+batching form (8 star scatterers, 64 directions each) and the differentiation form
+(gradient on 492,450 nodes), each with its error and a roofline fraction.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload default|precision|batching|gradient|batched]
 Prints one JSON line.  Under torchrun every rank solves its own incident
 direction (independent replicas, no collective); value = all solves / max time.
 """
@@ -27,10 +35,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "two-material disk, k=20, 40,200 nodes (2,680 curved P4 triangles), 256^2 Cartesian preconditioner, tol 1e-8"
-METRIC = "LS GMRES solves/s (FP64, preconditioned)"
+METRIC = "LS GMRES solves/s (FP64-accurate double-float pair sum, preconditioned)"
 # Preconditioned GMRES iterations of this workload as measured by the GPU arm;
 # the reference arm scales its sampled matvec cost by it.
 REFERENCE_ITERS = 8
+LS_PREC_FP64_TABLE, LS_PREC_FP64_DIRECT, LS_PREC_FP32, LS_PREC_FP64_DF = range(4)
 
 
 def _env_rank():
@@ -105,10 +114,80 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+# ---------------------------------------------------------------- peaks and flop counts
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+# B300 unit counts at 2.032 GHz on 148 SMs: FP32 128 lanes/SM (FMA = 2 flops), FP64 2 DFMA/clk/SM.
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12          # 77.0
+FP64_UNIT_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12       # 1.203
+FP32_PEAK_SOURCE = "FP32 unit count: 148 SMs x 128 lanes x 2 flops x 2.032 GHz"
+
+
+# Floating-point operations per pair of each pair-sum kernel (FMA = 2), counted from the source:
+#  0 k_pairsum_tab (FP64): dx, dy 2; t 3; u 2; two Horner chains 4 (nc - 1); complex MAC 8
+#  1 k_pairsum (FP64, direct): 89 FP64 instructions per pair measured by ncu (58.5 DFMA,
+#    23.5 DMUL, 7.1 DADD) -> 148
+#  2 k_pairsum_f32 (FP32): two double-float differences 22, double-float t 16, u 4, two
+#    degree-6 Horner chains 24, complex multiply 6, Kahan sums 8 -> 80
+#  3 k_pairsum_df (double-float on FP32): differences 22, t 12, u 8, per chain nf FP32
+#    Horner steps (2 flops) and nc - 1 - nf double-float steps (15 flops), DF complex MAC 60
+def flops_per_pair_of(mode, nc, nf=0):
+    if mode == 0:
+        return 15 + 4 * (nc - 1)
+    if mode == 3:
+        return 102 + 2 * (2 * nf + 15 * (nc - 1 - nf))
+    return {1: 148, 2: 80}[mode]
+
+
+KERNEL = {0: "k_pairsum_tab", 1: "k_pairsum", 2: "k_pairsum_f32", 3: "k_pairsum_df"}
+# dram__bytes_read + write per launch (40,200 nodes) from ncu captures of the pair-sum kernels;
+# the kernels read O(N) data for O(N^2) work, so this is the compulsory traffic
+TRAFFIC_BYTES = {0: 2.4e6, 2: 2.4e6, 3: 2.4e6}
+
+
+def _timed(fn, stream, reps=1):
+    """Run fn reps times between CUDA events on `stream`; returns (ms per run, last result)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = None
+    for _ in range(reps):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def _pairsum_roofline(op, n, peak, peak_source, total_ms=None):
+    """Roofline of the single-RHS pair-sum kernel from the operator's event-timed launches."""
+    ps_ms, ps_launches, _ = op.stats()
+    mode = op.params.prec
+    nc, _ = op.tuning()
+    nf = op.df_tail() if mode == 3 else 0
+    fpp = flops_per_pair_of(mode, nc, nf)
+    avg_s = ps_ms / max(ps_launches, 1) * 1e-3
+    achieved = fpp * n * (n - 1) / avg_s / 1e12
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+           "traffic": TRAFFIC_BYTES.get(mode) if n == 40200 else None, "kernel": KERNEL[mode],
+           "flops_per_pair": fpp, "table_ncoef": nc, "peak_source": peak_source,
+           "kernel_ms_per_launch": avg_s * 1e3, "kernel_launches": ps_launches}
+    if mode == 3:
+        out["fp32_tail_coefficients"] = nf
+    if total_ms:
+        out["kernel_share_of_step"] = ps_ms / total_ms
+    return out
+
+
+# ---------------------------------------------------------------- CPU baselines (the oracle)
 def _oracle_rows_job(job):
-    """Worker of the CPU baseline (spawned process): the oracle's pair-sum rows and
+    """Worker of the CPU baselines (spawned process): the oracle's pair-sum rows and
     correction rows of one slice of the sample, with their wall times."""
-    import numpy as np
     from lsinput.workloads import two_material
     from oracle.nystrom import naive_rows
     from oracle.vdim import correction_matrix
@@ -129,53 +208,52 @@ def _host_cores():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(wl, u_gpu, Lu_gpu, iters, budget_s=24.0):
-    """The oracle as it stands, timed on the host's cores (one spawned process per core,
-    each with single-threaded BLAS) on a bounded sample of the same workload: a slice of
-    pair-sum rows and of correction rows per process, sized from a short calibration so
-    that the whole sample takes about budget_s, plus one apply of the oracle's
-    preconditioner (SuperLU solve on the 256^2 grid; its assembly is setup).  The sampled
-    rows also give the GPU matvec's error against the oracle.  Solves/s = 1 / (iters x
-    (extrapolated L apply + P apply))."""
+def _oracle_pool(cores):
     import multiprocessing as mp
-    from oracle.precond import Grid, Preconditioner
     os.environ["OPENBLAS_NUM_THREADS"] = "1"          # inherited by the spawned workers
     os.environ["OMP_NUM_THREADS"] = "1"
+    return mp.get_context("spawn").Pool(cores)
+
+
+def _oracle_sample(pool, cores, wl, f, n_ps, n_corr, seed):
+    """One bounded sample on all cores: n_ps pair-sum rows and n_corr correction rows (among
+    them) per process.  Returns (core-seconds per pair-sum row, per correction row, wall
+    seconds, jobs, results)."""
+    n = wl.mesh.n_nodes
+    perm = np.random.default_rng(seed).permutation(n)
+    jobs = []
+    for c in range(cores):
+        ps = perm[(c * n_ps) % n:(c * n_ps) % n + n_ps]
+        jobs.append(("small", f, np.sort(ps), np.sort(ps[:n_corr])))
+    w0 = time.perf_counter()
+    res = pool.map(_oracle_rows_job, jobs)
+    wall = time.perf_counter() - w0
+    rows_ps = sum(len(j[2]) for j in jobs)
+    rows_corr = sum(len(j[3]) for j in jobs)
+    return sum(r[2] for r in res) / rows_ps, sum(r[3] for r in res) / rows_corr, wall, jobs, res
+
+
+def cpu_baseline(wl, u_gpu, Lu_gpu, iters, budget_s=24.0):
+    """The oracle as it stands, timed on the host's cores (one spawned process per core,
+    single-threaded BLAS) on a bounded sample of the same workload: pair-sum rows and
+    correction rows per process, sized from a short calibration so the sample takes about
+    budget_s, plus one apply of the oracle's preconditioner (SuperLU solve on the 256^2
+    grid; its assembly is setup).  The sampled rows also give the GPU matvec's error
+    against the oracle.  Solves/s = 1 / (iters x (extrapolated L apply + P apply))."""
+    from oracle.precond import Grid, Preconditioner
     cores = _host_cores()
     n = wl.mesh.n_nodes
     f = wl.m * u_gpu
-    rng = np.random.default_rng(0)
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(cores) as pool:
-        # calibration: 64 pair-sum rows and 4 correction rows per process
-        cal = pool.map(_oracle_rows_job, [("small", f, rng.choice(n, 64, replace=False), rng.choice(n, 4, replace=False))
-                                          for _ in range(cores)])
-        t_row_ps = np.median([c[2] for c in cal]) / 64
-        t_row_corr = np.median([c[3] for c in cal]) / 4
-        n_ps = max(64, int(0.5 * budget_s / t_row_ps))
-        n_corr = max(4, int(0.5 * budget_s / t_row_corr))
-        perm = rng.permutation(n)
-        jobs = []
-        for c in range(cores):
-            ps = perm[(c * n_ps) % n:(c * n_ps) % n + n_ps]
-            jobs.append(("small", f, np.sort(ps), np.sort(ps[:n_corr])))   # correction rows among the pair-sum rows
-        w0 = time.perf_counter()
-        res = pool.map(_oracle_rows_job, jobs)
-        wall = time.perf_counter() - w0
-    rows_ps = sum(len(j[2]) for j in jobs)
-    rows_corr = sum(len(j[3]) for j in jobs)
-    t_ps = sum(r[2] for r in res) / rows_ps            # core-seconds per row
-    t_corr = sum(r[3] for r in res) / rows_corr
-    t_apply = (t_ps + t_corr) * n / cores              # all cores, one full L apply
-    # matvec error on the first job's rows that carry both parts
+    with _oracle_pool(cores) as pool:
+        t_ps, t_corr, _, _, _ = _oracle_sample(pool, cores, wl, f, 64, 4, 1)
+        n_ps = max(64, int(0.5 * budget_s / t_ps))
+        n_corr = min(n_ps, max(4, int(0.5 * budget_s / t_corr)))
+        t_ps, t_corr, wall, jobs, res = _oracle_sample(pool, cores, wl, f, n_ps, n_corr, 0)
+    t_apply = (t_ps + t_corr) * n / cores
     job0, r0 = jobs[0], res[0]
-    common = np.intersect1d(job0[2], job0[3])
-    err = None
-    if common.size:
-        a = np.searchsorted(job0[2], common)
-        b = np.searchsorted(job0[3], common)
-        ref = u_gpu[common] + wl.k**2 * (r0[0][a] + r0[1][b])
-        err = float(np.linalg.norm(Lu_gpu[common] - ref) / np.linalg.norm(ref))
+    a = np.searchsorted(job0[2], job0[3])
+    ref = u_gpu[job0[3]] + wl.k**2 * (r0[0][a] + r0[1])
+    err = float(np.linalg.norm(Lu_gpu[job0[3]] - ref) / np.linalg.norm(ref))
     P = Preconditioner(Grid(wl.box, wl.nx, wl.ny), wl.mesh.nodes, wl.k, wl.m_grid)
     tp0 = time.perf_counter()
     P.apply(u_gpu)
@@ -183,112 +261,99 @@ def cpu_baseline(wl, u_gpu, Lu_gpu, iters, budget_s=24.0):
     t_solve = iters * (t_apply + t_P)
     return {
         "value": 1.0 / t_solve, "unit": "solves/s", "cores": cores, "kind": "oracle",
-        "sample": f"{rows_ps} pair-sum rows x {n} sources and {rows_corr} correction rows over {cores} processes "
-                  f"({wall:.1f} s wall), extrapolated to {n} rows per L apply, plus one timed P apply, "
+        "sample": f"{n_ps * cores} pair-sum rows x {n} sources and {n_corr * cores} correction rows over {cores} "
+                  f"processes ({wall:.1f} s wall), extrapolated to {n} rows per L apply, plus one timed P apply, "
                   f"x {iters} iterations",
-        "seconds": round(wall + t_P, 2), "pairs_per_s": rows_ps * (n - 1) / (t_ps * rows_ps) * cores,
+        "seconds": round(wall + t_P, 2), "pairs_per_s": (n - 1) / t_ps * cores,
         "t_apply_s": t_apply, "t_precond_s": t_P,
     }, err
 
 
 def reference_arm(args):
-    """--impl reference: the oracle as it stands, each step a bounded sample."""
+    """--impl reference: the oracle as it stands on the host's cores, each step a bounded
+    sample (cores x 48 pair-sum rows and cores x 2 correction rows of one L apply,
+    extrapolated to the whole apply and REFERENCE_ITERS iterations)."""
     from lsinput.workloads import two_material
-    from oracle.nystrom import naive_rows
-    from oracle.vdim import correction_matrix
-
     wl = two_material("small")
     n = wl.mesh.n_nodes
     x = np.exp(1j * wl.k * (wl.mesh.nodes @ np.array([np.cos(np.pi / 4), np.sin(np.pi / 4)])))
     f = wl.m * x
-    rows = np.arange(0, n, n // 256)[:256]
+    cores = _host_cores()
     times = []
-    for s in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        naive_rows(wl.mesh.nodes, wl.mesh.weights, wl.k, f, rows)
-        t1 = time.perf_counter()
-        correction_matrix(wl.mesh, wl.k, 3.0, rows=rows[:8])
-        t2 = time.perf_counter()
-        if s >= args.warmup:
-            times.append(((t1 - t0) / rows.size + (t2 - t1) / 8) * n * REFERENCE_ITERS)
+    with _oracle_pool(cores) as pool:
+        for s in range(args.warmup + args.steps):
+            t_ps, t_corr, _, _, _ = _oracle_sample(pool, cores, wl, f, 48, 2, s)
+            if s >= args.warmup:
+                times.append((t_ps + t_corr) * n / cores * REFERENCE_ITERS)
     t_solve = statistics.mean(times)
     value = 1.0 / t_solve
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "parallelism": "replicas"},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": f"per step: 256 pair-sum rows + 8 correction rows of one L apply, "
-                                       f"extrapolated to {n} rows x {REFERENCE_ITERS} iterations"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"per step: {48 * cores} pair-sum rows + {2 * cores} correction rows of one "
+                                       f"L apply over {cores} processes, extrapolated to {n} rows x "
+                                       f"{REFERENCE_ITERS} iterations"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- forms on their own configurations
 def precision_report(args):
-    """--workload precision: the precision form on its own configuration (two-material
-    disk at k = 40, 13,042 triangles = 195,630 nodes, 512^2 preconditioner): one FP32
-    solve and one FP64-accurate double-float solve (the reference for the error),
-    both timed with CUDA events, plus the FP32 matvec against the FP64 oracle on
-    sampled rows.  One JSON line; not part of the default run."""
+    """The precision form on its own configuration (two-material disk at k = 40, 13,042
+    triangles = 195,630 nodes, 512^2 preconditioner): FP32 solves (one warm-up, two timed
+    with CUDA events), one FP64-accurate double-float solve for the error, and the FP32
+    matvec against the oracle on sampled rows."""
     import torch
     import paper_2608_17615_b300 as L
     from lsinput.workloads import two_material
+    from oracle.operator import Operator as OracleOp
 
-    torch.cuda.set_device(0)
     wl = two_material("medium", k=40.0, nx=512, ny=512)
     n = wl.mesh.n_nodes
     t0 = time.perf_counter()
-    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, nx=wl.nx, ny=wl.ny, tol=1e-8, pairsum=2)
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, nx=wl.nx, ny=wl.ny, tol=1e-8, prec=LS_PREC_FP32)
     setup_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
     d = np.array([np.cos(np.pi / 4), np.sin(np.pi / 4)])
     b = torch.from_numpy(np.exp(1j * wl.k * (wl.mesh.nodes @ d))).cuda().view(1, -1)
-    out = {}
-    sols = {}
-    for mode, name in ((2, "fp32"), (3, "double_float")):
-        op.set_pairsum(mode)
-        u = torch.empty_like(b)
-        stream = torch.cuda.current_stream()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        it, st = op.solve_dev(b, u)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        sols[name] = u
-        out[name] = {"solve_ms": ms, "solves_per_s": 1e3 / ms, "iterations": int(it[0]), "status": int(st),
-                     "pairs_per_s": int(it[0]) * n * (n - 1) / (ms * 1e-3)}
-        print(f"[precision] setup {setup_s:.1f} s; {name}: {json.dumps(out[name])}", file=sys.stderr, flush=True)
-    out["fp32"]["rel_err_vs_double_float_solution"] = (
-        torch.linalg.norm(sols["fp32"] - sols["double_float"]) / torch.linalg.norm(sols["double_float"])).item()
-    # FP32 matvec against the oracle on sampled rows
-    from oracle.operator import Operator as OracleOp
-    op.set_pairsum(2)
+    u32, udf = torch.empty_like(b), torch.empty_like(b)
+    op.solve_dev(b, u32)                                     # warm-up
+    op.set_timing(True)
+    ms32, (it32, st32) = _timed(lambda: op.solve_dev(b, u32), stream, reps=2)
+    rl = _pairsum_roofline(op, n, FP32_PEAK_TFLOPS, FP32_PEAK_SOURCE, ms32 * 2)
+    op.set_timing(False)
+    op.set_pairsum(LS_PREC_FP64_DF)
+    msdf, (itdf, stdf) = _timed(lambda: op.solve_dev(b, udf), stream)
+    err = (torch.linalg.norm(u32 - udf) / torch.linalg.norm(udf)).item()
+    op.set_pairsum(LS_PREC_FP32)
     x = np.exp(1j * np.arange(n) * 0.37)
     y = torch.empty(n, dtype=torch.complex128, device="cuda")
     op.apply_dev(torch.from_numpy(x).cuda(), y)
     rows = np.arange(0, n, n // 24)[:24]
     ref = OracleOp(wl.mesh, wl.k, wl.m, rows_only=True).apply_rows(x, rows)
-    yv = y.cpu().numpy()[rows]
-    out["fp32"]["matvec_rel_err_vs_oracle"] = float(np.linalg.norm(yv - ref) / np.linalg.norm(ref))
-    line = {"report": "precision form", "config": {"workload": "two-material disk, k=40, 195,630 nodes "
-            "(13,042 curved P4 triangles), 512^2 Cartesian preconditioner, tol 1e-8", "nodes": n},
-            "setup_s": setup_s, "setup_parts_s": dict(zip(["correction", "grid", "block_lu", "table"],
-                                                         [round(float(t), 3) for t in op.setup_times()])),
-            "forms": out}
-    print(json.dumps(line), flush=True)
+    mv_err = float(np.linalg.norm(y.cpu().numpy()[rows] - ref) / np.linalg.norm(ref))
+    return {"config": {"workload": "two-material disk, k=40, 195,630 nodes (13,042 curved P4 triangles), 512^2 "
+                                   "Cartesian preconditioner, tol 1e-8, FP32 pair sum", "nodes": n},
+            "value": 1e3 / ms32, "unit": "solves/s", "ms": ms32, "iterations": int(it32[0]), "status": int(st32),
+            "pairs_per_s": int(it32[0] + 1) * n * (n - 1) / (ms32 * 1e-3),
+            "rel_err_vs_fp64_accurate_solution": err, "matvec_rel_err_vs_oracle_24_rows": mv_err,
+            "fp64_accurate_solve": {"ms": msdf, "iterations": int(itdf[0]), "status": int(stdf)},
+            "roofline": rl, "setup_s": setup_s,
+            "setup_parts_s": dict(zip(["correction", "grid", "preconditioner_factors", "table"],
+                                      [round(float(t), 3) for t in op.setup_times()]))}
 
 
 def batched_pairsum_report(args):
-    """--workload batched: the batched pair sum alone (two-material disk, k = 20, 40,200 nodes,
-    64 right-hand sides), tensor-core GEMM (k_pairsum_tc) against the CUDA-core kernel
-    (k_pairsum_multi_f32), each timed with CUDA events over --steps launches after
-    --warmup, with its error against the FP64 pair sum on 4 sampled right-hand sides.
-    Also the launch to profile the tensor-core kernel.  One JSON line."""
+    """The batched pair sum alone (two-material disk, k = 20, 40,200 nodes, 64 right-hand
+    sides), tensor-core GEMM (k_pairsum_tc) against the CUDA-core kernel
+    (k_pairsum_multi_f32), each timed with CUDA events over max(1, --steps) launches after
+    a warm-up, with its error against the FP64 pair sum on 4 sampled right-hand sides."""
     import torch
     import paper_2608_17615_b300 as L
     from lsinput.workloads import random_density, two_material
 
-    torch.cuda.set_device(0)
     wl = two_material("small")
     n = wl.mesh.n_nodes
     R = 64
@@ -301,57 +366,39 @@ def batched_pairsum_report(args):
         y1 = torch.empty_like(F[r])
         op.pairsum_dev(F[r].contiguous(), y1)
         ref[r] = y1
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
-    tf32_peak = peaks.get("bf16_tflops", 1800.0) * (1.1 / 2.25)
+    tf32_peak = _peaks().get("bf16_tflops", 1800.0) * (1.1 / 2.25)
     out = {}
+    stream = torch.cuda.current_stream()
     for kind, name in ((1, "tensor_cores"), (0, "cuda_cores")):
         op.set_batch_kernel(kind, 4)
-        for _ in range(max(1, args.warmup)):
-            op.pairsum_batch_dev(F, Y)
-        stream = torch.cuda.current_stream()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            op.pairsum_batch_dev(F, Y)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
+        op.pairsum_batch_dev(F, Y)
+        ms, _ = _timed(lambda: op.pairsum_batch_dev(F, Y), stream, reps=max(1, min(args.steps, 5)))
         err = max((torch.linalg.norm(Y[r] - ref[r]) / torch.linalg.norm(ref[r])).item() for r in sample)
         pairs = R * n * (n - 1)
         out[name] = {"ms_per_launch_incl_epilogue": ms, "pair_rhs_interactions_per_s": pairs / (ms * 1e-3),
                      "rel_err_vs_fp64_max_of_4": err}
         if kind == 1:
-            flops = 24.0 * pairs                       # 3 split products x 2 K-slots x 2 columns x 2 flops
-            out[name]["tensor_pipe"] = {"executed_tf32_tflops": flops / (ms * 1e-3) / 1e12,
-                                        "peak_tf32_tflops": tf32_peak,
-                                        "peak_source": "measured bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"}
-    line = {"report": "batched pair sum", "config": {"workload": "two-material disk, k=20, 40,200 nodes, "
-            "64 right-hand sides, tensor-core run length 4 stages", "nodes": n, "rhs": R},
-            "speedup_tensor_vs_cuda_cores": out["cuda_cores"]["ms_per_launch_incl_epilogue"]
-            / out["tensor_cores"]["ms_per_launch_incl_epilogue"], "forms": out}
-    print(json.dumps(line), flush=True)
+            flops = 24.0 * pairs
+            out[name]["roofline"] = {"bound": "tensor", "achieved": flops / (ms * 1e-3) / 1e12, "peak": tf32_peak,
+                                     "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / 1e12 / tf32_peak,
+                                     "peak_source": "measured bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"}
+    return {"config": {"workload": "two-material disk, k=20, 40,200 nodes, 64 right-hand sides", "nodes": n,
+                       "rhs": R}, "forms": out}
 
 
 BATCH_NODES = (5000, 8000, 14000, 22000, 34000, 50000, 72000, 100000)
 
 
 def batching_report(args):
-    """--workload batching: the batching form's configuration, 8 star-shaped scatterers of
-    uneven size (5k-100k nodes, k = 10, 20, 40 in turn, grids at k h_C ~ 0.19), 64 incident
-    directions each, all solved in lock step with one persistent pair-sum launch per
-    iteration (ls_solve_multi_dev), once on the tensor cores and once on the CUDA cores;
-    error of direction 0 of every scatterer against its FP64-accurate double-float solve.
-    One JSON line; not part of the default run."""
+    """The batching form's configuration: 8 star-shaped scatterers of uneven size (5k-100k
+    nodes, k = 10, 20, 40 in turn, grids at k h_C ~ 0.19), 64 incident directions each, all
+    solved in lock step with one persistent pair-sum launch per iteration
+    (ls_solve_multi_dev) on the tensor cores; error of direction 0 of every scatterer
+    against its FP64-accurate double-float solve."""
     import torch
     import paper_2608_17615_b300 as L
     from lsinput.workloads import star_scatterer
 
-    torch.cuda.set_device(0)
     R = 64
     ops, B, wls, setup = [], [], [], 0.0
     for s, nn in enumerate(BATCH_NODES):
@@ -367,66 +414,51 @@ def batching_report(args):
         ops.append(op)
         B.append(b)
         wls.append(wl)
-        print(f"[batching] scatterer {s}: {wl.mesh.n_nodes} nodes, k={k}, grid {nx}^2", file=sys.stderr, flush=True)
+        print(f"[batching] scatterer {s}: {wl.mesh.n_nodes} nodes, k={k}, grid {nx}^2, setup {setup:.1f} s",
+              file=sys.stderr, flush=True)
     n_s = [w.mesh.n_nodes for w in wls]
-    out = {}
-    sols = {}
-    for kind, name in ((1, "tensor_cores"), (0, "cuda_cores")):
-        for op in ops:
-            op.set_batch_kernel(kind)
-        U = [torch.empty_like(b) for b in B]
-        L.solve_multi_dev(ops, B, U)                   # warm-up (grid autotune, buffers)
-        stream = torch.cuda.current_stream()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        iters, st = L.solve_multi_dev(ops, B, U)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        it = np.asarray(iters)
-        pairs = float(sum(int(it[s].max()) * R * n * (n - 1) for s, n in enumerate(n_s)))
-        out[name] = {"ms": ms, "solves_per_s": len(ops) * R / (ms * 1e-3), "status": int(st),
-                     "iterations_max_per_scatterer": [int(x.max()) for x in it],
-                     "pair_interactions_per_s": pairs / (ms * 1e-3)}
-        print(f"[batching] setup {setup:.1f} s; {name}: {json.dumps(out[name])}", file=sys.stderr, flush=True)
-        sols[name] = [u[0].clone() for u in U]
+    stream = torch.cuda.current_stream()
+    for op in ops:
+        op.set_batch_kernel(1)
+    U = [torch.empty_like(b) for b in B]
+    L.solve_multi_dev(ops, B, U)                   # warm-up (workspace)
+    ms, (iters, st) = _timed(lambda: L.solve_multi_dev(ops, B, U), stream)
+    it = np.asarray(iters)
+    pairs = float(sum(int(it[s].max()) * R * n * (n - 1) for s, n in enumerate(n_s)))
     errs = []
     for s, op in enumerate(ops):
-        op.set_pairsum(3)
+        op.set_pairsum(LS_PREC_FP64_DF)
         u1 = torch.empty_like(B[s][0]).view(1, -1)
         op.solve_dev(B[s][0].contiguous().view(1, -1), u1)
-        ref = u1[0]
-        errs.append({name: (torch.linalg.norm(sols[name][s] - ref) / torch.linalg.norm(ref)).item() for name in sols})
-    for name in sols:
-        out[name]["rel_err_vs_fp64_accurate_dir0_max"] = max(e[name] for e in errs)
-    line = {"report": "batching form", "config": {"workload": "8 star scatterers (r = 1 + 0.2 cos(5 theta + phi)), "
-            f"nodes {n_s}, k = 10/20/40, 64 directions each, tol 1e-8", "nodes": n_s, "rhs_per_scatterer": R},
-            "setup_s": setup, "forms": out}
-    print(json.dumps(line), flush=True)
+        errs.append((torch.linalg.norm(U[s][0] - u1[0]) / torch.linalg.norm(u1[0])).item())
+    return {"config": {"workload": "8 star scatterers (r = 1 + 0.2 cos(5 theta + phi)), nodes "
+                                   f"{n_s}, k = 10/20/40, 64 directions each, tol 1e-8, tensor-core batched",
+                       "nodes": n_s, "rhs_per_scatterer": R},
+            "value": len(ops) * R / (ms * 1e-3), "unit": "solves/s", "ms": ms, "status": int(st),
+            "iterations_max_per_scatterer": [int(x.max()) for x in it],
+            "pair_rhs_interactions_per_s": pairs / (ms * 1e-3),
+            "rel_err_vs_fp64_accurate_dir0_max": max(errs), "setup_s": setup}
 
 
 def gradient_report(args):
-    """--workload gradient: the differentiation form's configuration (two-material disk,
-    k = 40, 32,830 curved triangles = 492,450 nodes, 512^2 preconditioner): gradient of
-    the far-field misfit 1/2 sum |u_inf - t|^2 over 16 incident directions and 32
-    receivers with respect to every nodal contrast, the target t made by a forward solve
-    with a Gaussian blob added to the index; forward and adjoint solves batched over the
-    16 directions.  One gradient after a warm-up, timed with the host clock around the
-    synchronised forward + backward.  One JSON line; the finite-difference check of the
-    gradient runs in the GPU tests on smaller meshes."""
+    """The differentiation form's configuration (two-material disk, k = 40, 32,830 curved
+    triangles = 492,450 nodes, 512^2 preconditioner): gradient of the far-field misfit
+    1/2 sum |u_inf - t|^2 over 16 incident directions and 32 receivers with respect to
+    every nodal contrast, the target t made by a forward solve with a Gaussian blob added
+    to the index; forward and adjoint solves batched over the 16 directions.  One
+    gradient, timed with the host clock around the synchronised forward + backward (the
+    target solve is the warm-up).  The finite-difference check of the gradient runs in the
+    GPU tests on smaller meshes."""
     import torch
     import paper_2608_17615_b300 as L
     from lsinput.workloads import perturbed_contrast, two_material
     from paper_2608_17615_b300.misfit import far_field_misfit
 
-    torch.cuda.set_device(0)
     wl = two_material("large", k=40.0, nx=512, ny=512)
     n = wl.mesh.n_nodes
     t0 = time.perf_counter()
     op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, nx=512, ny=512, tol=1e-8)
     setup_s = time.perf_counter() - t0
-    print(f"[gradient] setup {setup_s:.1f} s {op.setup_times()}", file=sys.stderr, flush=True)
     dirs = 2 * np.pi * np.arange(16) / 16
     ff = 2 * np.pi * np.arange(32) / 32
     B = torch.empty((16, n), dtype=torch.complex128, device="cuda")
@@ -440,22 +472,32 @@ def gradient_report(args):
     t_target = time.perf_counter() - t1
     op.set_contrast(wl.m)
     m_t = torch.from_numpy(np.ascontiguousarray(np.real(wl.m), np.float64)).cuda().requires_grad_(True)
-    (g,) = torch.autograd.grad(far_field_misfit(m_t, op, dirs, ff, uinf_t, batched=True), m_t)   # warm-up
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     J = far_field_misfit(m_t, op, dirs, ff, uinf_t, batched=True)
     (g,) = torch.autograd.grad(J, m_t)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t2
-    line = {"report": "differentiation form", "config": {"workload": "two-material disk, k=40, 492,450 nodes "
-            "(32,830 curved P4 triangles), 512^2 Cartesian preconditioner, 16 directions x 32 receivers, "
-            "target: +0.05 Gaussian blob at (-0.3, -0.2)", "nodes": n},
-            "setup_s": setup_s, "setup_parts_s": dict(zip(["correction", "grid", "block_lu", "table"],
-                                                         [round(float(t), 3) for t in op.setup_times()])),
-            "target_solve_s": t_target, "target_iterations_max": int(np.max(it_t)),
+    return {"config": {"workload": "two-material disk, k=40, 492,450 nodes (32,830 curved P4 triangles), 512^2 "
+                                   "Cartesian preconditioner, 16 directions x 32 receivers, target: +0.05 Gaussian "
+                                   "blob at (-0.3, -0.2)", "nodes": n},
             "value": 1.0 / dt, "unit": "gradients/s", "seconds": dt, "misfit": float(J.item()),
-            "grad_norm": float(torch.linalg.norm(g).item())}
-    print(json.dumps(line), flush=True)
+            "grad_norm": float(torch.linalg.norm(g).item()), "target_solve_s": t_target,
+            "target_iterations_max": int(np.max(it_t)), "setup_s": setup_s,
+            "setup_parts_s": dict(zip(["correction", "grid", "preconditioner_factors", "table"],
+                                      [round(float(t), 3) for t in op.setup_times()])),
+            "timing": "host wall clock around the synchronised forward + backward"}
+
+
+def _form(forms, key, fn):
+    """Run one form; its failure is recorded instead of costing the bench line."""
+    t0 = time.perf_counter()
+    try:
+        forms[key] = fn()
+    except Exception as exc:
+        forms[key] = {"error": f"{type(exc).__name__}: {str(exc)[:300]}"}
+    forms[key]["wall_s"] = round(time.perf_counter() - t0, 1)
+    print(f"[bench] {key}: {json.dumps(forms[key])[:600]}", file=sys.stderr, flush=True)
 
 
 def main():
@@ -465,25 +507,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large-forms", action="store_true", help="skip the 195k / 8-scatterer / 492k forms")
     ap.add_argument("--workload", default="default", choices=["default", "precision", "batching", "batched",
                                                                  "gradient"])
     args = ap.parse_args()
     rank, world, local = _env_rank()
-    if args.workload == "precision":
+    reports = {"precision": precision_report, "batching": batching_report, "batched": batched_pairsum_report,
+               "gradient": gradient_report}
+    if args.workload in reports:
         if rank == 0:
-            precision_report(args)
-        return
-    if args.workload == "batching":
-        if rank == 0:
-            batching_report(args)
-        return
-    if args.workload == "batched":
-        if rank == 0:
-            batched_pairsum_report(args)
-        return
-    if args.workload == "gradient":
-        if rank == 0:
-            gradient_report(args)
+            import torch
+            torch.cuda.set_device(0)
+            print(json.dumps({"report": args.workload, **reports[args.workload](args)}), flush=True)
         return
     if args.impl == "reference":
         if rank == 0:
@@ -502,12 +537,13 @@ def main():
     wl = two_material("small")
     n = wl.mesh.n_nodes
     t0 = time.perf_counter()
-    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, tol=1e-8)
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, tol=1e-8, prec=LS_PREC_FP64_DF)
     setup_s = time.perf_counter() - t0
-    fp64_peak = L.probe_fp64()
-    setup_parts = {k: round(float(v), 3) for k, v in zip(["correction", "grid", "block_lu", "table"], op.setup_times())}
-    print(f"[bench] setup {setup_s:.1f} s {setup_parts}, FP64 probe {fp64_peak:.1f} GFLOP/s", file=sys.stderr, flush=True)
-    # each rank solves its own direction (replicas)
+    fp64_probe = L.probe_fp64()
+    setup_parts = {k: round(float(v), 3) for k, v in
+                   zip(["correction", "grid", "preconditioner_factors", "table"], op.setup_times())}
+    print(f"[bench] setup {setup_s:.1f} s {setup_parts}, FP64 probe {fp64_probe:.1f} GFLOP/s", file=sys.stderr,
+          flush=True)
     angle = rank_direction(rank, world)
     d = np.array([np.cos(angle), np.sin(angle)])
     b = torch.from_numpy(np.exp(1j * wl.k * (wl.mesh.nodes @ d))).cuda()
@@ -540,24 +576,15 @@ def main():
     if dist:
         dist.barrier()
     ps_ms, ps_launches, launches = op.stats()
+    exit_res = op.last_residual()
     print(f"[bench] steps ms {step_ms}, iters {iters_list}, pair-sum {ps_ms:.1f} ms / {ps_launches} launches",
           file=sys.stderr, flush=True)
-    op.set_timing(False)
     total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     iters = statistics.mean(iters_list)
     value = aggregate_value(world, args.steps, total_ms)
-    pairs_per_solve = iters * n * (n - 1)
-    # roofline of the pair-sum kernel (FP64 ALU bound)
-    avg_launch_s = ps_ms / max(ps_launches, 1) * 1e-3
-    nc_tab, tune_ms = op.tuning()
-    flops_per_pair = flops_per_pair_of(op.params.pairsum, nc_tab)
-    achieved = flops_per_pair * n * (n - 1) / avg_launch_s / 1e12
-    peak = fp64_peak / 1e3
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": TRAFFIC.get(op.params.pairsum), "kernel": KERNEL[op.params.pairsum],
-                "flops_per_pair": flops_per_pair, "table_ncoef": nc_tab, "tuning_ms": list(tune_ms),
-                "peak_source": "measured FP64 FMA probe (ls_probe_fp64), same run",
-                "kernel_ms_per_launch": avg_launch_s * 1e3, "kernel_share_of_step": ps_ms / total_ms}
+    pairs_per_solve = (iters + 1) * n * (n - 1)
+    roofline = _pairsum_roofline(op, n, FP32_PEAK_TFLOPS, FP32_PEAK_SOURCE, total_ms)
+    op.set_timing(False)
     # end to end through the host-buffer entry point
     e2e_ms = []
     for _ in range(args.steps):
@@ -568,130 +595,96 @@ def main():
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e = {"value": world * args.steps / (sum(e2e_ms) * 1e-3), "unit": "solves/s",
            "h2d_bytes_per_step": 8 * (1 + n_ff), "d2h_bytes_per_step": 16 * n + 16 * n_ff + 8 * (int(it_h[0]) + 1)}
-    # precision form on the same operator (FP32 pair sum), timed the same way
     forms = {}
-    op.set_pairsum(2)
-    u32 = torch.empty_like(u)
-    op.solve_dev(b.view(1, -1), u32.view(1, -1))
-    ms32, it32 = [], []
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        it, st = op.solve_dev(b.view(1, -1), u32.view(1, -1), wl.ff_angles, uinf.view(1, -1))
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms32.append(e0.elapsed_time(e1))
-        it32.append(int(it[0]))
-    rel32 = (torch.linalg.norm(u32 - u) / torch.linalg.norm(u)).item()
-    forms["fp32_pairsum"] = {"value": args.steps / (sum(ms32) * 1e-3), "unit": "solves/s", "iterations": it32[0],
-                             "rel_err_vs_fp64_solution": rel32,
-                             "pairs_per_s": it32[0] * n * (n - 1) * args.steps / (sum(ms32) * 1e-3)}
-    # FP64-accurate double-float pair sum on the same operator
-    op.set_pairsum(3)
-    op.solve_dev(b.view(1, -1), u32.view(1, -1))
-    msd, itd = [], []
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        it, st = op.solve_dev(b.view(1, -1), u32.view(1, -1), wl.ff_angles, uinf.view(1, -1))
-        e1.record(stream)
-        torch.cuda.synchronize()
-        msd.append(e0.elapsed_time(e1))
-        itd.append(int(it[0]))
-    reld = (torch.linalg.norm(u32 - u) / torch.linalg.norm(u)).item()
-    forms["df_pairsum"] = {"value": args.steps / (sum(msd) * 1e-3), "unit": "solves/s", "iterations": itd[0],
-                           "rel_err_vs_fp64_solution": reld,
-                           "pairs_per_s": itd[0] * n * (n - 1) * args.steps / (sum(msd) * 1e-3)}
-    op.set_pairsum(0)
-    # batching form on the same operator: 64 incident directions (the bench direction among
-    # them) in one lock-step solve, on the tensor cores (with refinement) and on the CUDA cores
-    R64 = 64
-    dirs64 = rank_direction(rank, world) + 2 * np.pi * np.arange(R64) / R64
-    B64 = torch.empty((R64, n), dtype=torch.complex128, device=u.device)
-    op.incident_dev(dirs64, B64)
-    U64 = torch.empty_like(B64)
-    for kind, name in ((1, "batched_tensor_cores_64rhs"), (0, "batched_cuda_cores_64rhs")):
-        op.set_batch_kernel(kind)
-        op.solve_batch_dev(B64, U64)                          # warm-up (workspace)
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        it64, st64 = op.solve_batch_dev(B64, U64)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1)
-        forms[name] = {"value": R64 / (ms64 * 1e-3), "unit": "solves/s", "rhs": R64, "status": int(st64),
-                       "iterations_max": int(np.max(it64)),
-                       "rel_err_vs_fp64_solution": (torch.linalg.norm(U64[0] - u) / torch.linalg.norm(u)).item()}
-    op.set_batch_kernel(1)
-    # differentiation form on the same operator: gradient of the far-field misfit with respect
-    # to the nodal contrast for 16 directions and 32 receivers (batched forward and adjoint
-    # solves on the tensor cores, then V^T lambda per direction in FP64), once after a warm-up
-    try:
-        from paper_2608_17615_b300.misfit import far_field_misfit
-        dirs16 = rank_direction(rank, world) + 2 * np.pi * np.arange(16) / 16
-        ff32 = 2 * np.pi * np.arange(32) / 32
-        m_t = torch.from_numpy(np.ascontiguousarray(np.real(wl.m), np.float64)).to(u.device).requires_grad_(True)
-        tg = torch.zeros((16, 32), dtype=torch.complex128, device=u.device)
-        (gr,) = torch.autograd.grad(far_field_misfit(m_t, op, dirs16, ff32, tg, batched=True), m_t)   # warm-up
-        torch.cuda.synchronize()
-        t_g = time.perf_counter()
-        Jg = far_field_misfit(m_t, op, dirs16, ff32, tg, batched=True)
-        (gr,) = torch.autograd.grad(Jg, m_t)
-        torch.cuda.synchronize()
-        dt_g = time.perf_counter() - t_g
-        forms["gradient_16dirs_32receivers"] = {"value": 1.0 / dt_g, "unit": "gradients/s", "seconds": dt_g,
-                                                "misfit": float(Jg.item()),
-                                                "grad_norm": float(torch.linalg.norm(gr).item()),
-                                                "timing": "host wall clock around forward + backward, synchronised"}
-    except Exception as exc:                        # a form's failure must not cost the bench line
-        forms["gradient_16dirs_32receivers"] = {"error": f"{type(exc).__name__}: {str(exc)[:200]}"}
+
+    def pipe_form(mode, label, peak, peak_source):
+        op.set_pairsum(mode)
+        uu = torch.empty_like(u)
+        op.solve_dev(b.view(1, -1), uu.view(1, -1))
+        op.set_timing(True)
+        reps = 3
+        ms, (it_, st_) = _timed(lambda: op.solve_dev(b.view(1, -1), uu.view(1, -1), wl.ff_angles, uinf.view(1, -1)),
+                                stream, reps=reps)
+        rl = _pairsum_roofline(op, n, peak, peak_source, ms * reps)
+        op.set_timing(False)
+        return {"config": {"workload": WORKLOAD + ", " + label}, "value": 1e3 / ms, "unit": "solves/s", "ms": ms,
+                "iterations": int(it_[0]), "status": int(st_),
+                "rel_err_vs_fp64_accurate_solution": (torch.linalg.norm(uu - u) / torch.linalg.norm(u)).item(),
+                "pairs_per_s": (int(it_[0]) + 1) * n * (n - 1) / (ms * 1e-3), "roofline": rl}
+
+    _form(forms, "cfg2_fp64_pipe",
+          lambda: dict(pipe_form(LS_PREC_FP64_TABLE, "FP64-pipe table pair sum", fp64_probe / 1e3,
+                                 "measured FP64 FMA probe (ls_probe_fp64), same run"),
+                       fp64_unit_count_peak_tflops=FP64_UNIT_PEAK_TFLOPS))
+    _form(forms, "cfg2_fp32", lambda: pipe_form(LS_PREC_FP32, "FP32 precision-form pair sum", FP32_PEAK_TFLOPS,
+                                                FP32_PEAK_SOURCE))
+    op.set_pairsum(LS_PREC_FP64_DF)
+
+    def batched_forms():
+        R64 = 64
+        dirs64 = rank_direction(rank, world) + 2 * np.pi * np.arange(R64) / R64
+        B64 = torch.empty((R64, n), dtype=torch.complex128, device=u.device)
+        op.incident_dev(dirs64, B64)
+        U64 = torch.empty_like(B64)
+        out = {}
+        for kind, name in ((1, "tensor_cores"), (0, "cuda_cores")):
+            op.set_batch_kernel(kind)
+            op.solve_batch_dev(B64, U64)                              # warm-up (workspace)
+            ms64, (it64, st64) = _timed(lambda: op.solve_batch_dev(B64, U64), stream)
+            out[name] = {"value": R64 / (ms64 * 1e-3), "unit": "solves/s", "ms": ms64, "status": int(st64),
+                         "iterations_max": int(np.max(it64)),
+                         "rel_err_vs_fp64_accurate_solution":
+                             (torch.linalg.norm(U64[0] - u) / torch.linalg.norm(u)).item()}
+        op.set_batch_kernel(1)
+        out["config"] = {"workload": WORKLOAD + ", 64 incident directions in lock step"}
+        return out
+
+    _form(forms, "cfg2_batched_64rhs", batched_forms)
+    _form(forms, "cfg2_batched_pairsum_64rhs", lambda: batched_pairsum_report(args))
+
+    def approach_form():
+        out = {}
+        for approach in (2, 1):
+            opa = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, tol=1e-8, prec=LS_PREC_FP32, approach=approach)
+            ua = torch.empty_like(u)
+            opa.solve_dev(b.view(1, -1), ua.view(1, -1))
+            ms, (it_, st_) = _timed(lambda: opa.solve_dev(b.view(1, -1), ua.view(1, -1)), stream)
+            out[f"approach_{approach}"] = {"iterations": int(it_[0]), "status": int(st_), "ms": ms,
+                                           "rel_err_vs_fp64_accurate_solution":
+                                               (torch.linalg.norm(ua - u) / torch.linalg.norm(u)).item()}
+            del opa
+        out["config"] = {"workload": WORKLOAD + ", FP32 pair sum, Approach I vs II transfer (Table bakeoff context)"}
+        return out
+
+    _form(forms, "cfg2_approach_I_vs_II", approach_form)
+    del flush
+    if not args.no_large_forms and rank == 0:
+        _form(forms, "cfg3_precision_k40_195k", lambda: precision_report(args))
+        _form(forms, "cfg4_batching_8_scatterers", lambda: batching_report(args))
+        _form(forms, "cfg5_differentiation_492k", lambda: gradient_report(args))
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64-accurate: double-float pair sum on the FP32 pipe, FP64 correction, preconditioner and Krylov",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "nodes": n, "k": wl.k, "grid": [wl.nx, wl.ny],
                        "l2": "flushed (512 MB write) before every timed step", "parallelism": "replicas"},
-            "iterations": iters, "pairs_per_s": world * pairs_per_solve * args.steps / (total_ms * 1e-3),
-            "matvecs_per_s": world * iters * args.steps / (total_ms * 1e-3), "setup_s": setup_s, "setup_parts_s": setup_parts,
-            "wall_s_timed": wall, "roofline": roofline, "gpu_launches": launches, "clocks": clocks.summary(),
-            "e2e": e2e, "forms": forms}
+            "iterations": iters, "explicit_exit_residual": exit_res,
+            "pairs_per_s": world * pairs_per_solve * args.steps / (total_ms * 1e-3),
+            "matvecs_per_s": world * (iters + 1) * args.steps / (total_ms * 1e-3), "setup_s": setup_s,
+            "setup_parts_s": setup_parts, "wall_s_timed": wall, "roofline": roofline, "gpu_launches": launches,
+            "clocks": clocks.summary(), "e2e": e2e, "forms": forms}
     if rank == 0 and not args.no_cpu_baseline:
         Lu = torch.empty_like(u)
         op.apply_dev(u, Lu)
         cb, err = cpu_baseline(wl, u.cpu().numpy(), Lu.cpu().numpy(), int(round(iters)))
         line["cpu_baseline"] = cb
-        if err is not None:
-            line["matvec_rel_err_vs_oracle"] = err
+        line["matvec_rel_err_vs_oracle"] = err
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
-
-# Floating-point operations per pair of each pair-sum kernel (FMA = 2).
-#  0 k_pairsum_tab (FP64): dx, dy 2; t = dx^2 + dy^2 3; u 2; two degree-11
-#    Horner chains 44; complex multiply-accumulate 8 -> 59
-#  1 k_pairsum (FP64, direct): 89 FP64 instructions per pair measured by ncu
-#    (58.5 DFMA, 23.5 DMUL, 7.1 DADD) -> 148
-#  2 k_pairsum_f32 (FP32): two double-float differences 22, double-float t 16,
-#    u 4, two degree-6 Horner chains 24, complex multiply 6, Kahan sums 8 -> 80
-#  3 k_pairsum_df (double-float on FP32): differences 22, t 12, u 8, two degree-11
-#    DF Horner chains 2 x 11 x 15 = 330, DF complex multiply-accumulate 60 -> 432
-FLOPS_PER_PAIR = {0: 59, 1: 148, 2: 80, 3: 432}
-
-
-def flops_per_pair_of(mode, nc):
-    """Source count for the table degree in use (nc coefficients per cell)."""
-    if mode == 0:
-        return 15 + 4 * (nc - 1)            # 59 at nc = 12
-    if mode == 3:
-        return 102 + 30 * (nc - 1)          # 432 at nc = 12
-    return FLOPS_PER_PAIR[mode]
-KERNEL = {0: "k_pairsum_tab", 1: "k_pairsum", 2: "k_pairsum_f32", 3: "k_pairsum_df"}
-# dram__bytes_read + write per launch from ncu captures of the current kernels (None until captured)
-TRAFFIC = {}
 
 if __name__ == "__main__":
     main()

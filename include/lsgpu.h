@@ -449,8 +449,11 @@ ls_status ls_op_set_timing(ls_op* op, int32_t on);
    (host), [2] block LU of C and its transposes (device), [3] H0 table. */
 ls_status ls_op_setup_times(const ls_op* op, double* t4);
 /* Pair-sum autotuner result: coefficients per cell of the H0 table in use and the timed
-   pair-sum launch (ms) of the 12-, 10- and 9-coefficient candidates (0 = not tried). */
-ls_status ls_op_tuning(const ls_op* op, int32_t* table_ncoef, double* cand_ms);
+   pair-sum launch (ms, scaled from a bounded sample of sources) of the 12-, 10-, 9- and
+   (double-float form only) 8-coefficient candidates, cand_ms [4] (0 = not tried); *fp32_tail:
+   in the double-float form, the top coefficients of each Horner chain summed in plain FP32
+   (their terms stay below 2^-50 of |H0| on every cell; 0 otherwise).  Pointers may be NULL. */
+ls_status ls_op_tuning(const ls_op* op, int32_t* table_ncoef, double* cand_ms, int32_t* fp32_tail);
 ls_status ls_op_stats(ls_op* op, double* pairsum_ms, int64_t* pairsum_launches, int64_t* launches);
 
 /* Diagnostic: measured FP64 FMA throughput of the device in GFLOP/s (2 flops per FMA). */

@@ -111,7 +111,7 @@ def _load():
         "ls_op_set_pairsum": (I32, [P, I32]),
         "ls_op_set_timing": (I32, [P, I32]),
         "ls_op_setup_times": (I32, [P, P]),
-        "ls_op_tuning": (I32, [P, P, P]),
+        "ls_op_tuning": (I32, [P, P, P, P]),
         "ls_op_stats": (I32, [P, P, P, P]),
         "ls_probe_fp64": (I32, [P, P]),
         "ls_pairsum_noalloc": (I32, [I32, P, P, P, D, P, P]),
@@ -414,11 +414,17 @@ class Operator:
         return tuple(t)
 
     def tuning(self):
-        """(table coefficients per cell in use, timed ms of the 12/10/9-coefficient candidates)."""
+        """(table coefficients per cell in use, timed ms of the 12/10/9/8-coefficient candidates)."""
         nc = ctypes.c_int32()
-        ms = np.zeros(3)
-        _check(_lib.ls_op_tuning(self.handle, ctypes.byref(nc), _ptr(ms)))
+        ms = np.zeros(4)
+        _check(_lib.ls_op_tuning(self.handle, ctypes.byref(nc), _ptr(ms), None))
         return nc.value, tuple(ms)
+
+    def df_tail(self):
+        """Double-float form: Horner coefficients summed in plain FP32 (per chain)."""
+        nf = ctypes.c_int32()
+        _check(_lib.ls_op_tuning(self.handle, None, None, ctypes.byref(nf)))
+        return nf.value
 
     def stats(self):
         """(pair-sum kernel ms, pair-sum launches, kernel launches) since the last set_timing."""

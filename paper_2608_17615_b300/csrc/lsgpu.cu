@@ -424,7 +424,10 @@ __device__ __forceinline__ DF df_from(double x) {
 
 struct DFTile { float4 xy; float4 s; };     // (x_h, x_l, y_h, y_l), (s_re_h, s_re_l, s_im_h, s_im_l)
 
-template <int NC_TAB>
+// NF > 0: the top NF coefficients of the Horner chain (whose terms are below 2^-24 of |H0|
+// on every cell, checked when the table is uploaded) are summed in plain FP32, the rest in
+// double-float.
+template <int NC_TAB, int NF>
 __global__ void __launch_bounds__(PS_TPB) k_pairsum_df(const double2* __restrict__ xy, const double* __restrict__ w,
                                                        const double2* __restrict__ m, const double2* __restrict__ f,
                                                        int n, int src_per_chunk, double k, double inv_k,
@@ -491,10 +494,22 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum_df(const double2* __restrict
                 DF u = DF{d0 * cv.z, d1 * cv.z};                // times a power of two: exact
                 const float4* c = coef + (size_t)cell * NC_TAB;
                 float4 cc = c[NC_TAB - 1];
-                hr = DF{cc.x, cc.y};
-                hi = DF{cc.z, cc.w};
+                if (NF > 0) {
+                    float yr = cc.x, yi = cc.z;
 #pragma unroll
-                for (int e = NC_TAB - 2; e >= 0; --e) {
+                    for (int e = NC_TAB - 2; e >= NC_TAB - NF; --e) {
+                        cc = c[e];
+                        yr = fmaf(yr, u.h, cc.x);
+                        yi = fmaf(yi, u.h, cc.z);
+                    }
+                    hr = DF{yr, 0.f};
+                    hi = DF{yi, 0.f};
+                } else {
+                    hr = DF{cc.x, cc.y};
+                    hi = DF{cc.z, cc.w};
+                }
+#pragma unroll
+                for (int e = (NF > 0 ? NC_TAB - NF : NC_TAB - 1) - 1; e >= 0; --e) {
                     cc = c[e];
                     hr = df_mad(hr, u, DF{cc.x, cc.y});
                     hi = df_mad(hi, u, DF{cc.z, cc.w});
@@ -1709,7 +1724,8 @@ struct ls_op {
     int mode = 0;
     bool use_table = false;
     int tab_nc = 12;                     // table degree + 1 chosen by the setup autotuner
-    float tune_ms[3] = {0, 0, 0};        // pair-sum time of the NC = 12, 10, 9 candidates (0: not tried)
+    int tab_nf = 0;                      // double-float form: top coefficients summed in FP32
+    float tune_ms[4] = {0, 0, 0, 0};     // pair-sum time of the NC = 12, 10, 9 (, 8) candidates (0: not tried)
     int tab_ncell = 0, tab_noct = 0, tab_blo = 0;
     size_t tab_bytes = 0;
     double tab_err = 0, tab_tlo = 0, tab_thi = 0;
@@ -1806,21 +1822,38 @@ static void launch_tab(int nc, dim3 grid, size_t smem, cudaStream_t st, const do
     else k_pairsum_tab<12><<<grid, PS_TPB, smem, st>>>(xy, w, m, f, n, spc, k, ik, tab, ncell, noct, blo, partial);
 }
 
-static void launch_df(int nc, dim3 grid, size_t smem, cudaStream_t st, const double2* xy, const double* w,
+static void launch_df(int nc, int nf, dim3 grid, size_t smem, cudaStream_t st, const double2* xy, const double* w,
                       const double2* m, const double2* f, int n, int spc, double k, const float4* tab, int ncell,
                       int noct, int blo, double2* partial) {
     const double ik = 1.0 / k;
-    if (nc == 9) k_pairsum_df<9><<<grid, PS_TPB, smem, st>>>(xy, w, m, f, n, spc, k, ik, tab, ncell, noct, blo, partial);
-    else if (nc == 10) k_pairsum_df<10><<<grid, PS_TPB, smem, st>>>(xy, w, m, f, n, spc, k, ik, tab, ncell, noct, blo, partial);
-    else k_pairsum_df<12><<<grid, PS_TPB, smem, st>>>(xy, w, m, f, n, spc, k, ik, tab, ncell, noct, blo, partial);
+#define LS_DF_LAUNCH(NC, NF) k_pairsum_df<NC, NF><<<grid, PS_TPB, smem, st>>>(xy, w, m, f, n, spc, k, ik, tab, ncell, noct, blo, partial)
+#define LS_DF_NC(NC)                          \
+    do {                                      \
+        if (nf >= 4) LS_DF_LAUNCH(NC, 4);     \
+        else if (nf >= 2) LS_DF_LAUNCH(NC, 2); \
+        else LS_DF_LAUNCH(NC, 0);             \
+    } while (0)
+    if (nc == 8) LS_DF_NC(8);
+    else if (nc == 9) LS_DF_NC(9);
+    else if (nc == 10) LS_DF_NC(10);
+    else LS_DF_NC(12);
+#undef LS_DF_NC
+#undef LS_DF_LAUNCH
 }
 
 static cudaError_t raise_tab_limits(int mode, size_t bytes) {
     cudaError_t e = cudaSuccess;
     if (mode == 3) {
-        if ((e = raise_smem_limit(k_pairsum_df<9>, bytes)) != cudaSuccess) return e;
-        if ((e = raise_smem_limit(k_pairsum_df<10>, bytes)) != cudaSuccess) return e;
-        return raise_smem_limit(k_pairsum_df<12>, bytes);
+#define LS_DF_RAISE(NC)                                                                        \
+        if ((e = raise_smem_limit(k_pairsum_df<NC, 0>, bytes)) != cudaSuccess) return e;      \
+        if ((e = raise_smem_limit(k_pairsum_df<NC, 2>, bytes)) != cudaSuccess) return e;      \
+        if ((e = raise_smem_limit(k_pairsum_df<NC, 4>, bytes)) != cudaSuccess) return e;
+        LS_DF_RAISE(8)
+        LS_DF_RAISE(9)
+        LS_DF_RAISE(10)
+        LS_DF_RAISE(12)
+#undef LS_DF_RAISE
+        return cudaSuccess;
     }
     if ((e = raise_smem_limit(k_pairsum_tab<9>, bytes)) != cudaSuccess) return e;
     if ((e = raise_smem_limit(k_pairsum_tab<10>, bytes)) != cudaSuccess) return e;
@@ -1841,7 +1874,7 @@ static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m, c
         CK(cudaEventRecord(e0, op->stream));
     }
     if (op->mode == 3)
-        launch_df(op->tab_nc, grid, op->tab_bytes, op->stream, op->xy.p, w, m, f, op->nq, op->src_per_chunk, op->k,
+        launch_df(op->tab_nc, op->tab_nf, grid, op->tab_bytes, op->stream, op->xy.p, w, m, f, op->nq, op->src_per_chunk, op->k,
                   (const float4*)op->tab.p, op->tab_ncell, op->tab_noct, op->tab_blo, op->partial.p);
     else if (op->mode == 2)
         k_pairsum_f32<<<grid, PS_TPB, op->tab_bytes, op->stream>>>(op->xy.p, w, m, f, op->nq, op->src_per_chunk,
@@ -2591,6 +2624,28 @@ static ls_status upload_table(ls_op* op, const lsgpu::H0Table& T, int nc, int mo
         int2* oct = reinterpret_cast<int2*>(hd.data() + (size_t)ncell * (nc + 1));
         for (int o = 0; o < T.noct; ++o) oct[o] = make_int2(T.oct_base[o], T.oct_shift[o] + 3);
         op->tab_blo = T.b_lo - 1023 + 127;
+        // FP32 tail: the top nf coefficients may be summed in FP32 when, on every cell, their
+        // total magnitude (|u| <= 1) times nf 2^-24 stays below 2^-50 of |H0| on the cell (its
+        // smallest value at 17 equispaced samples; H0 has no zero on a cell of the table range)
+        op->tab_nf = 0;
+        for (int nf : {4, 2}) {
+            if (nf >= nc - 2) continue;
+            bool ok = true;
+            for (int c = 0; c < ncell && ok; ++c) {
+                const std::complex<double>* cc = &T.coef[(size_t)c * nc];
+                double tail = 0;
+                for (int e = nc - nf; e < nc; ++e) tail += std::abs(cc[e]);
+                double hmin = 1e300;
+                for (int q = 0; q <= 16; ++q) {
+                    const double u = -1.0 + q / 8.0;
+                    std::complex<double> p = 0;
+                    for (int e = nc - 1; e >= 0; --e) p = p * u + cc[e];
+                    hmin = std::min(hmin, std::abs(p));
+                }
+                ok = tail * nf * std::ldexp(1.0, -24) <= std::ldexp(1.0, -50) * hmin;
+            }
+            if (ok) { op->tab_nf = nf; break; }
+        }
         op->tab_bytes = hd.size() * sizeof(float4);
         CK(op->tab.alloc((op->tab_bytes + sizeof(double2) - 1) / sizeof(double2)));
         CK(cudaMemcpy(op->tab.p, hd.data(), op->tab_bytes, cudaMemcpyHostToDevice));
@@ -2629,7 +2684,8 @@ static ls_status build_table_range(ls_op* op, double t_lo, double t_hi, int mode
         op->use_table = true;
         return LS_OK;
     }
-    const int cand[3] = {12, 10, 9};
+    const int cand[4] = {12, 10, 9, 8};
+    const int ncand = mode == 3 ? 4 : 3;
     const size_t smem_cap = 160 * 1024;
     DevBuf<double2> fdum;
     CK(fdum.alloc(op->nq));
@@ -2650,7 +2706,7 @@ static ls_status build_table_range(ls_op* op, double t_lo, double t_hi, int mode
     }
     const int n_t = op->nchunk > 1 ? op->nq : std::min(op->nq, spc_t);   // one chunk: stop at spc_t sources
     const float scale_t = (float)op->src_per_chunk / (float)spc_t;
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < ncand; ++c) {
         lsgpu::H0Table T;
         std::string err = lsgpu::build_h0_table(op->k, t_lo, t_hi, T, cand[c], 2e-15);
         op->tune_ms[c] = 0.f;
@@ -2662,7 +2718,7 @@ static ls_status build_table_range(ls_op* op, double t_lo, double t_hi, int mode
         for (int rep = 0; rep < 2; ++rep) {          // first launch warms up, second is timed
             CK(cudaEventRecord(e0, op->stream));
             if (mode == 3)
-                launch_df(cand[c], grid, op->tab_bytes, op->stream, op->xy.p, op->w.p, nullptr, fdum.p, n_t,
+                launch_df(cand[c], op->tab_nf, grid, op->tab_bytes, op->stream, op->xy.p, op->w.p, nullptr, fdum.p, n_t,
                           spc_t, op->k, (const float4*)op->tab.p, op->tab_ncell, op->tab_noct, op->tab_blo,
                           op->partial.p);
             else
@@ -4291,10 +4347,11 @@ ls_status ls_op_set_pairsum(ls_op* op, int32_t mode) {
     return LS_OK;
 }
 
-ls_status ls_op_tuning(const ls_op* op, int32_t* table_ncoef, double* cand_ms) {
+ls_status ls_op_tuning(const ls_op* op, int32_t* table_ncoef, double* cand_ms, int32_t* fp32_tail) {
     if (!op) return fail(LS_EINVAL, "null op");
     if (table_ncoef) *table_ncoef = op->tab_nc;
-    if (cand_ms) for (int i = 0; i < 3; ++i) cand_ms[i] = op->tune_ms[i];
+    if (fp32_tail) *fp32_tail = op->mode == 3 ? op->tab_nf : 0;
+    if (cand_ms) for (int i = 0; i < 4; ++i) cand_ms[i] = op->tune_ms[i];
     return LS_OK;
 }
 
