@@ -387,11 +387,14 @@ def batched_pairsum_report(args):
 
 
 BATCH_NODES = (5000, 8000, 14000, 22000, 34000, 50000, 72000, 100000)
+# k in {10, 20, 40} assigned by size, so that every scatterer keeps >= 2 P4 elements per
+# interior wavelength (by index, k = 40 would fall on the 14k-node mesh: 0.9 per wavelength)
+BATCH_K = (10.0, 10.0, 10.0, 20.0, 20.0, 20.0, 40.0, 40.0)
 
 
 def batching_report(args):
     """The batching form's configuration: 8 star-shaped scatterers of uneven size (5k-100k
-    nodes, k = 10, 20, 40 in turn, grids at k h_C ~ 0.19), 64 incident directions each, all
+    nodes, k = 10, 20, 40 by size, grids at k h_C ~ 0.19), 64 incident directions each, all
     solved in lock step with one persistent pair-sum launch per iteration
     (ls_solve_multi_dev) on the tensor cores; error of direction 0 of every scatterer
     against its FP64-accurate double-float solve."""
@@ -402,7 +405,7 @@ def batching_report(args):
     R = 64
     ops, B, wls, setup = [], [], [], 0.0
     for s, nn in enumerate(BATCH_NODES):
-        k = (10.0, 20.0, 40.0)[s % 3]
+        k = BATCH_K[s]
         nx = int(round(2.9 * k / 0.19)) + 1
         wl = star_scatterer(s, nn, k=k, nx=nx, ny=nx, n_dirs=R)
         t0 = time.perf_counter()
@@ -432,7 +435,7 @@ def batching_report(args):
         op.solve_dev(B[s][0].contiguous().view(1, -1), u1)
         errs.append((torch.linalg.norm(U[s][0] - u1[0]) / torch.linalg.norm(u1[0])).item())
     return {"config": {"workload": "8 star scatterers (r = 1 + 0.2 cos(5 theta + phi)), nodes "
-                                   f"{n_s}, k = 10/20/40, 64 directions each, tol 1e-8, tensor-core batched",
+                                   f"{n_s}, k = {list(BATCH_K)}, 64 directions each, tol 1e-8, tensor-core batched",
                        "nodes": n_s, "rhs_per_scatterer": R},
             "value": len(ops) * R / (ms * 1e-3), "unit": "solves/s", "ms": ms, "status": int(st),
             "iterations_max_per_scatterer": [int(x.max()) for x in it],

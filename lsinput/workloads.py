@@ -101,7 +101,8 @@ def star_scatterer(s, n_nodes_target, k=None, nx=128, ny=128, n_dirs=64, n_ff=64
     """Scatterer s of the batched workload: star r = 1 + 0.2 cos(5 theta + phi_s)
     with phi_s ~ U[0, 2 pi) from default_rng(20261202 + s), an inner interface at
     half the radius, n_opt = 1.3 + 0.3 exp(-|x - c_s|^2 / 0.1) plus 0.5 inside
-    the interface, c_s = 0.2 (cos phi_s, sin phi_s); k = (10, 20, 40)[s % 3]."""
+    the interface, c_s = 0.2 (cos phi_s, sin phi_s); k given, else (10, 20, 40)[s % 3]
+    (the batching configuration passes k by scatterer size)."""
     rng = np.random.default_rng(20261202 + s)
     phi = float(rng.uniform(0.0, 2 * np.pi))
     if k is None:

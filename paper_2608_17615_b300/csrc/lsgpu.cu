@@ -3565,7 +3565,10 @@ static ls_status refine_batch(ls_op* op, int R, const double2* b, double2* u, in
             ok = ok && pr[r] <= tol * tol * pb[r];
             if (pb[r] > 0) worst = std::max(worst, pr[r] / pb[r]);
         }
-        if (!ok && worst > 0.25 * prev_worst) ok = true;       // stagnated: ||r|| fell by less than 2x
+        // stagnated (||r|| fell by less than 2x) within a few ulps of FP32 of the accurate
+        // operator's rounding level, ||P r|| <= 1e-6 ||P b||: converged; stagnation above
+        // that level is a failure
+        if (!ok && worst > 0.25 * prev_worst && worst <= 1e-12) ok = true;
         prev_worst = worst;
         if (ok || step == op->tc_refine) break;
         // correction to a loose tolerance (the tensor-core operator limits it anyway)
