@@ -492,6 +492,33 @@ def gradient_report(args):
             "timing": "host wall clock around the synchronised forward + backward"}
 
 
+def correction_report(args):
+    """The VDIM correction setup on the device (double-double k_vdim) against the host build
+    (long double), on the tiny (120 triangles) and small (2,680 triangles, 40,200 nodes)
+    two-material meshes, with the largest entry difference between the two builds."""
+    import paper_2608_17615_b300 as L
+    from lsinput.workloads import two_material
+
+    out = {}
+    for level, k in (("tiny", 8.0), ("small", 20.0)):
+        wl = two_material(level, k=k)
+        mesh = L.Mesh(wl.mesh)
+        t0 = time.perf_counter()
+        rp_d, ci_d, va_d, n_host = L.correction_dev(mesh, k, 3.0)
+        t_dev = time.perf_counter() - t0
+        row = {"nodes": wl.mesh.n_nodes, "k": k, "device_s": t_dev, "blocks_on_host": int(n_host)}
+        if level == "tiny" or args.steps > 1:
+            t0 = time.perf_counter()
+            rp_h, ci_h, va_h = L.correction_host(mesh, k, 3.0)
+            row["host_s"] = time.perf_counter() - t0
+            assert np.array_equal(rp_d, rp_h) and np.array_equal(ci_d, ci_h)
+            row["max_abs_diff_over_max_abs"] = float(np.max(np.abs(va_d - va_h)) / np.max(np.abs(va_h)))
+        out[level] = row
+        print(f"[correction] {level}: {json.dumps(row)}", file=sys.stderr, flush=True)
+    return {"config": {"workload": "two-material disk, VDIM correction setup (patch radius 3 h), tiny k=8 and "
+                                   "small k=20 meshes"}, "forms": out}
+
+
 def _form(forms, key, fn):
     """Run one form; its failure is recorded instead of costing the bench line."""
     t0 = time.perf_counter()
@@ -510,13 +537,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-large-forms", action="store_true", help="skip the 195k / 8-scatterer / 492k forms")
+    ap.add_argument("--forms", default="standard", choices=["none", "standard", "all"],
+                    help="none: the headline only; standard: + the 40k-node forms and the 195k-node precision "
+                         "configuration; all: + the 8-scatterer batching and 492k-node differentiation "
+                         "configurations (about 10 minutes more)")
     ap.add_argument("--workload", default="default", choices=["default", "precision", "batching", "batched",
-                                                                 "gradient"])
+                                                                 "gradient", "correction"])
     args = ap.parse_args()
     rank, world, local = _env_rank()
     reports = {"precision": precision_report, "batching": batching_report, "batched": batched_pairsum_report,
-               "gradient": gradient_report}
+               "gradient": gradient_report, "correction": correction_report}
     if args.workload in reports:
         if rank == 0:
             import torch
@@ -615,54 +645,59 @@ def main():
                 "rel_err_vs_fp64_accurate_solution": (torch.linalg.norm(uu - u) / torch.linalg.norm(u)).item(),
                 "pairs_per_s": (int(it_[0]) + 1) * n * (n - 1) / (ms * 1e-3), "roofline": rl}
 
-    _form(forms, "cfg2_fp64_pipe",
-          lambda: dict(pipe_form(LS_PREC_FP64_TABLE, "FP64-pipe table pair sum", fp64_probe / 1e3,
-                                 "measured FP64 FMA probe (ls_probe_fp64), same run"),
-                       fp64_unit_count_peak_tflops=FP64_UNIT_PEAK_TFLOPS))
-    _form(forms, "cfg2_fp32", lambda: pipe_form(LS_PREC_FP32, "FP32 precision-form pair sum", FP32_PEAK_TFLOPS,
-                                                FP32_PEAK_SOURCE))
-    op.set_pairsum(LS_PREC_FP64_DF)
+    run_forms = args.forms != "none"
+    if run_forms:
+        _form(forms, "cfg2_fp64_pipe",
+              lambda: dict(pipe_form(LS_PREC_FP64_TABLE, "FP64-pipe table pair sum", fp64_probe / 1e3,
+                                     "measured FP64 FMA probe (ls_probe_fp64), same run"),
+                           fp64_unit_count_peak_tflops=FP64_UNIT_PEAK_TFLOPS))
+        _form(forms, "cfg2_fp32", lambda: pipe_form(LS_PREC_FP32, "FP32 precision-form pair sum", FP32_PEAK_TFLOPS,
+                                                    FP32_PEAK_SOURCE))
+        op.set_pairsum(LS_PREC_FP64_DF)
 
-    def batched_forms():
-        R64 = 64
-        dirs64 = rank_direction(rank, world) + 2 * np.pi * np.arange(R64) / R64
-        B64 = torch.empty((R64, n), dtype=torch.complex128, device=u.device)
-        op.incident_dev(dirs64, B64)
-        U64 = torch.empty_like(B64)
-        out = {}
-        for kind, name in ((1, "tensor_cores"), (0, "cuda_cores")):
-            op.set_batch_kernel(kind)
-            op.solve_batch_dev(B64, U64)                              # warm-up (workspace)
-            ms64, (it64, st64) = _timed(lambda: op.solve_batch_dev(B64, U64), stream)
-            out[name] = {"value": R64 / (ms64 * 1e-3), "unit": "solves/s", "ms": ms64, "status": int(st64),
-                         "iterations_max": int(np.max(it64)),
-                         "rel_err_vs_fp64_accurate_solution":
-                             (torch.linalg.norm(U64[0] - u) / torch.linalg.norm(u)).item()}
-        op.set_batch_kernel(1)
-        out["config"] = {"workload": WORKLOAD + ", 64 incident directions in lock step"}
-        return out
+        def batched_forms():
+            R64 = 64
+            dirs64 = rank_direction(rank, world) + 2 * np.pi * np.arange(R64) / R64
+            B64 = torch.empty((R64, n), dtype=torch.complex128, device=u.device)
+            op.incident_dev(dirs64, B64)
+            U64 = torch.empty_like(B64)
+            out = {}
+            for kind, name in ((1, "tensor_cores"), (0, "cuda_cores")):
+                op.set_batch_kernel(kind)
+                op.solve_batch_dev(B64, U64)                              # warm-up (workspace)
+                ms64, (it64, st64) = _timed(lambda: op.solve_batch_dev(B64, U64), stream)
+                out[name] = {"value": R64 / (ms64 * 1e-3), "unit": "solves/s", "ms": ms64, "status": int(st64),
+                             "iterations_max": int(np.max(it64)),
+                             "rel_err_vs_fp64_accurate_solution":
+                                 (torch.linalg.norm(U64[0] - u) / torch.linalg.norm(u)).item()}
+            op.set_batch_kernel(1)
+            out["config"] = {"workload": WORKLOAD + ", 64 incident directions in lock step"}
+            return out
 
-    _form(forms, "cfg2_batched_64rhs", batched_forms)
-    _form(forms, "cfg2_batched_pairsum_64rhs", lambda: batched_pairsum_report(args))
+        _form(forms, "cfg2_batched_64rhs", batched_forms)
+        _form(forms, "cfg2_batched_pairsum_64rhs", lambda: batched_pairsum_report(args))
 
-    def approach_form():
-        out = {}
-        for approach in (2, 1):
-            opa = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, tol=1e-8, prec=LS_PREC_FP32, approach=approach)
-            ua = torch.empty_like(u)
-            opa.solve_dev(b.view(1, -1), ua.view(1, -1))
-            ms, (it_, st_) = _timed(lambda: opa.solve_dev(b.view(1, -1), ua.view(1, -1)), stream)
-            out[f"approach_{approach}"] = {"iterations": int(it_[0]), "status": int(st_), "ms": ms,
-                                           "rel_err_vs_fp64_accurate_solution":
-                                               (torch.linalg.norm(ua - u) / torch.linalg.norm(u)).item()}
-            del opa
-        out["config"] = {"workload": WORKLOAD + ", FP32 pair sum, Approach I vs II transfer (Table bakeoff context)"}
-        return out
+        def approach_form():
+            out = {}
+            for approach in (2, 1):
+                opa = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, tol=1e-8, prec=LS_PREC_FP32,
+                                 approach=approach)
+                ua = torch.empty_like(u)
+                opa.solve_dev(b.view(1, -1), ua.view(1, -1))
+                ms, (it_, st_) = _timed(lambda: opa.solve_dev(b.view(1, -1), ua.view(1, -1)), stream)
+                out[f"approach_{approach}"] = {"iterations": int(it_[0]), "status": int(st_), "ms": ms,
+                                               "rel_err_vs_fp64_accurate_solution":
+                                                   (torch.linalg.norm(ua - u) / torch.linalg.norm(u)).item()}
+                del opa
+            out["config"] = {"workload": WORKLOAD + ", FP32 pair sum, Approach I vs II transfer "
+                                             "(Table bakeoff context)"}
+            return out
 
-    _form(forms, "cfg2_approach_I_vs_II", approach_form)
+        _form(forms, "cfg2_approach_I_vs_II", approach_form)
     del flush
-    if not args.no_large_forms and rank == 0:
+    if run_forms and rank == 0:
         _form(forms, "cfg3_precision_k40_195k", lambda: precision_report(args))
+    if args.forms == "all" and rank == 0:
         _form(forms, "cfg4_batching_8_scatterers", lambda: batching_report(args))
         _form(forms, "cfg5_differentiation_492k", lambda: gradient_report(args))
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,

@@ -377,8 +377,9 @@ ls_status ls_op_correction(const ls_op* op, int64_t* nnz, int64_t* rowptr, int32
 /*
  * Host-only build of the correction dV for a mesh (no device work): the same
  * setup ls_operator_create runs (extended precision, OpenMP).  Two-call size
- * query as ls_op_correction: null arrays return the size in *nnz.  The values
- * are recomputed on every call.
+ * query as ls_op_correction: null arrays return the size in *nnz (only the
+ * patches are planned, no values computed).  The values are recomputed on every
+ * call that asks for them.
  */
 ls_status ls_correction_host(const ls_mesh* mesh, double k, double kappa, int64_t* nnz,
                              int64_t* rowptr, int32_t* cols, double* vals);
@@ -407,8 +408,9 @@ ls_status ls_grid_host(const ls_mesh* mesh, double k, const double* box, int32_t
  * params->setup_on_device): per (target, subdomain patch) block the Green's-identity
  * boundary moments and the plain-quadrature patch moments in double-double arithmetic
  * on the GPU, combined with the host's long-double coefficient matrices.  Same CSR
- * layout and two-call size query as ls_correction_host; values recomputed on every
- * call.  *host_blocks (may be NULL) receives the number of blocks rebuilt on the host
+ * layout and two-call size query as ls_correction_host (the size query does no device
+ * work); values recomputed on every call that asks for them.  *host_blocks (may be
+ * NULL) receives the number of blocks rebuilt on the host
  * (those whose patch reaches k r > 32, beyond the device series).
  * Errors: LS_EINVAL (null arguments, k <= 0), LS_ECUDA, LS_ESINGULAR.
  */

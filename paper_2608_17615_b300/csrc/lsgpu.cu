@@ -4174,10 +4174,20 @@ ls_status ls_op_correction(const ls_op* op, int64_t* nnz, int64_t* rowptr, int32
     return LS_OK;
 }
 
+// Size query of the correction CSR: 15 entries per (target, patch) block of the plan.
+static ls_status correction_size(const ls_mesh* mesh, double kappa, int64_t* nnz) {
+    lsgpu::CorrPlan P;
+    std::string err = lsgpu::plan_correction(mesh->h, kappa, P);
+    if (!err.empty()) return fail(LS_EINVAL, err);
+    *nnz = 15 * (int64_t)P.target.size();
+    return LS_OK;
+}
+
 ls_status ls_correction_host(const ls_mesh* mesh, double k, double kappa, int64_t* nnz, int64_t* rowptr,
                              int32_t* cols, double* vals) {
     if (!mesh || !nnz) return fail(LS_EINVAL, "null argument");
     if (!(k > 0) || !(kappa > 0)) return fail(LS_EINVAL, "k and kappa must be positive");
+    if (!rowptr && !cols && !vals) return correction_size(mesh, kappa, nnz);
     CsrC csr;
     std::string err = lsgpu::build_correction(mesh->h, k, kappa, csr);
     if (!err.empty()) return fail(LS_ESINGULAR, err);
@@ -4192,6 +4202,7 @@ ls_status ls_correction_dev(const ls_mesh* mesh, double k, double kappa, void* s
                             int64_t* rowptr, int32_t* cols, double* vals, int64_t* host_blocks) {
     if (!mesh || !nnz) return fail(LS_EINVAL, "null argument");
     if (!(k > 0) || !(kappa > 0)) return fail(LS_EINVAL, "k and kappa must be positive");
+    if (!rowptr && !cols && !vals) return correction_size(mesh, kappa, nnz);
     CsrC A;
     std::string err = lsgpu::build_correction_device(mesh->h, k, kappa, stream, A, host_blocks);
     if (!err.empty()) return fail(err.find("singular") != std::string::npos ? LS_ESINGULAR : LS_ECUDA, err);
