@@ -39,7 +39,7 @@ METRIC = "LS GMRES solves/s (FP64-accurate double-float pair sum, preconditioned
 # Preconditioned GMRES iterations of this workload as measured by the GPU arm;
 # the reference arm scales its sampled matvec cost by it.
 REFERENCE_ITERS = 8
-LS_PREC_FP64_TABLE, LS_PREC_FP64_DIRECT, LS_PREC_FP32, LS_PREC_FP64_DF = range(4)
+LS_PREC_FP64_TABLE, LS_PREC_FP64_DIRECT, LS_PREC_FP32, LS_PREC_FP64_DF, LS_PREC_MIXED = range(5)
 
 
 def _env_rank():
@@ -303,8 +303,9 @@ def reference_arm(args):
 def precision_report(args):
     """The precision form on its own configuration (two-material disk at k = 40, 13,042
     triangles = 195,630 nodes, 512^2 preconditioner): FP32 solves (one warm-up, two timed
-    with CUDA events), one FP64-accurate double-float solve for the error, and the FP32
-    matvec against the oracle on sampled rows."""
+    with CUDA events), one FP64-accurate double-float solve for the error, the mixed form
+    (FP32 GMRES refined against the double-float operator; one warm-up, one timed), and
+    the FP32 matvec against the oracle on sampled rows."""
     import torch
     import paper_2608_17615_b300 as L
     from lsinput.workloads import two_material
@@ -327,6 +328,13 @@ def precision_report(args):
     op.set_pairsum(LS_PREC_FP64_DF)
     msdf, (itdf, stdf) = _timed(lambda: op.solve_dev(b, udf), stream)
     err = (torch.linalg.norm(u32 - udf) / torch.linalg.norm(udf)).item()
+    op.set_pairsum(LS_PREC_MIXED)
+    umx = torch.empty_like(b)
+    op.solve_dev(b, umx)                                     # warm-up
+    msmx, (itmx, stmx) = _timed(lambda: op.solve_dev(b, umx), stream)
+    mixed = {"ms": msmx, "solves_per_s": 1e3 / msmx, "iterations_all_inner": int(itmx[0]), "status": int(stmx),
+             "explicit_exit_residual_accurate_operator": op.last_residual(),
+             "rel_err_vs_fp64_accurate_solution": (torch.linalg.norm(umx - udf) / torch.linalg.norm(udf)).item()}
     op.set_pairsum(LS_PREC_FP32)
     x = np.exp(1j * np.arange(n) * 0.37)
     y = torch.empty(n, dtype=torch.complex128, device="cuda")
@@ -340,6 +348,7 @@ def precision_report(args):
             "pairs_per_s": int(it32[0] + 1) * n * (n - 1) / (ms32 * 1e-3),
             "rel_err_vs_fp64_accurate_solution": err, "matvec_rel_err_vs_oracle_24_rows": mv_err,
             "fp64_accurate_solve": {"ms": msdf, "iterations": int(itdf[0]), "status": int(stdf)},
+            "mixed_fp32_refined_against_double_float": mixed,
             "roofline": rl, "setup_s": setup_s,
             "setup_parts_s": dict(zip(["correction", "grid", "preconditioner_factors", "table"],
                                       [round(float(t), 3) for t in op.setup_times()]))}
@@ -638,10 +647,10 @@ def main():
         reps = 3
         ms, (it_, st_) = _timed(lambda: op.solve_dev(b.view(1, -1), uu.view(1, -1), wl.ff_angles, uinf.view(1, -1)),
                                 stream, reps=reps)
-        rl = _pairsum_roofline(op, n, peak, peak_source, ms * reps)
+        rl = _pairsum_roofline(op, n, peak, peak_source, ms * reps) if peak else None
         op.set_timing(False)
         return {"config": {"workload": WORKLOAD + ", " + label}, "value": 1e3 / ms, "unit": "solves/s", "ms": ms,
-                "iterations": int(it_[0]), "status": int(st_),
+                "iterations": int(it_[0]), "status": int(st_), "explicit_exit_residual": op.last_residual(),
                 "rel_err_vs_fp64_accurate_solution": (torch.linalg.norm(uu - u) / torch.linalg.norm(u)).item(),
                 "pairs_per_s": (int(it_[0]) + 1) * n * (n - 1) / (ms * 1e-3), "roofline": rl}
 
@@ -653,6 +662,8 @@ def main():
                            fp64_unit_count_peak_tflops=FP64_UNIT_PEAK_TFLOPS))
         _form(forms, "cfg2_fp32", lambda: pipe_form(LS_PREC_FP32, "FP32 precision-form pair sum", FP32_PEAK_TFLOPS,
                                                     FP32_PEAK_SOURCE))
+        _form(forms, "cfg2_mixed", lambda: pipe_form(LS_PREC_MIXED, "mixed precision: FP32 GMRES refined against the "
+                                                     "double-float operator (iterations: all inner ones)", None, None))
         op.set_pairsum(LS_PREC_FP64_DF)
 
         def batched_forms():

@@ -55,8 +55,17 @@ enum {
     LS_PREC_FP64_DIRECT = 1,  /* FP64 direct evaluation of H0 (series / fitted asymptotic form)  */
     LS_PREC_FP32 = 2,         /* precision form: FP32 table (degree 6, validated to 2e-8),
                                  double-float coordinate differences, Kahan-compensated FP32 sums */
-    LS_PREC_FP64_DF = 3       /* FP64-accurate: the FP64 table evaluated in double-float (pairs of
+    LS_PREC_FP64_DF = 3,      /* FP64-accurate: the FP64 table evaluated in double-float (pairs of
                                  FP32) arithmetic and accumulated on the FP32 pipe                */
+    LS_PREC_MIXED = 4         /* mixed precision: every GMRES solve runs with the FP32 pair sum
+                                 (as LS_PREC_FP32) and is refined against the double-float
+                                 operator (as LS_PREC_FP64_DF): r = b - L u accurate, an FP32
+                                 GMRES correction, u += d, until ||P r|| <= tol ||P b|| with the
+                                 accurate L (at most 4 corrections).  Single applies
+                                 (ls_apply*) use the accurate operator; iters_out counts every
+                                 inner iteration, hist_out holds the first FP32 solve's history;
+                                 ls_op_last_residual is the accurate operator's residual.  The
+                                 batched solves are not affected (they refine on their own).   */
 };
 
 /* Build parameters of an operator. */

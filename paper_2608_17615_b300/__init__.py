@@ -38,7 +38,7 @@ class LsError(RuntimeError):
         self.status = status
 
 
-LS_PREC_FP64_TABLE, LS_PREC_FP64_DIRECT, LS_PREC_FP32, LS_PREC_FP64_DF = range(4)
+LS_PREC_FP64_TABLE, LS_PREC_FP64_DIRECT, LS_PREC_FP32, LS_PREC_FP64_DF, LS_PREC_MIXED = range(5)
 
 
 class Params(ctypes.Structure):

@@ -1720,11 +1720,13 @@ struct ls_op {
     // pair-sum decomposition and scratch
     int nchunk = 1, src_per_chunk = 0;
     DevBuf<double2> partial;
-    // tabulated H0 (pairsum mode 0: FP64 table, mode 2: FP32 table)
+    // tabulated H0 (pairsum mode 0: FP64 table, mode 2: FP32 table, modes 3 and 4: double-float
+    // table; mode 4 also keeps the FP32 table tab32 for its inner solves)
     int mode = 0;
     bool use_table = false;
     int tab_nc = 12;                     // table degree + 1 chosen by the setup autotuner
     int tab_nf = 0;                      // double-float form: top coefficients summed in FP32
+    bool inner32 = false;                // mixed form (mode 4): pair sums of the inner solves in FP32
     float tune_ms[4] = {0, 0, 0, 0};     // pair-sum time of the NC = 12, 10, 9 (, 8) candidates (0: not tried)
     int tab_ncell = 0, tab_noct = 0, tab_blo = 0;
     size_t tab_bytes = 0;
@@ -1873,13 +1875,17 @@ static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m, c
         op->ev.emplace_back(e0, e1);
         CK(cudaEventRecord(e0, op->stream));
     }
-    if (op->mode == 3)
+    if (op->mode == 3 || (op->mode == 4 && !op->inner32))
         launch_df(op->tab_nc, op->tab_nf, grid, op->tab_bytes, op->stream, op->xy.p, w, m, f, op->nq, op->src_per_chunk, op->k,
                   (const float4*)op->tab.p, op->tab_ncell, op->tab_noct, op->tab_blo, op->partial.p);
     else if (op->mode == 2)
         k_pairsum_f32<<<grid, PS_TPB, op->tab_bytes, op->stream>>>(op->xy.p, w, m, f, op->nq, op->src_per_chunk,
                                                                     op->k, 1.0 / op->k, (const float4*)op->tab.p,
                                                                     op->tab_ncell, op->tab_noct, op->tab_blo, op->partial.p);
+    else if (op->mode == 4)
+        k_pairsum_f32<<<grid, PS_TPB, op->t32_bytes, op->stream>>>(op->xy.p, w, m, f, op->nq, op->src_per_chunk,
+                                                                    op->k, 1.0 / op->k, (const float4*)op->tab32.p,
+                                                                    op->t32_ncell, op->t32_noct, op->t32_blo, op->partial.p);
     else if (op->use_table)
         launch_tab(op->tab_nc, grid, op->tab_bytes, op->stream, op->xy.p, w, m, f, op->nq, op->src_per_chunk, op->k,
                    op->tab.p, op->tab_ncell, op->tab_noct, op->tab_blo, op->partial.p);
@@ -2480,6 +2486,80 @@ static ls_status residual_full(ls_op* op, const double2* b, const double2* u, do
     return LS_OK;
 }
 
+// Mixed-precision solve (pairsum mode 4): GMRES with the FP32 pair sum, then iterative
+// refinement against the double-float (FP64-accurate) operator.  Each step forms
+// r = b - L u with the accurate L; while ||P r|| > tol ||P b|| an FP32 GMRES solves
+// L d = r to the relative tolerance that brings ||P r|| below tol / 2 (at most 0.5, at
+// least 1e-3, where the FP32 operator's own error starts to limit the correction) and
+// u += d.  The exit residual (ls_op_last_residual) is the accurate operator's.
+#define MIXED_REFINE 4
+static ls_status solve_mixed(ls_op* op, const double2* b, double2* u, double* hist_host, int* iters, bool transpose) {
+    const int n = op->nq, nb = (n + 255) / 256;
+    const double tol = op->prm.tol;
+    const double lr0 = op->last_res;
+    const bool prec = op->has_prec && op->prm.use_precond;
+    if (op->ir_r.n < (size_t)n) {
+        CK(op->ir_r.alloc(n));
+        CK(op->ir_d.alloc(n));
+        CK(op->ir_y.alloc(n));
+    }
+    op->inner32 = true;
+    int it = 0;
+    ls_status s = gmres_one(op, b, u, hist_host, &it, transpose);
+    op->inner32 = false;
+    if (s != LS_OK && s != LS_ENOCONV) return s;
+    int total = it;
+    // ||P x||^2 into scal[slot] (ir_y as scratch)
+    auto pnorm2 = [&](const double2* x, int slot, double& out) -> ls_status {
+        const double2* px = x;
+        if (prec) {
+            TRY(transpose ? apply_PT(op, x, op->ir_y.p) : apply_P(op, x, op->ir_y.p));
+            px = op->ir_y.p;
+        }
+        TRY(dots(op, 1, px, px, op->scal.p + slot, 0));
+        double2 v;
+        CK(cudaMemcpyAsync(&v, op->scal.p + slot, sizeof(double2), cudaMemcpyDeviceToHost, op->stream));
+        CK(cudaStreamSynchronize(op->stream));
+        out = v.x;
+        return LS_OK;
+    };
+    double pb2 = 0, pr2 = 0, rel = 0;
+    TRY(pnorm2(b, 3, pb2));
+    for (int step = 0;; ++step) {
+        TRY(transpose ? apply_LT(op, u, op->ir_y.p) : apply_L(op, u, op->ir_y.p));
+        k_sub_vec<<<nb, 256, 0, op->stream>>>(n, b, op->ir_y.p, op->ir_r.p);
+        CK(cudaGetLastError());
+        op->launches++;
+        TRY(pnorm2(op->ir_r.p, 2, pr2));
+        rel = pb2 > 0 ? std::sqrt(pr2 / pb2) : 0.0;
+        if (rel <= tol || step == MIXED_REFINE) break;
+        const double tol_save = op->prm.tol;
+        op->prm.tol = std::min(0.5, std::max(0.5 * tol / rel, 1e-3));
+        op->inner32 = true;
+        ls_status sc = gmres_one(op, op->ir_r.p, op->ir_d.p, nullptr, &it, transpose);
+        op->inner32 = false;
+        op->prm.tol = tol_save;
+        if (sc != LS_OK && sc != LS_ENOCONV) return sc;
+        total += it;
+        k_accumulate_multi<<<nb, 256, 0, op->stream>>>(n, op->ir_d.p, u);
+        CK(cudaGetLastError());
+        op->launches++;
+    }
+    op->last_res = std::max(lr0, rel);
+    op->last_it = total;
+    if (iters) *iters = total;
+    if (rel <= tol) return LS_OK;
+    fail(LS_ENOCONV, "mixed-precision refinement: accurate residual " + std::to_string(rel) + " above tol");
+    return LS_ENOCONV;
+}
+
+// One single-RHS solve in the operator's pair-sum form.
+static ls_status solve_one(ls_op* op, const double2* b, double2* u, double* hist_host, int* iters,
+                           bool transpose = false) {
+    if (op->mode == 4 && !op->cartesian) return solve_mixed(op, b, u, hist_host, iters, transpose);
+    return gmres_one(op, b, u, hist_host, iters, transpose);
+}
+
 // Error reporting for other translation units of the library.
 ls_status lsgpu_set_error(ls_status s, const char* msg) { return fail(s, msg); }
 
@@ -2582,6 +2662,13 @@ static ls_status ensure_table32(ls_op* op) {
     double e = 0;
     TRY(upload_f32_table(T, op->tab32, op->t32_ncell, op->t32_noct, op->t32_blo, op->t32_bytes, e));
     CK(raise_smem_limit(k_pairsum_multi_f32, op->t32_bytes));
+    return LS_OK;
+}
+
+// The FP32 table of the mixed form's inner solves (shared with the batched kernels).
+static ls_status ensure_table32_single(ls_op* op) {
+    TRY(ensure_table32(op));
+    CK(raise_smem_limit(k_pairsum_f32, op->t32_bytes));
     return LS_OK;
 }
 
@@ -2871,8 +2958,8 @@ ls_status ls_operator_create(const ls_mesh* mesh, double k, const double* m, con
     ls_params_default(&prm);
     if (params) prm = *params;
     if (prm.max_iter < 1 || !(prm.tol > 0) || !(prm.kappa > 0)) return fail(LS_EINVAL, "bad tol / max_iter / kappa");
-    if (prm.prec < 0 || prm.prec > 3)
-        return fail(LS_EINVAL, "prec must be 0 (FP64 table), 1 (FP64 direct), 2 (FP32) or 3 (double-float)");
+    if (prm.prec < 0 || prm.prec > 4)
+        return fail(LS_EINVAL, "prec must be 0 (FP64 table), 1 (FP64 direct), 2 (FP32), 3 (double-float) or 4 (mixed)");
     if (prm.approach != 1 && prm.approach != 2) return fail(LS_EINVAL, "approach must be 1 or 2");
     if (prm.use_precond && !m_grid) return fail(LS_EINVAL, "m_grid is required with use_precond");
     const HostMesh& M = mesh->h;
@@ -2944,7 +3031,8 @@ ls_status ls_operator_create(const ls_mesh* mesh, double k, const double* m, con
     op->mode = prm.prec;
     table_range(op, M);
     auto tt0 = std::chrono::steady_clock::now();
-    if (prm.prec != 1) TRY(build_table_range(op, op->tab_tlo, op->tab_thi, prm.prec));
+    if (prm.prec != 1) TRY(build_table_range(op, op->tab_tlo, op->tab_thi, prm.prec == 4 ? 3 : prm.prec));
+    if (prm.prec == 4) TRY(ensure_table32_single(op));
     op->t_setup[3] = std::chrono::duration<double>(std::chrono::steady_clock::now() - tt0).count();
     TRY(alloc_gmres(op, nsm));
     if (prm.use_precond) TRY(build_preconditioner(op, M, m_grid));
@@ -3921,7 +4009,7 @@ ls_status ls_solve_dev(ls_op* op, int32_t R, const void* b_dev, void* u_dev, int
         const double2* b = (const double2*)b_dev + (size_t)r * op->nq;
         double2* u = (double2*)u_dev + (size_t)r * op->nq;
         int it = 0;
-        ls_status s = gmres_one(op, b, u, nullptr, &it);
+        ls_status s = solve_one(op, b, u, nullptr, &it);
         if (s != LS_OK && s != LS_ENOCONV) return s;
         if (s == LS_ENOCONV) worst = s;
         if (iters_out) iters_out[r] = it;
@@ -3959,7 +4047,7 @@ ls_status ls_solve(ls_op* op, int32_t R, const double* dir_angles, const double*
             op->launches++;
         }
         int it = 0;
-        ls_status s = gmres_one(op, b.p, u.p, hist.data(), &it);
+        ls_status s = solve_one(op, b.p, u.p, hist.data(), &it);
         if (s != LS_OK && s != LS_ENOCONV) return s;
         if (s == LS_ENOCONV) worst = s;
         if (iters_out) iters_out[r] = it;
@@ -4008,7 +4096,7 @@ ls_status ls_solve_adjoint(ls_op* op, int32_t R, const double* g, double* lambda
     for (int r = 0; r < R; ++r) {
         CK(cudaMemcpyAsync(gd.p, g + 2 * (size_t)r * n, sizeof(double2) * n, cudaMemcpyHostToDevice, op->stream));
         int it = 0;
-        ls_status s = gmres_one(op, gd.p, ld.p, nullptr, &it, true);
+        ls_status s = solve_one(op, gd.p, ld.p, nullptr, &it, true);
         if (s != LS_OK && s != LS_ENOCONV) return s;
         if (s == LS_ENOCONV) worst = s;
         if (iters_out) iters_out[r] = it;
@@ -4281,7 +4369,7 @@ ls_status ls_solve_transpose_dev(ls_op* op, int32_t R, const void* g_dev, void* 
     op->last_res = 0.0;
     for (int r = 0; r < R; ++r) {
         int it = 0;
-        ls_status s = gmres_one(op, (const double2*)g_dev + (size_t)r * op->nq, (double2*)lambda_dev + (size_t)r * op->nq,
+        ls_status s = solve_one(op, (const double2*)g_dev + (size_t)r * op->nq, (double2*)lambda_dev + (size_t)r * op->nq,
                                 nullptr, &it, true);
         if (s != LS_OK && s != LS_ENOCONV) return s;
         if (s == LS_ENOCONV) worst = s;
@@ -4335,7 +4423,7 @@ ls_status ls_misfit_gradient_dev(ls_op* op, int32_t R, const void* u_dev, int32_
         CK(cudaGetLastError());
         op->launches += 2;
         int it = 0;
-        ls_status s = gmres_one(op, rhs.p, lam.p, nullptr, &it, true);
+        ls_status s = solve_one(op, rhs.p, lam.p, nullptr, &it, true);
         if (s != LS_OK && s != LS_ENOCONV) return s;
         if (s == LS_ENOCONV) worst = s;
         if (iters_out) iters_out[r] = it;
@@ -4352,11 +4440,12 @@ ls_status ls_misfit_gradient_dev(ls_op* op, int32_t R, const void* u_dev, int32_
 ls_status ls_op_set_pairsum(ls_op* op, int32_t mode) {
     if (!op) return fail(LS_EINVAL, "null op");
     if (op->cartesian) return fail(LS_EINVAL, "a purely Cartesian operator has no pair-sum kernel");
-    if (mode < 0 || mode > 3) return fail(LS_EINVAL, "pairsum must be 0, 1, 2 or 3");
+    if (mode < 0 || mode > 4) return fail(LS_EINVAL, "pairsum must be 0, 1, 2, 3 or 4");
     CK(cudaStreamSynchronize(op->stream));
     if (mode != 1 && !(op->tab_thi > 0)) return fail(LS_EINVAL, "operator has no table range (built with pairsum = 1)");
     op->use_table = false;
-    if (mode != 1) TRY(build_table_range(op, op->tab_tlo, op->tab_thi, mode));
+    if (mode != 1) TRY(build_table_range(op, op->tab_tlo, op->tab_thi, mode == 4 ? 3 : mode));
+    if (mode == 4) TRY(ensure_table32_single(op));
     op->mode = mode;
     return LS_OK;
 }
@@ -4364,7 +4453,7 @@ ls_status ls_op_set_pairsum(ls_op* op, int32_t mode) {
 ls_status ls_op_tuning(const ls_op* op, int32_t* table_ncoef, double* cand_ms, int32_t* fp32_tail) {
     if (!op) return fail(LS_EINVAL, "null op");
     if (table_ncoef) *table_ncoef = op->tab_nc;
-    if (fp32_tail) *fp32_tail = op->mode == 3 ? op->tab_nf : 0;
+    if (fp32_tail) *fp32_tail = (op->mode == 3 || op->mode == 4) ? op->tab_nf : 0;
     if (cand_ms) for (int i = 0; i < 4; ++i) cand_ms[i] = op->tune_ms[i];
     return LS_OK;
 }

@@ -163,6 +163,42 @@ def test_precision_form_solutions(cfg2):
     assert e_small < 1e-6 and e_full < 1e-6
 
 
+def test_mixed_form_solutions(cfg2):
+    # pairsum = 4: FP32 GMRES refined against the double-float operator.  The refinement
+    # stops on the accurate operator's residual, so the solution meets the FP64 solve's
+    # tolerance times the condition factor, far inside the 1e-6 precision-form target.
+    wl = two_material("tiny", k=8.0, nx=64, ny=64)
+    op4 = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, nx=64, ny=64, tol=1e-10, pairsum=4)
+    u, _, _, it, st = op4.solve([np.pi / 4])
+    A = OracleOp(wl.mesh, wl.k, wl.m).dense()
+    b = plane_wave(wl.mesh.nodes, wl.k, np.pi / 4)
+    e_small = _rel(u[0], np.linalg.solve(A, b))
+    res_small = op4.last_residual()
+    # the adjoint solve takes the same refinement (transposed operators)
+    g = random_density(wl.mesh.n_nodes, 41)[None, :]
+    lam, _, st_a = op4.solve_adjoint(g)
+    e_adj = _rel(lam[0], np.linalg.solve(A.T, g[0]))
+    # single applies use the accurate operator: identical to the double-float form
+    op3 = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, nx=64, ny=64, tol=1e-10, pairsum=3)
+    x = _dev(random_density(wl.mesh.n_nodes, 42))
+    y3, y4 = torch.empty_like(x), torch.empty_like(x)
+    op3.apply_dev(x, y3)
+    op4.apply_dev(x, y4)
+    wl2, _ = cfg2
+    op2 = L.Operator(L.Mesh(wl2.mesh), wl2.k, wl2.m, wl2.m_grid, tol=1e-10, pairsum=4)
+    u4, _, _, it4, st4 = op2.solve([np.pi / 4])
+    res_full = op2.last_residual()
+    op64 = L.Operator(L.Mesh(wl2.mesh), wl2.k, wl2.m, wl2.m_grid, tol=1e-10)
+    u64, _, _, it64, st64 = op64.solve([np.pi / 4])
+    e_full = _rel(u4[0], u64[0])
+    print("mixed form: small vs oracle", e_small, "adjoint", e_adj, "full vs FP64 path", e_full,
+          "accurate exit residuals", res_small, res_full, "iterations (all inner)", it, it4, "FP64", it64)
+    assert st == st_a == st4 == st64 == L.LS_OK
+    assert torch.equal(y3, y4)
+    assert res_small <= 1e-10 and res_full <= 1e-10
+    assert e_small < 1e-8 and e_adj < 1e-8 and e_full < 1e-8
+
+
 def test_precond_parity_small():
     wl = constant_disk(k=5.0, n_rings=3, nx=48, ny=48)
     op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, nx=48, ny=48)
