@@ -342,9 +342,12 @@ ls_status ls_solve_transpose_batch_dev(ls_op* op, int32_t R, const void* g_dev, 
  *           to `refine` steps of iterative refinement whose residuals use the
  *           kind 0 operator, which restores the kind 0 accuracy (refine = 0: none).
  *           Refinement stops when ||P r|| <= max(tol, 2e-8) ||P b|| or when a
- *           correction no longer halves the residual (the kind 0 operator's
- *           rounding level, ~1e-7, reached); LS_ENOCONV if neither happens within
- *           `refine` steps.
+ *           correction no longer halves the residual while ||P r|| <= 1e-6 ||P b||
+ *           (the kind 0 operator's rounding level reached); LS_ENOCONV if neither
+ *           happens within `refine` steps.  On kind 1 the block-LU sweeps of the
+ *           preconditioner run in FP32 (FP32 copies of the factors, made on first
+ *           use); P only weights the residual norm, so the refined solution keeps
+ *           the kind 0 accuracy.  Kind 0 keeps the FP64 sweeps.
  * Defaults: kind 1, fold 4, refine 4.
  * Errors: LS_EINVAL for kind outside {0, 1}, fold < 1 or refine < 0.  A stalled
  * tensor-core pipeline (every wait in the kernel is bounded) makes the next call

@@ -1322,6 +1322,117 @@ __global__ void k_bt_bwd_multi(int nx, int ny, int b, const double2* __restrict_
     }
 }
 
+// Batched block-LU sweeps of C in FP32 (used by the tensor-core batched form, which refines
+// its solutions against an accurate residual, so the preconditioner only has to be close):
+// one launch per block row b; a CTA computes a tile of BT_ROWS rows x BT_RHS right-hand
+// sides of
+//   forward   y_b = W_b (t_b - L_b y_{b-1})       (L_b: the 3-point lower band of C)
+//   backward  y_b = y_b - G_b y_{b+1}
+// staging BT_KC columns of the factor and of the input vectors in shared memory per step,
+// with the K = nx reduction split over the 8 warps and summed in shared memory at the end.
+// Thread (lane) computes rows 4 rg .. 4 rg + 3 (rg = lane / 4) x RHS 2 rq, 2 rq + 1 (rq = lane % 4).
+#define BT_ROWS 32
+#define BT_RHS 8
+#define BT_KC 64
+__global__ void __launch_bounds__(256) k_bt_sweep32(int nx, int ny, int b, int R, int backward,
+                                                    const float2* __restrict__ M, const float2* __restrict__ cb,
+                                                    const double2* __restrict__ t, float2* __restrict__ y) {
+    __shared__ float2 Ws[BT_ROWS][BT_KC + 1];
+    __shared__ __align__(16) float2 Vs[BT_KC][BT_RHS];
+    __shared__ float2 red[8][BT_ROWS * BT_RHS];
+    const int row0 = blockIdx.x * BT_ROWS, rhs0 = blockIdx.y * BT_RHS;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rg = lane >> 2, rq = lane & 3;
+    const size_t plane = (size_t)nx * ny;
+    const float2* Mb = M + (size_t)b * nx * nx;
+    float ar[4][2], ai[4][2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) ar[i][q] = ai[i][q] = 0.f;
+    for (int k0 = 0; k0 < nx; k0 += BT_KC) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < BT_ROWS * BT_KC; i += blockDim.x) {
+            const int r = i / BT_KC, kk = i % BT_KC, row = row0 + r, k = k0 + kk;
+            Ws[r][kk] = (row < nx && k < nx) ? Mb[(size_t)row * nx + k] : make_float2(0.f, 0.f);
+        }
+        for (int i = threadIdx.x; i < BT_KC * BT_RHS; i += blockDim.x) {
+            const int kk = i % BT_KC, q = i / BT_KC, k = k0 + kk, r = rhs0 + q;
+            float2 v = make_float2(0.f, 0.f);
+            if (k < nx && r < R) {
+                const size_t o = (size_t)r * plane;
+                if (backward) {
+                    v = y[o + (size_t)(b + 1) * nx + k];
+                } else {
+                    const double2 tv = t[o + (size_t)b * nx + k];
+                    v = make_float2((float)tv.x, (float)tv.y);
+                    if (b > 0) {
+                        const float2* cbb = cb + (size_t)b * 9 * nx;
+                        const float2* yp = y + o + (size_t)(b - 1) * nx;
+#pragma unroll
+                        for (int da = -1; da <= 1; ++da) {
+                            const int kc = k + da;
+                            if (kc >= 0 && kc < nx) {
+                                const float2 c = cbb[(size_t)(da + 1) * nx + k], yv = yp[kc];
+                                v.x -= fmaf(c.x, yv.x, -c.y * yv.y);
+                                v.y -= fmaf(c.x, yv.y, c.y * yv.x);
+                            }
+                        }
+                    }
+                }
+            }
+            Vs[kk][q] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < BT_KC / 8; ++j) {
+            const int kk = warp * (BT_KC / 8) + j;
+            const float4 vv = *reinterpret_cast<const float4*>(&Vs[kk][2 * rq]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float2 w = Ws[4 * rg + i][kk];
+                ar[i][0] = fmaf(w.x, vv.x, fmaf(-w.y, vv.y, ar[i][0]));
+                ai[i][0] = fmaf(w.x, vv.y, fmaf(w.y, vv.x, ai[i][0]));
+                ar[i][1] = fmaf(w.x, vv.z, fmaf(-w.y, vv.w, ar[i][1]));
+                ai[i][1] = fmaf(w.x, vv.w, fmaf(w.y, vv.z, ai[i][1]));
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) red[warp][(4 * rg + i) * BT_RHS + 2 * rq + q] = make_float2(ar[i][q], ai[i][q]);
+    __syncthreads();
+    for (int o = threadIdx.x; o < BT_ROWS * BT_RHS; o += blockDim.x) {
+        float sr = 0.f, si = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            sr += red[w][o].x;
+            si += red[w][o].y;
+        }
+        const int row = row0 + o / BT_RHS, rhs = rhs0 + o % BT_RHS;
+        if (row < nx && rhs < R) {
+            float2* yo = y + (size_t)rhs * plane + (size_t)b * nx + row;
+            if (backward) {
+                const float2 v = *yo;
+                *yo = make_float2(v.x - sr, v.y - si);
+            } else {
+                *yo = make_float2(sr, si);
+            }
+        }
+    }
+}
+
+__global__ void k_to_f32(int64_t n, const double2* __restrict__ a, float2* __restrict__ b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+
+__global__ void k_to_f64(int64_t n, const float2* __restrict__ a, double2* __restrict__ b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = make_double2((double)a[i].x, (double)a[i].y);
+}
+
 __global__ void k_tcq_multi(int nq, int nc, const int* __restrict__ idx, const double* __restrict__ wt,
                             const double2* __restrict__ tp, const double2* __restrict__ g, const double2* __restrict__ win,
                             size_t sin_, double2* __restrict__ z, size_t sz) {
@@ -1742,6 +1853,7 @@ struct ls_op {
     DevBuf<double> tqc_cv;
     DevBuf<double2> cband, Wf, Gf;
     DevBuf<double2> WT, GT;              // transposed factors for P^T
+    DevBuf<float2> Wf32, Gf32, cband32, by32;   // FP32 copies for the tensor-core batched sweeps
     DevBuf<int64_t> tcqT_rp, tqcT_rp;    // (T_C^Q)^T over grid rows, (T_Q^C)^T over quadrature rows (for P^T)
     DevBuf<int> tcqT_ci, tqcT_ci;
     DevBuf<double> tcqT_cv, tqcT_cv;
@@ -3416,18 +3528,50 @@ static ls_status apply_L_batch(ls_op* op, int R, const double2* x, size_t sx, do
     return LS_OK;
 }
 
+// FP32 copies of the block-LU factors and of the band of C, and the FP32 sweep vectors.
+static ls_status ensure_sweeps32(ls_op* op, int R) {
+    const size_t nx = op->nx, ny = op->ny, nc = nx * ny;
+    if (!op->Wf32.p) {
+        const int64_t nf = (int64_t)(ny * nx * nx), nb = (int64_t)(ny * 9 * nx);
+        CK(op->Wf32.alloc(nf));
+        CK(op->Gf32.alloc(nf));
+        CK(op->cband32.alloc(nb));
+        k_to_f32<<<(unsigned)((nf + 255) / 256), 256, 0, op->stream>>>(nf, op->Wf.p, op->Wf32.p);
+        k_to_f32<<<(unsigned)((nf + 255) / 256), 256, 0, op->stream>>>(nf, op->Gf.p, op->Gf32.p);
+        k_to_f32<<<(unsigned)((nb + 255) / 256), 256, 0, op->stream>>>(nb, op->cband.p, op->cband32.p);
+        CK(cudaGetLastError());
+        op->launches += 3;
+    }
+    if (op->by32.n < (size_t)R * nc) CK(op->by32.alloc((size_t)R * nc));
+    return LS_OK;
+}
+
 static ls_status apply_P_batch(ls_op* op, int R, const double2* x, size_t sx, double2* z, size_t sz) {
     const int nx = op->nx, ny = op->ny, nc = nx * ny;
     dim3 gc((nc + 255) / 256, R);
     k_tqc_multi<<<gc, 256, 0, op->stream>>>(nc, op->tqc_rp.p, op->tqc_ci.p, op->tqc_cv.p, x, sx, op->bpg.p);
     k_stencil_multi<<<gc, 256, 0, op->stream>>>(nx, ny, op->st.p, op->bpg.p, op->bpt.p);
-    const int wpb = 8;
-    dim3 gb((nx + wpb - 1) / wpb, R);
-    const size_t shm = sizeof(double2) * nx;
-    for (int b = 0; b < ny; ++b)
-        k_bt_fwd_multi<<<gb, 32 * wpb, shm, op->stream>>>(nx, ny, b, op->Wf.p, op->cband.p, op->bpt.p, op->bptp.p);
-    for (int b = ny - 2; b >= 0; --b)
-        k_bt_bwd_multi<<<gb, 32 * wpb, shm, op->stream>>>(nx, ny, b, op->Gf.p, op->bptp.p);
+    if (op->batch_kernel == 1) {
+        // tensor-core form: FP32 sweeps (the solve is refined against the accurate operator)
+        TRY(ensure_sweeps32(op, R));
+        dim3 gs((nx + BT_ROWS - 1) / BT_ROWS, (R + BT_RHS - 1) / BT_RHS);
+        for (int b = 0; b < ny; ++b)
+            k_bt_sweep32<<<gs, 256, 0, op->stream>>>(nx, ny, b, R, 0, op->Wf32.p, op->cband32.p, op->bpt.p,
+                                                     op->by32.p);
+        for (int b = ny - 2; b >= 0; --b)
+            k_bt_sweep32<<<gs, 256, 0, op->stream>>>(nx, ny, b, R, 1, op->Gf32.p, nullptr, nullptr, op->by32.p);
+        const int64_t tot = (int64_t)R * nc;
+        k_to_f64<<<(unsigned)((tot + 255) / 256), 256, 0, op->stream>>>(tot, op->by32.p, op->bptp.p);
+        op->launches += 1;
+    } else {
+        const int wpb = 8;
+        dim3 gb((nx + wpb - 1) / wpb, R);
+        const size_t shm = sizeof(double2) * nx;
+        for (int b = 0; b < ny; ++b)
+            k_bt_fwd_multi<<<gb, 32 * wpb, shm, op->stream>>>(nx, ny, b, op->Wf.p, op->cband.p, op->bpt.p, op->bptp.p);
+        for (int b = ny - 2; b >= 0; --b)
+            k_bt_bwd_multi<<<gb, 32 * wpb, shm, op->stream>>>(nx, ny, b, op->Gf.p, op->bptp.p);
+    }
     dim3 gq((op->nq + 255) / 256, R);
     k_tcq_multi<<<gq, 256, 0, op->stream>>>(op->nq, nc, op->tcq_idx.p, op->tcq_w.p, op->bptp.p, op->bpg.p, x, sx, z, sz);
     CK(cudaGetLastError());
