@@ -3752,6 +3752,7 @@ static ls_status apply_L_batch_accurate(ls_op* op, int R, const double2* x, doub
 }
 
 #define TC_RESID_FLOOR 2e-8
+#define TC_FIRST_TOL 1e-6
 
 // Batched GMRES.  On the tensor cores the operator carries ~1e-6 relative error from the
 // FP32 accumulation in tensor memory, so the solve is followed by iterative refinement:
@@ -3762,7 +3763,12 @@ static ls_status refine_batch(ls_op* op, int R, const double2* b, double2* u, in
 
 static ls_status gmres_batch(ls_op* op, int R, const double2* b, double2* u, int* iters, bool transpose = false) {
     if (op->batch_kernel != 1 || op->tc_refine <= 0) return gmres_batch_plain(op, R, b, u, iters, transpose);
+    // the tensor-core operator is itself only ~3e-7 x fold accurate: a first solve tighter
+    // than TC_FIRST_TOL would refine nothing the accurate residual does not redo
+    const double tol_save = op->prm.tol;
+    op->prm.tol = std::max(tol_save, TC_FIRST_TOL);
     ls_status s0 = gmres_batch_plain(op, R, b, u, iters, transpose);
+    op->prm.tol = tol_save;
     if (s0 != LS_OK && s0 != LS_ENOCONV) return s0;
     return refine_batch(op, R, b, u, iters, transpose);
 }
@@ -3803,9 +3809,10 @@ static ls_status refine_batch(ls_op* op, int R, const double2* b, double2* u, in
         if (!ok && worst > 0.25 * prev_worst && worst <= 1e-12) ok = true;
         prev_worst = worst;
         if (ok || step == op->tc_refine) break;
-        // correction to a loose tolerance (the tensor-core operator limits it anyway)
+        // correction to the relative tolerance that brings the worst residual below tol / 2
+        // (at least 1e-3: the tensor-core operator limits a correction to about that)
         const double tol_save = op->prm.tol;
-        op->prm.tol = std::max(tol_save, 1e-3);
+        op->prm.tol = std::min(0.5, std::max(0.5 * tol / std::sqrt(worst), 1e-3));
         ls_status sc = gmres_batch_plain(op, R, op->ir_r.p, op->ir_d.p, its.data(), transpose);
         op->prm.tol = tol_save;
         if (sc != LS_OK && sc != LS_ENOCONV) return sc;
@@ -3846,6 +3853,18 @@ static ls_status solve_multi(int S, ls_op* const* ops, int R, const double2* con
         ops[s]->b_nchunk_cur = ops[s]->b_nchunk;      // the persistent CUDA-core kernel writes these partials
     }
     if (tcore) {
+        // first solves to TC_FIRST_TOL where refinement follows (as in gmres_batch); the
+        // guard restores every operator's tolerance on all exits
+        struct TolGuard {
+            std::vector<std::pair<ls_op*, double>> saved;
+            void restore() { for (auto& p : saved) p.first->prm.tol = p.second; saved.clear(); }
+            ~TolGuard() { restore(); }
+        } tg;
+        for (int s = 0; s < S; ++s)
+            if (ops[s]->tc_refine > 0) {
+                tg.saved.emplace_back(ops[s], ops[s]->prm.tol);
+                ops[s]->prm.tol = std::max(ops[s]->prm.tol, TC_FIRST_TOL);
+            }
         // one persistent tensor-core launch per iteration over the unconverged operators
         DevBuf<TCOp> tdesc;
         CK(tdesc.alloc(std::max(S, 1)));
@@ -3882,10 +3901,17 @@ static ls_status solve_multi(int S, ls_op* const* ops, int R, const double2* con
             TRY(tc_status(which[0]));
         }
         all_conv = true;
+        std::vector<char> conv(S, 0);
         for (int s = 0; s < S; ++s) {
             bool c = false;
             int* its = iters ? iters + (size_t)s * R : nullptr;
             TRY(gb_finish(ops[s], R, u[s], its, c));
+            conv[s] = c;
+        }
+        tg.restore();
+        for (int s = 0; s < S; ++s) {
+            bool c = conv[s] != 0;
+            int* its = iters ? iters + (size_t)s * R : nullptr;
             if (ops[s]->tc_refine > 0) {
                 // iterative refinement against the accurate operator (see gmres_batch)
                 ls_status sr = refine_batch(ops[s], R, b[s], u[s], its, false);
