@@ -161,6 +161,11 @@ ls_status ls_apply_dev(ls_op* op, const void* x_dev, void* y_dev);
 ls_status ls_apply(ls_op* op, const double* x, double* y);
 /* y = P x (Eq. preconditioner_factored) on device buffers; LS_EINVAL without a preconditioner. */
 ls_status ls_apply_precond_dev(ls_op* op, const void* x_dev, void* y_dev);
+/* y_r = P x_r for R right-hand sides x_dev, y_dev [R][N_Q] complex (no aliasing) with the
+   batched preconditioner kernels of ls_solve_batch_dev: FP64 block-LU sweeps under batch
+   kernel 0, FP32 sweeps under kernel 1 (ls_op_set_batch_kernel).  LS_EINVAL without a
+   preconditioner. */
+ls_status ls_apply_precond_batch_dev(ls_op* op, int32_t R, const void* x_dev, void* y_dev);
 
 /*
  * Plain pair sum y_j = sum_{n != j} G(y_j, y_n) w_n f_n (the naive Nystrom

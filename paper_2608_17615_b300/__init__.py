@@ -19,7 +19,8 @@ _STATUS = {0: "LS_OK", 1: "LS_EINVAL", 2: "LS_ENOMEM", 3: "LS_ECUDA", 4: "LS_ESI
 
 EXPORTED = ["ls_params_default", "ls_mesh_create", "ls_mesh_destroy", "ls_mesh_num_nodes", "ls_operator_create",
             "ls_cartesian_create",
-            "ls_op_destroy", "ls_op_num_nodes", "ls_apply_dev", "ls_apply", "ls_apply_precond_dev", "ls_pairsum_dev",
+            "ls_op_destroy", "ls_op_num_nodes", "ls_apply_dev", "ls_apply", "ls_apply_precond_dev",
+            "ls_apply_precond_batch_dev", "ls_pairsum_dev",
             "ls_solve", "ls_solve_dev", "ls_op_correction", "ls_correction_host", "ls_correction_dev", "ls_grid_host", "ls_transfer_host",
             "ls_hankel0_dev",
             "ls_pairsum_batch_dev", "ls_solve_batch_dev", "ls_solve_multi_dev", "ls_apply_transpose_dev", "ls_potential_transpose_dev", "ls_apply_precond_transpose_dev",
@@ -74,6 +75,7 @@ def _load():
         "ls_apply_dev": (I32, [P, P, P]),
         "ls_apply": (I32, [P, P, P]),
         "ls_apply_precond_dev": (I32, [P, P, P]),
+        "ls_apply_precond_batch_dev": (I32, [P, I32, P, P]),
         "ls_pairsum_dev": (I32, [P, P, P]),
         "ls_solve": (I32, [P, I32, P, P, I32, P, P, P, P, P]),
         "ls_apply_precond": (I32, [P, P, P]),
@@ -294,6 +296,10 @@ class Operator:
 
     def apply_precond_dev(self, x, y):
         _check(_lib.ls_apply_precond_dev(self.handle, _dptr(x), _dptr(y)))
+
+    def apply_precond_batch_dev(self, x, y):
+        """y_r = P x_r for device tensors x, y [R, N] with the batched kernels."""
+        _check(_lib.ls_apply_precond_batch_dev(self.handle, x.shape[0], _dptr(x), _dptr(y)))
 
     def pairsum_dev(self, f, y):
         _check(_lib.ls_pairsum_dev(self.handle, _dptr(f), _dptr(y)))

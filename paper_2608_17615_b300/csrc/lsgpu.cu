@@ -3996,6 +3996,15 @@ static ls_status solve_multi(int S, ls_op* const* ops, int R, const double2* con
 
 extern "C" {
 
+ls_status ls_apply_precond_batch_dev(ls_op* op, int32_t R, const void* x_dev, void* y_dev) {
+    if (!op || !x_dev || !y_dev || R < 1) return fail(LS_EINVAL, "null argument or R < 1");
+    if (!op->has_prec) return fail(LS_EINVAL, "operator was built without a preconditioner");
+    if (x_dev == y_dev) return fail(LS_EINVAL, "x and y may not alias");
+    TRY(ensure_batch(op, R));
+    TRY(apply_P_batch(op, R, (const double2*)x_dev, op->nq, (double2*)y_dev, op->nq));
+    return check_stream_sync(op);
+}
+
 ls_status ls_pairsum_batch_dev(ls_op* op, int32_t R, const void* f_dev, void* y_dev) {
     if (!op || R < 1 || !f_dev || !y_dev) return fail(LS_EINVAL, "null argument or R < 1");
     TRY(ensure_batch(op, R));
