@@ -30,7 +30,7 @@ EXPORTED = ["ls_params_default", "ls_mesh_create", "ls_mesh_destroy", "ls_mesh_n
             "ls_apply_precond", "ls_apply_transpose", "ls_solve_adjoint", "ls_residual_dev", "ls_op_last_residual",
             "ls_op_set_contrast_dev", "ls_misfit_dev", "ls_op_ritz", "ls_hessenberg_eigenvalues",
             "ls_precond_rho_dev",
-            "ls_op_set_pairsum", "ls_op_set_timing", "ls_op_setup_times", "ls_op_tuning", "ls_op_stats", "ls_probe_fp64", "ls_pairsum_noalloc", "ls_last_error"]
+            "ls_op_set_pairsum", "ls_op_set_pair_symmetry", "ls_op_set_timing", "ls_op_setup_times", "ls_op_tuning", "ls_op_stats", "ls_probe_fp64", "ls_pairsum_noalloc", "ls_last_error"]
 
 
 class LsError(RuntimeError):
@@ -111,6 +111,7 @@ def _load():
         "ls_tc_gemm_check": (I32, [I32, P]),
         "ls_misfit_gradient_batch_dev": (I32, [P, I32, P, I32, P, P, P, P]),
         "ls_op_set_pairsum": (I32, [P, I32]),
+        "ls_op_set_pair_symmetry": (I32, [P, I32]),
         "ls_op_set_timing": (I32, [P, I32]),
         "ls_op_setup_times": (I32, [P, P]),
         "ls_op_tuning": (I32, [P, P, P, P]),
@@ -396,9 +397,13 @@ class Operator:
         return iters, st
 
     def set_pairsum(self, mode):
-        """0: FP64 table, 1: FP64 direct, 2: FP32 precision form."""
+        """LS_PREC_*: 0 FP64 table, 1 FP64 direct, 2 FP32, 3 double-float, 4 mixed."""
         _check(_lib.ls_op_set_pairsum(self.handle, int(mode)))
         self.params.prec = int(mode)
+
+    def set_pair_symmetry(self, on):
+        """Double-float pair sum over unordered pairs (True, default) or every ordered pair."""
+        _check(_lib.ls_op_set_pair_symmetry(self.handle, int(bool(on))))
 
     def set_batch_kernel(self, kind, fold=4, refine=4):
         """Batched pair sum on 0: CUDA cores, 1: tensor cores (accumulator restarted every fold

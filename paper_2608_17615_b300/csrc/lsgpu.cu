@@ -424,6 +424,76 @@ __device__ __forceinline__ DF df_from(double x) {
 
 struct DFTile { float4 xy; float4 s; };     // (x_h, x_l, y_h, y_l), (s_re_h, s_re_l, s_im_h, s_im_l)
 
+// H0(k |y - x|) in double-float for target (tx, ty) and source coordinates sxy = (x_h, x_l,
+// y_h, y_l): DF coordinate differences, DF t = dx^2 + dy^2, exact DF cell variable u (t and
+// the cell centre share an octave, so t_hi - mid_hi is exact, and 1/half-width is a power of
+// two), DF Horner on the table (the top NF steps in plain FP32), the FP64 routine outside the
+// table range.  Returns false (H = 0) for t = 0, the self pair.
+template <int NC_TAB, int NF>
+__device__ __forceinline__ bool df_h0(DF tx, DF ty, float4 sxy, const float4* coef, const float4* cellv,
+                                      const int2* oct, int noct, int b_lo, double k, double inv_k, DF& hr, DF& hi) {
+    float dxh, dxl, dyh, dyl;
+    df_diff(tx.h, tx.l, sxy.x, sxy.y, dxh, dxl);
+    df_diff(ty.h, ty.l, sxy.z, sxy.w, dyh, dyl);
+    float p1 = dxh * dxh, e1 = fmaf(dxh, dxh, -p1);
+    e1 = fmaf(2.f * dxh, dxl, e1);
+    float p2 = dyh * dyh, e2 = fmaf(dyh, dyh, -p2);
+    e2 = fmaf(2.f * dyh, dyl, e2);
+    float th, tl;
+    two_sum(p1, p2, th, tl);
+    tl += e1 + e2;
+    DF t = df_fast(th, tl);
+    int bits = __float_as_int(t.h);
+    unsigned o = (unsigned)((bits >> 23) - b_lo);
+    if (o < (unsigned)noct) {
+        int2 ob = oct[o];
+        int cell = ob.x + ((bits & 0x7fffff) >> ob.y);
+        float4 cv = cellv[cell];
+        float d0, d1;
+        two_sum(t.h - cv.x, t.l - cv.y, d0, d1);      // t.h - mid.h is exact
+        DF u = DF{d0 * cv.z, d1 * cv.z};                // times a power of two: exact
+        const float4* c = coef + (size_t)cell * NC_TAB;
+        float4 cc = c[NC_TAB - 1];
+        if (NF > 0) {
+            float yr = cc.x, yi = cc.z;
+#pragma unroll
+            for (int e = NC_TAB - 2; e >= NC_TAB - NF; --e) {
+                cc = c[e];
+                yr = fmaf(yr, u.h, cc.x);
+                yi = fmaf(yi, u.h, cc.z);
+            }
+            hr = DF{yr, 0.f};
+            hi = DF{yi, 0.f};
+        } else {
+            hr = DF{cc.x, cc.y};
+            hi = DF{cc.z, cc.w};
+        }
+#pragma unroll
+        for (int e = (NF > 0 ? NC_TAB - NF : NC_TAB - 1) - 1; e >= 0; --e) {
+            cc = c[e];
+            hr = df_mad(hr, u, DF{cc.x, cc.y});
+            hi = df_mad(hi, u, DF{cc.z, cc.w});
+        }
+        return true;
+    }
+    if (t.h > 0.f) {
+        double2 h = ls_h0_r2((double)t.h + (double)t.l, k, inv_k);
+        hr = df_from(h.x);
+        hi = df_from(h.y);
+        return true;
+    }
+    hr = DF{0.f, 0.f};
+    hi = DF{0.f, 0.f};
+    return false;
+}
+
+// acc += h * s (complex, double-float)
+__device__ __forceinline__ void df_cmac(DF hr, DF hi, DF s_re, DF s_im, DF& ar, DF& ai) {
+    DF a1 = df_mul(hr, s_re), a2 = df_mul(hi, s_im), a3 = df_mul(hr, s_im), a4 = df_mul(hi, s_re);
+    ar = df_add(ar, df_add(a1, DF{-a2.h, -a2.l}));
+    ai = df_add(ai, df_add(a3, a4));
+}
+
 // NF > 0: the top NF coefficients of the Horner chain (whose terms are below 2^-24 of |H0|
 // on every cell, checked when the table is uploaded) are summed in plain FP32, the rest in
 // double-float.
@@ -471,56 +541,9 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum_df(const double2* __restrict
         const int cnt = min(PS_TILE, s_end - base);
         for (int i = 0; i < cnt; ++i) {
             DFTile src = tile[i];
-            float dxh, dxl, dyh, dyl;
-            df_diff(tx.h, tx.l, src.xy.x, src.xy.y, dxh, dxl);
-            df_diff(ty.h, ty.l, src.xy.z, src.xy.w, dyh, dyl);
-            float p1 = dxh * dxh, e1 = fmaf(dxh, dxh, -p1);
-            e1 = fmaf(2.f * dxh, dxl, e1);
-            float p2 = dyh * dyh, e2 = fmaf(dyh, dyh, -p2);
-            e2 = fmaf(2.f * dyh, dyl, e2);
-            float th, tl;
-            two_sum(p1, p2, th, tl);
-            tl += e1 + e2;
-            DF t = df_fast(th, tl);
-            int bits = __float_as_int(t.h);
-            unsigned o = (unsigned)((bits >> 23) - b_lo);
             DF hr, hi;
-            if (o < (unsigned)noct) {
-                int2 ob = oct[o];
-                int cell = ob.x + ((bits & 0x7fffff) >> ob.y);
-                float4 cv = cellv[cell];
-                float d0, d1;
-                two_sum(t.h - cv.x, t.l - cv.y, d0, d1);      // t.h - mid.h is exact
-                DF u = DF{d0 * cv.z, d1 * cv.z};                // times a power of two: exact
-                const float4* c = coef + (size_t)cell * NC_TAB;
-                float4 cc = c[NC_TAB - 1];
-                if (NF > 0) {
-                    float yr = cc.x, yi = cc.z;
-#pragma unroll
-                    for (int e = NC_TAB - 2; e >= NC_TAB - NF; --e) {
-                        cc = c[e];
-                        yr = fmaf(yr, u.h, cc.x);
-                        yi = fmaf(yi, u.h, cc.z);
-                    }
-                    hr = DF{yr, 0.f};
-                    hi = DF{yi, 0.f};
-                } else {
-                    hr = DF{cc.x, cc.y};
-                    hi = DF{cc.z, cc.w};
-                }
-#pragma unroll
-                for (int e = (NF > 0 ? NC_TAB - NF : NC_TAB - 1) - 1; e >= 0; --e) {
-                    cc = c[e];
-                    hr = df_mad(hr, u, DF{cc.x, cc.y});
-                    hi = df_mad(hi, u, DF{cc.z, cc.w});
-                }
-            } else if (t.h > 0.f) {
-                double2 h = ls_h0_r2((double)t.h + (double)t.l, k, inv_k);
-                hr = df_from(h.x);
-                hi = df_from(h.y);
-            } else {
+            if (!df_h0<NC_TAB, NF>(tx, ty, src.xy, coef, cellv, oct, noct, b_lo, k, inv_k, hr, hi))
                 continue;                     // the self pair
-            }
             DF s_re{src.s.x, src.s.y}, s_im{src.s.z, src.s.w};
             DF a1 = df_mul(hr, s_re), a2 = df_mul(hi, s_im), a3 = df_mul(hr, s_im), a4 = df_mul(hi, s_re);
             sr = df_add(sr, df_add(a1, DF{-a2.h, -a2.l}));
@@ -530,6 +553,122 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum_df(const double2* __restrict
         acci += (double)si.h + (double)si.l;
     }
     if (j < n) partial[(size_t)blockIdx.y * n + j] = make_double2(accr, acci);
+}
+
+// The same pair sum using the symmetry H(i, j) = H(j, i): every unordered pair is evaluated
+// once and feeds both the row sum of its target and the column sum of its source.
+// The nodes form nb blocks of 128 placed on a circle; strip I (blockIdx.x) pairs with the
+// blocks at circular distance d = 1 .. D after it, D = floor(nb / 2) (the distance nb / 2 of
+// an even nb only from I < nb / 2, so each unordered block pair occurs once), the distances
+// split into gridDim.y chunks of dper, one CTA per (strip, chunk); chunk 0 also takes the
+// diagonal block (ordered pairs i != j, rows only).  Deterministic output, no atomics:
+//   row sums     partial[c][I*128 + t]              c = chunk
+//   column sums  partial[nchunk + d - 1][J*128 + t]  J = (I + d) mod nb
+// (for an even nb the slot of d = nb / 2 of the blocks J < nb / 2 is left to the caller to
+// zero).  In a unit (I, J) a warp owns 32 targets and walks each 32-source sub-block of J
+// in 32 steps: at step r lane l pairs its target with source (l + r) mod 32 and carries
+// that source's column accumulator, passed to lane l - 1 after the step, so that after the
+// 32 steps lane l holds the sum for source l over the warp's targets; the four warps'
+// sums are added in shared memory.  Arithmetic per pair as k_pairsum_df.
+template <int NC_TAB, int NF>
+__global__ void __launch_bounds__(PS_TPB) k_pairsum_dfs(const double2* __restrict__ xy, const double* __restrict__ w,
+                                                        const double2* __restrict__ m, const double2* __restrict__ f,
+                                                        int n, int nb, int dper, double k, double inv_k,
+                                                        const float4* __restrict__ tab_g, int ncell, int noct, int b_lo,
+                                                        double2* __restrict__ partial) {
+    extern __shared__ float4 dtab[];
+    __shared__ DFTile tile[PS_TPB];
+    __shared__ float4 colbuf[PS_TPB / 32][PS_TPB];
+    const int words = ncell * (NC_TAB + 1) + (noct + 1) / 2;
+    for (int i = threadIdx.x; i < words; i += PS_TPB) dtab[i] = tab_g[i];
+    const float4* coef = dtab;
+    const float4* cellv = dtab + (size_t)ncell * NC_TAB;
+    const int2* oct = reinterpret_cast<const int2*>(cellv + ncell);
+    const int I = blockIdx.x, c = blockIdx.y, nchunk = gridDim.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = I * PS_TPB + threadIdx.x;
+    const int D = nb / 2;
+    // the strength of node q, (w m f)_q, as a DF tile entry (zero past n)
+    auto load_tile = [&](int blk) {
+        const int q = blk * PS_TPB + threadIdx.x;
+        DFTile v;
+        v.xy = make_float4(0.f, 0.f, 0.f, 0.f);
+        v.s = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (q < n) {
+            double2 p = xy[q];
+            double2 ff = f[q];
+            if (m) ff = cmul(m[q], ff);
+            double ww = w ? w[q] : 1.0;
+            DF a = df_from(p.x), b = df_from(p.y), cr = df_from(ww * ff.x), ci = df_from(ww * ff.y);
+            v.xy = make_float4(a.h, a.l, b.h, b.l);
+            v.s = make_float4(cr.h, cr.l, ci.h, ci.l);
+        }
+        tile[threadIdx.x] = v;
+    };
+    // this thread's target and its own strength (for the column sums)
+    __syncthreads();
+    load_tile(I);
+    __syncthreads();
+    const DFTile me = tile[threadIdx.x];
+    const double2 yi = xy[min(i, n - 1)];
+    const DF tx = df_from(yi.x), ty = df_from(yi.y);
+    const DF si_re{me.s.x, me.s.y}, si_im{me.s.z, me.s.w};
+    double accr = 0.0, acci = 0.0;
+    if (c == 0) {                          // the diagonal block: ordered pairs, rows only
+        DF sr{0.f, 0.f}, sim{0.f, 0.f};
+        for (int q = 0; q < PS_TPB; ++q) {
+            if (q == (int)threadIdx.x) continue;
+            const DFTile src = tile[q];
+            DF hr, hi;
+            if (!df_h0<NC_TAB, NF>(tx, ty, src.xy, coef, cellv, oct, noct, b_lo, k, inv_k, hr, hi)) continue;
+            df_cmac(hr, hi, DF{src.s.x, src.s.y}, DF{src.s.z, src.s.w}, sr, sim);
+        }
+        accr += (double)sr.h + (double)sr.l;
+        acci += (double)sim.h + (double)sim.l;
+    }
+    const int d0 = 1 + c * dper, d1 = min(D, (c + 1) * dper);
+    for (int d = d0; d <= d1; ++d) {
+        if (2 * D == nb && d == D && I >= D) continue;      // that block pair belongs to strip I - D
+        const int J = (I + d) % nb;
+        __syncthreads();
+        load_tile(J);
+        __syncthreads();
+        DF sr{0.f, 0.f}, sim{0.f, 0.f};
+#pragma unroll 1
+        for (int sub = 0; sub < PS_TPB / 32; ++sub) {
+            DF cr{0.f, 0.f}, ci{0.f, 0.f};
+#pragma unroll 2
+            for (int r = 0; r < 32; ++r) {
+                const DFTile src = tile[sub * 32 + ((lane + r) & 31)];
+                DF hr, hi;
+                df_h0<NC_TAB, NF>(tx, ty, src.xy, coef, cellv, oct, noct, b_lo, k, inv_k, hr, hi);
+                df_cmac(hr, hi, DF{src.s.x, src.s.y}, DF{src.s.z, src.s.w}, sr, sim);
+                df_cmac(hr, hi, si_re, si_im, cr, ci);
+                const int from = (lane + 1) & 31;
+                cr.h = __shfl_sync(0xffffffffu, cr.h, from);
+                cr.l = __shfl_sync(0xffffffffu, cr.l, from);
+                ci.h = __shfl_sync(0xffffffffu, ci.h, from);
+                ci.l = __shfl_sync(0xffffffffu, ci.l, from);
+            }
+            colbuf[warp][sub * 32 + lane] = make_float4(cr.h, cr.l, ci.h, ci.l);
+        }
+        accr += (double)sr.h + (double)sr.l;
+        acci += (double)sim.h + (double)sim.l;
+        __syncthreads();
+        const int jj = J * PS_TPB + threadIdx.x;
+        if (jj < n) {
+            DF tr{0.f, 0.f}, ti{0.f, 0.f};
+#pragma unroll
+            for (int wv = 0; wv < PS_TPB / 32; ++wv) {
+                const float4 v = colbuf[wv][threadIdx.x];
+                tr = df_add(tr, DF{v.x, v.y});
+                ti = df_add(ti, DF{v.z, v.w});
+            }
+            partial[(size_t)(nchunk + d - 1) * n + jj] = make_double2((double)tr.h + (double)tr.l,
+                                                                      (double)ti.h + (double)ti.l);
+        }
+    }
+    if (i < n) partial[(size_t)c * n + i] = make_double2(accr, acci);
 }
 
 // Batched form: R right-hand sides.  Each thread owns one target and a block of
@@ -1831,6 +1970,10 @@ struct ls_op {
     // pair-sum decomposition and scratch
     int nchunk = 1, src_per_chunk = 0;
     DevBuf<double2> partial;
+    int ps_slots = 1;                    // partial rows written by the last single-RHS pair sum
+    // symmetric double-float pair sum (k_pairsum_dfs): blocks, distance chunks, distances per chunk
+    bool df_sym = true;
+    int dfs_nb = 1, dfs_nchunk = 1, dfs_dper = 1;
     // tabulated H0 (pairsum mode 0: FP64 table, mode 2: FP32 table, modes 3 and 4: double-float
     // table; mode 4 also keeps the FP32 table tab32 for its inner solves)
     int mode = 0;
@@ -1955,13 +2098,36 @@ static void launch_df(int nc, int nf, dim3 grid, size_t smem, cudaStream_t st, c
 #undef LS_DF_LAUNCH
 }
 
+static void launch_dfs(int nc, int nf, dim3 grid, size_t smem, cudaStream_t st, const double2* xy, const double* w,
+                       const double2* m, const double2* f, int n, int nb, int dper, double k, const float4* tab,
+                       int ncell, int noct, int blo, double2* partial) {
+    const double ik = 1.0 / k;
+#define LS_DFS_LAUNCH(NC, NF) \
+    k_pairsum_dfs<NC, NF><<<grid, PS_TPB, smem, st>>>(xy, w, m, f, n, nb, dper, k, ik, tab, ncell, noct, blo, partial)
+#define LS_DFS_NC(NC)                          \
+    do {                                       \
+        if (nf >= 4) LS_DFS_LAUNCH(NC, 4);     \
+        else if (nf >= 2) LS_DFS_LAUNCH(NC, 2); \
+        else LS_DFS_LAUNCH(NC, 0);             \
+    } while (0)
+    if (nc == 8) LS_DFS_NC(8);
+    else if (nc == 9) LS_DFS_NC(9);
+    else if (nc == 10) LS_DFS_NC(10);
+    else LS_DFS_NC(12);
+#undef LS_DFS_NC
+#undef LS_DFS_LAUNCH
+}
+
 static cudaError_t raise_tab_limits(int mode, size_t bytes) {
     cudaError_t e = cudaSuccess;
     if (mode == 3) {
 #define LS_DF_RAISE(NC)                                                                        \
         if ((e = raise_smem_limit(k_pairsum_df<NC, 0>, bytes)) != cudaSuccess) return e;      \
         if ((e = raise_smem_limit(k_pairsum_df<NC, 2>, bytes)) != cudaSuccess) return e;      \
-        if ((e = raise_smem_limit(k_pairsum_df<NC, 4>, bytes)) != cudaSuccess) return e;
+        if ((e = raise_smem_limit(k_pairsum_df<NC, 4>, bytes)) != cudaSuccess) return e;      \
+        if ((e = raise_smem_limit(k_pairsum_dfs<NC, 0>, bytes)) != cudaSuccess) return e;     \
+        if ((e = raise_smem_limit(k_pairsum_dfs<NC, 2>, bytes)) != cudaSuccess) return e;     \
+        if ((e = raise_smem_limit(k_pairsum_dfs<NC, 4>, bytes)) != cudaSuccess) return e;
         LS_DF_RAISE(8)
         LS_DF_RAISE(9)
         LS_DF_RAISE(10)
@@ -1987,7 +2153,18 @@ static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m, c
         op->ev.emplace_back(e0, e1);
         CK(cudaEventRecord(e0, op->stream));
     }
-    if (op->mode == 3 || (op->mode == 4 && !op->inner32))
+    op->ps_slots = op->nchunk;
+    const bool df = op->mode == 3 || (op->mode == 4 && !op->inner32);
+    if (df && op->df_sym) {
+        const int D = op->dfs_nb / 2;
+        op->ps_slots = op->dfs_nchunk + D;
+        if (D > 0 && 2 * D == op->dfs_nb)      // slot of distance nb / 2: half of it stays unwritten
+            CK(cudaMemsetAsync(op->partial.p + (size_t)(op->ps_slots - 1) * op->nq, 0, sizeof(double2) * op->nq,
+                               op->stream));
+        launch_dfs(op->tab_nc, op->tab_nf, dim3(op->dfs_nb, op->dfs_nchunk), op->tab_bytes, op->stream, op->xy.p, w, m,
+                   f, op->nq, op->dfs_nb, op->dfs_dper, op->k, (const float4*)op->tab.p, op->tab_ncell, op->tab_noct,
+                   op->tab_blo, op->partial.p);
+    } else if (df)
         launch_df(op->tab_nc, op->tab_nf, grid, op->tab_bytes, op->stream, op->xy.p, w, m, f, op->nq, op->src_per_chunk, op->k,
                   (const float4*)op->tab.p, op->tab_ncell, op->tab_noct, op->tab_blo, op->partial.p);
     else if (op->mode == 2)
@@ -2076,7 +2253,7 @@ static ls_status apply_L(ls_op* op, const double2* x, double2* y) {
     if (s != LS_OK) return s;
     int threads = 256;
     int blocks = (int)(((int64_t)op->nq * 32 + threads - 1) / threads);
-    k_apply_epi<<<blocks, threads, 0, op->stream>>>(op->nq, op->nchunk, op->partial.p, op->rowptr.p, op->cols.p, op->vals.p,
+    k_apply_epi<<<blocks, threads, 0, op->stream>>>(op->nq, op->ps_slots, op->partial.p, op->rowptr.p, op->cols.p, op->vals.p,
                                                     op->m.p, x, op->k * op->k, y, 0);
     CK(cudaGetLastError());
     op->launches++;
@@ -2477,7 +2654,7 @@ static ls_status apply_LT(ls_op* op, const double2* x, double2* y, int mode = 0)
     if (s != LS_OK) return s;
     int threads = 256;
     int blocks = (int)(((int64_t)op->nq * 32 + threads - 1) / threads);
-    k_applyT_epi<<<blocks, threads, 0, op->stream>>>(op->nq, op->nchunk, op->partial.p, op->rowptrT.p, op->colsT.p,
+    k_applyT_epi<<<blocks, threads, 0, op->stream>>>(op->nq, op->ps_slots, op->partial.p, op->rowptrT.p, op->colsT.p,
                                                      op->valsT.p, op->m.p, op->w.p, x, op->k * op->k, y, mode);
     CK(cudaGetLastError());
     op->launches++;
@@ -3139,7 +3316,19 @@ ls_status ls_operator_create(const ls_mesh* mesh, double k, const double* m, con
     nchunk = (n + spc - 1) / spc;
     op->nchunk = nchunk;
     op->src_per_chunk = spc;
-    CK(op->partial.alloc((size_t)nchunk * n));
+    {   // symmetric decomposition: about 12 CTAs per SM over (strip, distance chunk)
+        const int nb = tblocks, D = nb / 2;
+        int C = 1, dper = 1;
+        if (D > 0) {
+            C = std::max(1, std::min(D, (12 * nsm + nb - 1) / nb));
+            dper = (D + C - 1) / C;
+            C = (D + dper - 1) / dper;
+        }
+        op->dfs_nb = nb;
+        op->dfs_nchunk = C;
+        op->dfs_dper = dper;
+    }
+    CK(op->partial.alloc((size_t)std::max(nchunk, op->dfs_nchunk + op->dfs_nb / 2) * n));
     op->mode = prm.prec;
     table_range(op, M);
     auto tt0 = std::chrono::steady_clock::now();
@@ -3278,7 +3467,7 @@ ls_status ls_pairsum_dev(ls_op* op, const void* f_dev, void* y_dev) {
     TRY(launch_pairsum(op, (const double2*)f_dev, nullptr));
     int threads = 256;
     int blocks = (int)(((int64_t)op->nq * 32 + threads - 1) / threads);
-    k_apply_epi<<<blocks, threads, 0, op->stream>>>(op->nq, op->nchunk, op->partial.p, op->rowptr.p, op->cols.p,
+    k_apply_epi<<<blocks, threads, 0, op->stream>>>(op->nq, op->ps_slots, op->partial.p, op->rowptr.p, op->cols.p,
                                                     op->vals.p, op->m.p, (const double2*)f_dev, 0.0, (double2*)y_dev, 1);
     CK(cudaGetLastError());
     return check_stream_sync(op);
@@ -4626,6 +4815,14 @@ ls_status ls_op_set_pairsum(ls_op* op, int32_t mode) {
     if (mode != 1) TRY(build_table_range(op, op->tab_tlo, op->tab_thi, mode == 4 ? 3 : mode));
     if (mode == 4) TRY(ensure_table32_single(op));
     op->mode = mode;
+    return LS_OK;
+}
+
+ls_status ls_op_set_pair_symmetry(ls_op* op, int32_t on) {
+    if (!op) return fail(LS_EINVAL, "null op");
+    if (on != 0 && on != 1) return fail(LS_EINVAL, "on must be 0 or 1");
+    CK(cudaStreamSynchronize(op->stream));
+    op->df_sym = on != 0;
     return LS_OK;
 }
 

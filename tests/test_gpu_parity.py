@@ -129,6 +129,37 @@ def test_double_float_form_full_size(cfg2):
     assert e_ps < 1e-13 and e_ap < 1e-11
 
 
+@pytest.mark.parametrize("case", ["two_material_tiny", "disk", "two_material_small"])
+def test_symmetric_double_float_pair_sum(case, cfg2):
+    # k_pairsum_dfs (one Hankel evaluation per unordered pair, rows and columns) against
+    # k_pairsum_df (every ordered pair): the same terms summed in another order, so equal to
+    # a few units of FP64 rounding of the sum; repeated launches are bitwise identical (no
+    # atomics).  Block counts: 15 (odd), 26 (even: the distance nb/2 handled once), 315.
+    if case == "two_material_tiny":
+        wl = two_material("tiny", k=8.0)
+    elif case == "disk":
+        wl = constant_disk(k=5.0)
+    else:
+        wl = cfg2[0]
+    n = wl.mesh.n_nodes
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, use_precond=0, pairsum=3)
+    f = _dev(random_density(n, 77))
+    ys, ys2, yo = torch.empty_like(f), torch.empty_like(f), torch.empty_like(f)
+    op.pairsum_dev(f, ys)
+    op.pairsum_dev(f, ys2)
+    op.set_pair_symmetry(False)
+    op.pairsum_dev(f, yo)
+    op.set_pair_symmetry(True)
+    e = (torch.linalg.norm(ys - yo) / torch.linalg.norm(yo)).item()
+    ref = naive_apply(wl.mesh.nodes, wl.mesh.weights, wl.k, random_density(n, 77)) if n < 5000 else None
+    e_or = _rel(ys.cpu().numpy(), ref) if ref is not None else None
+    print(case, n, "symmetric vs ordered pair sum", e, "vs oracle naive sum", e_or)
+    assert torch.equal(ys, ys2)
+    assert e < 1e-14
+    if ref is not None:
+        assert e_or < 1e-13
+
+
 def test_pairsum_precision_form_full_size(cfg2):
     # FP32 table (2e-8), FP32 strengths (6e-8), Kahan-compensated sums: ~1e-7 expected
     wl, op = cfg2
