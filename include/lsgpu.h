@@ -457,8 +457,8 @@ ls_status ls_hankel0_dev(int64_t n, const double* z_dev, void* h_dev, void* stre
 ls_status ls_op_set_pairsum(ls_op* op, int32_t mode);
 
 /*
- * Symmetry of the double-float pair sum (LS_PREC_FP64_DF and the accurate operator of
- * LS_PREC_MIXED).  on = 1 (default): H0(k |y_i - y_j|) is evaluated once per unordered pair
+ * Symmetry of the single-RHS table pair sums (LS_PREC_FP64_DF, LS_PREC_FP32 and both
+ * operators of LS_PREC_MIXED).  on = 1 (default): H0(k |y_i - y_j|) is evaluated once per unordered pair
  * and feeds both y_i (with s_j) and y_j (with s_i), half the Hankel evaluations; the
  * result is deterministic (no atomics) and equal to the on = 0 sum up to the order of
  * the floating-point additions.  on = 0: every ordered pair is evaluated.  Errors:

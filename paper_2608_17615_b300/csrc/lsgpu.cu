@@ -288,6 +288,55 @@ __device__ __forceinline__ void df_diff(float ah, float al, float bh, float bl, 
     dl = e - (dh - s);
 }
 
+// H0(k |y - x|) from the FP32 table for target (txh + txl, tyh + tyl) and source coordinates
+// sxy = (x_h, x_l, y_h, y_l): double-float differences and t, FP32 cell variable and Horner,
+// the FP64 routine outside the table range.  Returns false (H = 0) for t = 0, the self pair.
+__device__ __forceinline__ bool f32_h0(float txh, float txl, float tyh, float tyl, float4 sxy, const float2* coef,
+                                       const float4* cellv, const int2* oct, int noct, int b_lo, double k, double inv_k,
+                                       float& hr, float& him) {
+    float dxh, dxl, dyh, dyl;
+    df_diff(txh, txl, sxy.x, sxy.y, dxh, dxl);
+    df_diff(tyh, tyl, sxy.z, sxy.w, dyh, dyl);
+    float p1 = dxh * dxh, e1 = fmaf(dxh, dxh, -p1);
+    e1 = fmaf(2.f * dxh, dxl, e1);
+    float p2 = dyh * dyh, e2 = fmaf(dyh, dyh, -p2);
+    e2 = fmaf(2.f * dyh, dyl, e2);
+    float th, tl;
+    two_sum(p1, p2, th, tl);
+    tl += e1 + e2;
+    float t0 = th + tl;
+    tl = tl - (t0 - th);
+    th = t0;
+    int bits = __float_as_int(th);
+    unsigned o = (unsigned)((bits >> 23) - b_lo);
+    if (o < (unsigned)noct) {
+        int2 ob = oct[o];
+        int cell = ob.x + ((bits & 0x7fffff) >> ob.y);
+        float4 cv = cellv[cell];
+        float u = ((th - cv.x) + (tl - cv.y)) * cv.z;
+        const float2* c = coef + cell * NC_F32;
+        float2 cc = c[NC_F32 - 1];
+        hr = cc.x;
+        him = cc.y;
+#pragma unroll
+        for (int e = NC_F32 - 2; e >= 0; --e) {
+            cc = c[e];
+            hr = fmaf(hr, u, cc.x);
+            him = fmaf(him, u, cc.y);
+        }
+        return true;
+    }
+    if (th > 0.f) {
+        double2 h = ls_h0_r2((double)th + (double)tl, k, inv_k);
+        hr = (float)h.x;
+        him = (float)h.y;
+        return true;
+    }
+    hr = 0.f;
+    him = 0.f;
+    return false;
+}
+
 __global__ void __launch_bounds__(PS_TPB) k_pairsum_f32(const double2* __restrict__ xy, const double* __restrict__ w,
                                                         const double2* __restrict__ m, const double2* __restrict__ f,
                                                         int n, int src_per_chunk, double k, double inv_k,
@@ -331,44 +380,9 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum_f32(const double2* __restric
         const int cnt = min(PS_TILE, s_end - base);
         for (int i = 0; i < cnt; ++i) {
             F32Tile src = tile[i];
-            float dxh, dxl, dyh, dyl;
-            df_diff(txh, txl, src.xy.x, src.xy.y, dxh, dxl);
-            df_diff(tyh, tyl, src.xy.z, src.xy.w, dyh, dyl);
-            float p1 = dxh * dxh, e1 = fmaf(dxh, dxh, -p1);
-            e1 = fmaf(2.f * dxh, dxl, e1);
-            float p2 = dyh * dyh, e2 = fmaf(dyh, dyh, -p2);
-            e2 = fmaf(2.f * dyh, dyl, e2);
-            float th, tl;
-            two_sum(p1, p2, th, tl);
-            tl += e1 + e2;
-            float t0 = th + tl;
-            tl = tl - (t0 - th);
-            th = t0;
-            int bits = __float_as_int(th);
-            unsigned o = (unsigned)((bits >> 23) - b_lo);
             float hr, him;
-            if (o < (unsigned)noct) {
-                int2 ob = oct[o];
-                int cell = ob.x + ((bits & 0x7fffff) >> ob.y);
-                float4 cv = cellv[cell];
-                float u = ((th - cv.x) + (tl - cv.y)) * cv.z;
-                const float2* c = coef + cell * NC_F32;
-                float2 cc = c[NC_F32 - 1];
-                hr = cc.x;
-                him = cc.y;
-#pragma unroll
-                for (int e = NC_F32 - 2; e >= 0; --e) {
-                    cc = c[e];
-                    hr = fmaf(hr, u, cc.x);
-                    him = fmaf(him, u, cc.y);
-                }
-            } else if (th > 0.f) {
-                double2 h = ls_h0_r2((double)th + (double)tl, k, inv_k);
-                hr = (float)h.x;
-                him = (float)h.y;
-            } else {
+            if (!f32_h0(txh, txl, tyh, tyl, src.xy, coef, cellv, oct, noct, b_lo, k, inv_k, hr, him))
                 continue;                     // the self pair
-            }
             float tr = fmaf(hr, src.s.x, -him * src.s.y);
             float ti = fmaf(hr, src.s.y, him * src.s.x);
             float yr = tr - cr, yi = ti - ci;
@@ -380,6 +394,119 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum_f32(const double2* __restric
         }
     }
     if (j < n) partial[(size_t)blockIdx.y * n + j] = make_double2((double)sr - (double)cr, (double)si - (double)ci);
+}
+
+// Kahan step: (s, c) += v
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// The precision form's pair sum over unordered pairs: the decomposition and lane rotation
+// of k_pairsum_dfs (strips of 128 targets, circular block distances split in chunks,
+// chunk 0 also the diagonal block; rows to partial[c], columns to partial[nchunk + d - 1])
+// with the arithmetic of k_pairsum_f32 (FP32 table, double-float t, Kahan-compensated FP32
+// sums, folded into FP64 once per 128-source unit).
+__global__ void __launch_bounds__(PS_TPB) k_pairsum_f32s(const double2* __restrict__ xy, const double* __restrict__ w,
+                                                         const double2* __restrict__ m, const double2* __restrict__ f,
+                                                         int n, int nb, int dper, double k, double inv_k,
+                                                         const float4* __restrict__ tab_g, int ncell, int noct, int b_lo,
+                                                         double2* __restrict__ partial) {
+    extern __shared__ float4 ftab[];
+    __shared__ F32Tile tile[PS_TPB];
+    __shared__ float2 colbuf[PS_TPB / 32][PS_TPB];
+    const int coef_f4 = (ncell * NC_F32 + 1) / 2;
+    const int words = coef_f4 + ncell + (noct + 1) / 2;
+    for (int i = threadIdx.x; i < words; i += PS_TPB) ftab[i] = tab_g[i];
+    const float2* coef = reinterpret_cast<const float2*>(ftab);
+    const float4* cellv = ftab + coef_f4;
+    const int2* oct = reinterpret_cast<const int2*>(cellv + ncell);
+    const int I = blockIdx.x, c = blockIdx.y, nchunk = gridDim.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = I * PS_TPB + threadIdx.x;
+    const int D = nb / 2;
+    auto load_tile = [&](int blk) {
+        const int q = blk * PS_TPB + threadIdx.x;
+        F32Tile v;
+        v.xy = make_float4(0.f, 0.f, 0.f, 0.f);
+        v.s = make_float2(0.f, 0.f);
+        if (q < n) {
+            double2 p = xy[q];
+            double2 ff = f[q];
+            if (m) ff = cmul(m[q], ff);
+            double ww = w ? w[q] : 1.0;
+            float xh = (float)p.x, yh = (float)p.y;
+            v.xy = make_float4(xh, (float)(p.x - (double)xh), yh, (float)(p.y - (double)yh));
+            v.s = make_float2((float)(ww * ff.x), (float)(ww * ff.y));
+        }
+        tile[threadIdx.x] = v;
+    };
+    __syncthreads();
+    load_tile(I);
+    __syncthreads();
+    const float2 s_me = tile[threadIdx.x].s;
+    const double2 yi = xy[min(i, n - 1)];
+    const float txh = (float)yi.x, txl = (float)(yi.x - (double)txh);
+    const float tyh = (float)yi.y, tyl = (float)(yi.y - (double)tyh);
+    double accr = 0.0, acci = 0.0;
+    if (c == 0) {                          // the diagonal block: ordered pairs, rows only
+        float sr = 0.f, si = 0.f, er = 0.f, ei = 0.f;
+        for (int q = 0; q < PS_TPB; ++q) {
+            if (q == (int)threadIdx.x) continue;
+            const F32Tile src = tile[q];
+            float hr, him;
+            if (!f32_h0(txh, txl, tyh, tyl, src.xy, coef, cellv, oct, noct, b_lo, k, inv_k, hr, him)) continue;
+            kahan_add(sr, er, fmaf(hr, src.s.x, -him * src.s.y));
+            kahan_add(si, ei, fmaf(hr, src.s.y, him * src.s.x));
+        }
+        accr += (double)sr - (double)er;
+        acci += (double)si - (double)ei;
+    }
+    const int d0 = 1 + c * dper, d1 = min(D, (c + 1) * dper);
+    for (int d = d0; d <= d1; ++d) {
+        if (2 * D == nb && d == D && I >= D) continue;      // that block pair belongs to strip I - D
+        const int J = (I + d) % nb;
+        __syncthreads();
+        load_tile(J);
+        __syncthreads();
+        float sr = 0.f, si = 0.f, er = 0.f, ei = 0.f;
+#pragma unroll 1
+        for (int sub = 0; sub < PS_TPB / 32; ++sub) {
+            float cr = 0.f, ci = 0.f, ecr = 0.f, eci = 0.f;
+#pragma unroll 2
+            for (int r = 0; r < 32; ++r) {
+                const F32Tile src = tile[sub * 32 + ((lane + r) & 31)];
+                float hr, him;
+                f32_h0(txh, txl, tyh, tyl, src.xy, coef, cellv, oct, noct, b_lo, k, inv_k, hr, him);
+                kahan_add(sr, er, fmaf(hr, src.s.x, -him * src.s.y));
+                kahan_add(si, ei, fmaf(hr, src.s.y, him * src.s.x));
+                kahan_add(cr, ecr, fmaf(hr, s_me.x, -him * s_me.y));
+                kahan_add(ci, eci, fmaf(hr, s_me.y, him * s_me.x));
+                const int from = (lane + 1) & 31;
+                cr = __shfl_sync(0xffffffffu, cr, from);
+                ci = __shfl_sync(0xffffffffu, ci, from);
+                ecr = __shfl_sync(0xffffffffu, ecr, from);
+                eci = __shfl_sync(0xffffffffu, eci, from);
+            }
+            colbuf[warp][sub * 32 + lane] = make_float2(cr - ecr, ci - eci);
+        }
+        accr += (double)sr - (double)er;
+        acci += (double)si - (double)ei;
+        __syncthreads();
+        const int jj = J * PS_TPB + threadIdx.x;
+        if (jj < n) {
+            double tr = 0.0, ti = 0.0;
+#pragma unroll
+            for (int wv = 0; wv < PS_TPB / 32; ++wv) {
+                tr += (double)colbuf[wv][threadIdx.x].x;
+                ti += (double)colbuf[wv][threadIdx.x].y;
+            }
+            partial[(size_t)(nchunk + d - 1) * n + jj] = make_double2(tr, ti);
+        }
+    }
+    if (i < n) partial[(size_t)c * n + i] = make_double2(accr, acci);
 }
 
 // FP64-accurate pair sum in double-float (pairs of FP32, ~48-bit significand) on the
@@ -2167,14 +2294,27 @@ static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m, c
     } else if (df)
         launch_df(op->tab_nc, op->tab_nf, grid, op->tab_bytes, op->stream, op->xy.p, w, m, f, op->nq, op->src_per_chunk, op->k,
                   (const float4*)op->tab.p, op->tab_ncell, op->tab_noct, op->tab_blo, op->partial.p);
-    else if (op->mode == 2)
-        k_pairsum_f32<<<grid, PS_TPB, op->tab_bytes, op->stream>>>(op->xy.p, w, m, f, op->nq, op->src_per_chunk,
-                                                                    op->k, 1.0 / op->k, (const float4*)op->tab.p,
-                                                                    op->tab_ncell, op->tab_noct, op->tab_blo, op->partial.p);
-    else if (op->mode == 4)
-        k_pairsum_f32<<<grid, PS_TPB, op->t32_bytes, op->stream>>>(op->xy.p, w, m, f, op->nq, op->src_per_chunk,
-                                                                    op->k, 1.0 / op->k, (const float4*)op->tab32.p,
-                                                                    op->t32_ncell, op->t32_noct, op->t32_blo, op->partial.p);
+    else if (op->mode == 2 || op->mode == 4) {
+        // FP32 table: the operator's own (mode 2) or the mixed form's inner one (mode 4)
+        const bool inner = op->mode == 4;
+        const size_t bytes = inner ? op->t32_bytes : op->tab_bytes;
+        const float4* tab = (const float4*)(inner ? op->tab32.p : op->tab.p);
+        const int ncell = inner ? op->t32_ncell : op->tab_ncell, noct = inner ? op->t32_noct : op->tab_noct;
+        const int blo = inner ? op->t32_blo : op->tab_blo;
+        if (op->df_sym) {
+            const int D = op->dfs_nb / 2;
+            op->ps_slots = op->dfs_nchunk + D;
+            if (D > 0 && 2 * D == op->dfs_nb)
+                CK(cudaMemsetAsync(op->partial.p + (size_t)(op->ps_slots - 1) * op->nq, 0, sizeof(double2) * op->nq,
+                                   op->stream));
+            k_pairsum_f32s<<<dim3(op->dfs_nb, op->dfs_nchunk), PS_TPB, bytes, op->stream>>>(
+                op->xy.p, w, m, f, op->nq, op->dfs_nb, op->dfs_dper, op->k, 1.0 / op->k, tab, ncell, noct, blo,
+                op->partial.p);
+        } else {
+            k_pairsum_f32<<<grid, PS_TPB, bytes, op->stream>>>(op->xy.p, w, m, f, op->nq, op->src_per_chunk, op->k,
+                                                               1.0 / op->k, tab, ncell, noct, blo, op->partial.p);
+        }
+    }
     else if (op->use_table)
         launch_tab(op->tab_nc, grid, op->tab_bytes, op->stream, op->xy.p, w, m, f, op->nq, op->src_per_chunk, op->k,
                    op->tab.p, op->tab_ncell, op->tab_noct, op->tab_blo, op->partial.p);
@@ -2958,6 +3098,7 @@ static ls_status ensure_table32(ls_op* op) {
 static ls_status ensure_table32_single(ls_op* op) {
     TRY(ensure_table32(op));
     CK(raise_smem_limit(k_pairsum_f32, op->t32_bytes));
+    CK(raise_smem_limit(k_pairsum_f32s, op->t32_bytes));
     return LS_OK;
 }
 
@@ -3057,6 +3198,7 @@ static ls_status build_table_range(ls_op* op, double t_lo, double t_hi, int mode
         TRY(upload_f32_table(T, op->tab, op->tab_ncell, op->tab_noct, op->tab_blo, op->tab_bytes, err32));
         op->tab_err = err32;
         CK(raise_smem_limit(k_pairsum_f32, op->tab_bytes));
+        CK(raise_smem_limit(k_pairsum_f32s, op->tab_bytes));
         op->use_table = true;
         return LS_OK;
     }

@@ -161,18 +161,23 @@ def test_symmetric_double_float_pair_sum(case, cfg2):
 
 
 def test_pairsum_precision_form_full_size(cfg2):
-    # FP32 table (2e-8), FP32 strengths (6e-8), Kahan-compensated sums: ~1e-7 expected
+    # FP32 table (2e-8), FP32 strengths (6e-8), Kahan-compensated sums: ~1e-7 expected, for
+    # the unordered-pair kernel (default) and the ordered-pair one alike
     wl, op = cfg2
     n = wl.mesh.n_nodes
     op32 = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, use_precond=0, pairsum=2)
     f = _dev(random_density(n, 19))
     y0 = torch.empty_like(f)
     y1 = torch.empty_like(f)
+    y2 = torch.empty_like(f)
     op.pairsum_dev(f, y0)
     op32.pairsum_dev(f, y1)
+    op32.set_pair_symmetry(False)
+    op32.pairsum_dev(f, y2)
     err = (torch.linalg.norm(y1 - y0) / torch.linalg.norm(y0)).item()
-    print("precision-form pair sum rel err", err)
-    assert err < 5e-7
+    err_o = (torch.linalg.norm(y2 - y0) / torch.linalg.norm(y0)).item()
+    print("precision-form pair sum rel err: unordered pairs", err, "ordered pairs", err_o)
+    assert err < 5e-7 and err_o < 5e-7
 
 
 def test_precision_form_solutions(cfg2):
