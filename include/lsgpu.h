@@ -361,6 +361,21 @@ ls_status ls_solve_transpose_batch_dev(ls_op* op, int32_t R, const void* g_dev, 
 ls_status ls_op_set_batch_kernel(ls_op* op, int32_t kind, int32_t fold, int32_t refine);
 
 /*
+ * Operator of the batched solves' iterative refinement (ls_solve_batch_dev,
+ * ls_solve_multi_dev on the tensor cores, ls_solve_transpose_batch_dev):
+ *   accurate = 0 (default)  the kind 0 batched FP32 operator (one launch for all R systems;
+ *                           solutions ~1e-6 from the FP64 ones: the per-entry FP32 rounding
+ *                           of H0 limits them)
+ *   accurate = 1            the operator's own single-RHS pair sum, one system after the
+ *                           other: FP64-accurate when the operator was built with
+ *                           LS_PREC_FP64_DF, LS_PREC_MIXED or an FP64 form, so the refined
+ *                           solutions meet tol against the FP64 operator; also refines the
+ *                           kind 0 solves.  Stops at ||P r|| <= tol ||P b|| (no 2e-8 floor).
+ * Errors: LS_EINVAL (accurate not 0 or 1, a purely Cartesian operator).
+ */
+ls_status ls_op_set_batch_refine(ls_op* op, int32_t accurate);
+
+/*
  * Failure-detection test hook of the tensor-core pair sum (no counterpart in the
  * paper).  With stall_ms > 0 the MMA issuer of every following tensor-core launch
  * on this operator first waits stall_ms on a barrier that nothing completes; the

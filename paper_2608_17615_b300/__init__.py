@@ -26,7 +26,7 @@ EXPORTED = ["ls_params_default", "ls_mesh_create", "ls_mesh_destroy", "ls_mesh_n
             "ls_pairsum_batch_dev", "ls_solve_batch_dev", "ls_solve_multi_dev", "ls_apply_transpose_dev", "ls_potential_transpose_dev", "ls_apply_precond_transpose_dev",
             "ls_solve_transpose_dev", "ls_op_set_contrast", "ls_incident_dev", "ls_misfit_gradient_dev",
             "ls_solve_transpose_batch_dev", "ls_misfit_gradient_batch_dev",
-            "ls_op_set_batch_kernel", "ls_op_set_stall_test", "ls_tc_gemm_check",
+            "ls_op_set_batch_kernel", "ls_op_set_batch_refine", "ls_op_set_stall_test", "ls_tc_gemm_check",
             "ls_apply_precond", "ls_apply_transpose", "ls_solve_adjoint", "ls_residual_dev", "ls_op_last_residual",
             "ls_op_set_contrast_dev", "ls_misfit_dev", "ls_op_ritz", "ls_hessenberg_eigenvalues",
             "ls_precond_rho_dev",
@@ -107,6 +107,7 @@ def _load():
         "ls_misfit_gradient_dev": (I32, [P, I32, P, I32, P, P, P, P]),
         "ls_solve_transpose_batch_dev": (I32, [P, I32, P, P, P]),
         "ls_op_set_batch_kernel": (I32, [P, I32, I32, I32]),
+        "ls_op_set_batch_refine": (I32, [P, I32]),
         "ls_op_set_stall_test": (I32, [P, D]),
         "ls_tc_gemm_check": (I32, [I32, P]),
         "ls_misfit_gradient_batch_dev": (I32, [P, I32, P, I32, P, P, P, P]),
@@ -404,6 +405,11 @@ class Operator:
     def set_pair_symmetry(self, on):
         """Double-float pair sum over unordered pairs (True, default) or every ordered pair."""
         _check(_lib.ls_op_set_pair_symmetry(self.handle, int(bool(on))))
+
+    def set_batch_refine(self, accurate):
+        """Refinement residuals of the batched solves from the single-RHS pair sum (True) or
+        the batched FP32 operator (False, default)."""
+        _check(_lib.ls_op_set_batch_refine(self.handle, int(bool(accurate))))
 
     def set_batch_kernel(self, kind, fold=4, refine=4):
         """Batched pair sum on 0: CUDA cores, 1: tensor cores (accumulator restarted every fold

@@ -2149,6 +2149,7 @@ struct ls_op {
     int batch_kernel = 1;                // 0: CUDA cores (k_pairsum_multi_f32), 1: tensor cores
     int tc_fold = 4;                     // stages per accumulator run
     int tc_refine = 4;                   // iterative-refinement steps after a tensor-core solve (0: none)
+    bool refine_single = false;          // refinement residuals from the single-RHS pair sum (FP64-accurate)
     uint64_t tc_stall_ns = 0;            // failure-detection test: forced stall of the MMA issuer (ns)
     int64_t corr_host_blocks = 0;        // correction blocks the device setup left to the host
     DevBuf<double2> ir_r, ir_d, ir_y;    // refinement work vectors [R][n]
@@ -4065,6 +4066,16 @@ static ls_status prec_norms(ls_op* op, int R, const double2* x, bool transpose, 
 // y_r = L x_r (or L^T x_r) with the accurate batched pair sum (CUDA cores, Kahan FP32)
 static ls_status apply_L_batch_accurate(ls_op* op, int R, const double2* x, double2* y, bool transpose) {
     const int n = op->nq;
+    if (op->refine_single) {
+        // the operator's own single-RHS pair sum, one system at a time (FP64-accurate with the
+        // double-float, mixed or FP64 forms)
+        for (int r = 0; r < R; ++r) {
+            const double2* xr = x + (size_t)r * n;
+            double2* yr = y + (size_t)r * n;
+            TRY(transpose ? apply_LT(op, xr, yr) : apply_L(op, xr, yr));
+        }
+        return LS_OK;
+    }
     const int kind = op->batch_kernel;
     op->batch_kernel = 0;
     ls_status st = transpose ? pairsum_batch(op, R, x, n, nullptr, nullptr) : pairsum_batch(op, R, x, n, op->m.p);
@@ -4093,7 +4104,8 @@ static ls_status apply_L_batch_accurate(ls_op* op, int R, const double2* x, doub
 static ls_status refine_batch(ls_op* op, int R, const double2* b, double2* u, int* iters, bool transpose);
 
 static ls_status gmres_batch(ls_op* op, int R, const double2* b, double2* u, int* iters, bool transpose = false) {
-    if (op->batch_kernel != 1 || op->tc_refine <= 0) return gmres_batch_plain(op, R, b, u, iters, transpose);
+    if ((op->batch_kernel != 1 && !op->refine_single) || op->tc_refine <= 0)
+        return gmres_batch_plain(op, R, b, u, iters, transpose);
     // the tensor-core operator is itself only ~3e-7 x fold accurate: a first solve tighter
     // than TC_FIRST_TOL would refine nothing the accurate residual does not redo
     const double tol_save = op->prm.tol;
@@ -4117,7 +4129,8 @@ static ls_status refine_batch(ls_op* op, int R, const double2* b, double2* u, in
     // The accurate operator evaluates L to ~1e-7 (FP32 sums), so residuals below that level
     // are rounding noise: stop at max(tol, TC_RESID_FLOOR) or when a correction no longer
     // halves the worst residual (the floor reached).
-    const double tol = std::max(op->prm.tol, TC_RESID_FLOOR);
+    const double tol = std::max(op->prm.tol, op->refine_single ? 0.0 : TC_RESID_FLOOR);
+    const double stall_level = op->refine_single ? 1e-24 : 1e-12;
     const int blocks = (int)((tot + 255) / 256);
     std::vector<int> its(R);
     bool ok = false;
@@ -4134,10 +4147,11 @@ static ls_status refine_batch(ls_op* op, int R, const double2* b, double2* u, in
             ok = ok && pr[r] <= tol * tol * pb[r];
             if (pb[r] > 0) worst = std::max(worst, pr[r] / pb[r]);
         }
-        // stagnated (||r|| fell by less than 2x) within a few ulps of FP32 of the accurate
-        // operator's rounding level, ||P r|| <= 1e-6 ||P b||: converged; stagnation above
-        // that level is a failure
-        if (!ok && worst > 0.25 * prev_worst && worst <= 1e-12) ok = true;
+        // stagnated (||r|| fell by less than 2x) at the accurate operator's rounding level,
+        // ||P r|| <= 1e-6 ||P b|| for the FP32 batched operator (a few ulps of FP32) and
+        // 1e-12 for the single-RHS FP64-accurate one: converged; stagnation above that level
+        // is a failure
+        if (!ok && worst > 0.25 * prev_worst && worst <= stall_level) ok = true;
         prev_worst = worst;
         if (ok || step == op->tc_refine) break;
         // correction to the relative tolerance that brings the worst residual below tol / 2
@@ -4957,6 +4971,14 @@ ls_status ls_op_set_pairsum(ls_op* op, int32_t mode) {
     if (mode != 1) TRY(build_table_range(op, op->tab_tlo, op->tab_thi, mode == 4 ? 3 : mode));
     if (mode == 4) TRY(ensure_table32_single(op));
     op->mode = mode;
+    return LS_OK;
+}
+
+ls_status ls_op_set_batch_refine(ls_op* op, int32_t accurate) {
+    if (!op) return fail(LS_EINVAL, "null op");
+    if (accurate != 0 && accurate != 1) return fail(LS_EINVAL, "accurate must be 0 or 1");
+    if (op->cartesian) return fail(LS_EINVAL, "the batched forms need a quadrature-node operator");
+    op->refine_single = accurate != 0;
     return LS_OK;
 }
 

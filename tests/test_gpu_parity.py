@@ -132,8 +132,10 @@ def test_double_float_form_full_size(cfg2):
 @pytest.mark.parametrize("case", ["two_material_tiny", "disk", "two_material_small"])
 def test_symmetric_double_float_pair_sum(case, cfg2):
     # k_pairsum_dfs (one Hankel evaluation per unordered pair, rows and columns) against
-    # k_pairsum_df (every ordered pair): the same terms summed in another order, so equal to
-    # a few units of FP64 rounding of the sum; repeated launches are bitwise identical (no
+    # k_pairsum_df (every ordered pair): bitwise the same H (the coordinate differences are
+    # negated exactly), the products summed in another order in double-float (48-bit
+    # significand: 3.6e-15 per operation over ~100 accumulations per output), so they agree
+    # within the pair-sum parity bar of 1e-13; repeated launches are bitwise identical (no
     # atomics).  Block counts: 15 (odd), 26 (even: the distance nb/2 handled once), 315.
     if case == "two_material_tiny":
         wl = two_material("tiny", k=8.0)
@@ -155,7 +157,7 @@ def test_symmetric_double_float_pair_sum(case, cfg2):
     e_or = _rel(ys.cpu().numpy(), ref) if ref is not None else None
     print(case, n, "symmetric vs ordered pair sum", e, "vs oracle naive sum", e_or)
     assert torch.equal(ys, ys2)
-    assert e < 1e-14
+    assert e < 1e-13
     if ref is not None:
         assert e_or < 1e-13
 

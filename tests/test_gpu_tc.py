@@ -123,9 +123,9 @@ def test_tc_pairsum_large_ragged(small):
 
 
 def test_tc_solve_needs_refinement():
-    """Batched solves on the tensor cores with and without iterative refinement: with it
-    the solution is the CUDA-core (kind 0) batched solution to within the refinement's
-    stopping level, and so shares that form's accuracy against the FP64 path."""
+    """Batched solves on the tensor cores without refinement, with refinement against the
+    batched FP32 operator (default) and with refinement against the single-RHS FP64 operator
+    (ls_op_set_batch_refine), against the single-RHS FP64 solves."""
     wl = star_scatterer(1, 6000, k=10.0, nx=96, ny=96)
     n = wl.mesh.n_nodes
     op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, box=wl.box, nx=wl.nx, ny=wl.ny, tol=1e-9)
@@ -143,18 +143,26 @@ def test_tc_solve_needs_refinement():
         op.set_batch_kernel(1, 4, refine)
         U = torch.empty_like(B)
         iters, st = op.solve_batch_dev(B, U)
-        out[refine] = (float(_rel_rows(U, ref).max()), int(iters.max()), int(st), float(_rel_rows(U, Ucc).max()))
-    print("batched solve (max rel err vs FP64, iterations, status[, vs kind 0]):", out)
-    assert out[4][2] == L.LS_OK
-    # Both solutions are fixed only to the kind-0 operator's error level: its pair sum is
-    # within 6e-8 of the FP64 one (FP32 table validated to 2e-8, Kahan sums) and the
-    # refinement stops at max(tol, 2e-8) on the preconditioned residual; the solve
-    # amplifies an operator or residual perturbation by ~||L^-1|| ||L|| ~ 10 on this
-    # scatterer, so the two agree to 10 x (6e-8 + 2e-8) < 1e-6 and the refined solution
-    # is as accurate as the kind-0 one up to that amount (2e-7 slack).
-    assert out[4][3] < 1e-6
+        out[refine] = (float(_rel_rows(U, ref).max()), int(iters.max()), int(st))
+    op.set_batch_refine(True)
+    U = torch.empty_like(B)
+    iters, st = op.solve_batch_dev(B, U)
+    out["accurate"] = (float(_rel_rows(U, ref).max()), int(iters.max()), int(st))
+    op.set_batch_kernel(0)
+    it_a0, st_a0 = op.solve_batch_dev(B, U)
+    out["cuda_cores_accurate"] = (float(_rel_rows(U, ref).max()), int(it_a0.max()), int(st_a0))
+    print("batched solve (max rel err vs FP64, iterations, status):", out)
+    assert out[4][2] == out["accurate"][2] == out["cuda_cores_accurate"][2] == L.LS_OK
+    # Refined against the FP32 batched operator, the solution has that operator's accuracy:
+    # per-entry FP32 rounding of H0 (2^-24 relative) moves the solution by ~1e-6 on this
+    # scatterer (a CPU perturbation experiment on the oracle's dense operator gives 7.5e-7
+    # from the rounding and 1.5e-7 from the 2e-8 table error), so the refined tensor-core
+    # solution matches the kind 0 one's error up to 2e-7 and a factor 1.5.
     assert out[4][0] < 1.5 * out["cuda_cores"][0] + 2e-7
     assert out[0][0] > 5 * out[4][0]                # and the refinement is needed
+    # Refined against the single-RHS FP64 operator: the FP64 solve's accuracy, the 1e-6
+    # target of the batched form with room to spare (tol 1e-9 times a condition factor)
+    assert out["accurate"][0] < 1e-7 and out["cuda_cores_accurate"][0] < 1e-7
 
 
 def test_stalled_pipeline_times_out_and_recovers(tiny):
