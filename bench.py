@@ -132,22 +132,24 @@ FP32_PEAK_SOURCE = "FP32 unit count: 148 SMs x 128 lanes x 2 flops x 2.032 GHz"
 #  0 k_pairsum_tab (FP64): dx, dy 2; t 3; u 2; two Horner chains 4 (nc - 1); complex MAC 8
 #  1 k_pairsum (FP64, direct): 89 FP64 instructions per pair measured by ncu (58.5 DFMA,
 #    23.5 DMUL, 7.1 DADD) -> 148
-#  2 k_pairsum_f32 (FP32): two double-float differences 22, double-float t 16, u 4, two
-#    degree-6 Horner chains 24, complex multiply 6, Kahan sums 8 -> 80
-#  3 k_pairsum_df (double-float on FP32): differences 22, t 12, u 8, per chain nf FP32
-#    Horner steps (2 flops) and nc - 1 - nf double-float steps (15 flops), DF complex MAC 60
-# The unordered-pair kernels of modes 2 and 3 (k_pairsum_f32s, k_pairsum_dfs, the default)
-# form H once per unordered pair and do both multiply-adds: per ordered pair half the
-# H flops (differences, t, u, Horner) plus one multiply-add (mode 2: complex multiply 6 +
-# Kahan 8; mode 3: 60).
+#  2 FP32 table: H = two double-float differences 22, double-float t 21, u 4, two degree-6
+#    Horner chains 24 (71); multiply-add = complex multiply 6 + Kahan sums 8 (14)
+#  3 double-float table: H = differences 22, t 21, u 10, per chain nf FP32 Horner steps
+#    (2 flops) and nc - 1 - nf double-float steps (18 flops); multiply-add = four
+#    double-float products 40 + four double-float sums 44 (84)
+# The unordered-pair kernels (k_pairsum_f32s, k_pairsum_dfs, the default) form H once per
+# unordered pair and do both multiply-adds: per ordered pair H / 2 plus one multiply-add.
+# ncu check (k_pairsum_dfs<10, 2>, 40,200 nodes): FADD 167.2 + FMUL 14.1 + 2 x FFMA 39.3 =
+# 259.9 FP32 flops per ordered pair against 240.5 counted here (the rest: the diagonal
+# blocks' ordered pairs and the FP64 folds).
 def flops_per_pair_of(mode, nc, nf=0, symmetric=True):
     if mode == 0:
         return 15 + 4 * (nc - 1)
     if mode == 3:
-        h = 42 + 2 * (2 * nf + 15 * (nc - 1 - nf))
-        return h / 2 + 60 if symmetric else h + 60
+        h = 53 + 4 * nf + 36 * (nc - 1 - nf)
+        return h / 2 + 84 if symmetric else h + 84
     if mode == 2:
-        return 66 / 2 + 14 if symmetric else 80
+        return 71 / 2 + 14 if symmetric else 85
     return 148
 
 
