@@ -35,7 +35,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "two-material disk, k=20, 40,200 nodes (2,680 curved P4 triangles), 256^2 Cartesian preconditioner, tol 1e-8"
-METRIC = "LS GMRES solves/s (FP64-accurate double-float pair sum, preconditioned)"
+METRIC = ("LS GMRES solves/s (FP64-accurate: FP32 GMRES refined until the double-float operator's residual "
+          "meets tol, preconditioned)")
 # Preconditioned GMRES iterations of this workload as measured by the GPU arm;
 # the reference arm scales its sampled matvec cost by it.
 REFERENCE_ITERS = 8
@@ -175,10 +176,15 @@ def _timed(fn, stream, reps=1):
     return e0.elapsed_time(e1) / reps, out
 
 
-def _pairsum_roofline(op, n, peak, peak_source, total_ms=None):
-    """Roofline of the single-RHS pair-sum kernel from the operator's event-timed launches."""
-    ps_ms, ps_launches, _ = op.stats()
-    mode = op.params.prec
+def _pairsum_roofline(op, n, peak, peak_source, total_ms=None, kind=None):
+    """Roofline of a single-RHS pair-sum kernel from the operator's event-timed launches
+    (kind: the arithmetic of the launches to take, LS_PREC_*; default the operator's own)."""
+    if kind is None:
+        ps_ms, ps_launches, _ = op.stats()
+        mode = op.params.prec
+    else:
+        ps_ms, ps_launches = op.stats_kind(kind)
+        mode = kind
     nc, _ = op.tuning()
     nf = op.df_tail() if mode == 3 else 0
     fpp = flops_per_pair_of(mode, nc, nf)
@@ -604,7 +610,7 @@ def main():
     wl = two_material("small")
     n = wl.mesh.n_nodes
     t0 = time.perf_counter()
-    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, tol=1e-8, prec=LS_PREC_FP64_DF)
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, tol=1e-8, prec=LS_PREC_MIXED)
     setup_s = time.perf_counter() - t0
     fp64_probe = L.probe_fp64()
     setup_parts = {k: round(float(v), 3) for k, v in
@@ -649,8 +655,14 @@ def main():
     total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     iters = statistics.mean(iters_list)
     value = aggregate_value(world, args.steps, total_ms)
-    pairs_per_solve = (iters + 1) * n * (n - 1)
-    roofline = _pairsum_roofline(op, n, FP32_PEAK_TFLOPS, FP32_PEAK_SOURCE, total_ms)
+    pairs_per_solve = ps_launches / args.steps * n * (n - 1)
+    # the mixed form launches the FP32 kernel (inner GMRES) and the double-float one (accurate
+    # residuals); the roofline is the dominant one's, the other's share is listed beside it
+    by_kind = {kd: op.stats_kind(kd) for kd in (LS_PREC_FP32, LS_PREC_FP64_DF)}
+    dominant = max(by_kind, key=lambda kd: by_kind[kd][0])
+    roofline = _pairsum_roofline(op, n, FP32_PEAK_TFLOPS, FP32_PEAK_SOURCE, total_ms, kind=dominant)
+    other = LS_PREC_FP64_DF if dominant == LS_PREC_FP32 else LS_PREC_FP32
+    roofline["other_kernel"] = _pairsum_roofline(op, n, FP32_PEAK_TFLOPS, FP32_PEAK_SOURCE, total_ms, kind=other)
     op.set_timing(False)
     # end to end through the host-buffer entry point
     e2e_ms = []
@@ -661,7 +673,13 @@ def main():
         uh, uinfh, hist, it_h, st_h = op.solve([angle], wl.ff_angles)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e = {"value": world * args.steps / (sum(e2e_ms) * 1e-3), "unit": "solves/s",
-           "h2d_bytes_per_step": 8 * (1 + n_ff), "d2h_bytes_per_step": 16 * n + 16 * n_ff + 8 * (int(it_h[0]) + 1)}
+           "h2d_bytes_per_step": 8 * (1 + n_ff), "d2h_bytes_per_step": 16 * n + 16 * n_ff + 8 * (op.params.max_iter + 1)}
+    # reference: the double-float GMRES solve (every pair sum FP64-accurate) of the same system
+    op.set_pairsum(LS_PREC_FP64_DF)
+    u_ref = torch.empty_like(u)
+    it_ref, _ = op.solve_dev(b.view(1, -1), u_ref.view(1, -1))
+    iters_fp64 = int(it_ref[0])
+    err_headline = (torch.linalg.norm(u - u_ref) / torch.linalg.norm(u_ref)).item()
     forms = {}
 
     def pipe_form(mode, label, peak, peak_source):
@@ -676,19 +694,19 @@ def main():
         op.set_timing(False)
         return {"config": {"workload": WORKLOAD + ", " + label}, "value": 1e3 / ms, "unit": "solves/s", "ms": ms,
                 "iterations": int(it_[0]), "status": int(st_), "explicit_exit_residual": op.last_residual(),
-                "rel_err_vs_fp64_accurate_solution": (torch.linalg.norm(uu - u) / torch.linalg.norm(u)).item(),
+                "rel_err_vs_fp64_accurate_solution": (torch.linalg.norm(uu - u_ref) / torch.linalg.norm(u_ref)).item(),
                 "pairs_per_s": (int(it_[0]) + 1) * n * (n - 1) / (ms * 1e-3), "roofline": rl}
 
     run_forms = args.forms != "none"
     if run_forms:
+        _form(forms, "cfg2_double_float", lambda: pipe_form(LS_PREC_FP64_DF, "double-float pair sum in every GMRES "
+                                                            "iteration", FP32_PEAK_TFLOPS, FP32_PEAK_SOURCE))
         _form(forms, "cfg2_fp64_pipe",
               lambda: dict(pipe_form(LS_PREC_FP64_TABLE, "FP64-pipe table pair sum", fp64_probe / 1e3,
                                      "measured FP64 FMA probe (ls_probe_fp64), same run"),
                            fp64_unit_count_peak_tflops=FP64_UNIT_PEAK_TFLOPS))
         _form(forms, "cfg2_fp32", lambda: pipe_form(LS_PREC_FP32, "FP32 precision-form pair sum", FP32_PEAK_TFLOPS,
                                                     FP32_PEAK_SOURCE))
-        _form(forms, "cfg2_mixed", lambda: pipe_form(LS_PREC_MIXED, "mixed precision: FP32 GMRES refined against the "
-                                                     "double-float operator (iterations: all inner ones)", None, None))
         op.set_pairsum(LS_PREC_FP64_DF)
 
         def batched_forms():
@@ -707,7 +725,7 @@ def main():
                 out[name] = {"value": R64 / (ms64 * 1e-3), "unit": "solves/s", "ms": ms64, "status": int(st64),
                              "iterations_max": int(np.max(it64)),
                              "rel_err_vs_fp64_accurate_solution":
-                                 (torch.linalg.norm(U64[0] - u) / torch.linalg.norm(u)).item()}
+                                 (torch.linalg.norm(U64[0] - u_ref) / torch.linalg.norm(u_ref)).item()}
             op.set_batch_kernel(1)
             op.set_batch_refine(False)
             out["config"] = {"workload": WORKLOAD + ", 64 incident directions in lock step"}
@@ -726,7 +744,7 @@ def main():
                 ms, (it_, st_) = _timed(lambda: opa.solve_dev(b.view(1, -1), ua.view(1, -1)), stream)
                 out[f"approach_{approach}"] = {"iterations": int(it_[0]), "status": int(st_), "ms": ms,
                                                "rel_err_vs_fp64_accurate_solution":
-                                                   (torch.linalg.norm(ua - u) / torch.linalg.norm(u)).item()}
+                                                   (torch.linalg.norm(ua - u_ref) / torch.linalg.norm(u_ref)).item()}
                 del opa
             out["config"] = {"workload": WORKLOAD + ", FP32 pair sum, Approach I vs II transfer "
                                              "(Table bakeoff context)"}
@@ -742,19 +760,22 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64-accurate: double-float pair sum on the FP32 pipe, FP64 correction, preconditioner and Krylov",
+            "dtype": "f64-accurate (mixed): FP32 pair sum inside GMRES, double-float (FP64-accurate) pair sum for the "
+                     "residuals that decide convergence; FP64 correction, preconditioner and Krylov",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "nodes": n, "k": wl.k, "grid": [wl.nx, wl.ny],
                        "l2": "flushed (512 MB write) before every timed step", "parallelism": "replicas"},
-            "iterations": iters, "explicit_exit_residual": exit_res,
+            "iterations_all_inner": iters, "iterations_fp64_gmres": iters_fp64, "explicit_exit_residual": exit_res,
+            "rel_err_vs_double_float_gmres_solution": err_headline,
             "pairs_per_s": world * pairs_per_solve * args.steps / (total_ms * 1e-3),
-            "matvecs_per_s": world * (iters + 1) * args.steps / (total_ms * 1e-3), "setup_s": setup_s,
+            "matvecs_per_s": world * ps_launches / (total_ms * 1e-3), "setup_s": setup_s,
             "setup_parts_s": setup_parts, "wall_s_timed": wall, "roofline": roofline, "gpu_launches": launches,
             "clocks": clocks.summary(), "e2e": e2e, "forms": forms}
     if rank == 0 and not args.no_cpu_baseline:
         Lu = torch.empty_like(u)
+        op.set_pairsum(LS_PREC_FP64_DF)
         op.apply_dev(u, Lu)
-        cb, err = cpu_baseline(wl, u.cpu().numpy(), Lu.cpu().numpy(), int(round(iters)))
+        cb, err = cpu_baseline(wl, u.cpu().numpy(), Lu.cpu().numpy(), iters_fp64)
         line["cpu_baseline"] = cb
         line["matvec_rel_err_vs_oracle"] = err
     if rank == 0:

@@ -499,6 +499,10 @@ ls_status ls_op_setup_times(const ls_op* op, double* t4);
    (their terms stay below 2^-50 of |H0| on every cell; 0 otherwise).  Pointers may be NULL. */
 ls_status ls_op_tuning(const ls_op* op, int32_t* table_ncoef, double* cand_ms, int32_t* fp32_tail);
 ls_status ls_op_stats(ls_op* op, double* pairsum_ms, int64_t* pairsum_launches, int64_t* launches);
+/* The same restricted to the timed pair-sum launches of one arithmetic: kind = LS_PREC_* of the
+   kernel that ran (the mixed form's inner launches count as LS_PREC_FP32, its residuals as
+   LS_PREC_FP64_DF), 10 = the CUDA-core batched kernel, 11 = the tensor-core batched kernel. */
+ls_status ls_op_stats_kind(ls_op* op, int32_t kind, double* pairsum_ms, int64_t* pairsum_launches);
 
 /* Diagnostic: measured FP64 FMA throughput of the device in GFLOP/s (2 flops per FMA). */
 ls_status ls_probe_fp64(double* gflops, void* stream);

@@ -30,7 +30,7 @@ EXPORTED = ["ls_params_default", "ls_mesh_create", "ls_mesh_destroy", "ls_mesh_n
             "ls_apply_precond", "ls_apply_transpose", "ls_solve_adjoint", "ls_residual_dev", "ls_op_last_residual",
             "ls_op_set_contrast_dev", "ls_misfit_dev", "ls_op_ritz", "ls_hessenberg_eigenvalues",
             "ls_precond_rho_dev",
-            "ls_op_set_pairsum", "ls_op_set_pair_symmetry", "ls_op_set_timing", "ls_op_setup_times", "ls_op_tuning", "ls_op_stats", "ls_probe_fp64", "ls_pairsum_noalloc", "ls_last_error"]
+            "ls_op_set_pairsum", "ls_op_set_pair_symmetry", "ls_op_set_timing", "ls_op_setup_times", "ls_op_tuning", "ls_op_stats", "ls_op_stats_kind", "ls_probe_fp64", "ls_pairsum_noalloc", "ls_last_error"]
 
 
 class LsError(RuntimeError):
@@ -117,6 +117,7 @@ def _load():
         "ls_op_setup_times": (I32, [P, P]),
         "ls_op_tuning": (I32, [P, P, P, P]),
         "ls_op_stats": (I32, [P, P, P, P]),
+        "ls_op_stats_kind": (I32, [P, I32, P, P]),
         "ls_probe_fp64": (I32, [P, P]),
         "ls_pairsum_noalloc": (I32, [I32, P, P, P, D, P, P]),
         "ls_last_error": (ctypes.c_char_p, []),
@@ -450,6 +451,14 @@ class Operator:
         la = ctypes.c_int64()
         _check(_lib.ls_op_stats(self.handle, ctypes.byref(ms), ctypes.byref(pl), ctypes.byref(la)))
         return ms.value, pl.value, la.value
+
+    def stats_kind(self, kind):
+        """(ms, launches) of the timed pair-sum launches of one arithmetic (LS_PREC_*; 10, 11:
+        the CUDA-core and tensor-core batched kernels)."""
+        ms = ctypes.c_double()
+        pl = ctypes.c_int64()
+        _check(_lib.ls_op_stats_kind(self.handle, int(kind), ctypes.byref(ms), ctypes.byref(pl)))
+        return ms.value, pl.value
 
     def correction(self):
         """The library's correction dV as (rowptr, cols, vals)."""

@@ -2181,6 +2181,7 @@ struct ls_op {
     int64_t launches = 0, pairsum_launches = 0;
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    std::vector<int8_t> ev_kind;         // arithmetic of each timed launch (LS_PREC_*; 10/11 batched kernels)
     ~ls_op() {
         for (auto& e : ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
         if (gP) cudaGraphExecDestroy(gP);
@@ -2279,6 +2280,7 @@ static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m, c
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
         op->ev.emplace_back(e0, e1);
+        op->ev_kind.push_back((int8_t)(op->mode == 4 ? (op->inner32 ? 2 : 3) : op->mode));
         CK(cudaEventRecord(e0, op->stream));
     }
     op->ps_slots = op->nchunk;
@@ -3824,6 +3826,7 @@ static ls_status pairsum_batch(ls_op* op, int R, const double2* f, size_t sf, co
             CK(cudaEventCreate(&e0));
             CK(cudaEventCreate(&e1));
             op->ev.emplace_back(e0, e1);
+            op->ev_kind.push_back(11);
             CK(cudaEventRecord(e0, op->stream));
         }
         TRY(pairsum_batch_tc(op, R, f, sf, m, w));
@@ -3838,6 +3841,7 @@ static ls_status pairsum_batch(ls_op* op, int R, const double2* f, size_t sf, co
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
         op->ev.emplace_back(e0, e1);
+        op->ev_kind.push_back(10);
         CK(cudaEventRecord(e0, op->stream));
     }
     MultiArgs A = multi_args(op, R, f, sf, m);
@@ -5009,6 +5013,7 @@ ls_status ls_op_set_timing(ls_op* op, int32_t on) {
     CK(cudaStreamSynchronize(op->stream));
     for (auto& e : op->ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     op->ev.clear();
+    op->ev_kind.clear();
     op->timing = on != 0;
     op->launches = 0;
     op->pairsum_launches = 0;
@@ -5027,6 +5032,23 @@ ls_status ls_op_stats(ls_op* op, double* pairsum_ms, int64_t* pairsum_launches, 
     if (pairsum_ms) *pairsum_ms = tot;
     if (pairsum_launches) *pairsum_launches = op->timing ? (int64_t)op->ev.size() : op->pairsum_launches;
     if (launches) *launches = op->launches;
+    return LS_OK;
+}
+
+ls_status ls_op_stats_kind(ls_op* op, int32_t kind, double* pairsum_ms, int64_t* pairsum_launches) {
+    if (!op) return fail(LS_EINVAL, "null op");
+    CK(cudaStreamSynchronize(op->stream));
+    double tot = 0.0;
+    int64_t cnt = 0;
+    for (size_t i = 0; i < op->ev.size(); ++i) {
+        if (op->ev_kind[i] != kind) continue;
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, op->ev[i].first, op->ev[i].second));
+        tot += ms;
+        cnt++;
+    }
+    if (pairsum_ms) *pairsum_ms = tot;
+    if (pairsum_launches) *pairsum_launches = cnt;
     return LS_OK;
 }
 
