@@ -88,7 +88,7 @@ typedef struct {
 } ls_params;
 
 /* Defaults: tol 1e-8, max_iter 600, use_precond 1, kappa 3, box [-1.2,1.2]^2, 256 x 256,
-   prec LS_PREC_FP64_TABLE, approach 2, setup_on_device 1. */
+   prec LS_PREC_FP64_DF, approach 2, setup_on_device 1. */
 void ls_params_default(ls_params* p);
 
 /*

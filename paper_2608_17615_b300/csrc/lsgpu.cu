@@ -3009,7 +3009,7 @@ void ls_params_default(ls_params* p) {
     p->box[0] = -1.2; p->box[1] = 1.2; p->box[2] = -1.2; p->box[3] = 1.2;
     p->nx = 256;
     p->ny = 256;
-    p->prec = LS_PREC_FP64_TABLE;
+    p->prec = LS_PREC_FP64_DF;
     p->approach = 2;
     p->setup_on_device = 1;
 }

@@ -79,8 +79,10 @@ def test_apply_parity_full(case):
 
 @pytest.fixture(scope="module")
 def cfg2():
-    wl = two_material("small")                 # 40,200 nodes, k = 20, 256^2 grid
-    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, tol=1e-8)
+    # 40,200 nodes, k = 20, 256^2 grid; the FP64-pipe table form, the reference the other
+    # arithmetics are compared with
+    wl = two_material("small")
+    op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, tol=1e-8, pairsum=0)
     return wl, op
 
 

@@ -37,7 +37,7 @@ def test_params_default():
     p = L.params_default()
     assert p.tol == 1e-8 and p.max_iter == 600 and p.use_precond == 1 and p.kappa == 3.0
     assert list(p.box) == [-1.2, 1.2, -1.2, 1.2] and p.nx == 256 and p.ny == 256
-    assert p.prec == L.LS_PREC_FP64_TABLE and p.approach == 2 and p.setup_on_device == 1
+    assert p.prec == L.LS_PREC_FP64_DF and p.approach == 2 and p.setup_on_device == 1
 
 
 def test_mesh_rejects_clockwise_element():
