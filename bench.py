@@ -717,7 +717,7 @@ def main():
             U64 = torch.empty_like(B64)
             out = {}
             for kind, accurate, name in ((1, False, "tensor_cores"), (1, True, "tensor_cores_fp64_refined"),
-                                         (0, False, "cuda_cores")):
+                                         (0, False, "cuda_cores"), (2, False, "cuda_cores_double_float")):
                 op.set_batch_kernel(kind)
                 op.set_batch_refine(accurate)
                 op.solve_batch_dev(B64, U64)                              # warm-up (workspace)

@@ -355,8 +355,15 @@ ls_status ls_solve_transpose_batch_dev(ls_op* op, int32_t R, const void* g_dev, 
  *           preconditioner run in FP32 (FP32 copies of the factors, made on first
  *           use); P only weights the residual norm, so the refined solution keeps
  *           the kind 0 accuracy.  Kind 0 keeps the FP64 sweeps.
+ *   kind 2  CUDA cores in double-float (FP64-accurate): H from the operator's
+ *           double-float table, densities and sums in double-float pairs; needs an
+ *           operator built with LS_PREC_FP64_DF or LS_PREC_MIXED (LS_EINVAL
+ *           otherwise; switching the operator away from them resets kind 2 to 0);
+ *           no refinement; single-operator solves only (ls_solve_multi_dev takes 0
+ *           or 1).  The same kernel forms the refinement residuals of kinds 0 and 1
+ *           under ls_op_set_batch_refine(op, 1) on such operators.
  * Defaults: kind 1, fold 4, refine 4.
- * Errors: LS_EINVAL for kind outside {0, 1}, fold < 1 or refine < 0.  A stalled
+ * Errors: LS_EINVAL for kind outside {0, 1, 2}, fold < 1 or refine < 0.  A stalled
  * tensor-core pipeline (every wait in the kernel is bounded) makes the next call
  * that synchronises return LS_ETIMEOUT.
  */
@@ -368,10 +375,11 @@ ls_status ls_op_set_batch_kernel(ls_op* op, int32_t kind, int32_t fold, int32_t 
  *   accurate = 0 (default)  the kind 0 batched FP32 operator (one launch for all R systems;
  *                           solutions ~1e-6 from the FP64 ones: the per-entry FP32 rounding
  *                           of H0 limits them)
- *   accurate = 1            the operator's own single-RHS pair sum, one system after the
- *                           other: FP64-accurate when the operator was built with
- *                           LS_PREC_FP64_DF, LS_PREC_MIXED or an FP64 form, so the refined
- *                           solutions meet tol against the FP64 operator; also refines the
+ *   accurate = 1            an FP64-accurate operator: on an operator built with
+ *                           LS_PREC_FP64_DF or LS_PREC_MIXED the batched double-float pair
+ *                           sum (batch kernel 2's) over all R systems, on the FP64 forms the
+ *                           single-RHS pair sum one system after the other; the refined
+ *                           solutions meet tol against the FP64 operator.  Also refines the
  *                           kind 0 solves.  Stops at ||P r|| <= tol ||P b|| (no 2e-8 floor).
  * Errors: LS_EINVAL (accurate not 0 or 1, a purely Cartesian operator).
  */

@@ -413,8 +413,9 @@ class Operator:
         _check(_lib.ls_op_set_batch_refine(self.handle, int(bool(accurate))))
 
     def set_batch_kernel(self, kind, fold=4, refine=4):
-        """Batched pair sum on 0: CUDA cores, 1: tensor cores (accumulator restarted every fold
-        stages; batched solves refined up to `refine` times against the kind-0 operator)."""
+        """Batched pair sum on 0: CUDA cores (FP32), 1: tensor cores (accumulator restarted every
+        fold stages; batched solves refined up to `refine` times), 2: CUDA cores in double-float
+        (FP64-accurate; operators built with the double-float or mixed form)."""
         _check(_lib.ls_op_set_batch_kernel(self.handle, int(kind), int(fold), int(refine)))
 
     def set_stall_test(self, stall_ms):

@@ -942,6 +942,118 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum_multi_f32(MultiArgs A, const
     multi_unit(A, blockIdx.x, blockIdx.y, blockIdx.z, ftab, txy, ts);
 }
 
+// The batched pair sum in double-float (FP64-accurate), for the residuals of the batched
+// solves' refinement: the decomposition of k_pairsum_multi_f32 (target block x source chunk
+// x block of MRB right-hand sides), H from the double-float table (df_h0), the densities as
+// double-float pairs, and per right-hand side an accumulator kept as (hi, lo): each product
+// H s is formed exactly to first order (hi product, its FMA residual and the cross terms),
+// the hi parts added with TwoSum, the residuals into lo; folded into FP64 every
+// MDF_TILE sources.
+#define MDF_TILE 64
+template <int NC_TAB, int NF>
+__global__ void __launch_bounds__(PS_TPB) k_pairsum_multi_df(MultiArgs A, const float4* __restrict__ tab_g) {
+    extern __shared__ float4 dtab[];
+    __shared__ float4 txy[MDF_TILE];
+    __shared__ float4 ts[MDF_TILE][MRB];
+    const int words = A.ncell * (NC_TAB + 1) + (A.noct + 1) / 2;
+    for (int i = threadIdx.x; i < words; i += PS_TPB) dtab[i] = tab_g[i];
+    const float4* coef = dtab;
+    const float4* cellv = dtab + (size_t)A.ncell * NC_TAB;
+    const int2* oct = reinterpret_cast<const int2*>(cellv + A.ncell);
+    const int n = A.n;
+    const int j = blockIdx.x * PS_TPB + threadIdx.x;
+    const int chunk = blockIdx.y;
+    const int r0 = blockIdx.z * MRB;
+    const int nr = min(MRB, A.R - r0);
+    const int s_begin = chunk * A.spc;
+    const int s_end = min(n, s_begin + A.spc);
+    const double2 yj = A.xy[min(j, n - 1)];
+    const DF tx = df_from(yj.x), ty = df_from(yj.y);
+    double accr[MRB], acci[MRB];
+#pragma unroll
+    for (int q = 0; q < MRB; ++q) { accr[q] = 0.0; acci[q] = 0.0; }
+    for (int base = s_begin; base < s_end; base += MDF_TILE) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < MDF_TILE; i += PS_TPB) {
+            const int src = base + i;
+            float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (src < s_end) {
+                const double2 p = A.xy[src];
+                const DF a = df_from(p.x), b = df_from(p.y);
+                c = make_float4(a.h, a.l, b.h, b.l);
+            }
+            txy[i] = c;
+        }
+        for (int e = threadIdx.x; e < MDF_TILE * MRB; e += PS_TPB) {
+            const int i = e / MRB, q = e % MRB, src = base + i;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (src < s_end && q < nr) {
+                const double ww = A.w ? A.w[src] : 1.0;
+                double2 ff = A.f[(size_t)(r0 + q) * A.sf + src];
+                if (A.m) ff = cmul(A.m[src], ff);
+                const DF re = df_from(ww * ff.x), im = df_from(ww * ff.y);
+                v = make_float4(re.h, re.l, im.h, im.l);
+            }
+            ts[i][q] = v;
+        }
+        __syncthreads();
+        float rh[MRB], rl[MRB], ih[MRB], il[MRB];
+#pragma unroll
+        for (int q = 0; q < MRB; ++q) { rh[q] = 0.f; rl[q] = 0.f; ih[q] = 0.f; il[q] = 0.f; }
+        const int cnt = min(MDF_TILE, s_end - base);
+        for (int i = 0; i < cnt; ++i) {
+            DF hr, hi;
+            if (!df_h0<NC_TAB, NF>(tx, ty, txy[i], coef, cellv, oct, A.noct, A.b_lo, A.k, A.inv_k, hr, hi)) continue;
+#pragma unroll
+            for (int q = 0; q < MRB; ++q) {
+                const float4 sv = ts[i][q];
+                // re += hr s_re - hi s_im, im += hr s_im + hi s_re
+                const float p1 = hr.h * sv.x, p2 = hi.h * sv.z, p3 = hr.h * sv.z, p4 = hi.h * sv.x;
+                float e1 = fmaf(hr.h, sv.x, -p1), e2 = fmaf(hi.h, sv.z, -p2);
+                float e3 = fmaf(hr.h, sv.z, -p3), e4 = fmaf(hi.h, sv.x, -p4);
+                e1 = fmaf(hr.l, sv.x, fmaf(hr.h, sv.y, e1));
+                e2 = fmaf(hi.l, sv.z, fmaf(hi.h, sv.w, e2));
+                e3 = fmaf(hr.l, sv.z, fmaf(hr.h, sv.w, e3));
+                e4 = fmaf(hi.l, sv.x, fmaf(hi.h, sv.y, e4));
+                float t, err;
+                two_sum(rh[q], p1, t, err);
+                rl[q] += err + e1;
+                two_sum(t, -p2, rh[q], err);
+                rl[q] += err - e2;
+                two_sum(ih[q], p3, t, err);
+                il[q] += err + e3;
+                two_sum(t, p4, ih[q], err);
+                il[q] += err + e4;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < MRB; ++q) {
+            accr[q] += (double)rh[q] + (double)rl[q];
+            acci[q] += (double)ih[q] + (double)il[q];
+        }
+    }
+    if (j < n)
+        for (int q = 0; q < nr; ++q)
+            A.partial[((size_t)(r0 + q) * A.nchunk + chunk) * n + j] = make_double2(accr[q], acci[q]);
+}
+
+static void launch_multi_df(int nc, int nf, dim3 grid, size_t smem, cudaStream_t st, const MultiArgs& A,
+                            const float4* tab) {
+#define LS_MDF_LAUNCH(NC, NF) k_pairsum_multi_df<NC, NF><<<grid, PS_TPB, smem, st>>>(A, tab)
+#define LS_MDF_NC(NC)                          \
+    do {                                       \
+        if (nf >= 4) LS_MDF_LAUNCH(NC, 4);     \
+        else if (nf >= 2) LS_MDF_LAUNCH(NC, 2); \
+        else LS_MDF_LAUNCH(NC, 0);             \
+    } while (0)
+    if (nc == 8) LS_MDF_NC(8);
+    else if (nc == 9) LS_MDF_NC(9);
+    else if (nc == 10) LS_MDF_NC(10);
+    else LS_MDF_NC(12);
+#undef LS_MDF_NC
+#undef LS_MDF_LAUNCH
+}
+
 // Persistent form over several operators (scatterers): a block fetches work units
 // (operator, target block, source chunk, RHS block) from an atomic counter until
 // all units are done, reloading the shared-memory H0 table when the operator changes.
@@ -2263,7 +2375,10 @@ static cudaError_t raise_tab_limits(int mode, size_t bytes) {
         if ((e = raise_smem_limit(k_pairsum_df<NC, 4>, bytes)) != cudaSuccess) return e;      \
         if ((e = raise_smem_limit(k_pairsum_dfs<NC, 0>, bytes)) != cudaSuccess) return e;     \
         if ((e = raise_smem_limit(k_pairsum_dfs<NC, 2>, bytes)) != cudaSuccess) return e;     \
-        if ((e = raise_smem_limit(k_pairsum_dfs<NC, 4>, bytes)) != cudaSuccess) return e;
+        if ((e = raise_smem_limit(k_pairsum_dfs<NC, 4>, bytes)) != cudaSuccess) return e;     \
+        if ((e = raise_smem_limit(k_pairsum_multi_df<NC, 0>, bytes)) != cudaSuccess) return e; \
+        if ((e = raise_smem_limit(k_pairsum_multi_df<NC, 2>, bytes)) != cudaSuccess) return e; \
+        if ((e = raise_smem_limit(k_pairsum_multi_df<NC, 4>, bytes)) != cudaSuccess) return e;
         LS_DF_RAISE(8)
         LS_DF_RAISE(9)
         LS_DF_RAISE(10)
@@ -3859,7 +3974,10 @@ static ls_status tc_status(ls_op* op) {
     return LS_OK;
 }
 
+static ls_status pairsum_batch_df(ls_op* op, int R, const double2* f, size_t sf, const double2* m, const double* w);
+
 static ls_status pairsum_batch(ls_op* op, int R, const double2* f, size_t sf, const double2* m, const double* w) {
+    if (op->batch_kernel == 2) return pairsum_batch_df(op, R, f, sf, m, w);
     TRY(ensure_table32(op));
     if (op->batch_kernel == 1) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -4108,12 +4226,54 @@ static ls_status prec_norms(ls_op* op, int R, const double2* x, bool transpose, 
     return LS_OK;
 }
 
+// Batched double-float pair sum (k_pairsum_multi_df) on the operator's double-float table.
+static ls_status pairsum_batch_df(ls_op* op, int R, const double2* f, size_t sf, const double2* m, const double* w) {
+    TRY(ensure_batch(op, R));
+    op->b_nchunk_cur = op->b_nchunk;
+    dim3 grid((op->nq + PS_TPB - 1) / PS_TPB, op->b_nchunk, (R + MRB - 1) / MRB);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (op->timing && op->ev.size() < 65536) {
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        op->ev.emplace_back(e0, e1);
+        op->ev_kind.push_back(12);
+        CK(cudaEventRecord(e0, op->stream));
+    }
+    MultiArgs A;
+    A.xy = op->xy.p; A.w = w; A.m = m; A.f = f; A.sf = sf;
+    A.n = op->nq; A.R = R; A.spc = op->b_spc; A.nchunk = op->b_nchunk;
+    A.k = op->k; A.inv_k = 1.0 / op->k;
+    A.ncell = op->tab_ncell; A.noct = op->tab_noct; A.b_lo = op->tab_blo;
+    A.partial = op->bpartial.p;
+    launch_multi_df(op->tab_nc, op->tab_nf, grid, op->tab_bytes, op->stream, A, (const float4*)op->tab.p);
+    CK(cudaGetLastError());
+    if (e1) CK(cudaEventRecord(e1, op->stream));
+    op->launches++;
+    op->pairsum_launches++;
+    return LS_OK;
+}
+
 // y_r = L x_r (or L^T x_r) with the accurate batched pair sum (CUDA cores, Kahan FP32)
 static ls_status apply_L_batch_accurate(ls_op* op, int R, const double2* x, double2* y, bool transpose) {
     const int n = op->nq;
+    if (op->refine_single && (op->mode == 3 || op->mode == 4)) {
+        // double-float operator: the batched double-float pair sum over all R systems
+        TRY(pairsum_batch_df(op, R, x, n, transpose ? nullptr : op->m.p, transpose ? nullptr : op->w.p));
+        dim3 ge((unsigned)(((int64_t)n * 32 + 255) / 256), R);
+        if (transpose)
+            k_applyT_epi_multi<<<ge, 256, 0, op->stream>>>(n, op->b_nchunk_cur, op->bpartial.p, op->rowptrT.p,
+                                                           op->colsT.p, op->valsT.p, op->m.p, op->w.p, x, n,
+                                                           op->k * op->k, y, n);
+        else
+            k_apply_epi_multi<<<ge, 256, 0, op->stream>>>(n, op->b_nchunk_cur, op->bpartial.p, op->rowptr.p, op->cols.p,
+                                                          op->vals.p, op->m.p, x, n, op->k * op->k, y, n);
+        CK(cudaGetLastError());
+        op->launches++;
+        return LS_OK;
+    }
     if (op->refine_single) {
         // the operator's own single-RHS pair sum, one system at a time (FP64-accurate with the
-        // double-float, mixed or FP64 forms)
+        // FP64 forms)
         for (int r = 0; r < R; ++r) {
             const double2* xr = x + (size_t)r * n;
             double2* yr = y + (size_t)r * n;
@@ -4237,6 +4397,7 @@ static ls_status solve_multi(int S, ls_op* const* ops, int R, const double2* con
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pairsum_persist, PS_TPB, max_tab));
     occ = std::max(occ, 1);
     const bool tcore = ops[0]->batch_kernel == 1;
+    if (ops[0]->batch_kernel == 2) return fail(LS_EINVAL, "multi-operator solves take batch kernel 0 or 1");
     for (int s = 0; s < S; ++s) {
         TRY(gb_begin(ops[s], R, b[s]));
         if (tcore) TRY(ensure_tc(ops[s]));
@@ -4419,8 +4580,10 @@ ls_status ls_op_set_stall_test(ls_op* op, double stall_ms) {
 }
 
 ls_status ls_op_set_batch_kernel(ls_op* op, int32_t kind, int32_t fold, int32_t refine) {
-    if (!op || kind < 0 || kind > 1 || fold < 1 || refine < 0)
-        return fail(LS_EINVAL, "kind must be 0 or 1, fold >= 1, refine >= 0");
+    if (!op || kind < 0 || kind > 2 || fold < 1 || refine < 0)
+        return fail(LS_EINVAL, "kind must be 0, 1 or 2, fold >= 1, refine >= 0");
+    if (kind == 2 && op->mode != 3 && op->mode != 4)
+        return fail(LS_EINVAL, "kind 2 needs the double-float table (LS_PREC_FP64_DF or LS_PREC_MIXED)");
     op->batch_kernel = kind;
     op->tc_fold = fold;
     op->tc_refine = refine;
@@ -5015,6 +5178,7 @@ ls_status ls_op_set_pairsum(ls_op* op, int32_t mode) {
     op->use_table = false;
     if (mode != 1) TRY(build_table_range(op, op->tab_tlo, op->tab_thi, mode == 4 ? 3 : mode));
     if (mode == 4) TRY(ensure_table32_single(op));
+    if (op->batch_kernel == 2 && mode != 3 && mode != 4) op->batch_kernel = 0;   // kind 2 needs the DF table
     op->mode = mode;
     return LS_OK;
 }

@@ -209,3 +209,37 @@ def test_batched_preconditioner_fp32_sweeps():
     print("batched P vs single FP64 P: FP64 sweeps", out[0], "FP32 sweeps", out[1])
     assert out[0] < 1e-12
     assert out[1] < 1e-4
+
+
+def test_batched_double_float_kernel(small):
+    """Batch kernel 2 (double-float, FP64-accurate) against the single-RHS double-float pair
+    sum: both evaluate the same H to ~1e-14 and sum in double-float, so they agree within the
+    pair-sum parity bar 1e-13; the batched solve on it meets the FP64 solve to tol x a
+    condition factor with no refinement."""
+    wl, op = small
+    n = wl.mesh.n_nodes
+    R = 11                                   # one full block of 8 RHS and a ragged one
+    F = torch.from_numpy(np.stack([random_density(n, 500 + r) for r in range(R)])).cuda()
+    Y = torch.empty_like(F)
+    op.set_batch_kernel(2)
+    op.pairsum_batch_dev(F, Y)
+    ref = torch.empty_like(F)
+    for r in range(R):
+        op.pairsum_dev(F[r].contiguous(), ref[r])
+    e = float(_rel_rows(Y, ref).max())
+    wt = star_scatterer(3, 5000, k=10.0, nx=96, ny=96)
+    opt = L.Operator(L.Mesh(wt.mesh), wt.k, wt.m, wt.m_grid, box=wt.box, nx=wt.nx, ny=wt.ny, tol=1e-9)
+    dirs = wt.directions[::16]
+    B = torch.empty((dirs.size, wt.mesh.n_nodes), dtype=torch.complex128, device="cuda")
+    opt.incident_dev(dirs, B)
+    U1 = torch.empty_like(B)
+    for r in range(dirs.size):
+        opt.solve_dev(B[r].contiguous().view(1, -1), U1[r].view(1, -1))
+    opt.set_batch_kernel(2)
+    U = torch.empty_like(B)
+    it, st = opt.solve_batch_dev(B, U)
+    es = float(_rel_rows(U, U1).max())
+    op.set_batch_kernel(1)
+    print("batched double-float pair sum vs single-RHS", e, "batched solve vs single-RHS solves", es, "iters", it)
+    assert st == L.LS_OK
+    assert e < 1e-13 and es < 1e-7
