@@ -371,8 +371,10 @@ ls_status ls_op_set_batch_kernel(ls_op* op, int32_t kind, int32_t fold, int32_t 
 
 /*
  * Operator of the batched solves' iterative refinement (ls_solve_batch_dev,
- * ls_solve_multi_dev on the tensor cores, ls_solve_transpose_batch_dev):
- *   accurate = 0 (default)  the kind 0 batched FP32 operator (one launch for all R systems;
+ * ls_solve_multi_dev on the tensor cores, ls_solve_transpose_batch_dev).  Default: 1 on
+ * operators in the double-float or mixed form, 0 otherwise, following ls_op_set_pairsum
+ * until this call fixes it.
+ *   accurate = 0            the kind 0 batched FP32 operator (one launch for all R systems;
  *                           solutions ~1e-6 from the FP64 ones: the per-entry FP32 rounding
  *                           of H0 limits them)
  *   accurate = 1            an FP64-accurate operator: on an operator built with

@@ -2264,7 +2264,8 @@ struct ls_op {
     int batch_kernel = 1;                // 0: CUDA cores (k_pairsum_multi_f32), 1: tensor cores
     int tc_fold = 4;                     // stages per accumulator run
     int tc_refine = 4;                   // iterative-refinement steps after a tensor-core solve (0: none)
-    bool refine_single = false;          // refinement residuals from the single-RHS pair sum (FP64-accurate)
+    bool refine_single = false;          // refinement residuals from an FP64-accurate operator
+    bool refine_user = false;            // refine_single set by ls_op_set_batch_refine (else: follows the form)
     uint64_t tc_stall_ns = 0;            // failure-detection test: forced stall of the MMA issuer (ns)
     int64_t corr_host_blocks = 0;        // correction blocks the device setup left to the host
     DevBuf<double2> ir_r, ir_d, ir_y;    // refinement work vectors [R][n]
@@ -3631,6 +3632,7 @@ ls_status ls_operator_create(const ls_mesh* mesh, double k, const double* m, con
     }
     CK(op->partial.alloc((size_t)std::max(nchunk, op->dfs_nchunk + op->dfs_nb / 2) * n));
     op->mode = prm.prec;
+    op->refine_single = prm.prec == 3 || prm.prec == 4;   // the double-float batched residual is available
     table_range(op, M);
     auto tt0 = std::chrono::steady_clock::now();
     if (prm.prec != 1) TRY(build_table_range(op, op->tab_tlo, op->tab_thi, prm.prec == 4 ? 3 : prm.prec));
@@ -4403,19 +4405,36 @@ static ls_status solve_multi(int S, ls_op* const* ops, int R, const double2* con
         if (tcore) TRY(ensure_tc(ops[s]));
         ops[s]->b_nchunk_cur = ops[s]->b_nchunk;      // the persistent CUDA-core kernel writes these partials
     }
-    if (tcore) {
-        // first solves to TC_FIRST_TOL where refinement follows (as in gmres_batch); the
-        // guard restores every operator's tolerance on all exits
-        struct TolGuard {
-            std::vector<std::pair<ls_op*, double>> saved;
-            void restore() { for (auto& p : saved) p.first->prm.tol = p.second; saved.clear(); }
-            ~TolGuard() { restore(); }
-        } tg;
-        for (int s = 0; s < S; ++s)
-            if (ops[s]->tc_refine > 0) {
-                tg.saved.emplace_back(ops[s], ops[s]->prm.tol);
-                ops[s]->prm.tol = std::max(ops[s]->prm.tol, TC_FIRST_TOL);
+    // first solves to TC_FIRST_TOL where refinement follows (as in gmres_batch); the guard
+    // restores every operator's tolerance on all exits
+    auto refines = [](const ls_op* op) { return op->tc_refine > 0 && (op->batch_kernel == 1 || op->refine_single); };
+    struct TolGuard {
+        std::vector<std::pair<ls_op*, double>> saved;
+        void restore() { for (auto& p : saved) p.first->prm.tol = p.second; saved.clear(); }
+        ~TolGuard() { restore(); }
+    } tg;
+    for (int s = 0; s < S; ++s)
+        if (refines(ops[s])) {
+            tg.saved.emplace_back(ops[s], ops[s]->prm.tol);
+            ops[s]->prm.tol = std::max(ops[s]->prm.tol, TC_FIRST_TOL);
+        }
+    // iterative refinement of every operator that takes it, after the lock-step solves
+    auto refine_all = [&](std::vector<char>& conv) -> ls_status {
+        tg.restore();
+        all_conv = true;
+        for (int s = 0; s < S; ++s) {
+            bool c = conv[s] != 0;
+            int* its = iters ? iters + (size_t)s * R : nullptr;
+            if (refines(ops[s])) {
+                ls_status sr = refine_batch(ops[s], R, b[s], u[s], its, false);
+                if (sr != LS_OK && sr != LS_ENOCONV) return sr;
+                c = sr == LS_OK;
             }
+            all_conv = all_conv && c;
+        }
+        return LS_OK;
+    };
+    if (tcore) {
         // one persistent tensor-core launch per iteration over the unconverged operators
         DevBuf<TCOp> tdesc;
         CK(tdesc.alloc(std::max(S, 1)));
@@ -4451,7 +4470,6 @@ static ls_status solve_multi(int S, ls_op* const* ops, int R, const double2* con
             }
             TRY(tc_status(which[0]));
         }
-        all_conv = true;
         std::vector<char> conv(S, 0);
         for (int s = 0; s < S; ++s) {
             bool c = false;
@@ -4459,19 +4477,7 @@ static ls_status solve_multi(int S, ls_op* const* ops, int R, const double2* con
             TRY(gb_finish(ops[s], R, u[s], its, c));
             conv[s] = c;
         }
-        tg.restore();
-        for (int s = 0; s < S; ++s) {
-            bool c = conv[s] != 0;
-            int* its = iters ? iters + (size_t)s * R : nullptr;
-            if (ops[s]->tc_refine > 0) {
-                // iterative refinement against the accurate operator (see gmres_batch)
-                ls_status sr = refine_batch(ops[s], R, b[s], u[s], its, false);
-                if (sr != LS_OK && sr != LS_ENOCONV) return sr;
-                c = sr == LS_OK;
-            }
-            all_conv = all_conv && c;
-        }
-        return LS_OK;
+        return refine_all(conv);
     }
     DevBuf<PSDesc> ddesc;
     DevBuf<int> counter;
@@ -4536,13 +4542,13 @@ static ls_status solve_multi(int S, ls_op* const* ops, int R, const double2* con
             if (!any) done[s] = 1;
         }
     }
-    all_conv = true;
+    std::vector<char> conv(S, 0);
     for (int s = 0; s < S; ++s) {
         bool c = false;
         TRY(gb_finish(ops[s], R, u[s], iters ? iters + (size_t)s * R : nullptr, c));
-        all_conv = all_conv && c;
+        conv[s] = c;
     }
-    return LS_OK;
+    return refine_all(conv);
 }
 
 extern "C" {
@@ -5179,6 +5185,7 @@ ls_status ls_op_set_pairsum(ls_op* op, int32_t mode) {
     if (mode != 1) TRY(build_table_range(op, op->tab_tlo, op->tab_thi, mode == 4 ? 3 : mode));
     if (mode == 4) TRY(ensure_table32_single(op));
     if (op->batch_kernel == 2 && mode != 3 && mode != 4) op->batch_kernel = 0;   // kind 2 needs the DF table
+    if (!op->refine_user) op->refine_single = mode == 3 || mode == 4;
     op->mode = mode;
     return LS_OK;
 }
@@ -5188,6 +5195,7 @@ ls_status ls_op_set_batch_refine(ls_op* op, int32_t accurate) {
     if (accurate != 0 && accurate != 1) return fail(LS_EINVAL, "accurate must be 0 or 1");
     if (op->cartesian) return fail(LS_EINVAL, "the batched forms need a quadrature-node operator");
     op->refine_single = accurate != 0;
+    op->refine_user = true;
     return LS_OK;
 }
 

@@ -135,6 +135,7 @@ def test_tc_solve_needs_refinement():
     ref = torch.empty_like(B)
     for r in range(dirs.size):
         op.solve_dev(B[r].contiguous().view(1, -1), ref[r].view(1, -1))
+    op.set_batch_refine(False)              # first the FP32 refinement (the default is accurate)
     op.set_batch_kernel(0)
     Ucc = torch.empty_like(B)
     it_cc, st_cc = op.solve_batch_dev(B, Ucc)
