@@ -581,26 +581,36 @@ __device__ __forceinline__ bool df_h0(DF tx, DF ty, float4 sxy, const float4* co
         DF u = DF{d0 * cv.z, d1 * cv.z};                // times a power of two: exact
         const float4* c = coef + (size_t)cell * NC_TAB;
         float4 cc = c[NC_TAB - 1];
+        // compensated Horner: the FP32 Horner value (sr, si) and its running correction
+        // (kr, ki); each step adds the TwoProd residual of s u_h, the TwoSum residual of
+        // s u_h + a_h, the low parts a_l and s u_l, and the correction times u_h
+        float sr = cc.x, si = cc.z, kr = 0.f, ki = 0.f;
         if (NF > 0) {
-            float yr = cc.x, yi = cc.z;
 #pragma unroll
             for (int e = NC_TAB - 2; e >= NC_TAB - NF; --e) {
                 cc = c[e];
-                yr = fmaf(yr, u.h, cc.x);
-                yi = fmaf(yi, u.h, cc.z);
+                sr = fmaf(sr, u.h, cc.x);
+                si = fmaf(si, u.h, cc.z);
             }
-            hr = DF{yr, 0.f};
-            hi = DF{yi, 0.f};
         } else {
-            hr = DF{cc.x, cc.y};
-            hi = DF{cc.z, cc.w};
+            kr = cc.y;
+            ki = cc.w;
         }
 #pragma unroll
         for (int e = (NF > 0 ? NC_TAB - NF : NC_TAB - 1) - 1; e >= 0; --e) {
             cc = c[e];
-            hr = df_mad(hr, u, DF{cc.x, cc.y});
-            hi = df_mad(hi, u, DF{cc.z, cc.w});
+            const float pr = sr * u.h, pi_r = fmaf(sr, u.h, -pr);
+            const float pm = si * u.h, pi_m = fmaf(si, u.h, -pm);
+            float tr, er, tm, em;
+            two_sum(pr, cc.x, tr, er);
+            two_sum(pm, cc.z, tm, em);
+            kr = fmaf(kr, u.h, fmaf(sr, u.l, (pi_r + er) + cc.y));
+            ki = fmaf(ki, u.h, fmaf(si, u.l, (pi_m + em) + cc.w));
+            sr = tr;
+            si = tm;
         }
+        hr = df_fast(sr, kr);
+        hi = df_fast(si, ki);
         return true;
     }
     if (t.h > 0.f) {
