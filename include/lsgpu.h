@@ -159,9 +159,7 @@ int32_t ls_op_num_nodes(const ls_op* op);
 ls_status ls_apply_dev(ls_op* op, const void* x_dev, void* y_dev);
 /* Same with host buffers; includes the host<->device copies. */
 ls_status ls_apply(ls_op* op, const double* x, double* y);
-/* y = P x (Eq. preconditioner_factored) on device buffers; LS_EINVAL without a preconditioner.
-   Operators of the FP32 form (LS_PREC_FP32) solve C with FP32 copies of the cyclic-reduction
-   blocks (P is a preconditioner: its rounding changes iteration counts, not solutions). */
+/* y = P x (Eq. preconditioner_factored) on device buffers; LS_EINVAL without a preconditioner. */
 ls_status ls_apply_precond_dev(ls_op* op, const void* x_dev, void* y_dev);
 /* y_r = P x_r for R right-hand sides x_dev, y_dev [R][N_Q] complex (no aliasing) with the
    batched preconditioner kernels of ls_solve_batch_dev: FP64 block-LU sweeps under batch

@@ -104,17 +104,3 @@ def test_contrast_from_device_and_misfit(tiny):
     d = (uinf - tgt).cpu().numpy()
     assert torch.equal(res, uinf - tgt)
     assert abs(J - 0.5 * np.sum(np.abs(d) ** 2)) <= 1e-14 * J
-
-
-def test_fp32_form_preconditioner(tiny):
-    """The precision form applies P with FP32 copies of the cyclic-reduction blocks; against
-    the oracle's P it is within the a-priori bound cond_1(C) x 6e-8 ~ 1e-2 (cond_1(C) ~ 2e5),
-    measured far inside it; P and P^T of the FP64-accurate form stay at the matvec bar."""
-    wl, op, ora = tiny
-    op32 = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, nx=48, ny=48, tol=1e-10, pairsum=2)
-    x = random_density(wl.mesh.n_nodes, 33)
-    P = Preconditioner(Grid(wl.box, wl.nx, wl.ny), wl.mesh.nodes, wl.k, wl.m_grid)
-    e32 = _rel(op32.apply_precond(x), P.apply(x))
-    e64 = _rel(op.apply_precond(x), P.apply(x))
-    print("P with FP32 blocks vs oracle", e32, "FP64 blocks", e64)
-    assert e64 < 1e-11 and e32 < 1e-4
