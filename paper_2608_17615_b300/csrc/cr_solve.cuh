@@ -118,65 +118,6 @@ __global__ void __launch_bounds__(32 * CR_WARPS) k_cr_mv(int nx, int R, size_t s
     }
 }
 
-// The same products with FP32 copies of the factor blocks and FP32 arithmetic, single
-// right-hand side: the preconditioner of the FP32 solves (the precision form, the mixed
-// form's inner solves), where P only has to be close to C^{-1} A.  Half the bytes of the
-// FP64 blocks and no FP64 pipe, so the product runs at HBM speed; vectors stay FP64.
-struct CRJob32 {
-    double2* y;
-    const double2* base;
-    const float2* M1;
-    const double2* v1;
-    const float2* M2;
-    const double2* v2;
-};
-
-__global__ void __launch_bounds__(32 * CR_WARPS) k_cr_mv32(int nx, const CRJob32* __restrict__ jobs) {
-    extern __shared__ float2 crsh32[];                   // [2][nx]
-    const CRJob32 J = jobs[blockIdx.y];
-    for (int c = threadIdx.x; c < nx; c += blockDim.x) {
-        const double2 a = J.v1[c];
-        crsh32[c] = make_float2((float)a.x, (float)a.y);
-        const double2 b = J.M2 ? J.v2[c] : make_double2(0.0, 0.0);
-        crsh32[nx + c] = make_float2((float)b.x, (float)b.y);
-    }
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int q = 0; q < CR_ROWS_PER_WARP; ++q) {
-        const int row = (blockIdx.x * CR_WARPS + warp) * CR_ROWS_PER_WARP + q;
-        if (row >= nx) break;
-        float ar = 0.f, ai = 0.f;
-        const float2* m1 = J.M1 + (size_t)row * nx;
-#pragma unroll 4
-        for (int c = lane; c < nx; c += 32) {
-            const float2 a = m1[c], v = crsh32[c];
-            ar = fmaf(a.x, v.x, fmaf(-a.y, v.y, ar));
-            ai = fmaf(a.x, v.y, fmaf(a.y, v.x, ai));
-        }
-        if (J.M2) {
-            const float2* m2 = J.M2 + (size_t)row * nx;
-#pragma unroll 4
-            for (int c = lane; c < nx; c += 32) {
-                const float2 a = m2[c], v = crsh32[nx + c];
-                ar = fmaf(a.x, v.x, fmaf(-a.y, v.y, ar));
-                ai = fmaf(a.x, v.y, fmaf(a.y, v.x, ai));
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            ar += __shfl_down_sync(0xffffffffu, ar, o);
-            ai += __shfl_down_sync(0xffffffffu, ai, o);
-        }
-        if (lane == 0) {
-            if (J.base) {
-                const double2 b = J.base[row];
-                J.y[row] = make_double2(b.x - (double)ar, b.y - (double)ai);
-            } else {
-                J.y[row] = make_double2((double)ar, (double)ai);
-            }
-        }
-    }
-}
-
 // Level-0 updates with the tridiagonal band blocks of C (entry (a, a + da) of
 // L_b at cband[(9 b + da + 1) nx + a], of U_b at cband[(9 b + 6 + da + 1) nx + a]).
 // transposed = 0: y_a = base_a - sum_da L(a, a+da) vL_{a+da} - sum_da U(a, a+da) vU_{a+da}

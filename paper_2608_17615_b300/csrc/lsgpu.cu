@@ -2199,9 +2199,6 @@ struct CRPlan {
     DevBuf<CRJob> jobs;
     DevBuf<CRTriJob> tjobs;
     std::vector<Step> fwd, trn;
-    std::vector<CRJob> hjobs;                           // host copy of jobs (for the FP32 variant)
-    DevBuf<float2> store32;                             // FP32 copy of store (made on first FP32 use)
-    DevBuf<CRJob32> jobs32;
     double2* t() const { return arena.p; }
     double2* x() const { return arena.p + (size_t)nx * ny; }
 };
@@ -2295,9 +2292,7 @@ struct ls_op {
     cudaGraphExec_t gP = nullptr;
     DevBuf<double2> pin, pout;
     cudaGraphExec_t gPT = nullptr;         // graph of the P^T apply
-    cudaGraphExec_t gP32 = nullptr, gPT32 = nullptr;   // the same with the FP32 cyclic-reduction blocks
     int nlaunch_P = 0, nlaunch_PT = 0;     // kernels in each graph
-    int nlaunch_P32 = 0, nlaunch_PT32 = 0;
     CRPlan cr;                           // cyclic reduction of C for the single-RHS P and P^T
     // purely Cartesian operator (ls_cartesian_create): the unknowns are the grid nodes,
     // L^(C) = I + k^2 V^(C) M^(C) with V^(C) applied by FFT convolution, P = S^(C) = C^{-1} A
@@ -2314,8 +2309,6 @@ struct ls_op {
         for (auto& e : ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
         if (gP) cudaGraphExecDestroy(gP);
         if (gPT) cudaGraphExecDestroy(gPT);
-        if (gP32) cudaGraphExecDestroy(gP32);
-        if (gPT32) cudaGraphExecDestroy(gPT32);
         if (cap) cudaStreamDestroy(cap);
         if (tc_herr) cudaFreeHost(tc_herr);
         if (fft) cufftDestroy(fft);
@@ -2831,7 +2824,6 @@ static ls_status build_cr(ls_op* op) {
         if (!j.M1 || !j.v1 || !j.y) return fail(LS_ECUDA, "cyclic reduction: incomplete job table");
     CK(P.jobs.alloc(J.size()));
     CK(cudaMemcpy(P.jobs.p, J.data(), sizeof(CRJob) * J.size(), cudaMemcpyHostToDevice));
-    P.hjobs = J;
     if (!TJ.empty()) {
         CK(P.tjobs.alloc(TJ.size()));
         CK(cudaMemcpy(P.tjobs.p, TJ.data(), sizeof(CRTriJob) * TJ.size(), cudaMemcpyHostToDevice));
@@ -2840,43 +2832,14 @@ static ls_status build_cr(ls_op* op) {
 }
 
 // The steps of C x = t (transposed: C^T x = t) on P.t() -> P.x(), single right-hand side.
-// FP32 copies of the cyclic-reduction blocks and the job table pointing into them.
-static ls_status ensure_cr32(ls_op* op) {
-    CRPlan& P = op->cr;
-    if (P.store32.p || P.hjobs.empty()) return LS_OK;
-    const int64_t ns = (int64_t)P.store.n;
-    CK(P.store32.alloc(ns));
-    k_to_f32<<<(unsigned)((ns + 255) / 256), 256, 0, op->stream>>>(ns, P.store.p, P.store32.p);
-    CK(cudaGetLastError());
-    op->launches++;
-    auto to32 = [&](const double2* M) -> const float2* {
-        if (!M) return nullptr;
-        return P.store32.p + (M - P.store.p);
-    };
-    std::vector<CRJob32> J32(P.hjobs.size());
-    for (size_t i = 0; i < J32.size(); ++i) {
-        const CRJob& j = P.hjobs[i];
-        if (j.M1 && (j.M1 < P.store.p || j.M1 >= P.store.p + ns)) return fail(LS_ECUDA, "cyclic reduction: job outside the block store");
-        if (j.M2 && (j.M2 < P.store.p || j.M2 >= P.store.p + ns)) return fail(LS_ECUDA, "cyclic reduction: job outside the block store");
-        J32[i] = CRJob32{j.y, j.base, to32(j.M1), j.v1, to32(j.M2), j.v2};
-    }
-    CK(P.jobs32.alloc(J32.size()));
-    CK(cudaMemcpy(P.jobs32.p, J32.data(), sizeof(CRJob32) * J32.size(), cudaMemcpyHostToDevice));
-    CK(raise_smem_limit(k_cr_mv32, sizeof(float2) * 2 * P.nx));
-    return LS_OK;
-}
-
-static int launch_cr(ls_op* op, cudaStream_t st, bool transposed, bool fp32 = false) {
+static int launch_cr(ls_op* op, cudaStream_t st, bool transposed) {
     const CRPlan& P = op->cr;
     const int nx = P.nx;
     const size_t shm = sizeof(double2) * 2 * nx;
     const int rows = CR_WARPS * CR_ROWS_PER_WARP;
     int nl = 0;
     for (const auto& s : transposed ? P.trn : P.fwd) {
-        if (s.kind == 0 && fp32)
-            k_cr_mv32<<<dim3((nx + rows - 1) / rows, s.count, 1), 32 * CR_WARPS, sizeof(float2) * 2 * nx, st>>>(
-                nx, P.jobs32.p + s.first);
-        else if (s.kind == 0)
+        if (s.kind == 0)
             k_cr_mv<1><<<dim3((nx + rows - 1) / rows, s.count, 1), 32 * CR_WARPS, shm, st>>>(nx, 1, P.svec,
                                                                                          P.jobs.p + s.first);
         else
@@ -2889,11 +2852,11 @@ static int launch_cr(ls_op* op, cudaStream_t st, bool transposed, bool fp32 = fa
 
 // The kernel sequence of P x on stream st (T_Q^C, the stencil A, the cyclic-reduction
 // solve of C, then T_C^Q fused with the identity term); returns the number of launches.
-static int launch_P_kernels(ls_op* op, cudaStream_t st, const double2* x, double2* z, bool fp32 = false) {
+static int launch_P_kernels(ls_op* op, cudaStream_t st, const double2* x, double2* z) {
     const int nc = op->nx * op->ny, nx = op->nx, ny = op->ny;
     k_tqc<<<(nc + 255) / 256, 256, 0, st>>>(nc, op->tqc_rp.p, op->tqc_ci.p, op->tqc_cv.p, x, op->pg.p);
     k_stencil<<<(nc + 255) / 256, 256, 0, st>>>(nx, ny, op->st.p, op->pg.p, op->cr.t());
-    const int ncr = launch_cr(op, st, false, fp32);
+    const int ncr = launch_cr(op, st, false);
     k_tcq<<<(op->nq + 255) / 256, 256, 0, st>>>(op->nq, op->tcq_idx.p, op->tcq_w.p, op->cr.x(), op->pg.p, x, z);
     return 3 + ncr;
 }
@@ -2914,10 +2877,10 @@ static int launch_S_kernels(ls_op* op, cudaStream_t st, const double2* x, double
 }
 
 // P^T x = x + T_Q^C^T (A^T C^{-T} - I) T_C^Q^T x on stream st; returns the number of launches.
-static int launch_PT_kernels(ls_op* op, cudaStream_t st, const double2* x, double2* z, bool fp32 = false) {
+static int launch_PT_kernels(ls_op* op, cudaStream_t st, const double2* x, double2* z) {
     const int nc = op->nx * op->ny, nx = op->nx, ny = op->ny;
     k_tqc<<<(nc + 255) / 256, 256, 0, st>>>(nc, op->tcqT_rp.p, op->tcqT_ci.p, op->tcqT_cv.p, x, op->cr.t());
-    const int ncr = launch_cr(op, st, true, fp32);
+    const int ncr = launch_cr(op, st, true);
     k_stencilT<<<(nc + 255) / 256, 256, 0, st>>>(nx, ny, op->st.p, op->cr.x(), op->cr.t(), op->ptp.p);
     k_tqcT<<<(op->nq + 255) / 256, 256, 0, st>>>(op->nq, op->tqcT_rp.p, op->tqcT_ci.p, op->tqcT_cv.p, op->ptp.p, nc, x,
                                                  op->nq, z, op->nq);
@@ -2928,21 +2891,17 @@ static int launch_PT_kernels(ls_op* op, cudaStream_t st, const double2* x, doubl
 // private stream, with fixed input/output buffers) and replayed; x and z are copied
 // in and out.
 static ls_status apply_P_graph(ls_op* op, const double2* x, double2* z, bool transpose) {
-    // the FP32 solves (precision form, the mixed form's inner solves) take the FP32 blocks
-    const bool fp32 = !op->cartesian && (op->mode == 2 || (op->mode == 4 && op->inner32));
-    if (fp32) TRY(ensure_cr32(op));
-    cudaGraphExec_t& ge = fp32 ? (transpose ? op->gPT32 : op->gP32) : (transpose ? op->gPT : op->gP);
-    int& nlaunch = fp32 ? (transpose ? op->nlaunch_PT32 : op->nlaunch_P32) : (transpose ? op->nlaunch_PT : op->nlaunch_P);
+    cudaGraphExec_t& ge = transpose ? op->gPT : op->gP;
+    int& nlaunch = transpose ? op->nlaunch_PT : op->nlaunch_P;
     if (!ge) {
         if (!op->cap) CK(cudaStreamCreateWithFlags(&op->cap, cudaStreamNonBlocking));
         if (!op->pin.p) CK(op->pin.alloc(op->nq));
         if (!op->pout.p) CK(op->pout.alloc(op->nq));
-        CK(cudaStreamSynchronize(op->stream));           // the FP32 blocks are ready before the capture
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(op->cap, cudaStreamCaptureModeThreadLocal));
         nlaunch = op->cartesian ? launch_S_kernels(op, op->cap, op->pin.p, op->pout.p, transpose)
-                  : transpose   ? launch_PT_kernels(op, op->cap, op->pin.p, op->pout.p, fp32)
-                                : launch_P_kernels(op, op->cap, op->pin.p, op->pout.p, fp32);
+                  : transpose   ? launch_PT_kernels(op, op->cap, op->pin.p, op->pout.p)
+                                : launch_P_kernels(op, op->cap, op->pin.p, op->pout.p);
         CK(cudaStreamEndCapture(op->cap, &g));
         cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
         cudaGraphDestroy(g);
