@@ -631,6 +631,30 @@ __device__ __forceinline__ void df_cmac(DF hr, DF hi, DF s_re, DF s_im, DF& ar, 
     ai = df_add(ai, df_add(a3, a4));
 }
 
+// The same with an unnormalised accumulator (ar.h, ar.l), (ai.h, ai.l): each product is
+// formed to first order (high product, its FMA residual, the two cross terms), the high
+// parts are added with TwoSum and every residual goes into the low word; normalise with
+// df_fast before the low word can grow past 2^-24 of the high one (here: every 32 to 128
+// terms, whose residuals are each below 2^-23 of their product).
+__device__ __forceinline__ void df_cmac_lazy(DF hr, DF hi, float4 sv, DF& ar, DF& ai) {
+    const float p1 = hr.h * sv.x, p2 = hi.h * sv.z, p3 = hr.h * sv.z, p4 = hi.h * sv.x;
+    float e1 = fmaf(hr.h, sv.x, -p1), e2 = fmaf(hi.h, sv.z, -p2);
+    float e3 = fmaf(hr.h, sv.z, -p3), e4 = fmaf(hi.h, sv.x, -p4);
+    e1 = fmaf(hr.l, sv.x, fmaf(hr.h, sv.y, e1));
+    e2 = fmaf(hi.l, sv.z, fmaf(hi.h, sv.w, e2));
+    e3 = fmaf(hr.l, sv.z, fmaf(hr.h, sv.w, e3));
+    e4 = fmaf(hi.l, sv.x, fmaf(hi.h, sv.y, e4));
+    float t, err;
+    two_sum(ar.h, p1, t, err);
+    ar.l += err + e1;
+    two_sum(t, -p2, ar.h, err);
+    ar.l += err - e2;
+    two_sum(ai.h, p3, t, err);
+    ai.l += err + e3;
+    two_sum(t, p4, ai.h, err);
+    ai.l += err + e4;
+}
+
 // NF > 0: the top NF coefficients of the Horner chain (whose terms are below 2^-24 of |H0|
 // on every cell, checked when the table is uploaded) are summed in plain FP32, the rest in
 // double-float.
@@ -749,16 +773,19 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum_dfs(const double2* __restric
     const DFTile me = tile[threadIdx.x];
     const double2 yi = xy[min(i, n - 1)];
     const DF tx = df_from(yi.x), ty = df_from(yi.y);
-    const DF si_re{me.s.x, me.s.y}, si_im{me.s.z, me.s.w};
     double accr = 0.0, acci = 0.0;
     if (c == 0) {                          // the diagonal block: ordered pairs, rows only
         DF sr{0.f, 0.f}, sim{0.f, 0.f};
         for (int q = 0; q < PS_TPB; ++q) {
-            if (q == (int)threadIdx.x) continue;
             const DFTile src = tile[q];
             DF hr, hi;
-            if (!df_h0<NC_TAB, NF>(tx, ty, src.xy, coef, cellv, oct, noct, b_lo, k, inv_k, hr, hi)) continue;
-            df_cmac(hr, hi, DF{src.s.x, src.s.y}, DF{src.s.z, src.s.w}, sr, sim);
+            if (q != (int)threadIdx.x &&
+                df_h0<NC_TAB, NF>(tx, ty, src.xy, coef, cellv, oct, noct, b_lo, k, inv_k, hr, hi))
+                df_cmac_lazy(hr, hi, src.s, sr, sim);
+            if ((q & 31) == 31) {
+                sr = df_fast(sr.h, sr.l);
+                sim = df_fast(sim.h, sim.l);
+            }
         }
         accr += (double)sr.h + (double)sr.l;
         acci += (double)sim.h + (double)sim.l;
@@ -779,15 +806,19 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum_dfs(const double2* __restric
                 const DFTile src = tile[sub * 32 + ((lane + r) & 31)];
                 DF hr, hi;
                 df_h0<NC_TAB, NF>(tx, ty, src.xy, coef, cellv, oct, noct, b_lo, k, inv_k, hr, hi);
-                df_cmac(hr, hi, DF{src.s.x, src.s.y}, DF{src.s.z, src.s.w}, sr, sim);
-                df_cmac(hr, hi, si_re, si_im, cr, ci);
+                df_cmac_lazy(hr, hi, src.s, sr, sim);
+                df_cmac_lazy(hr, hi, me.s, cr, ci);
                 const int from = (lane + 1) & 31;
                 cr.h = __shfl_sync(0xffffffffu, cr.h, from);
                 cr.l = __shfl_sync(0xffffffffu, cr.l, from);
                 ci.h = __shfl_sync(0xffffffffu, ci.h, from);
                 ci.l = __shfl_sync(0xffffffffu, ci.l, from);
             }
+            cr = df_fast(cr.h, cr.l);
+            ci = df_fast(ci.h, ci.l);
             colbuf[warp][sub * 32 + lane] = make_float4(cr.h, cr.l, ci.h, ci.l);
+            sr = df_fast(sr.h, sr.l);             // keep the row's low word small (32 terms per step)
+            sim = df_fast(sim.h, sim.l);
         }
         accr += (double)sr.h + (double)sr.l;
         acci += (double)sim.h + (double)sim.l;
