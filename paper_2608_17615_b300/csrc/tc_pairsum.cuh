@@ -382,30 +382,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairsum_tc(TCArgs a) {
                 txh = t.x; txl = t.y; tyh = t.z; tyl = t.w;
             }
             const uint32_t slot = gs % TC_NS, stgi = gs % nstg;
-            bool ok = true;
-            if (gs >= TC_NS) ok = tc::mbar_wait_or_abort(&sh.empty[slot], ((gs / TC_NS) - 1) & 1, &sh.abort_flag);
-            if (ok) ok = tc::mbar_wait_or_abort(&sh.stfull[stgi], (gs / nstg) & 1, &sh.abort_flag);
+            // 1. the staged densities and coordinates of this stage: form H (and read this
+            //    thread's B operands) while the MMAs of earlier stages still hold the ring slot
+            bool ok = tc::mbar_wait_or_abort(&sh.stfull[stgi], (gs / nstg) & 1, &sh.abort_flag);
             ok = __all_sync(0xffffffffu, ok);                 // one decision per warp
             if (!ok) {
                 if (lane == 0) { atomicOr(a.err, 1); sh.abort_flag = 1; }
                 break;
             }
             if (__any_sync(0xffffffffu, *(volatile int*)&sh.abort_flag)) break;
-            unsigned char* st = ring + slot * stage_bytes;
-            float4* Ahi = (float4*)st;
-            float4* Alo = (float4*)(st + a_bytes);
-            float4* Bhi = (float4*)(st + 2 * a_bytes);
-            float4* Blo = (float4*)(st + 2 * a_bytes + b_bytes);
             const float4* sc = (const float4*)(stg + stgi * stg_bytes);
             const float4* sxy = (const float4*)(stg + stgi * stg_bytes + sc_bytes);
-            // B: K-element pair c2 = sources (2 c2, 2 c2 + 1); element (col, kk) at float4 (kk / 4) * N + col
-            for (int it = p; it < 8 * Rp; it += TC_PROD_WARPS * 32) {
-                const int c2 = it / Rp, r = it - c2 * Rp;
-                const float4 v0 = sc[(2 * c2) * Rp + r], v1 = sc[(2 * c2 + 1) * Rp + r];
-                Bhi[c2 * N + r] = make_float4(v0.x, -v0.z, v1.x, -v1.z);
-                Bhi[c2 * N + Rp + r] = make_float4(v0.z, v0.x, v1.z, v1.x);
-                Blo[c2 * N + r] = make_float4(v0.y, -v0.w, v1.y, -v1.w);
-                Blo[c2 * N + Rp + r] = make_float4(v0.w, v0.y, v1.w, v1.y);
+            // B: K-element pair c2 = sources (2 c2, 2 c2 + 1); element (col, kk) at float4 (kk / 4) * N + col;
+            // 8 Rp <= 512 items, at most one per producer thread
+            const bool has_b = p < 8 * Rp;
+            float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+            int b_c2 = 0, b_r = 0;
+            if (has_b) {
+                b_c2 = p / Rp;
+                b_r = p - b_c2 * Rp;
+                v0 = sc[(2 * b_c2) * Rp + b_r];
+                v1 = sc[(2 * b_c2 + 1) * Rp + b_r];
             }
             // A: sources 4q .. 4q + 3 of the stage for target j; element (row, kk) at float4 (kk / 4) * 128 + row
             float hr[4], hi[4];
@@ -458,6 +455,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairsum_tc(TCArgs a) {
             // the staging slot has been read (densities and coordinates): free for the next copy
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&sh.stempty[stgi]);
+            // 2. the ring slot: wait for the MMAs of stage gs - TC_NS, then store the operands
+            if (gs >= TC_NS) ok = tc::mbar_wait_or_abort(&sh.empty[slot], ((gs / TC_NS) - 1) & 1, &sh.abort_flag);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) { atomicOr(a.err, 1); sh.abort_flag = 1; }
+                break;
+            }
+            if (__any_sync(0xffffffffu, *(volatile int*)&sh.abort_flag)) break;
+            unsigned char* st = ring + slot * stage_bytes;
+            float4* Ahi = (float4*)st;
+            float4* Alo = (float4*)(st + a_bytes);
+            float4* Bhi = (float4*)(st + 2 * a_bytes);
+            float4* Blo = (float4*)(st + 2 * a_bytes + b_bytes);
+            if (has_b) {
+                Bhi[b_c2 * N + b_r] = make_float4(v0.x, -v0.z, v1.x, -v1.z);
+                Bhi[b_c2 * N + Rp + b_r] = make_float4(v0.z, v0.x, v1.z, v1.x);
+                Blo[b_c2 * N + b_r] = make_float4(v0.y, -v0.w, v1.y, -v1.w);
+                Blo[b_c2 * N + Rp + b_r] = make_float4(v0.w, v0.y, v1.w, v1.y);
+            }
 #pragma unroll
             for (int h2 = 0; h2 < 2; ++h2) {
                 const float x0 = hr[2 * h2], y0 = hi[2 * h2], x1 = hr[2 * h2 + 1], y1 = hi[2 * h2 + 1];
