@@ -1139,6 +1139,21 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum_persist(const PSDesc* __rest
 #include "cr_solve.cuh"
 
 // mode 0: y = x + k2 * ((i/4) sum_c partial + dV (m x));  mode 1: y = (i/4) sum_c partial
+// partial[0][j] = sum over the slots of partial[c][j] (thread per node: every slot row is read
+// coalesced), for the unordered-pair kernels' many slots; the epilogues then read one slot.
+__global__ void k_sum_slots(int n, int nslots, double2* __restrict__ partial) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double sr = 0.0, si = 0.0;
+#pragma unroll 8
+    for (int c = 0; c < nslots; ++c) {
+        const double2 p = partial[(size_t)c * n + j];
+        sr += p.x;
+        si += p.y;
+    }
+    partial[j] = make_double2(sr, si);
+}
+
 __global__ void k_apply_epi(int n, int nchunk, const double2* __restrict__ partial, const int64_t* __restrict__ rowptr,
                             const int* __restrict__ cols, const double2* __restrict__ vals,
                             const double2* __restrict__ m, const double2* __restrict__ x, double k2,
@@ -2429,6 +2444,17 @@ static cudaError_t raise_tab_limits(int mode, size_t bytes) {
 static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m, const double* w);
 static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m) { return launch_pairsum(op, f, m, op->w.p); }
 
+// Many partial slots (the unordered-pair kernels): sum them into slot 0 with coalesced reads
+// before the epilogue, which then reads one slot.
+static ls_status collapse_slots(ls_op* op) {
+    if (op->ps_slots <= 32) return LS_OK;
+    k_sum_slots<<<(op->nq + 255) / 256, 256, 0, op->stream>>>(op->nq, op->ps_slots, op->partial.p);
+    CK(cudaGetLastError());
+    op->launches++;
+    op->ps_slots = 1;
+    return LS_OK;
+}
+
 static ls_status launch_pairsum(ls_op* op, const double2* f, const double2* m, const double* w) {
     if (op->cartesian) return fail(LS_EINVAL, "a purely Cartesian operator has no quadrature-node pair sum");
     dim3 grid((op->nq + PS_TPB - 1) / PS_TPB, op->nchunk);
@@ -2551,6 +2577,7 @@ static ls_status apply_L(ls_op* op, const double2* x, double2* y) {
     if (op->cartesian) return cart_apply(op, x, y, 0);
     ls_status s = launch_pairsum(op, x, op->m.p);
     if (s != LS_OK) return s;
+    TRY(collapse_slots(op));
     int threads = 256;
     int blocks = (int)(((int64_t)op->nq * 32 + threads - 1) / threads);
     k_apply_epi<<<blocks, threads, 0, op->stream>>>(op->nq, op->ps_slots, op->partial.p, op->rowptr.p, op->cols.p, op->vals.p,
@@ -2952,6 +2979,7 @@ static ls_status apply_LT(ls_op* op, const double2* x, double2* y, int mode = 0)
     if (op->cartesian) return cart_apply(op, x, y, mode == 2 ? 2 : 1);   // V^(C) is symmetric
     ls_status s = launch_pairsum(op, x, nullptr, nullptr);
     if (s != LS_OK) return s;
+    TRY(collapse_slots(op));
     int threads = 256;
     int blocks = (int)(((int64_t)op->nq * 32 + threads - 1) / threads);
     k_applyT_epi<<<blocks, threads, 0, op->stream>>>(op->nq, op->ps_slots, op->partial.p, op->rowptrT.p, op->colsT.p,
@@ -3768,6 +3796,7 @@ ls_status ls_apply_precond_dev(ls_op* op, const void* x_dev, void* y_dev) {
 ls_status ls_pairsum_dev(ls_op* op, const void* f_dev, void* y_dev) {
     if (!op || !f_dev || !y_dev) return fail(LS_EINVAL, "null argument");
     TRY(launch_pairsum(op, (const double2*)f_dev, nullptr));
+    TRY(collapse_slots(op));
     int threads = 256;
     int blocks = (int)(((int64_t)op->nq * 32 + threads - 1) / threads);
     k_apply_epi<<<blocks, threads, 0, op->stream>>>(op->nq, op->ps_slots, op->partial.p, op->rowptr.p, op->cols.p,
