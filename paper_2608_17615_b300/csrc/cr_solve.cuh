@@ -118,6 +118,102 @@ __global__ void __launch_bounds__(32 * CR_WARPS) k_cr_mv(int nx, int R, size_t s
     }
 }
 
+// The same products with the factor blocks stored as double-float pairs (hi.re, hi.im,
+// lo.re, lo.im per complex entry: the 16 bytes of a complex128) and double-float arithmetic
+// on the FP32 pipe, single right-hand side: B300's FP64 pipe caps the complex128 product at
+// about a third of HBM speed, the double-float one reads the same bytes with FP32
+// instructions (rounding ~1e-13 instead of ~1e-16, far below what the forms that take it,
+// the FP32 and mixed solves, can see).  Vectors stay FP64.
+struct CRJobDF {
+    double2* y;
+    const double2* base;
+    const float4* M1;
+    const double2* v1;
+    const float4* M2;
+    const double2* v2;
+};
+
+__device__ __forceinline__ void cr_df_fast(float& h, float& l) {      // renormalise |h| >= |l|
+    const float s = h + l;
+    l = l - (s - h);
+    h = s;
+}
+__device__ __forceinline__ void cr_two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bv = s - a;
+    const float av = s - bv;
+    e = (a - av) + (b - bv);
+}
+// (rh, rl) + i (ih, il) += a * v, a and v double-float complex as (hi.re, hi.im, lo.re, lo.im);
+// products to first order (high product, FMA residual, cross terms), high parts by TwoSum,
+// every residual into the low word
+__device__ __forceinline__ void cr_df_cmac(float4 a, float4 v, float& rh, float& rl, float& ih, float& il) {
+    const float p1 = a.x * v.x, p2 = a.y * v.y, p3 = a.x * v.y, p4 = a.y * v.x;
+    float e1 = fmaf(a.x, v.x, -p1), e2 = fmaf(a.y, v.y, -p2), e3 = fmaf(a.x, v.y, -p3), e4 = fmaf(a.y, v.x, -p4);
+    e1 = fmaf(a.z, v.x, fmaf(a.x, v.z, e1));
+    e2 = fmaf(a.w, v.y, fmaf(a.y, v.w, e2));
+    e3 = fmaf(a.z, v.y, fmaf(a.x, v.w, e3));
+    e4 = fmaf(a.w, v.x, fmaf(a.y, v.z, e4));
+    float t, err;
+    cr_two_sum(rh, p1, t, err);
+    rl += err + e1;
+    cr_two_sum(t, -p2, rh, err);
+    rl += err - e2;
+    cr_two_sum(ih, p3, t, err);
+    il += err + e3;
+    cr_two_sum(t, p4, ih, err);
+    il += err + e4;
+}
+
+__global__ void __launch_bounds__(32 * CR_WARPS) k_cr_mv_df(int nx, const CRJobDF* __restrict__ jobs) {
+    extern __shared__ float4 crshdf[];                   // [2][nx] double-float vectors
+    const CRJobDF J = jobs[blockIdx.y];
+    for (int c = threadIdx.x; c < nx; c += blockDim.x) {
+        const double2 a = J.v1[c];
+        const float ah = (float)a.x, bh = (float)a.y;
+        crshdf[c] = make_float4(ah, bh, (float)(a.x - (double)ah), (float)(a.y - (double)bh));
+        const double2 b = J.M2 ? J.v2[c] : make_double2(0.0, 0.0);
+        const float ch = (float)b.x, dh = (float)b.y;
+        crshdf[nx + c] = make_float4(ch, dh, (float)(b.x - (double)ch), (float)(b.y - (double)dh));
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = 0; q < CR_ROWS_PER_WARP; ++q) {
+        const int row = (blockIdx.x * CR_WARPS + warp) * CR_ROWS_PER_WARP + q;
+        if (row >= nx) break;
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+        const float4* m1 = J.M1 + (size_t)row * nx;
+        int n_acc = 0;
+#pragma unroll 2
+        for (int c = lane; c < nx; c += 32) {
+            cr_df_cmac(m1[c], crshdf[c], rh, rl, ih, il);
+            if (++n_acc == 16) { cr_df_fast(rh, rl); cr_df_fast(ih, il); n_acc = 0; }
+        }
+        if (J.M2) {
+            const float4* m2 = J.M2 + (size_t)row * nx;
+#pragma unroll 2
+            for (int c = lane; c < nx; c += 32) {
+                cr_df_cmac(m2[c], crshdf[nx + c], rh, rl, ih, il);
+                if (++n_acc == 16) { cr_df_fast(rh, rl); cr_df_fast(ih, il); n_acc = 0; }
+            }
+        }
+        // warp sum in FP64 of the lanes' double-float partials
+        double sr = (double)rh + (double)rl, si = (double)ih + (double)il;
+        for (int o = 16; o > 0; o >>= 1) {
+            sr += __shfl_down_sync(0xffffffffu, sr, o);
+            si += __shfl_down_sync(0xffffffffu, si, o);
+        }
+        if (lane == 0) {
+            if (J.base) {
+                const double2 b = J.base[row];
+                J.y[row] = make_double2(b.x - sr, b.y - si);
+            } else {
+                J.y[row] = make_double2(sr, si);
+            }
+        }
+    }
+}
+
 // Level-0 updates with the tridiagonal band blocks of C (entry (a, a + da) of
 // L_b at cband[(9 b + da + 1) nx + a], of U_b at cband[(9 b + 6 + da + 1) nx + a]).
 // transposed = 0: y_a = base_a - sum_da L(a, a+da) vL_{a+da} - sum_da U(a, a+da) vU_{a+da}

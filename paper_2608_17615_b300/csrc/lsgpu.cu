@@ -2245,6 +2245,9 @@ struct CRPlan {
     DevBuf<CRJob> jobs;
     DevBuf<CRTriJob> tjobs;
     std::vector<Step> fwd, trn;
+    std::vector<CRJob> hjobs;                           // host copy of jobs (for the double-float variant)
+    DevBuf<float4> store_df;                            // store as double-float pairs (made on first use)
+    DevBuf<CRJobDF> jobs_df;
     double2* t() const { return arena.p; }
     double2* x() const { return arena.p + (size_t)nx * ny; }
 };
@@ -2338,7 +2341,9 @@ struct ls_op {
     cudaGraphExec_t gP = nullptr;
     DevBuf<double2> pin, pout;
     cudaGraphExec_t gPT = nullptr;         // graph of the P^T apply
+    cudaGraphExec_t gPdf = nullptr, gPTdf = nullptr;   // the same with the double-float blocks
     int nlaunch_P = 0, nlaunch_PT = 0;     // kernels in each graph
+    int nlaunch_Pdf = 0, nlaunch_PTdf = 0;
     CRPlan cr;                           // cyclic reduction of C for the single-RHS P and P^T
     // purely Cartesian operator (ls_cartesian_create): the unknowns are the grid nodes,
     // L^(C) = I + k^2 V^(C) M^(C) with V^(C) applied by FFT convolution, P = S^(C) = C^{-1} A
@@ -2355,6 +2360,8 @@ struct ls_op {
         for (auto& e : ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
         if (gP) cudaGraphExecDestroy(gP);
         if (gPT) cudaGraphExecDestroy(gPT);
+        if (gPdf) cudaGraphExecDestroy(gPdf);
+        if (gPTdf) cudaGraphExecDestroy(gPTdf);
         if (cap) cudaStreamDestroy(cap);
         if (tc_herr) cudaFreeHost(tc_herr);
         if (fft) cufftDestroy(fft);
@@ -2882,6 +2889,7 @@ static ls_status build_cr(ls_op* op) {
         if (!j.M1 || !j.v1 || !j.y) return fail(LS_ECUDA, "cyclic reduction: incomplete job table");
     CK(P.jobs.alloc(J.size()));
     CK(cudaMemcpy(P.jobs.p, J.data(), sizeof(CRJob) * J.size(), cudaMemcpyHostToDevice));
+    P.hjobs = J;
     if (!TJ.empty()) {
         CK(P.tjobs.alloc(TJ.size()));
         CK(cudaMemcpy(P.tjobs.p, TJ.data(), sizeof(CRTriJob) * TJ.size(), cudaMemcpyHostToDevice));
@@ -2890,14 +2898,52 @@ static ls_status build_cr(ls_op* op) {
 }
 
 // The steps of C x = t (transposed: C^T x = t) on P.t() -> P.x(), single right-hand side.
-static int launch_cr(ls_op* op, cudaStream_t st, bool transposed) {
+__global__ void k_to_dfc(int64_t n, const double2* __restrict__ a, float4* __restrict__ b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double2 v = a[i];
+    const float xh = (float)v.x, yh = (float)v.y;
+    b[i] = make_float4(xh, yh, (float)(v.x - (double)xh), (float)(v.y - (double)yh));
+}
+
+// Double-float copy of the cyclic-reduction blocks and the job table pointing into it.
+static ls_status ensure_cr_df(ls_op* op) {
+    CRPlan& P = op->cr;
+    if (P.store_df.p || P.hjobs.empty()) return LS_OK;
+    const int64_t ns = (int64_t)P.store.n;
+    CK(P.store_df.alloc(ns));
+    k_to_dfc<<<(unsigned)((ns + 255) / 256), 256, 0, op->stream>>>(ns, P.store.p, P.store_df.p);
+    CK(cudaGetLastError());
+    op->launches++;
+    std::vector<CRJobDF> JD(P.hjobs.size());
+    for (size_t i = 0; i < JD.size(); ++i) {
+        const CRJob& j = P.hjobs[i];
+        const double2* m[2] = {j.M1, j.M2};
+        const float4* md[2] = {nullptr, nullptr};
+        for (int t = 0; t < 2; ++t) {
+            if (!m[t]) continue;
+            if (m[t] < P.store.p || m[t] >= P.store.p + ns) return fail(LS_ECUDA, "cyclic reduction: job outside the block store");
+            md[t] = P.store_df.p + (m[t] - P.store.p);
+        }
+        JD[i] = CRJobDF{j.y, j.base, md[0], j.v1, md[1], j.v2};
+    }
+    CK(P.jobs_df.alloc(JD.size()));
+    CK(cudaMemcpy(P.jobs_df.p, JD.data(), sizeof(CRJobDF) * JD.size(), cudaMemcpyHostToDevice));
+    CK(raise_smem_limit(k_cr_mv_df, sizeof(float4) * 2 * P.nx));
+    return LS_OK;
+}
+
+static int launch_cr(ls_op* op, cudaStream_t st, bool transposed, bool df = false) {
     const CRPlan& P = op->cr;
     const int nx = P.nx;
     const size_t shm = sizeof(double2) * 2 * nx;
     const int rows = CR_WARPS * CR_ROWS_PER_WARP;
     int nl = 0;
     for (const auto& s : transposed ? P.trn : P.fwd) {
-        if (s.kind == 0)
+        if (s.kind == 0 && df)
+            k_cr_mv_df<<<dim3((nx + rows - 1) / rows, s.count, 1), 32 * CR_WARPS, sizeof(float4) * 2 * nx, st>>>(
+                nx, P.jobs_df.p + s.first);
+        else if (s.kind == 0)
             k_cr_mv<1><<<dim3((nx + rows - 1) / rows, s.count, 1), 32 * CR_WARPS, shm, st>>>(nx, 1, P.svec,
                                                                                          P.jobs.p + s.first);
         else
@@ -2910,11 +2956,11 @@ static int launch_cr(ls_op* op, cudaStream_t st, bool transposed) {
 
 // The kernel sequence of P x on stream st (T_Q^C, the stencil A, the cyclic-reduction
 // solve of C, then T_C^Q fused with the identity term); returns the number of launches.
-static int launch_P_kernels(ls_op* op, cudaStream_t st, const double2* x, double2* z) {
+static int launch_P_kernels(ls_op* op, cudaStream_t st, const double2* x, double2* z, bool df = false) {
     const int nc = op->nx * op->ny, nx = op->nx, ny = op->ny;
     k_tqc<<<(nc + 255) / 256, 256, 0, st>>>(nc, op->tqc_rp.p, op->tqc_ci.p, op->tqc_cv.p, x, op->pg.p);
     k_stencil<<<(nc + 255) / 256, 256, 0, st>>>(nx, ny, op->st.p, op->pg.p, op->cr.t());
-    const int ncr = launch_cr(op, st, false);
+    const int ncr = launch_cr(op, st, false, df);
     k_tcq<<<(op->nq + 255) / 256, 256, 0, st>>>(op->nq, op->tcq_idx.p, op->tcq_w.p, op->cr.x(), op->pg.p, x, z);
     return 3 + ncr;
 }
@@ -2935,10 +2981,10 @@ static int launch_S_kernels(ls_op* op, cudaStream_t st, const double2* x, double
 }
 
 // P^T x = x + T_Q^C^T (A^T C^{-T} - I) T_C^Q^T x on stream st; returns the number of launches.
-static int launch_PT_kernels(ls_op* op, cudaStream_t st, const double2* x, double2* z) {
+static int launch_PT_kernels(ls_op* op, cudaStream_t st, const double2* x, double2* z, bool df = false) {
     const int nc = op->nx * op->ny, nx = op->nx, ny = op->ny;
     k_tqc<<<(nc + 255) / 256, 256, 0, st>>>(nc, op->tcqT_rp.p, op->tcqT_ci.p, op->tcqT_cv.p, x, op->cr.t());
-    const int ncr = launch_cr(op, st, true);
+    const int ncr = launch_cr(op, st, true, df);
     k_stencilT<<<(nc + 255) / 256, 256, 0, st>>>(nx, ny, op->st.p, op->cr.x(), op->cr.t(), op->ptp.p);
     k_tqcT<<<(op->nq + 255) / 256, 256, 0, st>>>(op->nq, op->tqcT_rp.p, op->tqcT_ci.p, op->tqcT_cv.p, op->ptp.p, nc, x,
                                                  op->nq, z, op->nq);
@@ -2949,17 +2995,22 @@ static int launch_PT_kernels(ls_op* op, cudaStream_t st, const double2* x, doubl
 // private stream, with fixed input/output buffers) and replayed; x and z are copied
 // in and out.
 static ls_status apply_P_graph(ls_op* op, const double2* x, double2* z, bool transpose) {
-    cudaGraphExec_t& ge = transpose ? op->gPT : op->gP;
-    int& nlaunch = transpose ? op->nlaunch_PT : op->nlaunch_P;
+    // the FP32 and mixed forms take the double-float blocks (their solves cannot see the
+    // ~1e-13 rounding); the FP64-accurate forms keep the complex128 ones
+    const bool df = !op->cartesian && (op->mode == 2 || op->mode == 4);
+    if (df) TRY(ensure_cr_df(op));
+    cudaGraphExec_t& ge = df ? (transpose ? op->gPTdf : op->gPdf) : (transpose ? op->gPT : op->gP);
+    int& nlaunch = df ? (transpose ? op->nlaunch_PTdf : op->nlaunch_Pdf) : (transpose ? op->nlaunch_PT : op->nlaunch_P);
     if (!ge) {
         if (!op->cap) CK(cudaStreamCreateWithFlags(&op->cap, cudaStreamNonBlocking));
         if (!op->pin.p) CK(op->pin.alloc(op->nq));
         if (!op->pout.p) CK(op->pout.alloc(op->nq));
+        CK(cudaStreamSynchronize(op->stream));           // the double-float blocks are ready before the capture
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(op->cap, cudaStreamCaptureModeThreadLocal));
         nlaunch = op->cartesian ? launch_S_kernels(op, op->cap, op->pin.p, op->pout.p, transpose)
-                  : transpose   ? launch_PT_kernels(op, op->cap, op->pin.p, op->pout.p)
-                                : launch_P_kernels(op, op->cap, op->pin.p, op->pout.p);
+                  : transpose   ? launch_PT_kernels(op, op->cap, op->pin.p, op->pout.p, df)
+                                : launch_P_kernels(op, op->cap, op->pin.p, op->pout.p, df);
         CK(cudaStreamEndCapture(op->cap, &g));
         cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
         cudaGraphDestroy(g);
