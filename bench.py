@@ -135,20 +135,21 @@ FP32_PEAK_SOURCE = "FP32 unit count: 148 SMs x 128 lanes x 2 flops x 2.032 GHz"
 #    23.5 DMUL, 7.1 DADD) -> 148
 #  2 FP32 table: H = two double-float differences 22, double-float t 21, u 4, two degree-6
 #    Horner chains 24 (71); multiply-add = complex multiply 6 + Kahan sums 8 (14)
-#  3 double-float table: H = differences 22, t 21, u 10, per chain nf FP32 Horner steps
-#    (2 flops) and nc - 1 - nf double-float steps (18 flops); multiply-add = four
-#    double-float products 40 + four double-float sums 44 (84)
+#  3 double-float table: H = differences 22, t 21, u 10, normalisation 6, per chain nf FP32
+#    Horner steps (2 flops) and nc - 1 - nf compensated double-float steps (15 flops);
+#    multiply-add = four products to first order 28 + four TwoSums with residual sums 32 (60);
+#    the ordered-pair kernel normalises every sum (84)
 # The unordered-pair kernels (k_pairsum_f32s, k_pairsum_dfs, the default) form H once per
 # unordered pair and do both multiply-adds: per ordered pair H / 2 plus one multiply-add.
-# ncu check (k_pairsum_dfs<10, 2>, 40,200 nodes): FADD 167.2 + FMUL 14.1 + 2 x FFMA 39.3 =
-# 259.9 FP32 flops per ordered pair against 240.5 counted here (the rest: the diagonal
+# ncu check (k_pairsum_dfs<10, 2>, 40,200 nodes): FADD 122.0 + FMUL 14.1 + 2 x FFMA 39.3 =
+# 214.8 FP32 flops per ordered pair against 198.5 counted here (the rest: the diagonal
 # blocks' ordered pairs and the FP64 folds).
 def flops_per_pair_of(mode, nc, nf=0, symmetric=True):
     if mode == 0:
         return 15 + 4 * (nc - 1)
     if mode == 3:
-        h = 53 + 4 * nf + 36 * (nc - 1 - nf)
-        return h / 2 + 84 if symmetric else h + 84
+        h = 59 + 4 * nf + 30 * (nc - 1 - nf)
+        return h / 2 + 60 if symmetric else h + 84
     if mode == 2:
         return 71 / 2 + 14 if symmetric else 85
     return 148
@@ -157,9 +158,9 @@ def flops_per_pair_of(mode, nc, nf=0, symmetric=True):
 KERNEL = {0: "k_pairsum_tab", 1: "k_pairsum", 2: "k_pairsum_f32s", 3: "k_pairsum_dfs"}
 # dram__bytes_read + write per launch (40,200 nodes) from ncu captures of the pair-sum kernels
 # (the ordered-pair kernels read the nodes and densities once: 2.4 MB; the unordered-pair
-# kernels also write one partial row per block distance, measured for k_pairsum_dfs); None
-# where the current kernel has not been captured
-TRAFFIC_BYTES = {0: 2.4e6, 2: None, 3: 4.935e7}
+# kernels also write one partial row per block distance: k_pairsum_f32s 2.43 + 46.45 MB,
+# k_pairsum_dfs 3.20 + 46.99 MB)
+TRAFFIC_BYTES = {0: 2.4e6, 2: 4.889e7, 3: 5.019e7}
 
 
 def _timed(fn, stream, reps=1):
