@@ -281,7 +281,7 @@ struct TCCursor {
     }
 };
 
-__global__ void __maxnreg__(96) k_pairsum_tc(TCArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, 1) k_pairsum_tc(TCArgs a) {
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     __shared__ TCShared sh;
     // dynamic shared memory: ring of TC_NS stages {A_hi, A_lo, B_hi, B_lo}, nstg staging slots
