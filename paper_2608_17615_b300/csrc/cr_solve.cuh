@@ -178,37 +178,51 @@ __global__ void __launch_bounds__(32 * CR_WARPS) k_cr_mv_df(int nx, const CRJobD
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int q = 0; q < CR_ROWS_PER_WARP; ++q) {
-        const int row = (blockIdx.x * CR_WARPS + warp) * CR_ROWS_PER_WARP + q;
-        if (row >= nx) break;
-        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-        const float4* m1 = J.M1 + (size_t)row * nx;
-        int n_acc = 0;
-#pragma unroll 2
+    // the warp's CR_ROWS_PER_WARP (= 2) rows side by side: two independent accumulation
+    // chains and twice the loads in flight per column step
+    static_assert(CR_ROWS_PER_WARP == 2, "k_cr_mv_df interleaves two rows per warp");
+    const int row0 = (blockIdx.x * CR_WARPS + warp) * CR_ROWS_PER_WARP;
+    if (row0 >= nx) return;
+    const bool two = row0 + 1 < nx;
+    const int row1 = two ? row0 + 1 : row0;
+    float r0h = 0.f, r0l = 0.f, i0h = 0.f, i0l = 0.f, r1h = 0.f, r1l = 0.f, i1h = 0.f, i1l = 0.f;
+    int n_acc = 0;
+    for (int m = 0; m < 2; ++m) {
+        const float4* M = m ? J.M2 : J.M1;
+        if (!M) break;
+        const float4* a0 = M + (size_t)row0 * nx;
+        const float4* a1 = M + (size_t)row1 * nx;
+        const float4* v = crshdf + m * nx;
+#pragma unroll 4
         for (int c = lane; c < nx; c += 32) {
-            cr_df_cmac(m1[c], crshdf[c], rh, rl, ih, il);
-            if (++n_acc == 16) { cr_df_fast(rh, rl); cr_df_fast(ih, il); n_acc = 0; }
-        }
-        if (J.M2) {
-            const float4* m2 = J.M2 + (size_t)row * nx;
-#pragma unroll 2
-            for (int c = lane; c < nx; c += 32) {
-                cr_df_cmac(m2[c], crshdf[nx + c], rh, rl, ih, il);
-                if (++n_acc == 16) { cr_df_fast(rh, rl); cr_df_fast(ih, il); n_acc = 0; }
+            const float4 x0 = a0[c], x1 = a1[c], vv = v[c];
+            cr_df_cmac(x0, vv, r0h, r0l, i0h, i0l);
+            cr_df_cmac(x1, vv, r1h, r1l, i1h, i1l);
+            if (++n_acc == 16) {
+                cr_df_fast(r0h, r0l); cr_df_fast(i0h, i0l);
+                cr_df_fast(r1h, r1l); cr_df_fast(i1h, i1l);
+                n_acc = 0;
             }
         }
-        // warp sum in FP64 of the lanes' double-float partials
-        double sr = (double)rh + (double)rl, si = (double)ih + (double)il;
-        for (int o = 16; o > 0; o >>= 1) {
-            sr += __shfl_down_sync(0xffffffffu, sr, o);
-            si += __shfl_down_sync(0xffffffffu, si, o);
-        }
-        if (lane == 0) {
+    }
+    // warp sums in FP64 of the lanes' double-float partials
+    double s0r = (double)r0h + (double)r0l, s0i = (double)i0h + (double)i0l;
+    double s1r = (double)r1h + (double)r1l, s1i = (double)i1h + (double)i1l;
+    for (int o = 16; o > 0; o >>= 1) {
+        s0r += __shfl_down_sync(0xffffffffu, s0r, o);
+        s0i += __shfl_down_sync(0xffffffffu, s0i, o);
+        s1r += __shfl_down_sync(0xffffffffu, s1r, o);
+        s1i += __shfl_down_sync(0xffffffffu, s1i, o);
+    }
+    if (lane == 0) {
+        const int rows[2] = {row0, row1};
+        const double sr[2] = {s0r, s1r}, si[2] = {s0i, s1i};
+        for (int q = 0; q < (two ? 2 : 1); ++q) {
             if (J.base) {
-                const double2 b = J.base[row];
-                J.y[row] = make_double2(b.x - sr, b.y - si);
+                const double2 b = J.base[rows[q]];
+                J.y[rows[q]] = make_double2(b.x - sr[q], b.y - si[q]);
             } else {
-                J.y[row] = make_double2(sr, si);
+                J.y[rows[q]] = make_double2(sr[q], si[q]);
             }
         }
     }
