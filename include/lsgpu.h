@@ -59,13 +59,15 @@ enum {
                                  FP32) arithmetic and accumulated on the FP32 pipe                */
     LS_PREC_MIXED = 4         /* mixed precision: every GMRES solve runs with the FP32 pair sum
                                  (as LS_PREC_FP32) and is refined against the double-float
-                                 operator (as LS_PREC_FP64_DF): r = b - L u accurate, an FP32
-                                 GMRES correction, u += d, until ||P r|| <= tol ||P b|| with the
-                                 accurate L (at most 4 corrections).  Single applies
-                                 (ls_apply*) use the accurate operator; iters_out counts every
-                                 inner iteration, hist_out holds the first FP32 solve's history;
-                                 ls_op_last_residual is the accurate operator's residual.  The
-                                 batched solves are not affected (they refine on their own).   */
+                                 operator (as LS_PREC_FP64_DF): r = b - L u with the accurate L,
+                                 an FP32 GMRES correction d, u += d, r -= L d (the product of the
+                                 small correction in FP32: its error, eps32 cond(L) ||r||, is far
+                                 below tol ||b||), until ||P r|| <= tol ||P b|| (at most 4
+                                 corrections).  Single applies (ls_apply*) use the accurate
+                                 operator; iters_out counts every inner iteration, hist_out holds
+                                 the first FP32 solve's history; ls_op_last_residual is the
+                                 refinement's final residual.  The batched solves are not
+                                 affected (they refine on their own).                           */
 };
 
 /* Build parameters of an operator. */

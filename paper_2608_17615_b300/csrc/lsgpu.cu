@@ -3157,11 +3157,12 @@ static ls_status residual_full(ls_op* op, const double2* b, const double2* u, do
 }
 
 // Mixed-precision solve (pairsum mode 4): GMRES with the FP32 pair sum, then iterative
-// refinement against the double-float (FP64-accurate) operator.  Each step forms
-// r = b - L u with the accurate L; while ||P r|| > tol ||P b|| an FP32 GMRES solves
-// L d = r to the relative tolerance that brings ||P r|| below tol / 2 (at most 0.5, at
-// least 1e-3, where the FP32 operator's own error starts to limit the correction) and
-// u += d.  The exit residual (ls_op_last_residual) is the accurate operator's.
+// refinement against the double-float (FP64-accurate) operator.  The residual of the FP32
+// solution, r = b - L u, is formed with the accurate L; while ||P r|| > tol ||P b|| an FP32
+// GMRES solves L d = r to the relative tolerance that brings ||P r|| below tol / 2 (at most
+// 0.5, at least 1e-3, where the FP32 operator's own error starts to limit the correction),
+// u += d and r -= L d (FP32: the product of the small correction needs no more).  The
+// exit residual (ls_op_last_residual) is that residual's.
 #define MIXED_REFINE 4
 static ls_status solve_mixed(ls_op* op, const double2* b, double2* u, double* hist_host, int* iters, bool transpose) {
     const int n = op->nq, nb = (n + 255) / 256;
@@ -3196,8 +3197,20 @@ static ls_status solve_mixed(ls_op* op, const double2* b, double2* u, double* hi
     double pb2 = 0, pr2 = 0, rel = 0;
     TRY(pnorm2(b, 3, pb2));
     for (int step = 0;; ++step) {
-        TRY(transpose ? apply_LT(op, u, op->ir_y.p) : apply_L(op, u, op->ir_y.p));
-        k_sub_vec<<<nb, 256, 0, op->stream>>>(n, b, op->ir_y.p, op->ir_r.p);
+        if (step == 0) {
+            // r = b - L u with the double-float operator
+            TRY(transpose ? apply_LT(op, u, op->ir_y.p) : apply_L(op, u, op->ir_y.p));
+            k_sub_vec<<<nb, 256, 0, op->stream>>>(n, b, op->ir_y.p, op->ir_r.p);
+        } else {
+            // after u += d: r -= L d with the FP32 operator.  Its error is relative to |d|,
+            // eps32 ||k^2 V M|| ||d|| <= eps32 cond(L) ||r||, about 1e-13 of ||b|| for an FP32
+            // solve's residual of ~1e-7 ||b||: far below tol
+            op->inner32 = true;
+            ls_status sa = transpose ? apply_LT(op, op->ir_d.p, op->ir_y.p) : apply_L(op, op->ir_d.p, op->ir_y.p);
+            op->inner32 = false;
+            TRY(sa);
+            k_sub_vec<<<nb, 256, 0, op->stream>>>(n, op->ir_r.p, op->ir_y.p, op->ir_r.p);
+        }
         CK(cudaGetLastError());
         op->launches++;
         TRY(pnorm2(op->ir_r.p, 2, pr2));
@@ -3219,7 +3232,7 @@ static ls_status solve_mixed(ls_op* op, const double2* b, double2* u, double* hi
     op->last_it = total;
     if (iters) *iters = total;
     if (rel <= tol) return LS_OK;
-    fail(LS_ENOCONV, "mixed-precision refinement: accurate residual " + std::to_string(rel) + " above tol");
+    fail(LS_ENOCONV, "mixed-precision refinement: residual " + std::to_string(rel) + " above tol");
     return LS_ENOCONV;
 }
 
