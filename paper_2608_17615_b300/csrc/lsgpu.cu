@@ -268,12 +268,10 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum_tab(const double2* __restric
 // dx, dy and t = dx^2 + dy^2 are formed in double-float arithmetic (TwoSum /
 // FMA-based TwoProduct) so that t keeps a relative error near 1e-14 and the
 // cell variable u near 1e-7; H0 comes from an FP32 table (complex64 degree-7
-// polynomials, validated to 2e-8 at setup; a cell's 8 coefficients are 4 aligned 16-byte
-// shared-memory words, and cells sit 5 words apart so that the cells of a warp's lanes
-// spread over all shared-memory banks); terms are accumulated with Kahan compensation in
-// FP32.  Pairs below the table range use the FP64 routine.
+// polynomials, validated to 2e-8 at setup; 8 coefficients per cell so that a cell's
+// coefficients are 4 aligned 16-byte shared-memory words); terms are accumulated with
+// Kahan compensation in FP32.  Pairs below the table range use the FP64 routine.
 #define NC_F32 8
-#define NC_F32_STRIDE 10                 // float2 slots per cell (the last 2 unused)
 struct F32Tile { float4 xy; float2 s; };
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -318,7 +316,7 @@ __device__ __forceinline__ bool f32_h0(float txh, float txl, float tyh, float ty
         float4 cv = cellv[cell];
         float u = ((th - cv.x) + (tl - cv.y)) * cv.z;
         // coefficients e = 2 i, 2 i + 1 in the float4 word i (re, im, re, im)
-        const float4* c4 = reinterpret_cast<const float4*>(coef + cell * NC_F32_STRIDE);
+        const float4* c4 = reinterpret_cast<const float4*>(coef + cell * NC_F32);
         float4 w = c4[NC_F32 / 2 - 1];
         hr = fmaf(w.z, u, w.x);
         him = fmaf(w.w, u, w.y);
@@ -348,8 +346,8 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum_f32(const double2* __restric
                                                         double2* __restrict__ partial) {
     extern __shared__ float4 ftab[];
     __shared__ F32Tile tile[PS_TILE];
-    // layout: coef [ncell][NC_F32_STRIDE] float2, cell (mid_hi, mid_lo, inv_hw, 0) [ncell], oct int2 [noct]
-    const int coef_f4 = (ncell * NC_F32_STRIDE + 1) / 2;
+    // layout: coef [ncell][NC_F32] float2 (as float4 pairs), cell (mid_hi, mid_lo, inv_hw, 0) [ncell], oct int2 [noct]
+    const int coef_f4 = (ncell * NC_F32 + 1) / 2;
     const int words = coef_f4 + ncell + (noct + 1) / 2;
     for (int i = threadIdx.x; i < words; i += PS_TPB) ftab[i] = tab_g[i];
     const float2* coef = reinterpret_cast<const float2*>(ftab);
@@ -421,7 +419,7 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum_f32s(const double2* __restri
     extern __shared__ float4 ftab[];
     __shared__ F32Tile tile[PS_TPB];
     __shared__ float2 colbuf[PS_TPB / 32][PS_TPB];
-    const int coef_f4 = (ncell * NC_F32_STRIDE + 1) / 2;
+    const int coef_f4 = (ncell * NC_F32 + 1) / 2;
     const int words = coef_f4 + ncell + (noct + 1) / 2;
     for (int i = threadIdx.x; i < words; i += PS_TPB) ftab[i] = tab_g[i];
     const float2* coef = reinterpret_cast<const float2*>(ftab);
@@ -866,7 +864,7 @@ struct MultiArgs {
 
 __device__ __forceinline__ void multi_unit(const MultiArgs& A, int tb, int chunk, int rb, const float4* ftab,
                                            float4* txy, float2 (*ts)[MRB]) {
-    const int coef_f4 = (A.ncell * NC_F32_STRIDE + 1) / 2;
+    const int coef_f4 = (A.ncell * NC_F32 + 1) / 2;
     const float2* coef = reinterpret_cast<const float2*>(ftab);
     const float4* cellv = ftab + coef_f4;
     const int2* oct = reinterpret_cast<const int2*>(cellv + A.ncell);
@@ -937,7 +935,7 @@ __device__ __forceinline__ void multi_unit(const MultiArgs& A, int tb, int chunk
                     int cell = ob.x + ((bits & 0x7fffff) >> ob.y);
                     float4 cv = cellv[cell];
                     float u = ((th - cv.x) + (tl - cv.y)) * cv.z;
-                    const float2* c = coef + cell * NC_F32_STRIDE;
+                    const float2* c = coef + cell * NC_F32;
                     float2 cc = c[NC_F32 - 1];
                     hr = cc.x;
                     him = cc.y;
@@ -982,7 +980,7 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum_multi_f32(MultiArgs A, const
     extern __shared__ float4 ftab[];
     __shared__ float4 txy[PS_TILE];
     __shared__ float2 ts[PS_TILE][MRB];
-    const int words = (A.ncell * NC_F32_STRIDE + 1) / 2 + A.ncell + (A.noct + 1) / 2;
+    const int words = (A.ncell * NC_F32 + 1) / 2 + A.ncell + (A.noct + 1) / 2;
     for (int i = threadIdx.x; i < words; i += PS_TPB) ftab[i] = tab_g[i];
     multi_unit(A, blockIdx.x, blockIdx.y, blockIdx.z, ftab, txy, ts);
 }
@@ -3316,19 +3314,14 @@ int32_t ls_op_num_nodes(const ls_op* op) { return op ? op->nq : 0; }
 // Tabulated H0 for the pair sum: t from (1e-2 h_min)^2 to the squared bounding-box diagonal.
 static ls_status build_table_range(ls_op* op, double t_lo, double t_hi, int mode);
 
-// FP32 table layout: coef [ncell][NC_F32_STRIDE] float2 (NC_F32 used), cells (mid_hi, mid_lo,
-// inv_hw, 0), oct (base, 23 - m)
+// FP32 table layout: coef [ncell][NC_F32] float2, cells (mid_hi, mid_lo, inv_hw, 0), oct (base, 23 - m)
 static ls_status upload_f32_table(const lsgpu::H0Table& T, DevBuf<double2>& buf, int& ncell, int& noct, int& blo,
                                   size_t& bytes, double& err) {
     ncell = (int)T.mid.size();
-    const int coef_f4 = (ncell * NC_F32_STRIDE + 1) / 2;
+    const int coef_f4 = (ncell * NC_F32 + 1) / 2;
     std::vector<float4> hf((size_t)coef_f4 + ncell + (T.noct + 1) / 2, make_float4(0.f, 0.f, 0.f, 0.f));
     float2* cf = reinterpret_cast<float2*>(hf.data());
-    for (size_t c = 0; c < (size_t)ncell; ++c)
-        for (int e = 0; e < NC_F32; ++e) {
-            const std::complex<double> v = T.coef[c * NC_F32 + e];
-            cf[c * NC_F32_STRIDE + e] = make_float2((float)v.real(), (float)v.imag());
-        }
+    for (size_t i = 0; i < (size_t)ncell * NC_F32; ++i) cf[i] = make_float2((float)T.coef[i].real(), (float)T.coef[i].imag());
     for (int c = 0; c < ncell; ++c) {
         float mh = (float)T.mid[c];
         hf[(size_t)coef_f4 + c] = make_float4(mh, (float)(T.mid[c] - (double)mh), (float)T.inv_hw[c], 0.f);

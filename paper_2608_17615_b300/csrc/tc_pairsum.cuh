@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairsum_tc(TCArgs a) {
                     if (lane == 0) { atomicOr(a.err, 32); sh.abort_flag = 1; }
                     break;
                 }
-                const int coef_f4 = (o.ncell * NC_F32_STRIDE + 1) / 2;
+                const int coef_f4 = (o.ncell * NC_F32 + 1) / 2;
                 coef = reinterpret_cast<const float2*>(ftab);
                 cellv = ftab + coef_f4;
                 oct = reinterpret_cast<const int2*>(cellv + o.ncell);
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairsum_tc(TCArgs a) {
                     const int cell = ob.x + ((bits & 0x7fffff) >> ob.y);
                     const float4 cv = cellv[cell];
                     const float u = ((th - cv.x) + (tl - cv.y)) * cv.z;
-                    const float2* cc = coef + cell * NC_F32_STRIDE;
+                    const float2* cc = coef + cell * NC_F32;
                     float2 k2 = cc[NC_F32 - 1];
                     float vr = k2.x, vi = k2.y;
 #pragma unroll
