@@ -267,11 +267,10 @@ __global__ void __launch_bounds__(PS_TPB) k_pairsum_tab(const double2* __restric
 // Precision form: FP32 pair sum.  Coordinates travel as float pairs (hi, lo);
 // dx, dy and t = dx^2 + dy^2 are formed in double-float arithmetic (TwoSum /
 // FMA-based TwoProduct) so that t keeps a relative error near 1e-14 and the
-// cell variable u near 1e-7; H0 comes from an FP32 table (complex64 degree-7
-// polynomials, validated to 2e-8 at setup; 8 coefficients per cell so that a cell's
-// coefficients are 4 aligned 16-byte shared-memory words); terms are accumulated with
-// Kahan compensation in FP32.  Pairs below the table range use the FP64 routine.
-#define NC_F32 8
+// cell variable u near 1e-7; H0 comes from an FP32 table (complex64 degree-6
+// polynomials, validated to 2e-8 at setup); terms are accumulated with Kahan
+// compensation in FP32.  Pairs below the table range use the FP64 routine.
+#define NC_F32 7
 struct F32Tile { float4 xy; float2 s; };
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -315,16 +314,15 @@ __device__ __forceinline__ bool f32_h0(float txh, float txl, float tyh, float ty
         int cell = ob.x + ((bits & 0x7fffff) >> ob.y);
         float4 cv = cellv[cell];
         float u = ((th - cv.x) + (tl - cv.y)) * cv.z;
-        // coefficients e = 2 i, 2 i + 1 in the float4 word i (re, im, re, im)
-        const float4* c4 = reinterpret_cast<const float4*>(coef + cell * NC_F32);
-        float4 w = c4[NC_F32 / 2 - 1];
-        hr = fmaf(w.z, u, w.x);
-        him = fmaf(w.w, u, w.y);
+        const float2* c = coef + cell * NC_F32;
+        float2 cc = c[NC_F32 - 1];
+        hr = cc.x;
+        him = cc.y;
 #pragma unroll
-        for (int i = NC_F32 / 2 - 2; i >= 0; --i) {
-            w = c4[i];
-            hr = fmaf(fmaf(hr, u, w.z), u, w.x);
-            him = fmaf(fmaf(him, u, w.w), u, w.y);
+        for (int e = NC_F32 - 2; e >= 0; --e) {
+            cc = c[e];
+            hr = fmaf(hr, u, cc.x);
+            him = fmaf(him, u, cc.y);
         }
         return true;
     }
