@@ -4108,16 +4108,6 @@ static ls_status pairsum_batch(ls_op* op, int R, const double2* f, size_t sf, co
     return LS_OK;
 }
 
-static ls_status apply_L_batch(ls_op* op, int R, const double2* x, size_t sx, double2* y, size_t sy) {
-    TRY(pairsum_batch(op, R, x, sx, op->m.p));
-    dim3 grid((unsigned)(((int64_t)op->nq * 32 + 255) / 256), R);
-    k_apply_epi_multi<<<grid, 256, 0, op->stream>>>(op->nq, op->b_nchunk_cur, op->bpartial.p, op->rowptr.p, op->cols.p,
-                                                    op->vals.p, op->m.p, x, sx, op->k * op->k, y, sy);
-    CK(cudaGetLastError());
-    op->launches++;
-    return LS_OK;
-}
-
 // FP32 copies of the block-LU factors and of the band of C, and the FP32 sweep vectors.
 static ls_status ensure_sweeps32(ls_op* op, int R) {
     const size_t nx = op->nx, ny = op->ny, nc = nx * ny;
