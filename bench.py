@@ -374,9 +374,10 @@ def precision_report(args):
 
 def batched_pairsum_report(args):
     """The batched pair sum alone (two-material disk, k = 20, 40,200 nodes, 64 right-hand
-    sides), tensor-core GEMM (k_pairsum_tc) against the CUDA-core kernel
-    (k_pairsum_multi_f32), each timed with CUDA events over max(1, --steps) launches after
-    a warm-up, with its error against the FP64 pair sum on 4 sampled right-hand sides."""
+    sides): tensor-core GEMM (k_pairsum_tc), the CUDA-core FP32 kernel (k_pairsum_multi_f32)
+    and the double-float one (k_pairsum_multi_df), each timed with CUDA events over
+    max(1, --steps) launches after a warm-up, with its error against the FP64-accurate
+    single-RHS pair sum on 4 sampled right-hand sides."""
     import torch
     import paper_2608_17615_b300 as L
     from lsinput.workloads import random_density, two_material
@@ -396,7 +397,7 @@ def batched_pairsum_report(args):
     tf32_peak = _peaks().get("bf16_tflops", 1800.0) * (1.1 / 2.25)
     out = {}
     stream = torch.cuda.current_stream()
-    for kind, name in ((1, "tensor_cores"), (0, "cuda_cores")):
+    for kind, name in ((1, "tensor_cores"), (0, "cuda_cores"), (2, "cuda_cores_double_float")):
         op.set_batch_kernel(kind, 4)
         op.pairsum_batch_dev(F, Y)
         ms, _ = _timed(lambda: op.pairsum_batch_dev(F, Y), stream, reps=max(1, min(args.steps, 5)))
