@@ -701,13 +701,13 @@ def main():
 
     run_forms = args.forms != "none"
     if run_forms:
-        _form(forms, "cfg2_double_float", lambda: pipe_form(LS_PREC_FP64_DF, "double-float pair sum in every GMRES "
+        _form(forms, "double_float_40k", lambda: pipe_form(LS_PREC_FP64_DF, "double-float pair sum in every GMRES "
                                                             "iteration", FP32_PEAK_TFLOPS, FP32_PEAK_SOURCE))
-        _form(forms, "cfg2_fp64_pipe",
+        _form(forms, "fp64_pipe_40k",
               lambda: dict(pipe_form(LS_PREC_FP64_TABLE, "FP64-pipe table pair sum", fp64_probe / 1e3,
                                      "measured FP64 FMA probe (ls_probe_fp64), same run"),
                            fp64_unit_count_peak_tflops=FP64_UNIT_PEAK_TFLOPS))
-        _form(forms, "cfg2_fp32", lambda: pipe_form(LS_PREC_FP32, "FP32 precision-form pair sum", FP32_PEAK_TFLOPS,
+        _form(forms, "fp32_40k", lambda: pipe_form(LS_PREC_FP32, "FP32 precision-form pair sum", FP32_PEAK_TFLOPS,
                                                     FP32_PEAK_SOURCE))
         op.set_pairsum(LS_PREC_FP64_DF)
 
@@ -733,8 +733,8 @@ def main():
             out["config"] = {"workload": WORKLOAD + ", 64 incident directions in lock step"}
             return out
 
-        _form(forms, "cfg2_batched_64rhs", batched_forms)
-        _form(forms, "cfg2_batched_pairsum_64rhs", lambda: batched_pairsum_report(args))
+        _form(forms, "batched_64rhs_40k", batched_forms)
+        _form(forms, "batched_pairsum_64rhs_40k", lambda: batched_pairsum_report(args))
 
         def approach_form():
             out = {}
@@ -752,13 +752,13 @@ def main():
                                              "(Table bakeoff context)"}
             return out
 
-        _form(forms, "cfg2_approach_I_vs_II", approach_form)
+        _form(forms, "approach_I_vs_II_40k", approach_form)
     del flush
     if run_forms and rank == 0:
-        _form(forms, "cfg3_precision_k40_195k", lambda: precision_report(args))
+        _form(forms, "precision_195k_k40", lambda: precision_report(args))
     if args.forms == "all" and rank == 0:
-        _form(forms, "cfg4_batching_8_scatterers", lambda: batching_report(args))
-        _form(forms, "cfg5_differentiation_492k", lambda: gradient_report(args))
+        _form(forms, "batching_8_stars", lambda: batching_report(args))
+        _form(forms, "gradient_492k_k40", lambda: gradient_report(args))
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
