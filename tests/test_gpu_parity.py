@@ -78,7 +78,7 @@ def test_apply_parity_full(case):
 
 
 @pytest.fixture(scope="module")
-def cfg2():
+def tm40k():
     # 40,200 nodes, k = 20, 256^2 grid; the FP64-pipe table form, the reference the other
     # arithmetics are compared with
     wl = two_material("small")
@@ -86,8 +86,8 @@ def cfg2():
     return wl, op
 
 
-def test_apply_parity_two_material_full_size(cfg2):
-    wl, op = cfg2
+def test_apply_parity_two_material_full_size(tm40k):
+    wl, op = tm40k
     n = wl.mesh.n_nodes
     x = random_density(n, 11)
     y = torch.empty(n, dtype=torch.complex128, device="cuda")
@@ -97,8 +97,8 @@ def test_apply_parity_two_material_full_size(cfg2):
     assert _rel(y.cpu().numpy()[rows], ref) < 1e-11
 
 
-def test_pairsum_table_vs_direct_full_size(cfg2):
-    wl, op = cfg2
+def test_pairsum_table_vs_direct_full_size(tm40k):
+    wl, op = tm40k
     n = wl.mesh.n_nodes
     opd = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, use_precond=0, pairsum=1)
     f = _dev(random_density(n, 17))
@@ -109,10 +109,10 @@ def test_pairsum_table_vs_direct_full_size(cfg2):
     assert (torch.linalg.norm(y0 - y1) / torch.linalg.norm(y1)).item() < 1e-13
 
 
-def test_double_float_form_full_size(cfg2):
+def test_double_float_form_full_size(tm40k):
     # pairsum = 3 must meet the FP64 bar: pair sum within 1e-13 of the FP64 table
     # kernel and the L apply within 1e-11 of the oracle on sampled rows
-    wl, op = cfg2
+    wl, op = tm40k
     n = wl.mesh.n_nodes
     opd = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, use_precond=0, pairsum=3)
     f = _dev(random_density(n, 23))
@@ -132,7 +132,7 @@ def test_double_float_form_full_size(cfg2):
 
 
 @pytest.mark.parametrize("case", ["two_material_tiny", "disk", "two_material_small"])
-def test_symmetric_double_float_pair_sum(case, cfg2):
+def test_symmetric_double_float_pair_sum(case, tm40k):
     # k_pairsum_dfs (one Hankel evaluation per unordered pair, rows and columns) against
     # k_pairsum_df (every ordered pair): bitwise the same H (the coordinate differences are
     # negated exactly), the products summed in another order in double-float (48-bit
@@ -144,7 +144,7 @@ def test_symmetric_double_float_pair_sum(case, cfg2):
     elif case == "disk":
         wl = constant_disk(k=5.0)
     else:
-        wl = cfg2[0]
+        wl = tm40k[0]
     n = wl.mesh.n_nodes
     op = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, use_precond=0, pairsum=3)
     f = _dev(random_density(n, 77))
@@ -164,10 +164,10 @@ def test_symmetric_double_float_pair_sum(case, cfg2):
         assert e_or < 1e-13
 
 
-def test_pairsum_precision_form_full_size(cfg2):
+def test_pairsum_precision_form_full_size(tm40k):
     # FP32 table (2e-8), FP32 strengths (6e-8), Kahan-compensated sums: ~1e-7 expected, for
     # the unordered-pair kernel (default) and the ordered-pair one alike
-    wl, op = cfg2
+    wl, op = tm40k
     n = wl.mesh.n_nodes
     op32 = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, use_precond=0, pairsum=2)
     f = _dev(random_density(n, 19))
@@ -184,7 +184,7 @@ def test_pairsum_precision_form_full_size(cfg2):
     assert err < 5e-7 and err_o < 5e-7
 
 
-def test_precision_form_solutions(cfg2):
+def test_precision_form_solutions(tm40k):
     # target of the precision form: <= 1e-6 relative solution error vs FP64
     wl = two_material("tiny", k=8.0, nx=64, ny=64)
     op32 = L.Operator(L.Mesh(wl.mesh), wl.k, wl.m, wl.m_grid, nx=64, ny=64, tol=1e-10, pairsum=2)
@@ -192,7 +192,7 @@ def test_precision_form_solutions(cfg2):
     b = plane_wave(wl.mesh.nodes, wl.k, np.pi / 4)
     ud = np.linalg.solve(OracleOp(wl.mesh, wl.k, wl.m).dense(), b)
     e_small = _rel(u[0], ud)
-    wl2, op64 = cfg2
+    wl2, op64 = tm40k
     op2 = L.Operator(L.Mesh(wl2.mesh), wl2.k, wl2.m, wl2.m_grid, tol=1e-10, pairsum=2)
     u32, _, _, it32, st32 = op2.solve([np.pi / 4])
     op64b = L.Operator(L.Mesh(wl2.mesh), wl2.k, wl2.m, wl2.m_grid, tol=1e-10)
@@ -203,7 +203,7 @@ def test_precision_form_solutions(cfg2):
     assert e_small < 1e-6 and e_full < 1e-6
 
 
-def test_mixed_form_solutions(cfg2):
+def test_mixed_form_solutions(tm40k):
     # pairsum = 4: FP32 GMRES refined against the double-float operator.  The refinement
     # stops on the accurate operator's residual, so the solution meets the FP64 solve's
     # tolerance times the condition factor, far inside the 1e-6 precision-form target.
@@ -228,7 +228,7 @@ def test_mixed_form_solutions(cfg2):
     y3, y4 = torch.empty_like(x), torch.empty_like(x)
     op3.apply_dev(x, y3)
     op4.apply_dev(x, y4)
-    wl2, _ = cfg2
+    wl2, _ = tm40k
     op2 = L.Operator(L.Mesh(wl2.mesh), wl2.k, wl2.m, wl2.m_grid, tol=1e-10, pairsum=4)
     u4, _, _, it4, st4 = op2.solve([np.pi / 4])
     res_big = op2.last_residual()
@@ -254,12 +254,12 @@ def test_precond_parity_small():
     assert _rel(y.cpu().numpy(), P.apply(x)) < 1e-11
 
 
-def test_precond_parity_full_size(cfg2):
+def test_precond_parity_full_size(tm40k):
     # The library and the oracle build C = A L^(C) independently (entries agree to 4.7e-14
     # of max |C|) and cond_1(C) ~ 2.6e5 on this 256^2 grid (scipy onenormest), so the
     # worst case for C^{-1} t is ~1e-8; measured 4.0e-13 with the cyclic-reduction solve,
     # and the bar is the FP64 matvec bar 1e-11.
-    wl, op = cfg2
+    wl, op = tm40k
     n = wl.mesh.n_nodes
     x = random_density(n, 13)
     y = torch.empty(n, dtype=torch.complex128, device="cuda")
@@ -294,7 +294,7 @@ def test_solve_disk_mie_and_energy():
     b = plane_wave(wl.mesh.nodes, wl.k, 0.0)
     lhs = np.imag(np.sum(wl.mesh.weights * np.conj(wl.m * u[0]) * b))
     rhs = np.sum(np.abs(uinf[0]) ** 2) * 2 * np.pi / len(wl.ff_angles) / wl.k
-    print("cfg1 iters", iters[0], "Mie e_int", e_int, "far-field err", e_ff, "energy", lhs, rhs)
+    print("disk iters", iters[0], "Mie e_int", e_int, "far-field err", e_ff, "energy", lhs, rhs)
     assert e_int < 1e-5 and e_ff < 1e-5
     assert abs(lhs - rhs) < 1e-5 * rhs
 
@@ -314,10 +314,10 @@ def test_preconditioned_solve_two_material():
     assert _rel(up[0], ud) < 1e-8
 
 
-def test_two_material_full_size_solve(cfg2):
-    wl, op = cfg2
+def test_two_material_full_size_solve(tm40k):
+    wl, op = tm40k
     u, uinf, hist, iters, st = op.solve([np.pi / 4], wl.ff_angles)
-    print("cfg2 preconditioned iterations", iters[0])
+    print("tm40k preconditioned iterations", iters[0])
     assert st == L.LS_OK and iters[0] < 100
     # the true residual of the returned solution, with the library's own L and P
     n = wl.mesh.n_nodes
