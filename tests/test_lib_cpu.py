@@ -171,3 +171,18 @@ def test_hessenberg_eigenvalues_match_numpy():
     ref = np.linalg.eigvals(A)
     d = np.abs(e[:, None] - ref[None, :]).min(axis=1)
     assert np.max(d) < 1e-10
+
+
+def test_correction_size_query_plans_only():
+    """The size query of both correction builds (null output arrays) only plans the patches:
+    it runs without a GPU and gives the nnz of the full host build (15 entries per
+    target-patch block)."""
+    import ctypes
+    wl = two_material("tiny", k=8.0)
+    mesh = L.Mesh(wl.mesh)
+    nnz_d, nnz_h = ctypes.c_int64(), ctypes.c_int64()
+    st = L._lib.ls_correction_dev(mesh.handle, 8.0, 3.0, None, ctypes.byref(nnz_d), None, None, None, None)
+    assert st == L.LS_OK
+    assert L._lib.ls_correction_host(mesh.handle, 8.0, 3.0, ctypes.byref(nnz_h), None, None, None) == L.LS_OK
+    rp, ci, va = L.correction_host(mesh, 8.0, 3.0)
+    assert nnz_d.value == nnz_h.value == ci.size and nnz_d.value % 15 == 0
