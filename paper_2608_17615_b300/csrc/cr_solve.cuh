@@ -186,24 +186,22 @@ __global__ void __launch_bounds__(32 * CR_WARPS) k_cr_mv_df(int nx, const CRJobD
     const bool two = row0 + 1 < nx;
     const int row1 = two ? row0 + 1 : row0;
     float r0h = 0.f, r0l = 0.f, i0h = 0.f, i0l = 0.f, r1h = 0.f, r1l = 0.f, i1h = 0.f, i1l = 0.f;
-    int n_acc = 0;
     for (int m = 0; m < 2; ++m) {
         const float4* M = m ? J.M2 : J.M1;
         if (!M) break;
         const float4* a0 = M + (size_t)row0 * nx;
         const float4* a1 = M + (size_t)row1 * nx;
         const float4* v = crshdf + m * nx;
-#pragma unroll 4
+        // nx / 32 terms per lane and matrix (8 at 256 nodes, 16 at 512): the low words stay
+        // within a few ulps of the high ones until the normalisation after the matrix
+#pragma unroll 8
         for (int c = lane; c < nx; c += 32) {
             const float4 x0 = a0[c], x1 = a1[c], vv = v[c];
             cr_df_cmac(x0, vv, r0h, r0l, i0h, i0l);
             cr_df_cmac(x1, vv, r1h, r1l, i1h, i1l);
-            if (++n_acc == 16) {
-                cr_df_fast(r0h, r0l); cr_df_fast(i0h, i0l);
-                cr_df_fast(r1h, r1l); cr_df_fast(i1h, i1l);
-                n_acc = 0;
-            }
         }
+        cr_df_fast(r0h, r0l); cr_df_fast(i0h, i0l);
+        cr_df_fast(r1h, r1l); cr_df_fast(i1h, i1l);
     }
     // warp sums in FP64 of the lanes' double-float partials
     double s0r = (double)r0h + (double)r0l, s0i = (double)i0h + (double)i0l;
