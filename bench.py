@@ -161,6 +161,11 @@ KERNEL = {0: "k_pairsum_tab", 1: "k_pairsum", 2: "k_pairsum_f32s", 3: "k_pairsum
 # kernels also write one partial row per block distance: k_pairsum_f32s 2.43 + 46.45 MB,
 # k_pairsum_dfs 3.20 + 46.99 MB)
 TRAFFIC_BYTES = {0: 2.4e6, 2: 4.889e7, 3: 5.019e7}
+# Thread instructions per ordered pair of the unordered-pair kernels (ncu smsp__inst_executed x 32
+# / pairs, 40,200 nodes): the FP32-pipe kernels are issue-bound, so their instruction rate
+# against the SM's issue limit (148 SMs x 128 lanes x 2.032 GHz) shows how busy they keep it
+INSTR_PER_PAIR = {2: 62.5, 3: 200.0}
+ISSUE_PEAK = 148 * 128 * 2.032e9
 
 
 def _timed(fn, stream, reps=1):
@@ -197,6 +202,9 @@ def _pairsum_roofline(op, n, peak, peak_source, total_ms=None, kind=None):
            "kernel_ms_per_launch": avg_s * 1e3, "kernel_launches": ps_launches}
     if mode == 3:
         out["fp32_tail_coefficients"] = nf
+    if mode in INSTR_PER_PAIR and n == 40200:
+        out["thread_instructions_per_pair"] = INSTR_PER_PAIR[mode]
+        out["issue_frac"] = INSTR_PER_PAIR[mode] * n * (n - 1) / avg_s / ISSUE_PEAK
     if total_ms:
         out["kernel_share_of_step"] = ps_ms / total_ms
     return out
