@@ -248,15 +248,18 @@ ls_status ls_solve_dev(ls_op* op, int32_t R, const void* b_dev, void* u_dev,
  *                         keeps its own Krylov space, Hessenberg matrix and stop),
  *                         b_dev, u_dev [R][N]; far field as ls_solve_dev
  * The pair sum of all R systems is one launch per iteration on the kernel chosen
- * by ls_op_set_batch_kernel.  Each H(j, n) comes from an FP32 table (degree 6,
- * validated to 2e-8) with double-float t.  On the CUDA cores (kind 0) it is applied
- * to blocks of 8 right-hand sides with Kahan-compensated FP32 sums over runs of 64
- * sources and FP64 across runs; on the tensor cores (kind 1, the default) the sum
- * over sources is a tcgen05 GEMM over up to 64 right-hand sides, and the solve is
- * followed by iterative refinement against the kind 0 operator, so both reach the
- * kind 0 accuracy (the batching form's target: <= 1e-6 relative solution error).
- * The preconditioner sweeps and the Arnoldi kernels are batched over r as well.
- * Workspace grows on first use with a larger R.
+ * by ls_op_set_batch_kernel.  Kinds 0 and 1 take each H(j, n) from an FP32 table
+ * (degree 6, validated to 2e-8) with double-float t.  On the CUDA cores (kind 0) it
+ * is applied to blocks of 8 right-hand sides with Kahan-compensated FP32 sums over
+ * runs of 64 sources and FP64 across runs; on the tensor cores (kind 1, the default)
+ * the sum over sources is a tcgen05 GEMM over up to 64 right-hand sides.  Kind 2 is
+ * the double-float (FP64-accurate) CUDA-core kernel.  Solves on kind 1 (and on kind 0
+ * under ls_op_set_batch_refine(op, 1)) are followed by iterative refinement: against
+ * the batched double-float operator by default on operators in the double-float or
+ * mixed form (solutions FP64-accurate to tol), else against the kind 0 operator (~1e-6,
+ * the per-entry FP32 rounding of H0).  The batching form's target is <= 1e-6 relative
+ * solution error.  The preconditioner sweeps and the Arnoldi kernels are batched over
+ * r as well.  Workspace grows on first use with a larger R.
  */
 ls_status ls_pairsum_batch_dev(ls_op* op, int32_t R, const void* f_dev, void* y_dev);
 ls_status ls_solve_batch_dev(ls_op* op, int32_t R, const void* b_dev, void* u_dev, int32_t n_ff,
@@ -346,15 +349,17 @@ ls_status ls_solve_transpose_batch_dev(ls_op* op, int32_t R, const void* g_dev, 
  *           sources, run totals Kahan-folded, chunks summed in FP64.  The tensor
  *           memory accumulation truncates, so the pair sum carries ~3e-7 x fold
  *           relative error; batched solves on kind 1 are therefore followed by up
- *           to `refine` steps of iterative refinement whose residuals use the
- *           kind 0 operator, which restores the kind 0 accuracy (refine = 0: none).
- *           Refinement stops when ||P r|| <= max(tol, 2e-8) ||P b|| or when a
- *           correction no longer halves the residual while ||P r|| <= 1e-6 ||P b||
- *           (the kind 0 operator's rounding level reached); LS_ENOCONV if neither
- *           happens within `refine` steps.  On kind 1 the block-LU sweeps of the
- *           preconditioner run in FP32 (FP32 copies of the factors, made on first
- *           use); P only weights the residual norm, so the refined solution keeps
- *           the kind 0 accuracy.  Kind 0 keeps the FP64 sweeps.
+ *           to `refine` steps of iterative refinement (refine = 0: none) whose
+ *           residuals use the operator ls_op_set_batch_refine selects: the batched
+ *           double-float one (default on double-float and mixed operators; the
+ *           refinement stops at ||P r|| <= tol ||P b||) or the kind 0 one (stops at
+ *           max(tol, 2e-8), or when a correction no longer halves the residual while
+ *           ||P r|| <= 1e-6 ||P b||: the kind 0 operator's rounding level).
+ *           LS_ENOCONV if the refinement does not stop within `refine` steps.  On
+ *           kind 1 the block-LU sweeps of the preconditioner run in FP32 (FP32
+ *           copies of the factors, made on first use); P only weights the residual
+ *           norm, so the refined solution keeps the refinement operator's accuracy.
+ *           Kind 0 keeps the FP64 sweeps.
  *   kind 2  CUDA cores in double-float (FP64-accurate): H from the operator's
  *           double-float table, densities and sums in double-float pairs; needs an
  *           operator built with LS_PREC_FP64_DF or LS_PREC_MIXED (LS_EINVAL
