@@ -270,10 +270,10 @@ ls_status ls_solve_batch_dev(ls_op* op, int32_t R, const void* b_dev, void* u_de
  * sides each, advanced in lock step; every iteration runs ONE persistent pair-sum
  * launch over all (scatterer, target block, source chunk[, RHS block]) work units,
  * followed by each operator's batched epilogue, preconditioner and Arnoldi kernels.
- * Kernel as set on ops[0] by ls_op_set_batch_kernel: tensor cores (one CTA per SM
- * taking units round-robin, then each operator's iterative refinement) or CUDA
- * cores (units fetched from an atomic counter, grid size autotuned on the first
- * iteration).
+ * Kernel as set on ops[0] by ls_op_set_batch_kernel (0 or 1): tensor cores (one CTA
+ * per SM taking units round-robin) or CUDA cores (units fetched from an atomic
+ * counter, grid size autotuned on the first iteration); afterwards each operator's
+ * iterative refinement as ls_solve_batch_dev runs it (ls_op_set_batch_refine).
  *   ops [S]; b_devs[s], u_devs[s]: [R][N_s] complex; iters_out [S][R] (may be NULL)
  * All operators must share one stream and max_iter.  LS_ENOCONV if any system
  * hit max_iter.
