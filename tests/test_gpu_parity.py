@@ -317,7 +317,7 @@ def test_preconditioned_solve_two_material():
 def test_two_material_full_size_solve(tm40k):
     wl, op = tm40k
     u, uinf, hist, iters, st = op.solve([np.pi / 4], wl.ff_angles)
-    print("tm40k preconditioned iterations", iters[0])
+    print("two-material preconditioned iterations", iters[0])
     assert st == L.LS_OK and iters[0] < 100
     # the true residual of the returned solution, with the library's own L and P
     n = wl.mesh.n_nodes
